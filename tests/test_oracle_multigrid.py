@@ -1,0 +1,125 @@
+"""Pins of the oracle V-cycles (this build's geometric multigrid)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import geometry, multigrid as MG, operators
+from oracle.operators import shapes
+
+
+def _face_field(g, fn):
+    """Sample fn(component, x, y, z) at face centres in natural order."""
+    out = []
+    sh = shapes(g.nx, g.ny, g.nz)
+    for comp, key in ((0, "fx"), (1, "fy"), (2, "fz")):
+        K, J, I = np.meshgrid(*(np.arange(s) for s in sh[key]), indexing="ij")
+        x = (I + (0.0 if comp == 0 else 0.5)) * g.dx
+        y = (J + (0.0 if comp == 1 else 0.5)) * g.dy
+        z = (K + (0.0 if comp == 2 else 0.5)) * g.dz
+        out.append(fn(comp, x, y, z).ravel())
+    return np.concatenate(out)
+
+
+def _interior_mask(g, margin):
+    out = []
+    sh = shapes(g.nx, g.ny, g.nz)
+    for key in ("fx", "fy", "fz"):
+        K, J, I = np.meshgrid(*(np.arange(s) for s in sh[key]), indexing="ij")
+        m = ((I >= margin) & (I < sh[key][2] - margin) & (J >= margin) & (J < sh[key][1] - margin)
+             & (K >= margin) & (K < sh[key][0] - margin))
+        out.append(m.ravel())
+    return np.concatenate(out)
+
+
+def test_prolongation_partition_of_unity():
+    P = MG.face_prolongation(3, 4, 2)
+    assert np.allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0)
+
+
+def test_prolongation_exact_for_affine_fields():
+    from workloads import Grid
+    gc = Grid(4, 4, 4, 0.5, 0.5, 0.5)
+    gf = Grid(8, 8, 8, 0.25, 0.25, 0.25)
+    fn = lambda c, x, y, z: 1.0 + (c + 1) * x - 2.0 * y + 0.5 * z
+    P = MG.face_prolongation(4, 4, 4)
+    ef = P @ _face_field(gc, fn)
+    ref = _face_field(gf, fn)
+    m = _interior_mask(gf, 1)
+    assert np.max(np.abs(ef - ref)[m]) < 1e-13
+
+
+def test_restriction_preserves_constants_in_the_interior():
+    from workloads import Grid
+    P = MG.face_prolongation(4, 4, 4)
+    rc = P.T @ np.ones(P.shape[0]) / 8.0
+    m = _interior_mask(Grid(4, 4, 4, 1, 1, 1), 1)
+    assert np.allclose(rc[m], 1.0)
+
+
+def test_coarsened_fractions_preserve_measures():
+    w = W.sphere_workload(16, offset_seed=5)
+    fr = geometry.fractions(w.phi)
+    c = MG.coarsen_fractions(fr)
+    assert c["V"].sum() * 8 == pytest.approx(fr["V"].sum(), rel=1e-14)
+    assert c["Ax"].sum() * 4 == pytest.approx(fr["Ax"][:, :, 0::2].sum(), rel=1e-14)
+    b = MG.coarsen_fractions(geometry.fractions(W.box_workload(8, 8, 8, 1, 1, 1).phi))
+    for k, v in b.items():
+        assert set(np.unique(v)).issubset({0.0, 1.0}), k
+
+
+def _omegas(levels, attr="K", scale=1.7):
+    out = []
+    for lev in levels:
+        M = getattr(lev, attr)
+        idx = np.nonzero(lev.mask)[0]
+        Kd = M.tocsr()[idx][:, idx]
+        dinv = lev.inv_d[idx]
+        op = spla.LinearOperator(Kd.shape, matvec=lambda v: dinv * (Kd @ v))
+        lm = abs(spla.eigs(op, k=1, which="LM", return_eigenvectors=False, tol=1e-6)[0])
+        out.append(scale / lm)
+    return out
+
+
+def test_vcycle_contracts_on_box():
+    w = W.box_workload(16, 16, 16, 1.0, 1.0, 1.0)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, 0.0)
+    om = _omegas(levels)
+    lev = levels[0]
+    rng = np.random.default_rng(0)
+    e = rng.standard_normal(lev.mask.size) * lev.mask
+    for _ in range(3):
+        e_new = e - MG.vcycle(levels, lev.K @ e, om)
+        ratio = np.linalg.norm(e_new) / np.linalg.norm(e)
+        e = e_new
+    assert ratio < 0.5
+
+
+@pytest.mark.slow
+def test_fgmres_vcycle_rate_on_sphere():
+    """With the band sweeps the preconditioned inner solve contracts at about the
+    rate the paper reports for its AMG (Tab. invPerf: 0.25-0.27 on the sphere)."""
+    w = W.sphere_workload(32, offset_seed=W.SEED_BASE + 2, sigma=5.0)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, 5.0)
+    om = _omegas(levels)
+    lev = levels[0]
+    b = np.random.default_rng(0).standard_normal(lev.mask.size) * lev.mask
+    x, hist = MG.fgmres(lambda v: lev.K @ v, b, lambda v: MG.vcycle(levels, v, om), tol=1e-8)
+    rate = hist[-1] ** (1.0 / len(hist))
+    assert rate < 0.32, rate
+    assert np.linalg.norm(b - lev.K @ x) < 1e-7 * np.linalg.norm(b)
+
+
+def test_scalar_vcycle_solves_projection_system():
+    w = W.sphere_workload(16, offset_seed=9)
+    levels = MG.build_scalar_hierarchy(w.grid, w.phi)
+    om = _omegas(levels, attr="S")
+    lev = levels[0]
+    x = np.random.default_rng(1).standard_normal(lev.ops.a.size) * lev.ops.open
+    s = lev.ops.D @ (lev.ops.a * x)
+    S = lev.S + __import__("scipy.sparse", fromlist=["diags"]).diags(1.0 - lev.mask)
+    psi, hist = MG.fgmres(lambda v: S @ v, s, lambda v: MG.scalar_vcycle(levels, v, om), tol=1e-10)
+    assert hist[-1] < 1e-10 and len(hist) < 40
+    # the projected field is divergence free
+    y = x - (lev.ops.D.T @ psi) * lev.ops.open
+    assert np.linalg.norm(lev.ops.D @ (lev.ops.a * y)) < 1e-8 * np.linalg.norm(s)
