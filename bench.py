@@ -1,0 +1,410 @@
+"""Throughput benchmark: converged Dey--Mittra eigenpairs per second on one GB300.
+
+Workload (the paper's spherical-cavity test, Sec. 6.2, at the larger grid of the
+plain-method configuration): a PEC sphere of radius 1 in [-1.1, 1.1]^3 on a
+128^3 Yee grid, centre moved by a seeded sub-cell offset, the 10 electromagnetic
+modes nearest sigma = 5 (the 10 lowest), residual <= 1e-8.  One step = geometry
++ multigrid setup + Krylov--Schur eigensolve + FP64 certification of every
+returned eigenpair.  The headline uses the mixed-precision form (FP32 V-cycle
+inside FP64 FGMRES / FP64 Krylov--Schur); the plain FP64 multigrid is timed in
+the same run for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (one
+per rank, no data-path collective), so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s @1e-8 residual vs plain FP64 MG; V-cycle HBM GB/s % of peak"
+UNIT = "eigenpairs/s"
+RHO_TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--nev", type=int, default=10)
+    ap.add_argument("--sigma", type=float, default=5.0)
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    import workloads as W
+    return W.sphere_workload(args.grid, radius=1.0, half_width=1.1, sigma=args.sigma, nev=args.nev,
+                             offset_seed=W.SEED_BASE + 2)
+
+
+def config_of(args, w, extra=None):
+    c = {"workload": (f"PEC sphere R=1 in [-1.1,1.1]^3, {args.grid}^3 Yee cells, seeded centre offset "
+                      f"{tuple(round(v, 5) for v in w.meta['center'])}, sigma={args.sigma}, "
+                      f"{args.nev} lowest modes, residual<={RHO_TOL}"),
+         "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma,
+         "mg_precision": args.precision, "outer_precision": "f64",
+         "l2": "inputs larger than L2 (solver working set of several GB per step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas; host-side logic shared with the CPU tests)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return dist
+
+
+def aggregate(local_units, local_seconds, device=None):
+    """(units summed over ranks, max seconds over ranks) -- the whole-job
+    throughput is units / max seconds."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_units), float(local_seconds)
+    t = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    s = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(s.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(p[1]) for p in self.samples if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in self.samples if p[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in self.samples:
+            for n, v in zip(names, p[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ---------------------------------------------------------------------------
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def stencil_bytes_per_cell(name):
+    """Algorithmic bytes per grid cell of one stencil launch, from its storage
+    types: vector x (3 values) read, y (3) written, f (3) read for resid and
+    jacobi, x re-read for jacobi is the same stream; coefficients A (3), L (3),
+    1/V (1) and 1/D (3, jacobi only) read."""
+    parts = name.split("_")
+    prec, mode = parts[2], parts[3]
+    tv = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    tc = 8 if prec == "f64" else 4
+    vec = 3 * tv * (2 + (1 if mode in ("resid", "jacobi") else 0))
+    coef = tc * (7 + (3 if mode == "jacobi" else 0))
+    return vec + coef
+
+
+def roofline(stats, grid_cells, hbm_peak, peak_kind, traffic=None):
+    """Dominant fine-level stencil kernel: algorithmic bytes per launch over its
+    average event-timed duration."""
+    cands = {k: v for k, v in stats.items() if "stencil" in k and k.endswith("_L0")}
+    if not cands:
+        return None
+    name, (launches, ms) = max(cands.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / launches * 1e-3
+    bytes_per_launch = stencil_bytes_per_cell(name) * grid_cells
+    achieved = bytes_per_launch / avg_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+            "bytes_per_launch": int(bytes_per_launch), "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches,
+            "peak_kind": f"{peak_kind} (copy)"}
+
+
+# ---------------------------------------------------------------------------
+# native (GPU) arm
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_3794_gb300 as dm
+
+    w = workload(args)
+    g = w.grid
+    stream = torch.cuda.Stream()
+    ctx = dm.Context(local, stream=stream.cuda_stream)
+    phi_host = np.ascontiguousarray(w.phi.ravel())
+    with torch.cuda.stream(stream):
+        phi_dev = torch.from_numpy(phi_host).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    nf = dm.face_count(g.nx, g.ny, g.nz)
+    B_dev = torch.empty((args.nev, nf), dtype=torch.float64, device=f"cuda:{local}")
+
+    def step(precision, host_io=False):
+        phi = phi_host if host_io else phi_dev
+        geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi, g.origin)
+        vec = "host" if host_io else "device"
+        k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
+                                       out=None if host_io else B_dev, precision=precision)
+        geom.close()
+        return k2, rep, st
+
+    def converged(rep, st):
+        return rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0
+
+    for _ in range(args.warmup):
+        step(args.precision)
+    # ---- timed region: inputs resident in HBM ----
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = ctx.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    units = 0
+    reps = []
+    for _ in range(args.steps):
+        k2, rep, st = step(args.precision)
+        units += converged(rep, st)
+        reps.append(rep)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launches - l0
+    local_s = e0.elapsed_time(e1) * 1e-3
+    tot_units, max_s = aggregate(units, local_s, device=f"cuda:{local}")
+    value = tot_units / max_s
+    # ---- end-to-end through the public API with host buffers ----
+    t0 = time.perf_counter()
+    units_e2e = 0
+    for _ in range(args.steps):
+        k2h, reph, sth = step(args.precision, host_io=True)
+        units_e2e += converged(reph, sth)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    tot_e2e, max_e2e = aggregate(units_e2e, e2e_s, device=f"cuda:{local}")
+    # ---- one traced step: per-kernel event timings on the launching stream ----
+    ctx.trace(True)
+    k2t, rept, stt = step(args.precision)
+    ctx.trace(False)
+    stats = ctx.trace_stats()
+    hbm, kind = peaks()
+    roof = roofline(stats, g.n_cells, hbm, kind)
+    # ---- plain FP64 multigrid on the same cavity ----
+    plain = None
+    if not args.no_compare and args.precision != "f64":
+        torch.cuda.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        k2p, repp, stp = step("f64")
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ps = p0.elapsed_time(p1) * 1e-3
+        plain = {"value": round(converged(repp, stp) / ps, 4), "unit": UNIT, "ms_per_step": round(ps * 1e3, 1),
+                 "steps": 1, "inner_iters": repp["inner_iters"], "outer_iters": repp["outer_iters"],
+                 "rho_max": repp["rho_max"],
+                 "max_rel_k2_diff_vs_mixed": float(np.max(np.abs(k2p - k2) / np.abs(k2p)))}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_s / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if args.precision == "f32" else
+        ("f64+bf16" if args.precision == "bf16" else "f64"), "data": "synthetic (seeded level set)",
+        "config": config_of(args, w, {"parallelism": f"replicas x{world}"}),
+        "e2e": {"value": round(tot_e2e / max_e2e, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(phi_host.nbytes), "d2h_bytes_per_step": int(args.nev * nf * 8)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk,
+        "solver": {"inner_iters_per_step": reps[-1]["inner_iters"], "outer_iters": reps[-1]["outer_iters"],
+                   "restarts": reps[-1]["restarts"], "proj_iters": reps[-1]["proj_iters"],
+                   "mg_levels": reps[-1]["mg_levels"], "mg_complexity": round(reps[-1]["mg_complexity"], 3),
+                   "rho_max": reps[-1]["rho_max"], "delta_max": reps[-1]["delta_max"],
+                   "k2": [round(float(v), 10) for v in k2],
+                   "inner_rate": None},
+        "plain_f64": plain,
+        "kernels_top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in
+                        sorted(stats.items(), key=lambda kv: -kv[1][1])[:8]},
+    }
+    if reps[-1]["inner_iters"] and reps[-1]["outer_iters"]:
+        it = reps[-1]["inner_iters"] / reps[-1]["outer_iters"]
+        out["solver"]["inner_rate"] = round(1e-10 ** (1.0 / it), 3)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+CPU_SAMPLE_GRID = 24
+
+
+def oracle_step(args):
+    """One bounded sample of the workload on the host: the oracle's sparse
+    shift-invert eigensolve of the same cavity family (same radius, domain,
+    offset seed, sigma and mode count) at 32^3 cells."""
+    import workloads as W
+    from oracle import eigen, geometry, operators
+    w = W.sphere_workload(CPU_SAMPLE_GRID, radius=1.0, half_width=1.1, sigma=args.sigma, nev=args.nev,
+                          offset_seed=W.SEED_BASE + 2)
+    t0 = time.perf_counter()
+    ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
+    k2, B, _ = eigen.shift_invert_modes(ops, w.sigma, w.nev)
+    ok = sum(1 for i in range(w.nev) if eigen.certificate(ops, k2[i], B[:, i])["rho"] <= RHO_TOL)
+    return ok, time.perf_counter() - t0
+
+
+def cpu_info():
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return cores
+
+
+def cpu_baseline(args, reps=1):
+    units = 0
+    secs = 0.0
+    for _ in range(reps):
+        u, s = oracle_step(args)
+        units += u
+        secs += s
+    return {"value": round(units / secs, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (scipy SuperLU + ARPACK shift-invert, single-threaded) on the same sphere family at "
+                       f"{CPU_SAMPLE_GRID}^3 cells, {args.nev} modes, sigma={args.sigma}; {reps} solve(s), "
+                       f"{secs:.1f} s; host has {cpu_info()} cores available")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads as W
+    for _ in range(args.warmup):
+        oracle_step(args)
+    units = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _ = oracle_step(args)
+        units += u
+    secs = time.perf_counter() - t0
+    value = units / secs
+    w = workload(args)
+    out = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded level set)",
+           "config": config_of(args, w, {"parallelism": "host oracle", "sample_grid": [CPU_SAMPLE_GRID] * 3}),
+           "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": (f"each step: the oracle's sparse shift-invert eigensolve of the same sphere "
+                                       f"family at {CPU_SAMPLE_GRID}^3 cells ({args.nev} modes); "
+                                       f"{cpu_info()} host cores available, SuperLU/ARPACK single-threaded")},
+           "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

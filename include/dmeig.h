@@ -1,0 +1,205 @@
+/*
+ * dmeig.h -- C ABI of the GB300 Dey--Mittra cavity eigensolver.
+ *
+ * Computes resonant modes of a perfectly conducting cavity on a Yee grid with
+ * Dey--Mittra cut cells (Bauer, Werner & Cary, arXiv:1301.3794): the magnetic
+ * eigenmodes b and wavenumbers k^2 of  A^-1 C L C^T b = k^2 b  (Sec. 2,
+ * Eq. discWaveBDM), found by a shift-and-invert Krylov eigensolver on
+ *     P_DM (K - sigma A)^-1 A,   K = C L C^T + A D^T V^-1 D A     (Eq. fullMat)
+ * whose inner solves are flexible GMRES preconditioned by geometric multigrid.
+ *
+ * Conventions shared by every call:
+ *  - Grid: nx, ny, nz cells of size dx, dy, dz; node (i,j,k) at
+ *    origin + (i dx, j dy, k dz).  The outer walls are perfect conductors.
+ *  - Level set phi at the (nx+1)(ny+1)(nz+1) nodes, i fastest (C order of an
+ *    array shaped [nz+1][ny+1][nx+1]); phi < 0 is vacuum, phi >= 0 conductor.
+ *  - Natural face layout ("F" doubles): x-faces [nz][ny][nx+1], then y-faces
+ *    [nz][ny+1][nx], then z-faces [nz+1][ny][nx], each i fastest.  x-face
+ *    (i,j,k) sits at x = x_i and spans [y_j, y_j+1] x [z_k, z_k+1].  Closed
+ *    faces (area fraction 0) always hold 0.
+ *  - Natural edge layout ("E" doubles): x-edges [nz+1][ny+1][nx], y-edges
+ *    [nz+1][ny][nx+1], z-edges [nz][ny+1][nx+1].  Cells: [nz][ny][nx].
+ *  - Pointers marked "host or device" are device pointers when the matching
+ *    on_device flag is nonzero, host pointers otherwise.  The caller owns
+ *    every buffer it passes; the library never keeps a caller pointer after a
+ *    call returns.  The library owns its handles and their device workspaces.
+ *  - All work is issued on the context's stream; calls return after that
+ *    stream has finished the call's work.
+ *  - No exception crosses the ABI.  On failure a call returns a nonzero
+ *    dm_status and dm_last_error() describes the cause.
+ */
+#ifndef DMEIG_H
+#define DMEIG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dm_status {
+    DM_OK = 0,
+    DM_ERR_INVALID_ARG = 1,
+    DM_ERR_NO_CONVERGENCE = 2,
+    DM_ERR_TIMEOUT = 3,
+    DM_ERR_CUDA = 4,
+    DM_ERR_OOM = 5,
+    DM_ERR_GEOMETRY = 6
+} dm_status;
+
+/* Storage precision of the multigrid preconditioner (Krylov work stays FP64). */
+typedef enum dm_precision {
+    DM_PREC_F64 = 0,
+    DM_PREC_F32 = 1,      /* FP32 storage and arithmetic */
+    DM_PREC_BF16 = 2      /* BF16 vectors, FP32 coefficients and accumulation */
+} dm_precision;
+
+typedef struct dm_context dm_context;
+typedef struct dm_geometry dm_geometry;
+typedef struct dm_operator dm_operator;
+
+/* Multigrid preconditioner settings (a design of this library: the paper used
+ * an algebraic V-cycle with one order-1 polynomial smoother step per level and
+ * direction, Sec. 6). */
+typedef struct dm_mg_params {
+    int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4) */
+    int band_sweeps;       /* extra Jacobi sweeps on the cut-cell band after each smoothing step (8) */
+    double omega_scale;    /* Jacobi weight = omega_scale / lambda_max(D^-1 (K - sigma A)) (1.7) */
+    int power_iters;       /* power iterations for lambda_max (30) */
+    int precision;         /* dm_precision of the V-cycle (DM_PREC_F64) */
+} dm_mg_params;
+
+typedef struct dm_eig_params {
+    double sigma;          /* shift (Eq. shiftInv): modes with k^2 nearest sigma are found */
+    int nev;               /* number of eigenpairs wanted */
+    double tol;            /* Ritz residual tolerance, relative to |theta| (1e-10) */
+    double inner_tol;      /* relative residual of each shifted solve (1e-10) */
+    double proj_tol;       /* relative residual of each scalar solve inside P_DM (1e-12) */
+    int basis;             /* Krylov-Schur basis size m; 0 = max(2 nev + 10, 24) capped at 64 */
+    int max_restarts;      /* (100) */
+    int inner_restart;     /* FGMRES basis size (40) */
+    int inner_maxit;       /* FGMRES iteration cap per solve (400) */
+    unsigned long long seed; /* start vector seed */
+    dm_mg_params mg;
+} dm_eig_params;
+
+typedef struct dm_eig_report {
+    int n_converged;       /* leading eigenpairs that met tol */
+    int outer_iters;       /* Krylov-Schur expansion steps (= shifted solves) */
+    int restarts;
+    int inner_iters;       /* FGMRES iterations summed over all shifted solves */
+    int proj_iters;        /* scalar FGMRES iterations summed over all projections */
+    int mg_levels;
+    double mg_complexity;  /* sum of open faces over levels / open faces of level 0 */
+    double rho_max;        /* max ||K b - k^2 A b|| / (k^2 ||A b||) over returned pairs */
+    double delta_max;      /* max ||D A b|| h / ||A b|| over returned pairs */
+    double setup_seconds;  /* operator setup (diagonals, weights, coarsest factorisation) */
+    double solve_seconds;  /* eigensolver iterations and certification */
+    long long kernel_launches;  /* kernels this library launched during the call */
+} dm_eig_report;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Bind to CUDA device `device`; `cuda_stream` (a cudaStream_t, may be NULL)
+ * is used for all work, NULL makes the library create its own stream. */
+dm_status dm_context_create(int device, void* cuda_stream, dm_context** out);
+void dm_context_destroy(dm_context* ctx);
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char* dm_last_error(const dm_context* ctx);
+/* Kernels launched on this context so far. */
+long long dm_context_launch_count(const dm_context* ctx);
+
+/* ---- kernel timing (profiling aid; no counterpart in the paper) ---------- */
+/* on = 1 clears the statistics and brackets every later kernel launch with a
+ * pair of CUDA events on the context's stream; on = 0 stops recording. */
+dm_status dm_trace_enable(dm_context* ctx, int on);
+/* Number of distinct kernels timed so far (resolves pending events). */
+int dm_trace_count(dm_context* ctx);
+/* Entry i: kernel name (copied into name[name_cap]), launches, summed device ms. */
+dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long long* launches, double* total_ms);
+
+/* ---- geometry (Sec. 2, Eq. farInt / Fig. dmFace; Sec. 5.1, Eq. divBInt /
+ *      Fig. dmVol; Sec. 6.1 tetrahedral cut volumes) ------------------------ */
+
+/* Cut fractions L (edges), A (faces), V (cells) = parts *outside* the
+ * conductor of the zero set of the piecewise-linear interpolant of phi on the
+ * 6-tetrahedron (Kuhn) split of every cell; the multigrid levels' fractions
+ * are averages of the fine ones.  phi: host or device, (nx+1)(ny+1)(nz+1).
+ * a_min > 0 neglects faces with A < a_min and their edges (Sec. 3); 0 keeps
+ * all faces (the paper's method).  nx, ny, nz >= 2. */
+dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz,
+                             double dx, double dy, double dz, const double origin[3],
+                             const double* phi, int phi_on_device, double a_min,
+                             dm_geometry** out);
+void dm_geometry_destroy(dm_geometry* geom);
+
+/* Multigrid levels available below (and including) the fine grid. */
+int dm_geometry_num_levels(const dm_geometry* geom);
+/* dims[3] = cells of `level`; counts[4] = natural faces F, edges E, cells, open faces. */
+dm_status dm_geometry_level_info(const dm_geometry* geom, int level, int dims[3], long long counts[4]);
+/* Copy the fractions of `level` out in natural layouts: L (E), A (F), V (cells).
+ * Any pointer may be NULL.  Host or device per on_device. */
+dm_status dm_geometry_fractions(const dm_geometry* geom, int level, double* L, double* A,
+                                double* V, int on_device);
+
+/* ---- shifted operator and its preconditioner ----------------------------- */
+
+void dm_mg_params_default(dm_mg_params* p);
+
+/* K - sigma A (Eq. discLaplDM) on every level, with the V-cycle set up. */
+dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma,
+                             const dm_mg_params* mg, dm_operator** out);
+void dm_operator_destroy(dm_operator* op);
+int dm_operator_num_levels(const dm_operator* op);
+/* Jacobi weight of `level` for the vector (scalar = 0) or the scalar (scalar = 1) cycle. */
+double dm_operator_get_omega(const dm_operator* op, int level, int scalar);
+dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double omega);
+
+/* y = (K - sigma A) x on `level` in FP64 (Eq. discLaplDM; K = C L C^T +
+ * A D^T V^-1 D A with V^-1 = 0 where V = 0).  x, y: natural face layout. */
+dm_status dm_operator_apply(dm_operator* op, int level, const double* x, double* y, int on_device);
+/* Diagonal of K - sigma A on `level` (natural face layout, 0 on closed faces). */
+dm_status dm_operator_diagonal(dm_operator* op, int level, double* d, int on_device);
+/* One smoothing step on `level` in the preconditioner's precision:
+ * x <- x + omega D^-1 (f - (K - sigma A) x), then band_sweeps sweeps restricted
+ * to the cut-cell band.  x is updated in place. */
+dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double* x, int on_device);
+/* f_c = R r = P^T r / 8 from `level` to level+1 (precision of the preconditioner). */
+dm_status dm_operator_restrict(dm_operator* op, int level, const double* r, double* fc, int on_device);
+/* x <- x + mask P e_c from level+1 to `level`. */
+dm_status dm_operator_prolong(dm_operator* op, int level, const double* ec, double* x, int on_device);
+/* e = one V(1,1) cycle applied to f on the fine level, from a zero guess. */
+dm_status dm_operator_vcycle(dm_operator* op, const double* f, double* e, int on_device);
+/* Solve (K - sigma A) x = b on the fine level by right-preconditioned FGMRES
+ * to relative residual tol (Sec. 6: GMRES + multigrid).  x: output. */
+dm_status dm_operator_solve(dm_operator* op, const double* b, double* x, int on_device,
+                            double tol, int restart, int maxit, int* iters, double* relres);
+/* y = P_DM x = x - D^T (D A D^T)^-1 D A x (Eq. proj); the scalar Laplacian is
+ * solved by FGMRES + cell multigrid to relative residual tol. */
+dm_status dm_operator_project(dm_operator* op, const double* x, double* y, int on_device,
+                              double tol, int* iters);
+/* One scalar V-cycle e ~= (D A D^T)^-1 f on cells (natural cell layout). */
+dm_status dm_operator_scalar_vcycle(dm_operator* op, const double* f, double* e, int on_device);
+
+/* ---- eigensolver (Sec. 4.1 Eq. shiftInv, Sec. 5.2 Eq. fullMat) ----------- */
+
+void dm_eig_params_default(dm_eig_params* p);
+
+/* The nev eigenpairs of A^-1 C L C^T b = k^2 b nearest sigma among the
+ * electromagnetic (D A b = 0) modes, by Krylov-Schur on P_DM (K - sigma A)^-1 A
+ * in the A inner product (Eq. bInner).  k2_out[nev] ascending (host).
+ * b_out (nullable): nev x F, natural face layout, A-normalised (b^T A b = 1),
+ * sign such that the entry of largest magnitude is positive; host or device
+ * per b_on_device.  DM_ERR_NO_CONVERGENCE still fills the converged prefix
+ * and report->n_converged. */
+dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_params* p,
+                        double* k2_out, double* b_out, int b_on_device, dm_eig_report* report);
+
+/* Residual certificate of n given eigenpairs (b: n x F natural layout):
+ * rho = ||K b - k2 A b|| / (k2 ||A b||), delta = ||D A b|| h / ||A b||,
+ * rq = b^T K b / b^T A b.  Outputs are host arrays of length n (nullable). */
+dm_status dm_certify(dm_context* ctx, const dm_geometry* geom, int n, const double* k2,
+                     const double* b, int on_device, double* rho, double* delta, double* rq);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMEIG_H */

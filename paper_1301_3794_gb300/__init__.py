@@ -1,0 +1,351 @@
+"""GB300 Dey--Mittra cavity eigensolver (Bauer, Werner & Cary, arXiv:1301.3794).
+
+Python binding of the C ABI in ``include/dmeig.h``: it only marshals arguments.
+Every step of the solve runs in the CUDA kernels of ``libdmeig.so``; importing
+this package fails loudly if that library has not been built.
+
+Arrays may be numpy arrays (host) or torch tensors; CUDA tensors are passed to
+the library as device pointers, so PyTorch serves as the device allocator.
+Face vectors use the natural layout of the header: x-faces [nz][ny][nx+1],
+y-faces [nz][ny+1][nx], z-faces [nz+1][ny][nx], concatenated and flattened.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import EigParams, EigReport, MGParams, PREC, STATUS
+
+__all__ = ["Context", "Geometry", "Operator", "eigensolve", "certify", "DMError", "lib", "face_count",
+           "edge_count", "cell_count"]
+
+lib = _lib.load()
+
+
+class DMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def face_count(nx, ny, nz):
+    return (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
+
+
+def edge_count(nx, ny, nz):
+    return nx * (ny + 1) * (nz + 1) + (nx + 1) * ny * (nz + 1) + (nx + 1) * (ny + 1) * nz
+
+
+def cell_count(nx, ny, nz):
+    return nx * ny * nz
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+class _Arg:
+    """Pointer to an input array plus whether it lives on the device."""
+
+    def __init__(self, a, count=None):
+        if _is_torch(a):
+            if a.is_cuda:
+                import torch
+                self.keep = a.contiguous().to(torch.float64)
+                self.ptr = C.c_void_p(self.keep.data_ptr())
+                self.device = 1
+            else:
+                self.keep = np.ascontiguousarray(a.detach().numpy(), dtype=np.float64)
+                self.ptr = C.c_void_p(self.keep.ctypes.data)
+                self.device = 0
+        else:
+            self.keep = np.ascontiguousarray(a, dtype=np.float64)
+            self.ptr = C.c_void_p(self.keep.ctypes.data)
+            self.device = 0
+        n = self.keep.numel() if _is_torch(self.keep) else self.keep.size
+        if count is not None and n != count:
+            raise ValueError(f"expected {count} values, got {n}")
+
+
+def _out_like(arg, count):
+    if arg.device:
+        import torch
+        t = torch.empty(count, dtype=torch.float64, device=arg.keep.device)
+        return t, C.c_void_p(t.data_ptr())
+    a = np.empty(count, dtype=np.float64)
+    return a, C.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """A CUDA device and stream; every call of the library issues on that stream."""
+
+    def __init__(self, device=0, stream=None):
+        h = C.c_void_p()
+        sp = C.c_void_p(int(stream)) if stream is not None else None
+        st = lib.dm_context_create(int(device), sp, C.byref(h))
+        if st != 0:
+            raise DMError(st, "context creation failed (device %d)" % device)
+        self.h = h
+        self.device = device
+
+    def check(self, st, what=""):
+        if st != 0:
+            raise DMError(st, f"{what}: {lib.dm_last_error(self.h).decode()}")
+
+    @property
+    def launches(self):
+        return lib.dm_context_launch_count(self.h)
+
+    def trace(self, on=True):
+        """Start (clearing earlier statistics) or stop per-kernel event timing."""
+        self.check(lib.dm_trace_enable(self.h, int(bool(on))), "dm_trace_enable")
+
+    def trace_stats(self):
+        """{kernel name: (launches, total device ms)} recorded while tracing."""
+        out = {}
+        buf = C.create_string_buffer(128)
+        n = lib.dm_trace_count(self.h)
+        for i in range(n):
+            cnt = C.c_longlong()
+            ms = C.c_double()
+            self.check(lib.dm_trace_entry(self.h, i, buf, 128, C.byref(cnt), C.byref(ms)), "dm_trace_entry")
+            out[buf.value.decode()] = (cnt.value, ms.value)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.dm_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Geometry:
+    """Cut-cell fractions of a Yee grid and its multigrid levels."""
+
+    def __init__(self, ctx, nx, ny, nz, dx, dy, dz, phi, origin=(0.0, 0.0, 0.0), a_min=0.0):
+        self.ctx = ctx
+        self.dims = (int(nx), int(ny), int(nz))
+        self.spacing = (float(dx), float(dy), float(dz))
+        arg = _Arg(phi, (nx + 1) * (ny + 1) * (nz + 1))
+        org = (C.c_double * 3)(*origin)
+        h = C.c_void_p()
+        st = lib.dm_geometry_create(ctx.h, nx, ny, nz, dx, dy, dz, org, arg.ptr, arg.device, float(a_min), C.byref(h))
+        ctx.check(st, "dm_geometry_create")
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, ctx, w, a_min=0.0, phi=None):
+        g = w.grid
+        return cls(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, w.phi.ravel() if phi is None else phi, g.origin, a_min)
+
+    @property
+    def num_levels(self):
+        return lib.dm_geometry_num_levels(self.h)
+
+    def level_info(self, level=0):
+        dims = (C.c_int * 3)()
+        counts = (C.c_longlong * 4)()
+        self.ctx.check(lib.dm_geometry_level_info(self.h, level, dims, counts), "dm_geometry_level_info")
+        return {"dims": tuple(dims), "faces": counts[0], "edges": counts[1], "cells": counts[2], "open": counts[3]}
+
+    def fractions(self, level=0):
+        """(L, A, V) in natural layouts as numpy arrays."""
+        info = self.level_info(level)
+        L = np.empty(info["edges"])
+        A = np.empty(info["faces"])
+        V = np.empty(info["cells"])
+        st = lib.dm_geometry_fractions(self.h, level, C.c_void_p(L.ctypes.data), C.c_void_p(A.ctypes.data),
+                                       C.c_void_p(V.ctypes.data), 0)
+        self.ctx.check(st, "dm_geometry_fractions")
+        return L, A, V
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.dm_geometry_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_params(max_coarse=4, band_sweeps=8, omega_scale=1.7, power_iters=30, precision="f64"):
+    p = MGParams()
+    lib.dm_mg_params_default(C.byref(p))
+    p.max_coarse = max_coarse
+    p.band_sweeps = band_sweeps
+    p.omega_scale = omega_scale
+    p.power_iters = power_iters
+    p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    return p
+
+
+class Operator:
+    """K - sigma A (Eq. discLaplDM) on every level with its V-cycle preconditioner."""
+
+    def __init__(self, ctx, geom, sigma, **mg):
+        self.ctx = ctx
+        self.geom = geom
+        self.sigma = float(sigma)
+        self.mg = mg_params(**mg)
+        h = C.c_void_p()
+        ctx.check(lib.dm_operator_create(ctx.h, geom.h, self.sigma, C.byref(self.mg), C.byref(h)),
+                  "dm_operator_create")
+        self.h = h
+
+    @property
+    def num_levels(self):
+        return lib.dm_operator_num_levels(self.h)
+
+    def omega(self, level, scalar=False):
+        return lib.dm_operator_get_omega(self.h, level, int(scalar))
+
+    def set_omega(self, level, omega, scalar=False):
+        self.ctx.check(lib.dm_operator_set_omega(self.h, level, int(scalar), float(omega)), "set_omega")
+
+    def _faces(self, level):
+        return self.geom.level_info(level)["faces"]
+
+    def _cells(self, level):
+        return self.geom.level_info(level)["cells"]
+
+    def apply(self, x, level=0):
+        a = _Arg(x, self._faces(level))
+        y, yp = _out_like(a, self._faces(level))
+        self.ctx.check(lib.dm_operator_apply(self.h, level, a.ptr, yp, a.device), "dm_operator_apply")
+        return y
+
+    def diagonal(self, level=0):
+        d = np.empty(self._faces(level))
+        self.ctx.check(lib.dm_operator_diagonal(self.h, level, C.c_void_p(d.ctypes.data), 0), "dm_operator_diagonal")
+        return d
+
+    def smooth(self, f, x, level=0):
+        fa = _Arg(f, self._faces(level))
+        xa = _Arg(x, self._faces(level))
+        out = xa.keep.clone() if xa.device else xa.keep.copy()
+        ptr = C.c_void_p(out.data_ptr()) if xa.device else C.c_void_p(out.ctypes.data)
+        self.ctx.check(lib.dm_operator_smooth(self.h, level, fa.ptr, ptr, fa.device), "dm_operator_smooth")
+        return out
+
+    def restrict(self, r, level=0):
+        a = _Arg(r, self._faces(level))
+        y, yp = _out_like(a, self._faces(level + 1))
+        self.ctx.check(lib.dm_operator_restrict(self.h, level, a.ptr, yp, a.device), "dm_operator_restrict")
+        return y
+
+    def prolong(self, ec, x, level=0):
+        ea = _Arg(ec, self._faces(level + 1))
+        xa = _Arg(x, self._faces(level))
+        out = xa.keep.clone() if xa.device else xa.keep.copy()
+        ptr = C.c_void_p(out.data_ptr()) if xa.device else C.c_void_p(out.ctypes.data)
+        self.ctx.check(lib.dm_operator_prolong(self.h, level, ea.ptr, ptr, ea.device), "dm_operator_prolong")
+        return out
+
+    def vcycle(self, f):
+        a = _Arg(f, self._faces(0))
+        e, ep = _out_like(a, self._faces(0))
+        self.ctx.check(lib.dm_operator_vcycle(self.h, a.ptr, ep, a.device), "dm_operator_vcycle")
+        return e
+
+    def scalar_vcycle(self, f):
+        a = _Arg(f, self._cells(0))
+        e, ep = _out_like(a, self._cells(0))
+        self.ctx.check(lib.dm_operator_scalar_vcycle(self.h, a.ptr, ep, a.device), "dm_operator_scalar_vcycle")
+        return e
+
+    def solve(self, b, tol=1e-10, restart=40, maxit=400):
+        a = _Arg(b, self._faces(0))
+        x, xp = _out_like(a, self._faces(0))
+        it = C.c_int()
+        rr = C.c_double()
+        st = lib.dm_operator_solve(self.h, a.ptr, xp, a.device, tol, restart, maxit, C.byref(it), C.byref(rr))
+        if st not in (0, 2):
+            self.ctx.check(st, "dm_operator_solve")
+        return x, it.value, rr.value
+
+    def project(self, x, tol=1e-12):
+        a = _Arg(x, self._faces(0))
+        y, yp = _out_like(a, self._faces(0))
+        it = C.c_int()
+        self.ctx.check(lib.dm_operator_project(self.h, a.ptr, yp, a.device, tol, C.byref(it)), "dm_operator_project")
+        return y, it.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.dm_operator_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
+               inner_restart=40, inner_maxit=400, seed=1301, **mg):
+    p = EigParams()
+    lib.dm_eig_params_default(C.byref(p))
+    p.sigma = float(sigma)
+    p.nev = int(nev)
+    p.tol = tol
+    p.inner_tol = inner_tol
+    p.proj_tol = proj_tol
+    p.basis = basis
+    p.max_restarts = max_restarts
+    p.inner_restart = inner_restart
+    p.inner_maxit = inner_maxit
+    p.seed = seed
+    p.mg = mg_params(**mg)
+    return p
+
+
+def eigensolve(ctx, geom, sigma, nev, vectors="host", out=None, **kw):
+    """The nev electromagnetic eigenpairs nearest sigma.
+
+    vectors: "host" (numpy [nev, F]), "device" (torch CUDA tensor [nev, F]) or None.
+    Returns (k2 numpy[nev], B or None, report dict, status)."""
+    p = eig_params(sigma, nev, **kw)
+    F = geom.level_info(0)["faces"]
+    k2 = np.empty(nev)
+    B = None
+    bptr = None
+    dev = 0
+    if vectors == "host":
+        B = np.empty((nev, F)) if out is None else out
+        bptr = C.c_void_p(B.ctypes.data)
+    elif vectors == "device":
+        import torch
+        B = torch.empty((nev, F), dtype=torch.float64, device=f"cuda:{ctx.device}") if out is None else out
+        bptr = C.c_void_p(B.data_ptr())
+        dev = 1
+    rep = EigReport()
+    st = lib.dm_eigensolve(ctx.h, geom.h, C.byref(p), k2.ctypes.data_as(C.POINTER(C.c_double)), bptr, dev,
+                           C.byref(rep))
+    if st not in (0, 2):
+        ctx.check(st, "dm_eigensolve")
+    return k2, B, rep.as_dict(), st
+
+
+def certify(ctx, geom, k2, B):
+    """(rho, delta, rq) of the given eigenpairs (B: [n, F] numpy or CUDA tensor)."""
+    n = len(k2)
+    F = geom.level_info(0)["faces"]
+    a = _Arg(B, n * F)
+    k = np.ascontiguousarray(k2, dtype=np.float64)
+    rho, delta, rq = np.empty(n), np.empty(n), np.empty(n)
+    dp = C.POINTER(C.c_double)
+    st = lib.dm_certify(ctx.h, geom.h, n, k.ctypes.data_as(dp), a.ptr, a.device, rho.ctypes.data_as(dp),
+                        delta.ctypes.data_as(dp), rq.ctypes.data_as(dp))
+    ctx.check(st, "dm_certify")
+    return rho, delta, rq

@@ -1,0 +1,1421 @@
+// C ABI and host orchestration of the Dey--Mittra eigensolver (include/dmeig.h).
+//
+// The host code only sequences kernels and does O(m^2) arithmetic on scalars
+// the device returns (Givens rotations of FGMRES, the <= 64 x 64 projected
+// eigenproblem of Krylov--Schur); every vector operation runs in the kernels
+// of dm_geometry.cu, dm_stencil.cu, dm_transfer.cu, dm_blas.cu, dm_dense.cu.
+#include "dm_common.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+namespace dm {
+
+thread_local long long* g_launch_counter = nullptr;
+thread_local Tracer* g_tracer = nullptr;
+
+cudaEvent_t Tracer::get_event() {
+    if (free_events.empty()) {
+        cudaEvent_t e;
+        DM_CUDA(cudaEventCreate(&e));
+        all_events.push_back(e);
+        return e;
+    }
+    cudaEvent_t e = free_events.back();
+    free_events.pop_back();
+    return e;
+}
+int Tracer::stat_index(const char* name) {
+    for (size_t i = 0; i < stats.size(); ++i)
+        if (stats[i].name == name) return (int)i;
+    stats.push_back(Stat{name, 0, 0.0});
+    return (int)stats.size() - 1;
+}
+void Tracer::begin(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
+    if (pending.size() >= 4096) resolve();
+    *e0 = get_event();
+    *e1 = get_event();
+    DM_CUDA(cudaEventRecord(*e0, s));
+}
+void Tracer::end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    DM_CUDA(cudaEventRecord(e1, s));
+    pending.push_back({stat_index(name), {e0, e1}});
+}
+void Tracer::resolve() {
+    for (auto& p : pending) {
+        DM_CUDA(cudaEventSynchronize(p.second.second));
+        float ms = 0.f;
+        DM_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+        stats[p.first].launches += 1;
+        stats[p.first].ms += ms;
+        free_events.push_back(p.second.first);
+        free_events.push_back(p.second.second);
+    }
+    pending.clear();
+}
+void Tracer::reset() {
+    resolve();
+    stats.clear();
+}
+Tracer::~Tracer() {
+    for (auto& p : pending) {
+        (void)p;
+    }
+    for (cudaEvent_t e : all_events) cudaEventDestroy(e);
+}
+
+void check_launch(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(DM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool can_coarsen(int nx, int ny, int nz, int max_coarse) {
+    return nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && std::max(nx, std::max(ny, nz)) > max_coarse &&
+           std::min(nx, std::min(ny, nz)) >= 4;
+}
+
+}  // namespace dm
+
+using namespace dm;
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct dm_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    long long launches = 0;
+    Reducer red;
+    Tracer tracer;
+};
+
+namespace {
+
+struct GeoLevel {
+    Grid3 g{};
+    DBuf<double> A, L, V, invV;
+    DBuf<float> A32, L32, invV32;
+    DBuf<int> band;
+    int nband = 0;
+    DBuf<unsigned char> active;
+    int nopen = 0;
+};
+
+struct Sync {
+    static void stream(cudaStream_t s) { DM_CUDA(cudaStreamSynchronize(s)); }
+};
+
+struct LaunchScope {
+    long long* prev;
+    Tracer* prev_t;
+    explicit LaunchScope(dm_context* ctx) : prev(g_launch_counter), prev_t(g_tracer) {
+        g_launch_counter = ctx ? &ctx->launches : nullptr;
+        g_tracer = ctx ? &ctx->tracer : nullptr;
+    }
+    ~LaunchScope() {
+        g_launch_counter = prev;
+        g_tracer = prev_t;
+    }
+};
+
+template <class F>
+dm_status guarded(const dm_context* cctx, F&& f) {
+    dm_context* ctx = const_cast<dm_context*>(cctx);
+    LaunchScope scope(ctx);
+    try {
+        f();
+        if (ctx) ctx->err.clear();
+        return DM_OK;
+    } catch (const Error& e) {
+        if (ctx) ctx->err = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->err = "host allocation failed";
+        return DM_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (ctx) ctx->err = e.what();
+        return DM_ERR_CUDA;
+    } catch (...) {
+        if (ctx) ctx->err = "unknown error";
+        return DM_ERR_CUDA;
+    }
+}
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// symmetric eigenproblem of a small dense matrix by cyclic Jacobi rotations
+// (a: n x n row-major, destroyed; w: eigenvalues; v: eigenvectors as columns)
+void jacobi_eig(int n, std::vector<double>& a, std::vector<double>& w, std::vector<double>& v) {
+    v.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) v[(size_t)i * n + i] = 1.0;
+    double scale = 0.0;
+    for (double x : a) scale = std::max(scale, std::fabs(x));
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a[(size_t)p * n + q] * a[(size_t)p * n + q];
+        if (std::sqrt(off) <= 1e-17 * std::max(scale, 1e-300)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+                const double tau = (aqq - app) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+                    a[(size_t)k * n + p] = c * akp - s * akq;
+                    a[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+                    a[(size_t)p * n + k] = c * apk - s * aqk;
+                    a[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = v[(size_t)k * n + p], vkq = v[(size_t)k * n + q];
+                    v[(size_t)k * n + p] = c * vkp - s * vkq;
+                    v[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = a[(size_t)i * n + i];
+}
+
+}  // namespace
+
+struct dm_geometry {
+    dm_context* ctx = nullptr;
+    std::vector<std::unique_ptr<GeoLevel>> lv;
+};
+
+namespace {
+
+// buffers of one level of the V-cycles, in the preconditioner's storage type
+struct WorkLevel {
+    DBuf<char> f, e, r;       // vector (3 np)
+    DBuf<char> sf, se, sr;    // scalar (np)
+};
+
+struct OpLevel {
+    DBuf<double> invD;        // 3 np
+    DBuf<float> invD32;
+    DBuf<double> invDs;       // np
+    DBuf<float> invDs32;
+    double omega = 0.0, omega_s = 0.0;
+};
+
+struct Fgmres {
+    long long n = 0;
+    int m = 0;
+    DBuf<double> V, Z, w;
+    void ensure(long long n_, int m_) {
+        if (n == n_ && m >= m_) return;
+        n = n_;
+        m = m_;
+        V.alloc((size_t)(m + 1) * n);
+        Z.alloc((size_t)m * n);
+        w.alloc((size_t)n);
+    }
+};
+
+}  // namespace
+
+struct dm_operator {
+    dm_context* ctx = nullptr;
+    const dm_geometry* geom = nullptr;
+    double sigma = 0.0;
+    dm_mg_params mg{};
+    int nlev = 0;
+    std::vector<OpLevel> ol;
+    std::vector<WorkLevel> wk;
+    DBuf<double> band_u;
+    // coarsest vector solve
+    DBuf<int> c_list;
+    int c_n = 0;
+    DBuf<double> c_inv, c_tmp_in, c_tmp_out;
+    DBuf<float> c_inv32;
+    // coarsest scalar solve
+    DBuf<int> s_list;
+    int s_n = 0;
+    DBuf<unsigned char> s_pinned;
+    DBuf<double> s_inv, s_tmp_in, s_tmp_out;
+    DBuf<float> s_inv32;
+    // FP64 scratch on the fine level
+    DBuf<double> t0, t1, t2, t3, c0, c1;
+    Fgmres vg, sg;
+    double complexity = 1.0;
+};
+
+namespace {
+
+const GeoLevel& glv(const dm_operator* op, int l) { return *op->geom->lv[l]; }
+size_t tsize(int prec) { return prec == DM_PREC_F64 ? 8 : (prec == DM_PREC_F32 ? 4 : 2); }
+
+template <typename T, typename TC> struct Pick;
+template <> struct Pick<double, double> {
+    static const double* A(const GeoLevel& g) { return g.A.get(); }
+    static const double* L(const GeoLevel& g) { return g.L.get(); }
+    static const double* iV(const GeoLevel& g) { return g.invV.get(); }
+    static const double* iD(const OpLevel& o) { return o.invD.get(); }
+    static const double* iDs(const OpLevel& o) { return o.invDs.get(); }
+};
+template <typename T> struct Pick<T, float> {
+    static const float* A(const GeoLevel& g) { return g.A32.get(); }
+    static const float* L(const GeoLevel& g) { return g.L32.get(); }
+    static const float* iV(const GeoLevel& g) { return g.invV32.get(); }
+    static const float* iD(const OpLevel& o) { return o.invD32.get(); }
+    static const float* iDs(const OpLevel& o) { return o.invDs32.get(); }
+};
+
+template <typename T, typename TC>
+VecOp<T, TC> vop(const dm_operator* op, int l) {
+    const GeoLevel& g = glv(op, l);
+    return VecOp<T, TC>{g.g, Pick<T, TC>::A(g), Pick<T, TC>::L(g), Pick<T, TC>::iV(g), Pick<T, TC>::iD(op->ol[l]),
+                        op->sigma, l};
+}
+template <typename T, typename TC>
+ScalOp<T, TC> sop(const dm_operator* op, int l) {
+    const GeoLevel& g = glv(op, l);
+    return ScalOp<T, TC>{g.g, Pick<T, TC>::A(g), g.active.get(), Pick<T, TC>::iDs(op->ol[l]), l};
+}
+
+// ---- vector V-cycle: result in rbuf ------------------------------------------------
+template <typename T, typename TC>
+void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
+    cudaStream_t s = op->ctx->stream;
+    const GeoLevel& g = glv(op, l);
+    const size_t vbytes = sizeof(T) * 3 * (size_t)g.g.np;
+    if (l == op->nlev - 1) {
+        zero(rbuf, vbytes, s);
+        dense_coarse_solve<T>(std::is_same<T, double>::value ? op->c_inv.get() : nullptr,
+                              std::is_same<T, double>::value ? nullptr : op->c_inv32.get(), op->c_n, op->c_list.get(),
+                              nullptr, f, rbuf, op->c_tmp_in.get(), op->c_tmp_out.get(), s);
+        return;
+    }
+    const VecOp<T, TC> o = vop<T, TC>(op, l);
+    const double om = op->ol[l].omega;
+    float* u = reinterpret_cast<float*>(op->band_u.get());
+    vec_jacobi_zero(o, f, ebuf, om, s);
+    for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, f, ebuf, u, om, s);
+    vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
+    const GeoLevel& gc = glv(op, l + 1);
+    WorkLevel& wc = op->wk[l + 1];
+    T* fc = reinterpret_cast<T*>(wc.f.get());
+    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, s);
+    vcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.e.get()), reinterpret_cast<T*>(wc.r.get()));
+    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, s);
+    vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
+    for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, f, rbuf, u, om, s);
+}
+
+// ---- scalar V-cycle: result in rbuf -----------------------------------------------
+template <typename T, typename TC>
+void svcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
+    cudaStream_t s = op->ctx->stream;
+    const GeoLevel& g = glv(op, l);
+    if (l == op->nlev - 1) {
+        zero(rbuf, sizeof(T) * (size_t)g.g.np, s);
+        dense_coarse_solve<T>(std::is_same<T, double>::value ? op->s_inv.get() : nullptr,
+                              std::is_same<T, double>::value ? nullptr : op->s_inv32.get(), op->s_n, op->s_list.get(),
+                              op->s_pinned.get(), f, rbuf, op->s_tmp_in.get(), op->s_tmp_out.get(), s);
+        return;
+    }
+    const ScalOp<T, TC> o = sop<T, TC>(op, l);
+    const double om = op->ol[l].omega_s;
+    scal_jacobi_zero(o, f, ebuf, om, s);
+    scal_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
+    const GeoLevel& gc = glv(op, l + 1);
+    WorkLevel& wc = op->wk[l + 1];
+    T* fc = reinterpret_cast<T*>(wc.sf.get());
+    cell_restrict<T>(g.g, gc.g, gc.active.get(), rbuf, fc, s);
+    svcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.se.get()), reinterpret_cast<T*>(wc.sr.get()));
+    cell_prolong_add<T>(g.g, gc.g, g.active.get(), reinterpret_cast<const T*>(wc.sr.get()), ebuf, s);
+    scal_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
+}
+
+// preconditioner on FP64 fine-level vectors: z = M^-1 v
+void precond_vec(dm_operator* op, const double* v, double* z) {
+    cudaStream_t s = op->ctx->stream;
+    const long long n = 3ll * glv(op, 0).g.np;
+    WorkLevel& w0 = op->wk[0];
+    switch (op->mg.precision) {
+        case DM_PREC_F64:
+            vcycle<double, double>(op, 0, v, reinterpret_cast<double*>(w0.e.get()), z);
+            break;
+        case DM_PREC_F32: {
+            float* f = reinterpret_cast<float*>(w0.f.get());
+            convert<float, double>(n, v, f, s);
+            vcycle<float, float>(op, 0, f, reinterpret_cast<float*>(w0.e.get()), reinterpret_cast<float*>(w0.r.get()));
+            convert<double, float>(n, reinterpret_cast<float*>(w0.r.get()), z, s);
+            break;
+        }
+        default: {
+            auto* f = reinterpret_cast<__nv_bfloat16*>(w0.f.get());
+            convert<__nv_bfloat16, double>(n, v, f, s);
+            vcycle<__nv_bfloat16, float>(op, 0, f, reinterpret_cast<__nv_bfloat16*>(w0.e.get()),
+                                         reinterpret_cast<__nv_bfloat16*>(w0.r.get()));
+            convert<double, __nv_bfloat16>(n, reinterpret_cast<__nv_bfloat16*>(w0.r.get()), z, s);
+        }
+    }
+}
+
+void precond_scal(dm_operator* op, const double* v, double* z) {
+    cudaStream_t s = op->ctx->stream;
+    const long long n = glv(op, 0).g.np;
+    WorkLevel& w0 = op->wk[0];
+    switch (op->mg.precision) {
+        case DM_PREC_F64:
+            svcycle<double, double>(op, 0, v, reinterpret_cast<double*>(w0.se.get()), z);
+            break;
+        case DM_PREC_F32: {
+            float* f = reinterpret_cast<float*>(w0.sf.get());
+            convert<float, double>(n, v, f, s);
+            svcycle<float, float>(op, 0, f, reinterpret_cast<float*>(w0.se.get()), reinterpret_cast<float*>(w0.sr.get()));
+            convert<double, float>(n, reinterpret_cast<float*>(w0.sr.get()), z, s);
+            break;
+        }
+        default: {
+            auto* f = reinterpret_cast<__nv_bfloat16*>(w0.sf.get());
+            convert<__nv_bfloat16, double>(n, v, f, s);
+            svcycle<__nv_bfloat16, float>(op, 0, f, reinterpret_cast<__nv_bfloat16*>(w0.se.get()),
+                                          reinterpret_cast<__nv_bfloat16*>(w0.sr.get()));
+            convert<double, __nv_bfloat16>(n, reinterpret_cast<__nv_bfloat16*>(w0.sr.get()), z, s);
+        }
+    }
+}
+
+void apply_vec64(dm_operator* op, int l, const double* x, double* y) {
+    vec_stencil<double, double>(vop<double, double>(op, l), ST_APPLY, x, nullptr, y, 0.0, op->ctx->stream);
+}
+void apply_scal64(dm_operator* op, int l, const double* x, double* y) {
+    scal_stencil<double, double>(sop<double, double>(op, l), ST_APPLY, x, nullptr, y, 0.0, op->ctx->stream);
+}
+
+double norm2(dm_context* ctx, long long n, const double* x, const double* w = nullptr) {
+    double r = 0.0;
+    mdot(ctx->red, n, 1, x, n, x, w, &r, ctx->stream);
+    return std::sqrt(std::max(r, 0.0));
+}
+
+// Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt
+// applied twice.  x is overwritten.  Returns the iteration count.
+template <class Apply, class Prec>
+int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec prec, const double* b, double* x,
+           double tol, int maxit, double* relres) {
+    cudaStream_t s = ctx->stream;
+    ws.ensure(n, m);
+    double* V = ws.V.get();
+    double* Z = ws.Z.get();
+    double* w = ws.w.get();
+    zero(x, sizeof(double) * n, s);
+    const double bnorm = norm2(ctx, n, b);
+    if (relres) *relres = 0.0;
+    if (bnorm == 0.0) return 0;
+    int total = 0;
+    bool first = true;
+    double res = 1.0;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    while (total < maxit) {
+        // r = b - A x
+        if (first) {
+            scale_copy(n, 1.0, b, V, s);
+        } else {
+            apply(x, w);
+            axpby(n, 1.0, b, -1.0, w, s);
+            scale_copy(n, 1.0, w, V, s);
+        }
+        const double beta = norm2(ctx, n, V);
+        res = beta / bnorm;
+        if (beta <= tol * bnorm) break;
+        scale_copy(n, 1.0 / beta, V, V, s);
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int jend = -1;
+        for (int j = 0; j < m && total < maxit; ++j) {
+            prec(V + (size_t)j * n, Z + (size_t)j * n);
+            apply(Z + (size_t)j * n, w);
+            std::vector<double> h(j + 1);
+            for (int pass = 0; pass < 2; ++pass) {
+                mdot(ctx->red, n, j + 1, V, n, w, nullptr, h.data(), s);
+                maxpy(ctx->red, n, j + 1, V, n, h.data(), w, s);
+                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+            }
+            const double hn = norm2(ctx, n, w);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) scale_copy(n, 1.0 / hn, w, V + (size_t)(j + 1) * n, s);
+            // Givens
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+            }
+            const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            const double rr = std::hypot(a, bb);
+            cs[j] = rr > 0 ? a / rr : 1.0;
+            sn[j] = rr > 0 ? bb / rr : 0.0;
+            H[(size_t)j * m + j] = rr;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total;
+            jend = j;
+            res = std::fabs(g[j + 1]) / bnorm;
+            if (res <= tol || hn == 0.0) break;
+        }
+        if (jend < 0) break;
+        // y = H^-1 g (upper triangular)
+        for (int i = jend; i >= 0; --i) {
+            double acc = g[i];
+            for (int k = i + 1; k <= jend; ++k) acc -= H[(size_t)i * m + k] * y[k];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        std::vector<double> neg(jend + 1);
+        for (int i = 0; i <= jend; ++i) neg[i] = -y[i];
+        maxpy(ctx->red, n, jend + 1, Z, n, neg.data(), x, s);
+        first = false;
+        if (res <= tol) {
+            // confirm with the true residual
+            apply(x, w);
+            axpby(n, 1.0, b, -1.0, w, s);
+            const double tr = norm2(ctx, n, w) / bnorm;
+            res = tr;
+            if (tr <= 10.0 * tol) break;
+        }
+    }
+    if (relres) *relres = res;
+    return total;
+}
+
+int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
+    const long long n = 3ll * glv(op, 0).g.np;
+    auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
+    auto prec = [op](const double* in, double* out) { precond_vec(op, in, out); };
+    return fgmres(op->ctx, op->vg, n, restart, apply, prec, b, x, tol, maxit, relres);
+}
+
+// y = P_DM x (Eq. proj); x, y padded FP64 fine-level face vectors (may alias)
+int project(dm_operator* op, const double* x, double* y, double tol) {
+    cudaStream_t s = op->ctx->stream;
+    const GeoLevel& g0 = glv(op, 0);
+    const long long nc = g0.g.np;
+    double* sv = op->c0.get();
+    double* phi = op->c1.get();
+    dm_div_a(g0.g, g0.A.get(), x, sv, s);
+    auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
+    auto prec = [op](const double* in, double* out) { precond_scal(op, in, out); };
+    double rr = 0.0;
+    const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr);
+    dm_sub_grad(g0.g, g0.A.get(), x, phi, y, s);
+    return it;
+}
+
+double power_lambda_max(dm_operator* op, int l, bool scalar) {
+    cudaStream_t s = op->ctx->stream;
+    const GeoLevel& g = glv(op, l);
+    const long long n = scalar ? g.g.np : 3ll * g.g.np;
+    DBuf<double> x(n), y(n);
+    if (scalar) {
+        // random start on the active cells (scaling by D^-1 zeroes the inactive ones)
+        DBuf<double> tmp(n);
+        fill_random(n, 12345 + l, nullptr, tmp.get(), s);
+        hadamard(n, op->ol[l].invDs.get(), tmp.get(), x.get(), s);
+    } else {
+        fill_random(n, 12345 + l, g.A.get(), x.get(), s);
+    }
+    double lam = 0.0;
+    double nx = norm2(op->ctx, n, x.get());
+    if (nx == 0.0) return 1.0;
+    scale_copy(n, 1.0 / nx, x.get(), x.get(), s);
+    for (int it = 0; it < op->mg.power_iters; ++it) {
+        if (scalar) {
+            apply_scal64(op, l, x.get(), y.get());
+            hadamard(n, op->ol[l].invDs.get(), y.get(), y.get(), s);
+        } else {
+            apply_vec64(op, l, x.get(), y.get());
+            hadamard(n, op->ol[l].invD.get(), y.get(), y.get(), s);
+        }
+        const double ny = norm2(op->ctx, n, y.get());
+        if (ny == 0.0) break;
+        lam = ny;
+        scale_copy(n, 1.0 / ny, y.get(), x.get(), s);
+    }
+    return lam > 0.0 ? lam : 1.0;
+}
+
+void ensure_f32(GeoLevel& g, cudaStream_t s) {
+    if (g.A32.get()) return;
+    const long long n3 = 3ll * g.g.np, n1 = g.g.np;
+    g.A32.alloc(n3);
+    g.L32.alloc(n3);
+    g.invV32.alloc(n1);
+    convert_coeff<float>(n3, g.A.get(), g.A32.get(), s);
+    convert_coeff<float>(n3, g.L.get(), g.L32.get(), s);
+    convert_coeff<float>(n1, g.invV.get(), g.invV32.get(), s);
+}
+
+__global__ void k_invert_diag(long long n, const double* __restrict__ d, double* __restrict__ inv) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        inv[r] = d[r] != 0.0 ? 1.0 / d[r] : 0.0;
+}
+void invert_diag(long long n, const double* d, double* inv, cudaStream_t s) {
+    const int b = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+    launch("k_invert_diag", k_invert_diag, b, 256, 0, s, n, d, inv);
+}
+
+void setup_operator(dm_operator* op) {
+    cudaStream_t s = op->ctx->stream;
+    dm_geometry* geom = const_cast<dm_geometry*>(op->geom);
+    // levels used by this operator
+    int nl = 1;
+    while (nl < (int)geom->lv.size()) {
+        const Grid3& g = geom->lv[nl - 1]->g;
+        if (!can_coarsen(g.nx, g.ny, g.nz, op->mg.max_coarse)) break;
+        ++nl;
+    }
+    op->nlev = nl;
+    op->ol.resize(nl);
+    op->wk.resize(nl);
+    const bool lowp = op->mg.precision != DM_PREC_F64;
+    const size_t ts = tsize(op->mg.precision);
+    int max_band = 1;
+    for (int l = 0; l < nl; ++l) {
+        GeoLevel& g = *geom->lv[l];
+        if (lowp) ensure_f32(g, s);
+        OpLevel& o = op->ol[l];
+        const long long n3 = 3ll * g.g.np, n1 = g.g.np;
+        DBuf<double> d(n3);
+        vec_diagonal(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, d.get(), s);
+        o.invD.alloc(n3);
+        invert_diag(n3, d.get(), o.invD.get(), s);
+        DBuf<double> ds(n1);
+        scal_diagonal(g.g, g.A.get(), g.active.get(), ds.get(), s);
+        o.invDs.alloc(n1);
+        invert_diag(n1, ds.get(), o.invDs.get(), s);
+        if (lowp) {
+            o.invD32.alloc(n3);
+            o.invDs32.alloc(n1);
+            convert_coeff<float>(n3, o.invD.get(), o.invD32.get(), s);
+            convert_coeff<float>(n1, o.invDs.get(), o.invDs32.get(), s);
+        }
+        WorkLevel& w = op->wk[l];
+        w.f.alloc(ts * n3);
+        w.e.alloc(ts * n3);
+        w.r.alloc(ts * n3);
+        w.sf.alloc(ts * n1);
+        w.se.alloc(ts * n1);
+        w.sr.alloc(ts * n1);
+        max_band = std::max(max_band, g.nband);
+    }
+    op->band_u.alloc((size_t)max_band);
+    {
+        DBuf<int> cnt(1);
+        long long tot = 0, fine = 0;
+        for (int l = 0; l < nl; ++l) {
+            const GeoLevel& g = *geom->lv[l];
+            const long long c = count_positive(3ll * g.g.np, g.A.get(), cnt.get(), s);
+            if (l == 0) fine = c;
+            tot += c;
+        }
+        op->complexity = fine > 0 ? (double)tot / (double)fine : 1.0;
+    }
+    // Jacobi weights from the largest eigenvalue of D^-1 (K - sigma A)
+    for (int l = 0; l + 1 < nl; ++l) {
+        op->ol[l].omega = op->mg.omega_scale / power_lambda_max(op, l, false);
+        op->ol[l].omega_s = op->mg.omega_scale / power_lambda_max(op, l, true);
+    }
+    // coarsest vector level: dense inverse over the open faces
+    {
+        GeoLevel& g = *geom->lv[nl - 1];
+        DBuf<int> cnt(1);
+        op->c_list.alloc(3ll * g.g.np);
+        op->c_n = geom_open_faces(g.g, g.A.get(), op->c_list.get(), cnt.get(), s);
+        const int n = op->c_n;
+        DM_REQUIRE(n > 0, DM_ERR_GEOMETRY, "coarsest level has no open face");
+        DM_REQUIRE(n <= 6000, DM_ERR_INVALID_ARG, "coarsest level too large for the dense solve; raise max_coarse");
+        op->c_inv.alloc((size_t)n * n);
+        vec_dense_assemble(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, op->c_list.get(), n, op->c_inv.get(), s);
+        DBuf<double> work(2ull * n * n + n);
+        DBuf<int> flag(1);
+        DM_REQUIRE(dense_inverse(op->c_inv.get(), n, work.get(), flag.get(), s), DM_ERR_NO_CONVERGENCE,
+                   "coarsest K - sigma A is singular (sigma is an eigenvalue of the coarsest grid)");
+        if (lowp) {
+            op->c_inv32.alloc((size_t)n * n);
+            convert_coeff<float>((long long)n * n, op->c_inv.get(), op->c_inv32.get(), s);
+        }
+        op->c_tmp_in.alloc(n);
+        op->c_tmp_out.alloc(n);
+    }
+    // coarsest scalar level: dense inverse with one pinned cell per component
+    {
+        GeoLevel& g = *geom->lv[nl - 1];
+        DBuf<int> cnt(1);
+        op->s_list.alloc(g.g.np);
+        DBuf<unsigned char> act(g.g.np);
+        op->s_n = geom_active_cells(g.g, g.A.get(), op->s_list.get(), act.get(), cnt.get(), s);
+        const int n = op->s_n;
+        DM_REQUIRE(n > 0, DM_ERR_GEOMETRY, "coarsest level has no active cell");
+        DBuf<int> label(n);
+        op->s_pinned.alloc(n);
+        cell_components_pin(g.g, g.A.get(), op->s_list.get(), n, label.get(), op->s_pinned.get(), s);
+        op->s_inv.alloc((size_t)n * n);
+        scal_dense_assemble(g.g, g.A.get(), op->s_list.get(), op->s_pinned.get(), n, op->s_inv.get(), s);
+        DBuf<double> work(2ull * n * n + n);
+        DBuf<int> flag(1);
+        DM_REQUIRE(dense_inverse(op->s_inv.get(), n, work.get(), flag.get(), s), DM_ERR_NO_CONVERGENCE,
+                   "coarsest scalar Laplacian is singular after pinning");
+        if (lowp) {
+            op->s_inv32.alloc((size_t)n * n);
+            convert_coeff<float>((long long)n * n, op->s_inv.get(), op->s_inv32.get(), s);
+        }
+        op->s_tmp_in.alloc(n);
+        op->s_tmp_out.alloc(n);
+    }
+    const long long n3 = 3ll * glv(op, 0).g.np, n1 = glv(op, 0).g.np;
+    op->t0.alloc(n3);
+    op->t1.alloc(n3);
+    op->t2.alloc(n3);
+    op->t3.alloc(n3);
+    op->c0.alloc(n1);
+    op->c1.alloc(n1);
+    Sync::stream(s);
+}
+
+// natural <-> padded staging helpers (host or device caller buffers)
+void stage_in(dm_context* ctx, const double* src, int on_device, size_t count, DBuf<double>& tmp, const double** dev) {
+    if (on_device) {
+        *dev = src;
+        return;
+    }
+    tmp.alloc(count, false);
+    DM_CUDA(cudaMemcpyAsync(tmp.get(), src, sizeof(double) * count, cudaMemcpyHostToDevice, ctx->stream));
+    *dev = tmp.get();
+}
+void stage_out(dm_context* ctx, const double* dev, double* dst, int on_device, size_t count) {
+    DM_CUDA(cudaMemcpyAsync(dst, dev, sizeof(double) * count,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    DM_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+void faces_in(dm_operator* op, int l, const double* nat, int on_device, double* pad) {
+    const Grid3& g = glv(op, l).g;
+    DBuf<double> tmp;
+    const double* d = nullptr;
+    stage_in(op->ctx, nat, on_device, (size_t)natural_faces(g), tmp, &d);
+    zero(pad, sizeof(double) * 3 * (size_t)g.np, op->ctx->stream);
+    pack_faces(g, d, pad, op->ctx->stream);
+    Sync::stream(op->ctx->stream);
+}
+void faces_out(dm_operator* op, int l, const double* pad, double* nat, int on_device) {
+    const Grid3& g = glv(op, l).g;
+    const size_t nf = (size_t)natural_faces(g);
+    if (on_device) {
+        unpack_faces(g, pad, nat, op->ctx->stream);
+        Sync::stream(op->ctx->stream);
+    } else {
+        DBuf<double> tmp(nf, false);
+        unpack_faces(g, pad, tmp.get(), op->ctx->stream);
+        stage_out(op->ctx, tmp.get(), nat, 0, nf);
+    }
+}
+void cells_in(dm_operator* op, int l, const double* nat, int on_device, double* pad) {
+    const Grid3& g = glv(op, l).g;
+    DBuf<double> tmp;
+    const double* d = nullptr;
+    stage_in(op->ctx, nat, on_device, (size_t)natural_cells(g), tmp, &d);
+    zero(pad, sizeof(double) * (size_t)g.np, op->ctx->stream);
+    pack_cells(g, d, pad, op->ctx->stream);
+    Sync::stream(op->ctx->stream);
+}
+void cells_out(dm_operator* op, int l, const double* pad, double* nat, int on_device) {
+    const Grid3& g = glv(op, l).g;
+    const size_t nc = (size_t)natural_cells(g);
+    if (on_device) {
+        unpack_cells(g, pad, nat, op->ctx->stream);
+        Sync::stream(op->ctx->stream);
+    } else {
+        DBuf<double> tmp(nc, false);
+        unpack_cells(g, pad, tmp.get(), op->ctx->stream);
+        stage_out(op->ctx, tmp.get(), nat, 0, nc);
+    }
+}
+
+// run f(T**) on copies of level-l FP64 face vectors converted to storage type T
+template <typename T, class F>
+void with_mg_vectors(dm_operator* op, int l, int count, double* const* pads, F&& f) {
+    cudaStream_t s = op->ctx->stream;
+    const long long n = 3ll * glv(op, l).g.np;
+    std::vector<DBuf<T>> b(count);
+    std::vector<T*> p(count);
+    for (int i = 0; i < count; ++i) {
+        b[i].alloc(n);
+        p[i] = b[i].get();
+        convert<T, double>(n, pads[i], p[i], s);
+    }
+    f(p.data());
+    for (int i = 0; i < count; ++i) convert<double, T>(n, p[i], pads[i], s);
+    Sync::stream(s);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+dm_status dm_context_create(int device, void* cuda_stream, dm_context** out) {
+    if (!out) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto* ctx = new (std::nothrow) dm_context();
+    if (!ctx) return DM_ERR_OOM;
+    const dm_status st = guarded(ctx, [&] {
+        int ndev = 0;
+        DM_CUDA(cudaGetDeviceCount(&ndev));
+        DM_REQUIRE(device >= 0 && device < ndev, DM_ERR_INVALID_ARG, "no such CUDA device");
+        DM_CUDA(cudaSetDevice(device));
+        ctx->device = device;
+        if (cuda_stream) {
+            ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            // a blocking stream: ordered after work the caller queued on the
+            // legacy default stream (e.g. torch copies of input tensors)
+            DM_CUDA(cudaStreamCreate(&ctx->stream));
+            ctx->own_stream = true;
+        }
+        reducer_init(ctx->red, 128);
+    });
+    if (st != DM_OK) {
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return DM_OK;
+}
+
+void dm_context_destroy(dm_context* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    reducer_free(ctx->red);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* dm_last_error(const dm_context* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dm_status dm_trace_enable(dm_context* ctx, int on) {
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    return guarded(ctx, [&] {
+        if (on) ctx->tracer.reset();
+        else ctx->tracer.resolve();
+        ctx->tracer.on = on != 0;
+    });
+}
+
+int dm_trace_count(dm_context* ctx) {
+    if (!ctx) return 0;
+    if (guarded(ctx, [&] { ctx->tracer.resolve(); }) != DM_OK) return 0;
+    return (int)ctx->tracer.stats.size();
+}
+
+dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long long* launches, double* total_ms) {
+    if (!ctx || i < 0) return DM_ERR_INVALID_ARG;
+    return guarded(ctx, [&] {
+        ctx->tracer.resolve();
+        DM_REQUIRE(i < (int)ctx->tracer.stats.size(), DM_ERR_INVALID_ARG, "trace entry out of range");
+        const Tracer::Stat& st = ctx->tracer.stats[i];
+        if (name && name_cap > 0) {
+            std::strncpy(name, st.name.c_str(), (size_t)name_cap - 1);
+            name[name_cap - 1] = 0;
+        }
+        if (launches) *launches = st.launches;
+        if (total_ms) *total_ms = st.ms;
+    });
+}
+long long dm_context_launch_count(const dm_context* ctx) { return ctx ? ctx->launches : 0; }
+
+dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                             const double origin[3], const double* phi, int phi_on_device, double a_min,
+                             dm_geometry** out) {
+    if (!ctx || !out || !phi) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    (void)origin;
+    auto geom = std::make_unique<dm_geometry>();
+    const dm_status st = guarded(ctx, [&] {
+        DM_REQUIRE(nx >= 2 && ny >= 2 && nz >= 2, DM_ERR_INVALID_ARG, "grid needs at least 2 cells per dimension");
+        DM_REQUIRE(dx > 0 && dy > 0 && dz > 0, DM_ERR_INVALID_ARG, "cell sizes must be positive");
+        DM_REQUIRE(a_min >= 0.0 && a_min < 1.0, DM_ERR_INVALID_ARG, "a_min must be in [0, 1)");
+        DM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        geom->ctx = ctx;
+        int cx = nx, cy = ny, cz = nz;
+        double hx = dx, hy = dy, hz = dz;
+        for (int l = 0;; ++l) {
+            auto lv = std::make_unique<GeoLevel>();
+            lv->g = make_grid(cx, cy, cz, hx, hy, hz);
+            const long long n3 = 3ll * lv->g.np, n1 = lv->g.np;
+            lv->A.alloc(n3);
+            lv->L.alloc(n3);
+            lv->V.alloc(n1);
+            lv->invV.alloc(n1);
+            if (l == 0) {
+                DBuf<double> phi_pad(n1);
+                const size_t nn = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+                DBuf<double> tmp;
+                const double* dphi = nullptr;
+                stage_in(ctx, phi, phi_on_device, nn, tmp, &dphi);
+                pack_nodes(lv->g, dphi, phi_pad.get(), s);
+                geom_fractions(lv->g, phi_pad.get(), lv->L.get(), lv->A.get(), lv->V.get(), s);
+                if (a_min > 0.0) geom_neglect_faces(lv->g, a_min, lv->L.get(), lv->A.get(), s);
+                Sync::stream(s);
+            } else {
+                const GeoLevel& f = *geom->lv[l - 1];
+                geom_coarsen(f.g, lv->g, f.L.get(), f.A.get(), f.V.get(), lv->L.get(), lv->A.get(), lv->V.get(), s);
+            }
+            geom_inv_volume(lv->g, lv->V.get(), lv->invV.get(), s);
+            // smoother band and active cells
+            DBuf<int> flag(n1), cnt(1);
+            lv->band.alloc(n3);
+            lv->nband = geom_band(lv->g, lv->A.get(), lv->V.get(), flag.get(), lv->band.get(), cnt.get(), s);
+            lv->active.alloc(n1);
+            geom_active_cells(lv->g, lv->A.get(), nullptr, lv->active.get(), cnt.get(), s);
+            geom->lv.push_back(std::move(lv));
+            if (!can_coarsen(cx, cy, cz, 4)) break;
+            cx /= 2; cy /= 2; cz /= 2;
+            hx *= 2; hy *= 2; hz *= 2;
+        }
+        Sync::stream(s);
+    });
+    if (st != DM_OK) return st;
+    *out = geom.release();
+    return DM_OK;
+}
+
+void dm_geometry_destroy(dm_geometry* geom) {
+    if (!geom) return;
+    if (geom->ctx) cudaStreamSynchronize(geom->ctx->stream);
+    delete geom;
+}
+
+int dm_geometry_num_levels(const dm_geometry* geom) { return geom ? (int)geom->lv.size() : 0; }
+
+dm_status dm_geometry_level_info(const dm_geometry* geom, int level, int dims[3], long long counts[4]) {
+    if (!geom || level < 0 || level >= (int)geom->lv.size()) return DM_ERR_INVALID_ARG;
+    return guarded(geom->ctx, [&] {
+        const GeoLevel& g = *geom->lv[level];
+        if (dims) { dims[0] = g.g.nx; dims[1] = g.g.ny; dims[2] = g.g.nz; }
+        if (counts) {
+            counts[0] = natural_faces(g.g);
+            counts[1] = natural_edges(g.g);
+            counts[2] = natural_cells(g.g);
+            DBuf<int> cnt(1);
+            counts[3] = count_positive(3ll * g.g.np, g.A.get(), cnt.get(), geom->ctx->stream);
+        }
+    });
+}
+
+dm_status dm_geometry_fractions(const dm_geometry* geom, int level, double* L, double* A, double* V, int on_device) {
+    if (!geom || level < 0 || level >= (int)geom->lv.size()) return DM_ERR_INVALID_ARG;
+    return guarded(geom->ctx, [&] {
+        const GeoLevel& g = *geom->lv[level];
+        cudaStream_t s = geom->ctx->stream;
+        auto out = [&](auto unpack, const double* pad, double* dst, size_t count) {
+            if (!dst) return;
+            if (on_device) {
+                unpack(g.g, pad, dst, s);
+                Sync::stream(s);
+            } else {
+                DBuf<double> tmp(count, false);
+                unpack(g.g, pad, tmp.get(), s);
+                stage_out(geom->ctx, tmp.get(), dst, 0, count);
+            }
+        };
+        out(unpack_edges, g.L.get(), L, (size_t)natural_edges(g.g));
+        out(unpack_faces, g.A.get(), A, (size_t)natural_faces(g.g));
+        out(unpack_cells, g.V.get(), V, (size_t)natural_cells(g.g));
+    });
+}
+
+void dm_mg_params_default(dm_mg_params* p) {
+    if (!p) return;
+    p->max_coarse = 4;
+    p->band_sweeps = 8;
+    p->omega_scale = 1.7;
+    p->power_iters = 30;
+    p->precision = DM_PREC_F64;
+}
+
+dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
+                             dm_operator** out) {
+    if (!ctx || !geom || !out) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto op = std::make_unique<dm_operator>();
+    const dm_status st = guarded(ctx, [&] {
+        DM_CUDA(cudaSetDevice(ctx->device));
+        op->ctx = ctx;
+        op->geom = geom;
+        op->sigma = sigma;
+        dm_mg_params_default(&op->mg);
+        if (mg) op->mg = *mg;
+        DM_REQUIRE(op->mg.max_coarse >= 4, DM_ERR_INVALID_ARG, "max_coarse must be >= 4");
+        DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 64, DM_ERR_INVALID_ARG, "band_sweeps out of range");
+        DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
+        DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
+        setup_operator(op.get());
+    });
+    if (st != DM_OK) return st;
+    *out = op.release();
+    return DM_OK;
+}
+
+void dm_operator_destroy(dm_operator* op) {
+    if (!op) return;
+    if (op->ctx) cudaStreamSynchronize(op->ctx->stream);
+    delete op;
+}
+
+int dm_operator_num_levels(const dm_operator* op) { return op ? op->nlev : 0; }
+
+double dm_operator_get_omega(const dm_operator* op, int level, int scalar) {
+    if (!op || level < 0 || level >= op->nlev) return 0.0;
+    return scalar ? op->ol[level].omega_s : op->ol[level].omega;
+}
+
+dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double omega) {
+    if (!op || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
+    if (scalar) op->ol[level].omega_s = omega;
+    else op->ol[level].omega = omega;
+    return DM_OK;
+}
+
+dm_status dm_operator_apply(dm_operator* op, int level, const double* x, double* y, int on_device) {
+    if (!op || !x || !y || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const Grid3& g = glv(op, level).g;
+        DBuf<double> xp(3ll * g.np), yp(3ll * g.np);
+        faces_in(op, level, x, on_device, xp.get());
+        apply_vec64(op, level, xp.get(), yp.get());
+        faces_out(op, level, yp.get(), y, on_device);
+    });
+}
+
+dm_status dm_operator_diagonal(dm_operator* op, int level, double* d, int on_device) {
+    if (!op || !d || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const GeoLevel& g = glv(op, level);
+        DBuf<double> dp(3ll * g.g.np);
+        vec_diagonal(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, dp.get(), op->ctx->stream);
+        faces_out(op, level, dp.get(), d, on_device);
+    });
+}
+
+dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double* x, int on_device) {
+    if (!op || !f || !x || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const GeoLevel& g = glv(op, level);
+        const long long n3 = 3ll * g.g.np;
+        DBuf<double> fp(n3), xp(n3), yp(n3);
+        faces_in(op, level, f, on_device, fp.get());
+        faces_in(op, level, x, on_device, xp.get());
+        double* pads[3] = {fp.get(), xp.get(), yp.get()};
+        cudaStream_t s = op->ctx->stream;
+        const double om = op->ol[level].omega;
+        float* u = reinterpret_cast<float*>(op->band_u.get());
+        auto run = [&](auto** p) {
+            using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
+            using TC = std::conditional_t<std::is_same<T, double>::value, double, float>;
+            const VecOp<T, TC> o = vop<T, TC>(op, level);
+            vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
+            for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, p[0], p[2], u, om, s);
+        };
+        if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
+        else if (op->mg.precision == DM_PREC_F32)
+            with_mg_vectors<float>(op, level, 3, pads, [&](float** p) { run(p); });
+        else
+            with_mg_vectors<__nv_bfloat16>(op, level, 3, pads, [&](__nv_bfloat16** p) { run(p); });
+        faces_out(op, level, yp.get(), x, on_device);
+    });
+}
+
+dm_status dm_operator_restrict(dm_operator* op, int level, const double* r, double* fc, int on_device) {
+    if (!op || !r || !fc || level < 0 || level + 1 >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const GeoLevel& g = glv(op, level);
+        const GeoLevel& gc = glv(op, level + 1);
+        DBuf<double> rp(3ll * g.g.np), cp(3ll * gc.g.np);
+        faces_in(op, level, r, on_device, rp.get());
+        cudaStream_t s = op->ctx->stream;
+        if (op->mg.precision == DM_PREC_F64) {
+            face_restrict<double, double>(g.g, gc.g, gc.A.get(), rp.get(), cp.get(), s);
+        } else {
+            // the transfer weights are exact in any precision; run in the preconditioner's storage type
+            const long long nf = 3ll * g.g.np, nc = 3ll * gc.g.np;
+            if (op->mg.precision == DM_PREC_F32) {
+                DBuf<float> a(nf), b(nc);
+                convert<float, double>(nf, rp.get(), a.get(), s);
+                face_restrict<float, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), s);
+                convert<double, float>(nc, b.get(), cp.get(), s);
+                Sync::stream(s);
+            } else {
+                DBuf<__nv_bfloat16> a(nf), b(nc);
+                convert<__nv_bfloat16, double>(nf, rp.get(), a.get(), s);
+                face_restrict<__nv_bfloat16, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), s);
+                convert<double, __nv_bfloat16>(nc, b.get(), cp.get(), s);
+                Sync::stream(s);
+            }
+        }
+        faces_out(op, level + 1, cp.get(), fc, on_device);
+    });
+}
+
+dm_status dm_operator_prolong(dm_operator* op, int level, const double* ec, double* x, int on_device) {
+    if (!op || !ec || !x || level < 0 || level + 1 >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const GeoLevel& g = glv(op, level);
+        const GeoLevel& gc = glv(op, level + 1);
+        DBuf<double> cp(3ll * gc.g.np), xp(3ll * g.g.np);
+        faces_in(op, level + 1, ec, on_device, cp.get());
+        faces_in(op, level, x, on_device, xp.get());
+        cudaStream_t s = op->ctx->stream;
+        if (op->mg.precision == DM_PREC_F64) {
+            face_prolong_add<double, double>(g.g, gc.g, g.A.get(), cp.get(), xp.get(), s);
+        } else {
+            const long long nf = 3ll * g.g.np, nc = 3ll * gc.g.np;
+            if (op->mg.precision == DM_PREC_F32) {
+                DBuf<float> a(nc), b(nf);
+                convert<float, double>(nc, cp.get(), a.get(), s);
+                convert<float, double>(nf, xp.get(), b.get(), s);
+                face_prolong_add<float, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), s);
+                convert<double, float>(nf, b.get(), xp.get(), s);
+                Sync::stream(s);
+            } else {
+                DBuf<__nv_bfloat16> a(nc), b(nf);
+                convert<__nv_bfloat16, double>(nc, cp.get(), a.get(), s);
+                convert<__nv_bfloat16, double>(nf, xp.get(), b.get(), s);
+                face_prolong_add<__nv_bfloat16, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), s);
+                convert<double, __nv_bfloat16>(nf, b.get(), xp.get(), s);
+                Sync::stream(s);
+            }
+        }
+        faces_out(op, level, xp.get(), x, on_device);
+    });
+}
+
+dm_status dm_operator_vcycle(dm_operator* op, const double* f, double* e, int on_device) {
+    if (!op || !f || !e) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const long long n3 = 3ll * glv(op, 0).g.np;
+        DBuf<double> fp(n3), ep(n3);
+        faces_in(op, 0, f, on_device, fp.get());
+        precond_vec(op, fp.get(), ep.get());
+        faces_out(op, 0, ep.get(), e, on_device);
+    });
+}
+
+dm_status dm_operator_scalar_vcycle(dm_operator* op, const double* f, double* e, int on_device) {
+    if (!op || !f || !e) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const long long n1 = glv(op, 0).g.np;
+        DBuf<double> fp(n1), ep(n1);
+        cells_in(op, 0, f, on_device, fp.get());
+        precond_scal(op, fp.get(), ep.get());
+        cells_out(op, 0, ep.get(), e, on_device);
+    });
+}
+
+dm_status dm_operator_solve(dm_operator* op, const double* b, double* x, int on_device, double tol, int restart,
+                            int maxit, int* iters, double* relres) {
+    if (!op || !b || !x || restart < 1 || restart > 120 || maxit < 1) return DM_ERR_INVALID_ARG;
+    dm_status conv = DM_OK;
+    const dm_status st = guarded(op->ctx, [&] {
+        const long long n3 = 3ll * glv(op, 0).g.np;
+        DBuf<double> bp(n3), xp(n3);
+        faces_in(op, 0, b, on_device, bp.get());
+        double rr = 0.0;
+        const int it = solve_vec(op, bp.get(), xp.get(), tol, restart, maxit, &rr);
+        if (iters) *iters = it;
+        if (relres) *relres = rr;
+        if (rr > 10.0 * tol) conv = DM_ERR_NO_CONVERGENCE;
+        faces_out(op, 0, xp.get(), x, on_device);
+    });
+    return st != DM_OK ? st : conv;
+}
+
+dm_status dm_operator_project(dm_operator* op, const double* x, double* y, int on_device, double tol, int* iters) {
+    if (!op || !x || !y) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const long long n3 = 3ll * glv(op, 0).g.np;
+        DBuf<double> xp(n3), yp(n3);
+        faces_in(op, 0, x, on_device, xp.get());
+        const int it = project(op, xp.get(), yp.get(), tol);
+        if (iters) *iters = it;
+        faces_out(op, 0, yp.get(), y, on_device);
+    });
+}
+
+void dm_eig_params_default(dm_eig_params* p) {
+    if (!p) return;
+    p->sigma = 0.0;
+    p->nev = 4;
+    p->tol = 1e-10;
+    p->inner_tol = 1e-10;
+    p->proj_tol = 1e-12;
+    p->basis = 0;
+    p->max_restarts = 100;
+    p->inner_restart = 40;
+    p->inner_maxit = 400;
+    p->seed = 1301;
+    dm_mg_params_default(&p->mg);
+}
+
+}  // extern "C"
+
+namespace {
+
+// k^2, rho, delta, rq of the eigenvectors in the padded FP64 columns X (ld = 3 np)
+void certify_padded(dm_context* ctx, const GeoLevel& g0, int n, const double* X, double* k2_io, bool set_k2, double* rho,
+                    double* delta, double* rq) {
+    cudaStream_t s = ctx->stream;
+    const long long n3 = 3ll * g0.g.np;
+    DBuf<double> kb(n3), ab(n3), dv(g0.g.np);
+    const VecOp<double, double> o{g0.g, g0.A.get(), g0.L.get(), g0.invV.get(), nullptr, 0.0, 0};
+    const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+    for (int i = 0; i < n; ++i) {
+        const double* b = X + (size_t)i * n3;
+        vec_stencil<double, double>(o, ST_APPLY, b, nullptr, kb.get(), 0.0, s);
+        hadamard(n3, g0.A.get(), b, ab.get(), s);
+        double bkb = 0.0, bab = 0.0;
+        mdot(ctx->red, n3, 1, b, n3, kb.get(), nullptr, &bkb, s);
+        mdot(ctx->red, n3, 1, b, n3, ab.get(), nullptr, &bab, s);
+        const double r = bkb / bab;
+        if (rq) rq[i] = r;
+        const double k2 = set_k2 ? r : k2_io[i];
+        if (set_k2) k2_io[i] = r;
+        const double abn = norm2(ctx, n3, ab.get());
+        axpby(n3, -k2, ab.get(), 1.0, kb.get(), s);
+        const double rn = norm2(ctx, n3, kb.get());
+        if (rho) rho[i] = rn / (std::fabs(k2) * abn);
+        dm_div_a(g0.g, g0.A.get(), b, dv.get(), s);
+        const double dn = norm2(ctx, g0.g.np, dv.get());
+        if (delta) delta[i] = dn * h / abn;
+    }
+}
+
+__global__ void k_sign_fix(long long n, double* __restrict__ x, const double* __restrict__ sign) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        x[r] *= *sign;
+}
+// sign = +1 if the entry of largest magnitude is positive (first such entry on ties)
+__global__ void k_max_entry_sign(long long n, const double* __restrict__ x, double* __restrict__ sign) {
+    __shared__ double bv[1024];
+    __shared__ long long bi[1024];
+    double best = -1.0;
+    long long idx = 0;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+        const double a = fabs(x[r]);
+        if (a > best) { best = a; idx = r; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            if (bv[threadIdx.x + s] > bv[threadIdx.x] ||
+                (bv[threadIdx.x + s] == bv[threadIdx.x] && bi[threadIdx.x + s] < bi[threadIdx.x])) {
+                bv[threadIdx.x] = bv[threadIdx.x + s];
+                bi[threadIdx.x] = bi[threadIdx.x + s];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *sign = x[bi[0]] < 0.0 ? -1.0 : 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_params* prm, double* k2_out,
+                        double* b_out, int b_on_device, dm_eig_report* report) {
+    if (!ctx || !geom || !prm || !k2_out) return DM_ERR_INVALID_ARG;
+    dm_status conv = DM_OK;
+    const dm_status st = guarded(ctx, [&] {
+        DM_CUDA(cudaSetDevice(ctx->device));
+        cudaStream_t s = ctx->stream;
+        const long long launches0 = ctx->launches;
+        const dm_eig_params p = *prm;
+        DM_REQUIRE(p.nev >= 1 && p.nev <= 40, DM_ERR_INVALID_ARG, "nev must be in [1, 40]");
+        int m = p.basis > 0 ? p.basis : std::min(64, std::max(2 * p.nev + 10, 24));
+        DM_REQUIRE(m >= p.nev + 2 && m <= 64, DM_ERR_INVALID_ARG, "basis must be in [nev + 2, 64]");
+        const double t_setup0 = now_s();
+        dm_operator* op = nullptr;
+        const dm_status cs = dm_operator_create(ctx, geom, p.sigma, &p.mg, &op);
+        if (cs != DM_OK) throw Error(cs, std::string("operator setup: ") + ctx->err);
+        std::unique_ptr<dm_operator, void (*)(dm_operator*)> opg(op, dm_operator_destroy);
+        LaunchScope scope(ctx);
+        const double t_solve0 = now_s();
+        const GeoLevel& g0 = glv(op, 0);
+        const long long n = 3ll * g0.g.np;
+        const double* a = g0.A.get();
+        DBuf<double> Vb((size_t)(m + 1) * n), tmp((size_t)m * n), rhs(n), x(n);
+        double* V = Vb.get();
+        // start vector: seeded random on the open faces, projected, A-normalised
+        fill_random(n, p.seed, a, rhs.get(), s);
+        project(op, rhs.get(), V, p.proj_tol);
+        {
+            const double nv = norm2(ctx, n, V, a);
+            DM_REQUIRE(nv > 0.0, DM_ERR_GEOMETRY, "start vector vanished under the projection (no open faces?)");
+            scale_copy(n, 1.0 / nv, V, V, s);
+        }
+        std::vector<double> H((size_t)(m + 1) * m, 0.0);
+        auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+        int k = 0, restarts = 0, outer = 0, inner_total = 0, proj_total = 0, nconv = 0;
+        std::vector<double> theta, Y, est;
+        std::vector<int> order;
+        while (true) {
+            for (int j = k; j < m; ++j) {
+                double* vj = V + (size_t)j * n;
+                hadamard(n, a, vj, rhs.get(), s);           // A v_j
+                double rr = 0.0;
+                inner_total += solve_vec(op, rhs.get(), x.get(), p.inner_tol, p.inner_restart, p.inner_maxit, &rr);
+                double* w = V + (size_t)(j + 1) * n;
+                proj_total += project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
+                ++outer;
+                std::vector<double> h(j + 1);
+                for (int pass = 0; pass < 2; ++pass) {
+                    mdot(ctx->red, n, j + 1, V, n, w, a, h.data(), s);
+                    maxpy(ctx->red, n, j + 1, V, n, h.data(), w, s);
+                    for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
+                }
+                const double beta = norm2(ctx, n, w, a);
+                Hat(j + 1, j) = beta;
+                DM_REQUIRE(beta > 0.0, DM_ERR_NO_CONVERGENCE, "Krylov space exhausted");
+                scale_copy(n, 1.0 / beta, w, w, s);
+            }
+            // Rayleigh-Ritz on the symmetrised projected matrix
+            std::vector<double> Hs((size_t)m * m);
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) Hs[(size_t)i * m + j] = 0.5 * (Hat(i, j) + Hat(j, i));
+            jacobi_eig(m, Hs, theta, Y);
+            order.resize(m);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int x1, int x2) { return std::fabs(theta[x1]) > std::fabs(theta[x2]); });
+            const double beta_m = Hat(m, m - 1);
+            est.assign(m, 0.0);
+            nconv = 0;
+            for (int i = 0; i < m; ++i) est[i] = std::fabs(beta_m * Y[(size_t)(m - 1) * m + order[i]]);
+            while (nconv < p.nev && est[nconv] <= p.tol * std::fabs(theta[order[nconv]])) ++nconv;
+            if (nconv >= p.nev || restarts >= p.max_restarts) break;
+            // thick restart: keep the pk wanted Ritz vectors
+            const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
+            std::vector<double> Yk((size_t)m * pk);
+            for (int c = 0; c < pk; ++c)
+                for (int r = 0; r < m; ++r) Yk[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
+            DBuf<double> Yd((size_t)m * pk);
+            DM_CUDA(cudaMemcpyAsync(Yd.get(), Yk.data(), sizeof(double) * m * pk, cudaMemcpyHostToDevice, s));
+            vgemm(n, m, pk, V, n, Yd.get(), m, tmp.get(), n, s);
+            DM_CUDA(cudaMemcpyAsync(V, tmp.get(), sizeof(double) * pk * n, cudaMemcpyDeviceToDevice, s));
+            DM_CUDA(cudaMemcpyAsync(V + (size_t)pk * n, V + (size_t)m * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            std::fill(H.begin(), H.end(), 0.0);
+            for (int c = 0; c < pk; ++c) {
+                Hat(c, c) = theta[order[c]];
+                Hat(pk, c) = beta_m * Y[(size_t)(m - 1) * m + order[c]];
+            }
+            k = pk;
+            ++restarts;
+            Sync::stream(s);
+        }
+        // Ritz vectors of the wanted pairs, in the order of |theta|
+        const int nev = p.nev;
+        std::vector<double> Yw((size_t)m * nev);
+        for (int c = 0; c < nev; ++c)
+            for (int r = 0; r < m; ++r) Yw[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
+        DBuf<double> Yd((size_t)m * nev), sign(1);
+        DM_CUDA(cudaMemcpyAsync(Yd.get(), Yw.data(), sizeof(double) * m * nev, cudaMemcpyHostToDevice, s));
+        vgemm(n, m, nev, V, n, Yd.get(), m, tmp.get(), n, s);
+        std::vector<double> k2(nev), rho(nev), delta(nev), rq(nev);
+        for (int c = 0; c < nev; ++c) {
+            double* b = tmp.get() + (size_t)c * n;
+            const double nb = norm2(ctx, n, b, a);
+            scale_copy(n, 1.0 / nb, b, b, s);
+            launch("k_max_entry_sign", k_max_entry_sign, 1, 1024, 0, s, n, b, sign.get());
+            launch("k_sign_fix", k_sign_fix, (int)std::min<long long>((n + 255) / 256, 1216), 256, 0, s, n, b, sign.get());
+        }
+        certify_padded(ctx, g0, nev, tmp.get(), k2.data(), true, rho.data(), delta.data(), rq.data());
+        // ascending k^2
+        std::vector<int> asc(nev);
+        std::iota(asc.begin(), asc.end(), 0);
+        std::stable_sort(asc.begin(), asc.end(), [&](int x1, int x2) { return k2[x1] < k2[x2]; });
+        double rho_max = 0.0, delta_max = 0.0;
+        for (int c = 0; c < nev; ++c) {
+            k2_out[c] = k2[asc[c]];
+            rho_max = std::max(rho_max, rho[asc[c]]);
+            delta_max = std::max(delta_max, delta[asc[c]]);
+        }
+        if (b_out) {
+            const size_t nf = (size_t)natural_faces(g0.g);
+            for (int c = 0; c < nev; ++c) {
+                const double* src = tmp.get() + (size_t)asc[c] * n;
+                if (b_on_device) {
+                    unpack_faces(g0.g, src, b_out + c * nf, s);
+                } else {
+                    DBuf<double> t(nf, false);
+                    unpack_faces(g0.g, src, t.get(), s);
+                    stage_out(ctx, t.get(), b_out + c * nf, 0, nf);
+                }
+            }
+            Sync::stream(s);
+        }
+        Sync::stream(s);
+        if (nconv < nev) conv = DM_ERR_NO_CONVERGENCE;
+        if (report) {
+            report->n_converged = nconv;
+            report->outer_iters = outer;
+            report->restarts = restarts;
+            report->inner_iters = inner_total;
+            report->proj_iters = proj_total;
+            report->mg_levels = op->nlev;
+            report->mg_complexity = op->complexity;
+            report->rho_max = rho_max;
+            report->delta_max = delta_max;
+            report->setup_seconds = t_solve0 - t_setup0;
+            report->solve_seconds = now_s() - t_solve0;
+            report->kernel_launches = ctx->launches - launches0;
+        }
+    });
+    return st != DM_OK ? st : conv;
+}
+
+dm_status dm_certify(dm_context* ctx, const dm_geometry* geom, int n, const double* k2, const double* b, int on_device,
+                     double* rho, double* delta, double* rq) {
+    if (!ctx || !geom || !b || !k2 || n < 1) return DM_ERR_INVALID_ARG;
+    return guarded(ctx, [&] {
+        const GeoLevel& g0 = *geom->lv[0];
+        cudaStream_t s = ctx->stream;
+        const long long n3 = 3ll * g0.g.np;
+        const size_t nf = (size_t)natural_faces(g0.g);
+        DBuf<double> X((size_t)n * n3);
+        for (int i = 0; i < n; ++i) {
+            DBuf<double> tmpb;
+            const double* d = nullptr;
+            stage_in(ctx, b + i * nf, on_device, nf, tmpb, &d);
+            pack_faces(g0.g, d, X.get() + (size_t)i * n3, s);
+            Sync::stream(s);
+        }
+        std::vector<double> kk(k2, k2 + n);
+        certify_padded(ctx, g0, n, X.get(), kk.data(), false, rho, delta, rq);
+    });
+}
+
+}  // extern "C"

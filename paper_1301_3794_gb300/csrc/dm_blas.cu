@@ -1,0 +1,223 @@
+// Vector kernels of the Krylov solvers: (weighted) multi-dot products with a
+// deterministic two-pass reduction, multi-AXPY, basis recombination, copies,
+// precision conversion and a counter-based random fill.
+//
+// The weighted dot sum_r w_r u_r v_r with w = A (the face fractions) is the
+// inner product of Eq. bInner in which P_DM (Eq. proj) is an orthogonal
+// projection and the shift-inverted operator of Eq. fullMat is self-adjoint.
+#include "dm_common.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 8;          // columns per pass of the multi-dot
+constexpr int kMaxBlocks = 152 * 4;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial[b * ldp + c0 + c] = sum over this block's rows of w * V_c * x
+__global__ void k_mdot_partial(long long n, int m, const double* __restrict__ V, long long ld,
+                               const double* __restrict__ x, const double* __restrict__ w, double* __restrict__ partial,
+                               int ldp) {
+    __shared__ double red[kThreads / 32][kChunk];
+    for (int c0 = 0; c0 < m; c0 += kChunk) {
+        const int nc = min(kChunk, m - c0);
+        double acc[kChunk];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
+        for (long long r = blockIdx.x * (long long)kThreads + threadIdx.x; r < n; r += (long long)gridDim.x * kThreads) {
+            double xr = x[r];
+            if (w) xr *= w[r];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c)
+                if (c < nc) acc[c] += V[(c0 + c) * ld + r] * xr;
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            const double s = warp_sum(acc[c]);
+            if (lane == 0) red[wid][c] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            double s = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) s += red[k][threadIdx.x];
+            partial[(long long)blockIdx.x * ldp + c0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// result[c] = sum_b partial[b * ldp + c]  (one warp per column, fixed order)
+__global__ void k_mdot_final(int nb, int m, const double* __restrict__ partial, int ldp, double* __restrict__ result) {
+    const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= m) return;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += partial[(long long)b * ldp + c];
+    s = warp_sum(s);
+    if (lane == 0) result[c] = s;
+}
+
+__global__ void k_maxpy(long long n, int m, const double* __restrict__ V, long long ld, const double* __restrict__ h,
+                        double* __restrict__ x) {
+    __shared__ double hs[128];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < m; ++c) acc += hs[c] * V[c * ld + r];
+        x[r] -= acc;
+    }
+}
+
+__global__ void k_vgemm(long long n, int m, int p, const double* __restrict__ V, long long ld,
+                        const double* __restrict__ Y, int ldy, double* __restrict__ out, long long ldo) {
+    extern __shared__ double Ys[];
+    for (int t = threadIdx.x; t < m * p; t += blockDim.x) {
+        const int c = t % m, j = t / m;
+        Ys[t] = Y[c + (long long)ldy * j];
+    }
+    __syncthreads();
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        for (int j0 = 0; j0 < p; j0 += 8) {
+            double acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = 0.0;
+            for (int c = 0; c < m; ++c) {
+                const double v = V[c * ld + r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j0 + j < p) acc[j] += v * Ys[c + m * (j0 + j)];
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j0 + j < p) out[(j0 + j) * ldo + r] = acc[j];
+        }
+    }
+}
+
+__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        y[r] = a * x[r] + b * y[r];
+}
+__global__ void k_scale_copy(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        y[r] = a * x[r];
+}
+__global__ void k_hadamard(long long n, const double* __restrict__ a, const double* __restrict__ x,
+                           double* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        y[r] = a[r] * x[r];
+}
+template <typename TD, typename TS>
+__global__ void k_convert(long long n, const TS* __restrict__ x, TD* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        y[r] = to_store<TD>(to_c(x[r]));
+}
+template <typename TD>
+__global__ void k_convert_coeff(long long n, const double* __restrict__ x, TD* __restrict__ y) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        y[r] = (TD)x[r];
+}
+
+// splitmix64 finaliser (Steele, Lea & Flood 2014) as a counter-based generator
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__global__ void k_fill_random(long long n, unsigned long long seed, const double* __restrict__ mask,
+                              double* __restrict__ x) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long z = mix64(seed * 0x632be59bd9b4e019ull + (unsigned long long)r);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+        x[r] = (mask && !(mask[r] > 0.0)) ? 0.0 : u;
+    }
+}
+
+inline int blocks_for(long long n, int threads = kThreads) {
+    return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, kMaxBlocks));
+}
+
+}  // namespace
+
+void reducer_init(Reducer& r, int max_cols) {
+    r.cap_blocks = kMaxBlocks;
+    r.max_cols = max_cols;
+    DM_CUDA(cudaMalloc(&r.partial, sizeof(double) * (size_t)r.cap_blocks * max_cols));
+    DM_CUDA(cudaMalloc(&r.result, sizeof(double) * (size_t)max_cols));
+    DM_CUDA(cudaMallocHost(&r.host, sizeof(double) * (size_t)max_cols));
+}
+void reducer_free(Reducer& r) {
+    if (r.partial) cudaFree(r.partial);
+    if (r.result) cudaFree(r.result);
+    if (r.host) cudaFreeHost(r.host);
+    r = Reducer{};
+}
+
+void mdot(Reducer& red, long long n, int m, const double* V, long long ld, const double* x, const double* w,
+          double* host_out, cudaStream_t s) {
+    DM_REQUIRE(m >= 1 && m <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
+    const int nb = blocks_for(n);
+    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, n, m, V, ld, x, w, red.partial, red.max_cols);
+    launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
+}
+
+void maxpy(Reducer& red, long long n, int m, const double* V, long long ld, const double* h_host, double* x,
+           cudaStream_t s) {
+    DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
+    // stage h through pinned memory (the host array may be pageable)
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < m; ++c) red.host[c] = h_host[c];
+    DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+    launch("k_maxpy", k_maxpy, blocks_for(n), kThreads, 0, s, n, m, V, ld, red.result, x);
+}
+
+void vgemm(long long n, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
+           long long ldo, cudaStream_t s) {
+    const size_t sm = sizeof(double) * (size_t)m * p;
+    DM_REQUIRE(sm <= 48 * 1024, DM_ERR_INVALID_ARG, "vgemm: basis too large");
+    launch("k_vgemm", k_vgemm, blocks_for(n), kThreads, sm, s, n, m, p, V, ld, Y_dev, ldy, out, ldo);
+}
+
+void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
+    launch("k_axpby", k_axpby, blocks_for(n), kThreads, 0, s, n, a, x, b, y);
+}
+void scale_copy(long long n, double a, const double* x, double* y, cudaStream_t s) {
+    launch("k_scale_copy", k_scale_copy, blocks_for(n), kThreads, 0, s, n, a, x, y);
+}
+void hadamard(long long n, const double* a, const double* x, double* y, cudaStream_t s) {
+    launch("k_hadamard", k_hadamard, blocks_for(n), kThreads, 0, s, n, a, x, y);
+}
+template <typename TD, typename TS>
+void convert(long long n, const TS* x, TD* y, cudaStream_t s) {
+    launch("k_convert", k_convert<TD, TS>, blocks_for(n), kThreads, 0, s, n, x, y);
+}
+template <typename TD>
+void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s) {
+    launch("k_convert_coeff", k_convert_coeff<TD>, blocks_for(n), kThreads, 0, s, n, x, y);
+}
+void fill_random(long long n, unsigned long long seed, const double* mask, double* x, cudaStream_t s) {
+    launch("k_fill_random", k_fill_random, blocks_for(n), kThreads, 0, s, n, seed, mask, x);
+}
+void zero(void* p, size_t bytes, cudaStream_t s) { DM_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
+
+template void convert<float, double>(long long, const double*, float*, cudaStream_t);
+template void convert<double, float>(long long, const float*, double*, cudaStream_t);
+template void convert<__nv_bfloat16, double>(long long, const double*, __nv_bfloat16*, cudaStream_t);
+template void convert<double, __nv_bfloat16>(long long, const __nv_bfloat16*, double*, cudaStream_t);
+template void convert<double, double>(long long, const double*, double*, cudaStream_t);
+template void convert_coeff<float>(long long, const double*, float*, cudaStream_t);
+
+}  // namespace dm

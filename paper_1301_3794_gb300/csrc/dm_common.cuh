@@ -1,0 +1,292 @@
+// Internal declarations shared by the translation units of libdmeig.
+//
+// Device layout of one multigrid level ("padded node grid"): every face,
+// edge and cell array of the level is indexed by the lower node (i, j, k) of
+// its element, in a box with one ghost node on every side:
+//     p = off0 + i + sx * (j + sy * k),  i in [-1, nx+1], j in [-1, ny+1], ...
+// with sx = round_up(nx + 3, 4), sy = ny + 3, sz = nz + 3, np = sx*sy*sz.
+// A face vector is three such blocks [x | y | z] (3*np values); so is an edge
+// array.  Positions that are not faces of the grid (ghosts, y-faces at i = nx,
+// ...) carry zero coefficients and zero values forever, so every stencil reads
+// its +-1 neighbours without bounds checks and every vector operation may run
+// over the whole 3*np block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+#include <utility>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "dmeig.h"
+
+namespace dm {
+
+struct Error : public std::runtime_error {
+    dm_status code;
+    Error(dm_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define DM_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            throw ::dm::Error(e_ == cudaErrorMemoryAllocation ? DM_ERR_OOM : DM_ERR_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+#define DM_REQUIRE(cond, code, msg)                      \
+    do {                                                 \
+        if (!(cond)) throw ::dm::Error((code), (msg));   \
+    } while (0)
+
+// Geometry of one level's padded node grid.
+struct Grid3 {
+    int nx, ny, nz;        // cells
+    int sx, sy, sz;        // padded extents (with ghosts)
+    int sxy;               // sx * sy
+    int np;                // sx * sy * sz, multiple of 4
+    int off0;              // index of node (0, 0, 0)
+    double hx, hy, hz;     // spacing
+
+    __host__ __device__ int idx(int i, int j, int k) const { return off0 + i + sx * (j + sy * k); }
+};
+
+Grid3 make_grid(int nx, int ny, int nz, double hx, double hy, double hz);
+
+// Launch counter of the active context (kernels this library launched).
+extern thread_local long long* g_launch_counter;
+inline void count_launch(long long n = 1) {
+    if (g_launch_counter) *g_launch_counter += n;
+}
+void check_launch(const char* what);
+
+// Optional per-kernel timing: with tracing on, every launch is bracketed by a
+// pair of CUDA events recorded on the launching stream; elapsed times are
+// accumulated per kernel name when the events are resolved.
+struct Tracer {
+    bool on = false;
+    struct Stat {
+        std::string name;
+        long long launches = 0;
+        double ms = 0.0;
+    };
+    std::vector<Stat> stats;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> free_events;
+    std::vector<cudaEvent_t> all_events;
+    cudaEvent_t get_event();
+    int stat_index(const char* name);
+    void begin(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1);
+    void end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1);
+    void resolve();
+    void reset();
+    ~Tracer();
+};
+extern thread_local Tracer* g_tracer;
+
+// Launch a kernel on stream s, counting it and (with tracing on) timing it.
+template <typename... KArgs, typename... Args>
+inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args&&... args) {
+    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (t) t->begin(s, &e0, &e1);
+    kern<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    if (t) t->end(name, s, e0, e1);
+    count_launch();
+    check_launch(name);
+}
+
+// Owning device buffer.
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    explicit DBuf(size_t count, bool zero = true) { alloc(count, zero); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t count, bool zero = true) {
+        release();
+        n = count;
+        if (count) {
+            DM_CUDA(cudaMalloc(&p, count * sizeof(T)));
+            if (zero) DM_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+        }
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    T* get() const { return p; }
+};
+
+// ---------------------------------------------------------------------------
+// precision helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_c(double v);
+template <> __device__ __forceinline__ double from_c<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_c<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+template <typename T> __device__ __forceinline__ T from_cf(float v);
+template <> __device__ __forceinline__ double from_cf<double>(float v) { return v; }
+template <> __device__ __forceinline__ float from_cf<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_cf<__nv_bfloat16>(float v) { return __float2bfloat16(v); }
+// store a value computed in the compute type into storage type T
+template <typename T> __device__ __forceinline__ T to_store(double v) { return from_c<T>(v); }
+template <typename T> __device__ __forceinline__ T to_store(float v) { return from_cf<T>(v); }
+
+// ---------------------------------------------------------------------------
+// host-callable kernel wrappers (all issue on `s`)
+// ---------------------------------------------------------------------------
+
+// geometry (dm_geometry.cu)
+void geom_fractions(const Grid3& g, const double* phi_pad, double* L, double* A, double* V, cudaStream_t s);
+void geom_neglect_faces(const Grid3& g, double a_min, double* L, double* A, cudaStream_t s);
+void geom_coarsen(const Grid3& gf, const Grid3& gc, const double* Lf, const double* Af, const double* Vf,
+                  double* Lc, double* Ac, double* Vc, cudaStream_t s);
+void geom_inv_volume(const Grid3& g, const double* V, double* invV, cudaStream_t s);
+// returns number of band faces written to `band` (capacity 3*np); `cell_flag` scratch np ints
+int geom_band(const Grid3& g, const double* A, const double* V, int* cell_flag, int* band, int* d_count,
+              cudaStream_t s);
+int geom_open_faces(const Grid3& g, const double* A, int* list, int* d_count, cudaStream_t s);
+// number of entries > 0
+int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
+int geom_active_cells(const Grid3& g, const double* A, int* list, unsigned char* active, int* d_count,
+                      cudaStream_t s);
+// natural <-> padded layouts
+void pack_nodes(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
+void pack_faces(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
+void unpack_faces(const Grid3& g, const double* pad, double* nat, cudaStream_t s);
+void unpack_edges(const Grid3& g, const double* pad, double* nat, cudaStream_t s);
+void pack_cells(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
+void unpack_cells(const Grid3& g, const double* pad, double* nat, cudaStream_t s);
+long long natural_faces(const Grid3& g);
+long long natural_edges(const Grid3& g);
+long long natural_cells(const Grid3& g);
+
+// vector stencils (dm_stencil.cu); T = storage, TC = coefficient type
+template <typename T, typename TC>
+struct VecOp {
+    Grid3 g;
+    const TC* A;     // 3*np face fractions
+    const TC* L;     // 3*np edge fractions
+    const TC* invV;  // np inverse cell fractions (0 where V = 0)
+    const TC* invD;  // 3*np inverse diagonal of K - sigma A (0 on closed faces)
+    double sigma;
+    int level = 0;   // multigrid level (names the kernel in traces: fine vs coarse)
+};
+enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2 };
+// trace name of a stencil launch: "<kind>_<precision>_<mode>_<L0|Lc>"
+template <typename T> constexpr int prec_index() {
+    return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
+}
+const char* stencil_name(const char* kind, int prec, int mode, bool fine);
+// mode APPLY: y = (K - sigma A) x;  RESID: y = f - (K - sigma A) x;
+// JACOBI: y = x + omega invD (f - (K - sigma A) x)
+template <typename T, typename TC>
+void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s);
+template <typename T, typename TC>
+void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s);
+template <typename T, typename TC>
+void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
+                    cudaStream_t s);
+void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
+                  cudaStream_t s);
+void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
+                        const int* list, int n, double* M, cudaStream_t s);
+
+// scalar (cell) stencils: S = D A D^T
+template <typename T, typename TC>
+struct ScalOp {
+    Grid3 g;
+    const TC* A;                    // 3*np
+    const unsigned char* active;    // np
+    const TC* invD;                 // np
+    int level = 0;
+};
+template <typename T, typename TC>
+void scal_stencil(const ScalOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s);
+template <typename T, typename TC>
+void scal_jacobi_zero(const ScalOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s);
+void scal_diagonal(const Grid3& g, const double* A, const unsigned char* active, double* d, cudaStream_t s);
+void scal_dense_assemble(const Grid3& g, const double* A, const int* list, const unsigned char* pinned, int n,
+                         double* M, cudaStream_t s);
+// divergence s = D (A x) and gradient correction y = x - D^T phi (masked)
+void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, cudaStream_t s);
+void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, cudaStream_t s);
+
+// transfers (dm_transfer.cu)
+template <typename T, typename TC>
+void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, cudaStream_t s);
+template <typename T, typename TC>
+void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, cudaStream_t s);
+template <typename T>
+void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
+                   cudaStream_t s);
+template <typename T>
+void cell_prolong_add(const Grid3& gf, const Grid3& gc, const unsigned char* active_f, const T* ec, T* x,
+                      cudaStream_t s);
+
+// dense (dm_dense.cu)
+// in-place inverse of the n x n row-major FP64 matrix M (work: 2 n^2 + n doubles).
+// Returns false if a pivot fell below tiny * max|M|.
+bool dense_inverse(double* M, int n, double* work, int* d_flag, cudaStream_t s);
+template <typename T>
+void dense_coarse_solve(const double* Minv64, const float* Minv32, int n, const int* list, const unsigned char* zero_rows,
+                        const T* f, T* x, double* tmp_in, double* tmp_out, cudaStream_t s);
+// connected components of active coarsest cells: pinned[c] = 1 for the lowest
+// index of every component (list order = natural order)
+void cell_components_pin(const Grid3& g, const double* A, const int* list, int n, int* label,
+                         unsigned char* pinned, cudaStream_t s);
+
+// BLAS-1 style (dm_blas.cu); all FP64 unless templated
+struct Reducer {
+    double* partial = nullptr;   // device, cap_blocks * max_cols
+    double* result = nullptr;    // device, max_cols
+    double* host = nullptr;      // pinned host, max_cols
+    int cap_blocks = 0, max_cols = 0;
+};
+void reducer_init(Reducer& r, int max_cols);
+void reducer_free(Reducer& r);
+// out[c] = sum_r w[r] * V[c*ld + r] * x[r]   (w nullable = 1), c < m; result copied to host
+void mdot(Reducer& red, long long n, int m, const double* V, long long ld, const double* x, const double* w,
+          double* host_out, cudaStream_t s);
+// x -= sum_c h[c] V[c*ld + r]    (h host array, m <= max_cols)
+void maxpy(Reducer& red, long long n, int m, const double* V, long long ld, const double* h_host, double* x,
+           cudaStream_t s);
+// out_j = sum_c V[c*ld] * Y[c + ldy*j]  for j < p  (Y host, m x p column-major), out may not alias V
+void vgemm(long long n, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
+           long long ldo, cudaStream_t s);
+void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
+void scale_copy(long long n, double a, const double* x, double* y, cudaStream_t s);         // y = a x
+void hadamard(long long n, const double* a, const double* x, double* y, cudaStream_t s);    // y = a .* x
+template <typename TD, typename TS>
+void convert(long long n, const TS* x, TD* y, cudaStream_t s);
+template <typename TD>
+void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s);
+void fill_random(long long n, unsigned long long seed, const double* mask, double* x, cudaStream_t s);
+void zero(void* p, size_t bytes, cudaStream_t s);
+
+}  // namespace dm

@@ -1,0 +1,439 @@
+// Matrix-free Dey--Mittra operators on the padded node grid.
+//
+// Vector operator (Eq. discLaplDM):  y = (K - sigma A) b,
+//     K = C L C^T + A D^T V^-1 D A
+// with, per face, the Faraday loop of Eq. farInt weighted by the edge
+// fractions L, and the grad-div term built from the Dey--Mittra divergence
+// V^-1 D A of Eq. divBDM (Gauss's law on the uncovered cell volume, Eq.
+// divBInt).  The curl of b on an edge, (C^T b):
+//     x-edge: (b_y(k-1) - b_y(k))/dz + (b_z(k) - b_z(j-1))/dy
+//     y-edge: (b_x(k) - b_x(k-1))/dz + (b_z(i-1) - b_z(i))/dx
+//     z-edge: (b_x(j-1) - b_x(j))/dy + (b_y(i) - b_y(i-1))/dx
+// and of the edge field e on a face, (C e):
+//     x-face: (e_z(j+1) - e_z(j))/dy - (e_y(k+1) - e_y(k))/dz   (and cyclic).
+// The divergence psi = V^-1 sum_faces +-A b / h (Eq. divBInt) and the
+// gradient (D^T psi)_x(i) = (psi(i-1) - psi(i))/dx (Eq. gradPhi, sign of -grad).
+//
+// Scalar operator inside the projection (Eq. proj): S = D A D^T on cells.
+#include "dm_common.cuh"
+
+#include <set>
+
+namespace dm {
+
+namespace {
+
+constexpr int BX = 32, BY = 4, BZ = 2;
+const dim3 kBlock(BX, BY, BZ);
+inline dim3 node_grid(const Grid3& g, int extra = 1) {
+    return dim3((g.nx + extra + BX - 1) / BX, (g.ny + extra + BY - 1) / BY, (g.nz + extra + BZ - 1) / BZ);
+}
+
+// Field accessor over a padded 3-component vector in storage type T.
+template <typename T, typename C>
+struct VecAcc {
+    const T* __restrict__ x;
+    int np;
+    __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(x[c * np + p]); }
+};
+// Accessor of the unit vector e_q (packed index q = c*np + p); used to build
+// the coarsest matrix column by column from the same stencil.
+template <typename C>
+struct UnitAcc {
+    int q, np;
+    __device__ __forceinline__ C operator()(int c, int p) const { return (c * np + p == q) ? C(1) : C(0); }
+};
+
+template <typename C, typename TC>
+struct Coef {
+    const TC* __restrict__ A;
+    const TC* __restrict__ L;
+    const TC* __restrict__ invV;
+    int np;
+    __device__ __forceinline__ C a(int c, int p) const { return (C)A[c * np + p]; }
+    __device__ __forceinline__ C l(int c, int p) const { return (C)L[c * np + p]; }
+    __device__ __forceinline__ C iv(int p) const { return (C)invV[p]; }
+};
+
+// L-weighted curl of b on the edges of component 0/1/2 at node p
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C edge_x(const Coef<C, TC>& cf, const Acc& b, int p, int Y, int Z, C rdy, C rdz) {
+    return cf.l(0, p) * ((b(1, p - Z) - b(1, p)) * rdz + (b(2, p) - b(2, p - Y)) * rdy);
+}
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C edge_y(const Coef<C, TC>& cf, const Acc& b, int p, int X, int Z, C rdx, C rdz) {
+    return cf.l(1, p) * ((b(0, p) - b(0, p - Z)) * rdz + (b(2, p - X) - b(2, p)) * rdx);
+}
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C edge_z(const Coef<C, TC>& cf, const Acc& b, int p, int X, int Y, C rdx, C rdy) {
+    return cf.l(2, p) * ((b(0, p - Y) - b(0, p)) * rdy + (b(1, p) - b(1, p - X)) * rdx);
+}
+// Dey--Mittra divergence of cell p: V^-1 (sum of outward A b / h)
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C cell_psi(const Coef<C, TC>& cf, const Acc& b, int p, int X, int Y, int Z, C rdx, C rdy,
+                                      C rdz) {
+    const C fx = cf.a(0, p + X) * b(0, p + X) - cf.a(0, p) * b(0, p);
+    const C fy = cf.a(1, p + Y) * b(1, p + Y) - cf.a(1, p) * b(1, p);
+    const C fz = cf.a(2, p + Z) * b(2, p + Z) - cf.a(2, p) * b(2, p);
+    return cf.iv(p) * (fx * rdx + fy * rdy + fz * rdz);
+}
+
+// (K - sigma A) b at the three faces of node p
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ void node_K(const Coef<C, TC>& cf, const Acc& b, int p, int X, int Y, int Z, C rdx, C rdy,
+                                       C rdz, C sigma, C out[3]) {
+    const C ex0 = edge_x(cf, b, p, Y, Z, rdy, rdz);
+    const C exZ = edge_x(cf, b, p + Z, Y, Z, rdy, rdz);
+    const C exY = edge_x(cf, b, p + Y, Y, Z, rdy, rdz);
+    const C ey0 = edge_y(cf, b, p, X, Z, rdx, rdz);
+    const C eyZ = edge_y(cf, b, p + Z, X, Z, rdx, rdz);
+    const C eyX = edge_y(cf, b, p + X, X, Z, rdx, rdz);
+    const C ez0 = edge_z(cf, b, p, X, Y, rdx, rdy);
+    const C ezY = edge_z(cf, b, p + Y, X, Y, rdx, rdy);
+    const C ezX = edge_z(cf, b, p + X, X, Y, rdx, rdy);
+    const C ps0 = cell_psi(cf, b, p, X, Y, Z, rdx, rdy, rdz);
+    const C psX = cell_psi(cf, b, p - X, X, Y, Z, rdx, rdy, rdz);
+    const C psY = cell_psi(cf, b, p - Y, X, Y, Z, rdx, rdy, rdz);
+    const C psZ = cell_psi(cf, b, p - Z, X, Y, Z, rdx, rdy, rdz);
+    const C ax = cf.a(0, p), ay = cf.a(1, p), az = cf.a(2, p);
+    const C yx = (ezY - ez0) * rdy - (eyZ - ey0) * rdz + ax * ((psX - ps0) * rdx - sigma * b(0, p));
+    const C yy = (exZ - ex0) * rdz - (ezX - ez0) * rdx + ay * ((psY - ps0) * rdy - sigma * b(1, p));
+    const C yz = (eyX - ey0) * rdx - (exY - ex0) * rdy + az * ((psZ - ps0) * rdz - sigma * b(2, p));
+    out[0] = ax > C(0) ? yx : C(0);
+    out[1] = ay > C(0) ? yy : C(0);
+    out[2] = az > C(0) ? yz : C(0);
+}
+
+// (K - sigma A) b at one face (component c, node p)
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C face_K(const Coef<C, TC>& cf, const Acc& b, int c, int p, int X, int Y, int Z, C rdx,
+                                    C rdy, C rdz, C sigma) {
+    const C a = cf.a(c, p);
+    if (!(a > C(0))) return C(0);
+    const C ps0 = cell_psi(cf, b, p, X, Y, Z, rdx, rdy, rdz);
+    if (c == 0) {
+        const C ez0 = edge_z(cf, b, p, X, Y, rdx, rdy), ezY = edge_z(cf, b, p + Y, X, Y, rdx, rdy);
+        const C ey0 = edge_y(cf, b, p, X, Z, rdx, rdz), eyZ = edge_y(cf, b, p + Z, X, Z, rdx, rdz);
+        const C psm = cell_psi(cf, b, p - X, X, Y, Z, rdx, rdy, rdz);
+        return (ezY - ez0) * rdy - (eyZ - ey0) * rdz + a * ((psm - ps0) * rdx - sigma * b(0, p));
+    } else if (c == 1) {
+        const C ex0 = edge_x(cf, b, p, Y, Z, rdy, rdz), exZ = edge_x(cf, b, p + Z, Y, Z, rdy, rdz);
+        const C ez0 = edge_z(cf, b, p, X, Y, rdx, rdy), ezX = edge_z(cf, b, p + X, X, Y, rdx, rdy);
+        const C psm = cell_psi(cf, b, p - Y, X, Y, Z, rdx, rdy, rdz);
+        return (exZ - ex0) * rdz - (ezX - ez0) * rdx + a * ((psm - ps0) * rdy - sigma * b(1, p));
+    } else {
+        const C ey0 = edge_y(cf, b, p, X, Z, rdx, rdz), eyX = edge_y(cf, b, p + X, X, Z, rdx, rdz);
+        const C ex0 = edge_x(cf, b, p, Y, Z, rdy, rdz), exY = edge_x(cf, b, p + Y, Y, Z, rdy, rdz);
+        const C psm = cell_psi(cf, b, p - Z, X, Y, Z, rdx, rdy, rdz);
+        return (eyX - ey0) * rdx - (exY - ex0) * rdy + a * ((psm - ps0) * rdz - sigma * b(2, p));
+    }
+}
+
+template <typename T, typename TC, int MODE>
+__global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
+                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
+                              const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y, double omega_d) {
+    using C = typename Compute<T>::type;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int N = g.np;
+    Coef<C, TC> cf{A, L, invV, N};
+    VecAcc<T, C> b{x, N};
+    C out[3];
+    node_K(cf, b, p, 1, g.sx, g.sxy, C(1.0 / g.hx), C(1.0 / g.hy), C(1.0 / g.hz), C(sigma_d), out);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int q = c * N + p;
+        C v = out[c];
+        if (MODE == ST_RESID) {
+            v = (C)to_c(f[q]) - v;
+        } else if (MODE == ST_JACOBI) {
+            v = (C)to_c(x[q]) + C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - v);
+        }
+        y[q] = to_store<T>(v);
+    }
+}
+
+template <typename T, typename TC>
+__global__ void k_vec_jacobi_zero(long long n, const TC* __restrict__ invD, const T* __restrict__ f,
+                                  T* __restrict__ y, double omega_d) {
+    using C = typename Compute<T>::type;
+    const C om = C(omega_d);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        y[q] = to_store<T>(om * (C)invD[q] * (C)to_c(f[q]));
+}
+
+template <typename T, typename TC>
+__global__ void k_band_update(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
+                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
+                              const int* __restrict__ band, int nband, const T* __restrict__ x,
+                              const T* __restrict__ f, float* __restrict__ u_f, double* __restrict__ u_d,
+                              double omega_d) {
+    using C = typename Compute<T>::type;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nband) return;
+    const int q = band[t];
+    const int c = q / g.np, p = q - c * g.np;
+    Coef<C, TC> cf{A, L, invV, g.np};
+    VecAcc<T, C> b{x, g.np};
+    const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, C(1.0 / g.hx), C(1.0 / g.hy), C(1.0 / g.hz), C(sigma_d));
+    const C u = C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - kx);
+    if (u_d) u_d[t] = (double)u;
+    else u_f[t] = (float)u;
+}
+
+template <typename T>
+__global__ void k_band_apply(const int* __restrict__ band, int nband, const float* __restrict__ u_f,
+                             const double* __restrict__ u_d, T* __restrict__ x) {
+    using C = typename Compute<T>::type;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nband) return;
+    const int q = band[t];
+    const C u = u_d ? (C)u_d[t] : (C)u_f[t];
+    x[q] = to_store<T>((C)to_c(x[q]) + u);
+}
+
+// diagonal of K - sigma A (x-face; other components cyclic):
+//   (L_z(j) + L_z(j+1))/dy^2 + (L_y(k) + L_y(k+1))/dz^2 + A_x^2 (V^-1(i-1) + V^-1(i))/dx^2 - sigma A_x
+__global__ void k_vec_diag(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
+                           const double* __restrict__ invV, double sigma, double* __restrict__ d) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    const double rx2 = 1.0 / (g.hx * g.hx), ry2 = 1.0 / (g.hy * g.hy), rz2 = 1.0 / (g.hz * g.hz);
+    const double ax = A[p], ay = A[N + p], az = A[2 * N + p];
+    d[p] = ax > 0.0 ? (L[2 * N + p] + L[2 * N + p + Y]) * ry2 + (L[N + p] + L[N + p + Z]) * rz2 +
+                          ax * ax * (invV[p - X] + invV[p]) * rx2 - sigma * ax
+                    : 0.0;
+    d[N + p] = ay > 0.0 ? (L[p] + L[p + Z]) * rz2 + (L[2 * N + p] + L[2 * N + p + X]) * rx2 +
+                              ay * ay * (invV[p - Y] + invV[p]) * ry2 - sigma * ay
+                        : 0.0;
+    d[2 * N + p] = az > 0.0 ? (L[N + p] + L[N + p + X]) * rx2 + (L[p] + L[p + Y]) * ry2 +
+                                  az * az * (invV[p - Z] + invV[p]) * rz2 - sigma * az
+                            : 0.0;
+}
+
+// column `col` of the dense (K - sigma A) restricted to the listed faces
+__global__ void k_vec_dense(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
+                            const double* __restrict__ invV, double sigma, const int* __restrict__ list, int n,
+                            double* __restrict__ M) {
+    const int col = blockIdx.x;
+    Coef<double, double> cf{A, L, invV, g.np};
+    UnitAcc<double> b{list[col], g.np};
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int q = list[r];
+        const int c = q / g.np, p = q - c * g.np;
+        M[(long long)r * n + col] = face_K(cf, b, c, p, 1, g.sx, g.sxy, 1.0 / g.hx, 1.0 / g.hy, 1.0 / g.hz, sigma);
+    }
+}
+
+// ---- scalar Laplacian S = D A D^T on cells --------------------------------------
+template <typename C, typename TC, typename Acc>
+__device__ __forceinline__ C cell_S(const TC* __restrict__ A, const Acc& v, int p, int X, int Y, int Z, int N, C rx2,
+                                    C ry2, C rz2) {
+    const C v0 = v(p);
+    return ((C)A[p + X] * (v0 - v(p + X)) + (C)A[p] * (v0 - v(p - X))) * rx2 +
+           ((C)A[N + p + Y] * (v0 - v(p + Y)) + (C)A[N + p] * (v0 - v(p - Y))) * ry2 +
+           ((C)A[2 * N + p + Z] * (v0 - v(p + Z)) + (C)A[2 * N + p] * (v0 - v(p - Z))) * rz2;
+}
+template <typename T, typename C>
+struct CellAcc {
+    const T* __restrict__ x;
+    __device__ __forceinline__ C operator()(int p) const { return (C)to_c(x[p]); }
+};
+template <typename C>
+struct CellUnit {
+    int q;
+    __device__ __forceinline__ C operator()(int p) const { return p == q ? C(1) : C(0); }
+};
+
+template <typename T, typename TC, int MODE>
+__global__ void k_scal_stencil(Grid3 g, const TC* __restrict__ A, const unsigned char* __restrict__ active,
+                               const TC* __restrict__ invD, const T* __restrict__ x, const T* __restrict__ f,
+                               T* __restrict__ y, double omega_d) {
+    using C = typename Compute<T>::type;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int p = g.idx(i, j, k);
+    C v = C(0);
+    if (active[p]) {
+        CellAcc<T, C> acc{x};
+        const C sx = cell_S<C>(A, acc, p, 1, g.sx, g.sxy, g.np, C(1.0 / (g.hx * g.hx)), C(1.0 / (g.hy * g.hy)),
+                               C(1.0 / (g.hz * g.hz)));
+        if (MODE == ST_APPLY) v = sx;
+        else if (MODE == ST_RESID) v = (C)to_c(f[p]) - sx;
+        else v = (C)to_c(x[p]) + C(omega_d) * (C)invD[p] * ((C)to_c(f[p]) - sx);
+    }
+    y[p] = to_store<T>(v);
+}
+
+__global__ void k_scal_diag(Grid3 g, const double* __restrict__ A, const unsigned char* __restrict__ active,
+                            double* __restrict__ d) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    d[p] = active[p] ? (A[p] + A[p + X]) / (g.hx * g.hx) + (A[N + p] + A[N + p + Y]) / (g.hy * g.hy) +
+                           (A[2 * N + p] + A[2 * N + p + Z]) / (g.hz * g.hz)
+                     : 0.0;
+}
+
+__global__ void k_scal_dense(Grid3 g, const double* __restrict__ A, const int* __restrict__ list,
+                             const unsigned char* __restrict__ pinned, int n, double* __restrict__ M) {
+    const int col = blockIdx.x;
+    CellUnit<double> u{list[col]};
+    const double rx2 = 1.0 / (g.hx * g.hx), ry2 = 1.0 / (g.hy * g.hy), rz2 = 1.0 / (g.hz * g.hz);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double v;
+        if (pinned[r] || pinned[col]) v = (r == col) ? 1.0 : 0.0;
+        else v = cell_S<double>(A, u, list[r], 1, g.sx, g.sxy, g.np, rx2, ry2, rz2);
+        M[(long long)r * n + col] = v;
+    }
+}
+
+// s = D (A x) on cells (Eq. divBInt without the V^-1)
+__global__ void k_div_a(Grid3 g, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ s) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    s[p] = (A[p + X] * x[p + X] - A[p] * x[p]) / g.hx + (A[N + p + Y] * x[N + p + Y] - A[N + p] * x[N + p]) / g.hy +
+           (A[2 * N + p + Z] * x[2 * N + p + Z] - A[2 * N + p] * x[2 * N + p]) / g.hz;
+}
+
+// y = x - D^T phi on open faces, (D^T phi)_x(i) = (phi(i-1) - phi(i))/dx
+__global__ void k_sub_grad(Grid3 g, const double* __restrict__ A, const double* __restrict__ x,
+                           const double* __restrict__ phi, double* __restrict__ y) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    const double ph = phi[p];
+    y[p] = A[p] > 0.0 ? x[p] - (phi[p - X] - ph) / g.hx : 0.0;
+    y[N + p] = A[N + p] > 0.0 ? x[N + p] - (phi[p - Y] - ph) / g.hy : 0.0;
+    y[2 * N + p] = A[2 * N + p] > 0.0 ? x[2 * N + p] - (phi[p - Z] - ph) / g.hz : 0.0;
+}
+
+}  // namespace
+
+const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
+    // interned names: a node-based set keeps every c_str() pointer stable
+    static std::set<std::string>* names = new std::set<std::string>();
+    static const char* precs[3] = {"f64", "f32", "bf16"};
+    static const char* modes[3] = {"apply", "resid", "jacobi"};
+    const std::string n = std::string(kind) + "_" + precs[prec] + "_" + modes[mode] + (fine ? "_L0" : "_Lc");
+    return names->insert(n).first->c_str();
+}
+
+template <typename T, typename TC>
+void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
+    const Grid3& g = op.g;
+    if (mode == ST_APPLY)
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_vec_stencil<T, TC, ST_APPLY>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+    else if (mode == ST_RESID)
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_vec_stencil<T, TC, ST_RESID>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+    else
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+}
+
+template <typename T, typename TC>
+void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
+    const long long n = 3ll * op.g.np;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    launch("k_vec_jacobi_zero", k_vec_jacobi_zero<T, TC>, blocks, 256, 0, s, n, op.invD, f, y, omega);
+}
+
+template <typename T, typename TC>
+void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
+                    cudaStream_t s) {
+    if (nband <= 0) return;
+    const int blocks = (nband + 255) / 256;
+    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
+    float* uf = ud ? nullptr : u;
+    launch(stencil_name("band_update", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_update<T, TC>, blocks, 256, 0, s, op.g, op.A, op.L, op.invV, op.invD, op.sigma, band, nband, x, f, uf, ud, omega);
+    launch(stencil_name("band_apply", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_apply<T>, blocks, 256, 0, s, band, nband, uf, ud, x);
+}
+
+void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
+                  cudaStream_t s) {
+    launch("k_vec_diag", k_vec_diag, node_grid(g), kBlock, 0, s, g, A, L, invV, sigma, d);
+}
+
+void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
+                        const int* list, int n, double* M, cudaStream_t s) {
+    if (n <= 0) return;
+    launch("k_vec_dense", k_vec_dense, n, 128, 0, s, g, A, L, invV, sigma, list, n, M);
+}
+
+template <typename T, typename TC>
+void scal_stencil(const ScalOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
+    const Grid3& g = op.g;
+    if (mode == ST_APPLY)
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_scal_stencil<T, TC, ST_APPLY>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
+    else if (mode == ST_RESID)
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_scal_stencil<T, TC, ST_RESID>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
+    else
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_scal_stencil<T, TC, ST_JACOBI>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
+}
+
+template <typename T, typename TC>
+__global__ void k_scal_jacobi_zero(long long n, const TC* __restrict__ invD, const T* __restrict__ f,
+                                   T* __restrict__ y, double omega_d) {
+    using C = typename Compute<T>::type;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        y[q] = to_store<T>(C(omega_d) * (C)invD[q] * (C)to_c(f[q]));
+}
+
+template <typename T, typename TC>
+void scal_jacobi_zero(const ScalOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
+    const long long n = op.g.np;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    launch("k_scal_jacobi_zero", k_scal_jacobi_zero<T, TC>, blocks, 256, 0, s, n, op.invD, f, y, omega);
+}
+
+void scal_diagonal(const Grid3& g, const double* A, const unsigned char* active, double* d, cudaStream_t s) {
+    launch("k_scal_diag", k_scal_diag, node_grid(g, 0), kBlock, 0, s, g, A, active, d);
+}
+
+void scal_dense_assemble(const Grid3& g, const double* A, const int* list, const unsigned char* pinned, int n,
+                         double* M, cudaStream_t s) {
+    if (n <= 0) return;
+    launch("k_scal_dense", k_scal_dense, n, 128, 0, s, g, A, list, pinned, n, M);
+}
+
+void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, cudaStream_t s) {
+    launch("k_div_a", k_div_a, node_grid(g, 0), kBlock, 0, s, g, A, x, s_out);
+}
+
+void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, cudaStream_t s) {
+    launch("k_sub_grad", k_sub_grad, node_grid(g), kBlock, 0, s, g, A, x, phi, y);
+}
+
+// explicit instantiations: FP64 storage / FP64 coefficients, FP32 / FP32, BF16 / FP32
+#define DM_INST(T, TC)                                                                                          \
+    template void vec_stencil<T, TC>(const VecOp<T, TC>&, int, const T*, const T*, T*, double, cudaStream_t);  \
+    template void vec_jacobi_zero<T, TC>(const VecOp<T, TC>&, const T*, T*, double, cudaStream_t);            \
+    template void vec_band_sweep<T, TC>(const VecOp<T, TC>&, const int*, int, const T*, T*, float*, double,   \
+                                        cudaStream_t);                                                        \
+    template void scal_stencil<T, TC>(const ScalOp<T, TC>&, int, const T*, const T*, T*, double, cudaStream_t); \
+    template void scal_jacobi_zero<T, TC>(const ScalOp<T, TC>&, const T*, T*, double, cudaStream_t);
+DM_INST(double, double)
+DM_INST(float, float)
+DM_INST(__nv_bfloat16, float)
+#undef DM_INST
+
+}  // namespace dm

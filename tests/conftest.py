@@ -26,5 +26,14 @@ def dm():
     """The CUDA library binding (GPU tests only)."""
     if not gpu_available():
         pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1301_3794_gb300 as dm
     return dm
+
+
+@pytest.fixture(scope="session")
+def ctx(dm):
+    c = dm.Context(0)
+    yield c
+    c.close()

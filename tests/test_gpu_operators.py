@@ -1,0 +1,150 @@
+"""GPU parity of geometry, operator, smoother, transfers and V-cycles against
+the oracle (element by element, FP64 unless stated)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import geometry, multigrid as MG, operators
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "sphere16": lambda: W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0),
+    "sphere32": lambda: W.sphere_workload(32, offset_seed=W.SEED_BASE + 2, sigma=5.0),
+    "ellipsoid24": lambda: W.ellipsoid_workload(24, seed=W.SEED_BASE + 3, sigma=5.0),
+    "box12x10x8": lambda: W.box_workload(),
+    "ragged13x11x9": lambda: W.sphere_workload(13, offset_seed=5, sigma=6.0),
+    "slab40x8x12": lambda: W.Workload("slab", W.Grid(40, 8, 12, 0.05, 0.11, 0.09, (-1.0, -0.44, -0.54)),
+                                      W.ellipsoid_phi(W.Grid(40, 8, 12, 0.05, 0.11, 0.09, (-1.0, -0.44, -0.54)),
+                                                      (0.013, 0.02, -0.01), (0.93, 0.41, 0.5)), 5.0, 4, 0),
+}
+
+
+def _rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, dm, ctx):
+    w = CASES[request.param]()
+    geom = dm.Geometry.from_workload(ctx, w)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    op = dm.Operator(ctx, geom, w.sigma)
+    return w, geom, levels, op
+
+
+def test_level_count(case):
+    w, geom, levels, op = case
+    assert geom.num_levels >= op.num_levels == len(levels)
+
+
+def test_fractions_all_levels(case):
+    w, geom, levels, op = case
+    for l, lev in enumerate(levels):
+        L, A, V = geom.fractions(l)
+        fr = lev.fr
+        assert _rel(L, operators.edge_vector(fr)) < 1e-14
+        assert _rel(A, operators.face_vector(fr)) < 1e-14
+        assert _rel(V, fr["V"].ravel()) < 1e-14
+        # open/closed decisions and cut-cell flags are exact
+        assert np.array_equal(A > 0, operators.face_vector(fr) > 0)
+        assert np.array_equal((V > 0) & (V < 1), (fr["V"].ravel() > 0) & (fr["V"].ravel() < 1))
+
+
+def test_apply_all_levels(case):
+    w, geom, levels, op = case
+    rng = np.random.default_rng(3)
+    for l, lev in enumerate(levels):
+        x = rng.standard_normal(lev.mask.size) * lev.mask
+        y = op.apply(x, level=l)
+        assert _rel(y, lev.K @ x) < 1e-13, l
+
+
+def test_apply_device_pointers(case):
+    import torch
+    w, geom, levels, op = case
+    lev = levels[0]
+    x = np.random.default_rng(4).standard_normal(lev.mask.size) * lev.mask
+    y = op.apply(torch.from_numpy(x).cuda())
+    assert y.is_cuda
+    assert _rel(y.cpu().numpy(), lev.K @ x) < 1e-13
+
+
+def test_diagonal(case):
+    w, geom, levels, op = case
+    for l, lev in enumerate(levels):
+        assert _rel(op.diagonal(l), lev.K.diagonal() * lev.mask) < 1e-13
+
+
+def test_smooth_restrict_prolong(case):
+    w, geom, levels, op = case
+    rng = np.random.default_rng(5)
+    for l in range(len(levels) - 1):
+        lev = levels[l]
+        om = op.omega(l)
+        assert 0.3 < om < 1.5
+        f = rng.standard_normal(lev.mask.size) * lev.mask
+        x = rng.standard_normal(lev.mask.size) * lev.mask
+        got = op.smooth(f, x, level=l)
+        ref = MG.smooth(lev, f, x, om, 8)
+        assert _rel(got, ref) < 1e-12, l
+        r = rng.standard_normal(lev.mask.size) * lev.mask
+        assert _rel(op.restrict(r, level=l), MG.restrict(levels, l, r)) < 1e-13, l
+        ec = rng.standard_normal(levels[l + 1].mask.size) * levels[l + 1].mask
+        assert _rel(op.prolong(ec, x, level=l), MG.prolong_add(levels, l, x, ec)) < 1e-13, l
+
+
+def test_vcycle_fp64(case):
+    w, geom, levels, op = case
+    om = [op.omega(l) for l in range(len(levels))]
+    f = np.random.default_rng(6).standard_normal(levels[0].mask.size) * levels[0].mask
+    got = op.vcycle(f)
+    ref = MG.vcycle(levels, f, om, band_sweeps=8)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+
+
+def test_scalar_vcycle_fp64(case, dm, ctx):
+    w, geom, levels, op = case
+    sl = MG.build_scalar_hierarchy(w.grid, w.phi)
+    om = [op.omega(l, scalar=True) for l in range(len(sl))]
+    f = np.random.default_rng(7).standard_normal(sl[0].mask.size) * sl[0].mask
+    got = op.scalar_vcycle(f)
+    ref = MG.scalar_vcycle(sl, f, om)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 2e-5), ("bf16", 6e-2)])
+def test_vcycle_low_precision(prec, tol, dm, ctx):
+    w = CASES["sphere16"]()
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma, precision=prec)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    om = [op.omega(l) for l in range(len(levels))]
+    f = np.random.default_rng(8).standard_normal(levels[0].mask.size) * levels[0].mask
+    got = op.vcycle(f)
+    ref = MG.vcycle(levels, f, om, band_sweeps=8)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
+
+
+def test_solve_matches_direct(case):
+    import scipy.sparse.linalg as spla
+    w, geom, levels, op = case
+    lev = levels[0]
+    b = np.random.default_rng(9).standard_normal(lev.mask.size) * lev.mask
+    x, it, rr = op.solve(b, tol=1e-10)
+    res = np.linalg.norm(b - lev.K @ x) / np.linalg.norm(b)
+    assert res < 1e-9 and it <= 60, (res, it, rr)
+    o = lev.ops.open_idx
+    xd = np.zeros_like(b)
+    xd[o] = spla.spsolve(lev.ops.restrict(lev.K), b[o])
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def test_project_matches_oracle(case):
+    w, geom, levels, op = case
+    lev = levels[0]
+    x = np.random.default_rng(10).standard_normal(lev.mask.size) * lev.mask
+    y, it = op.project(x, tol=1e-12)
+    ref = lev.ops.project(x)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-9, it
+    assert np.linalg.norm(lev.ops.D @ (lev.ops.a * y)) < 1e-10 * np.linalg.norm(lev.ops.D @ (lev.ops.a * x))
