@@ -1,0 +1,112 @@
+"""Oracle: the learned smoother's 3-layer convolutional network (plain FP64 numpy).
+
+The network is this build's design for the learned smoother that sits inside
+flexible GMRES next to the V-cycle preconditioner of the inner solve (the paper
+itself has no learned part).  On the node grid of a level (shape (nz+1, ny+1,
+nx+1)), with channel-last arrays X[k, j, i, c]:
+
+    H1 = relu(conv(X, W1)),  H2 = relu(conv(H1, W2)),  Y = conv(H2, W3)
+
+conv is a 3x3x3 cross-correlation with zero padding and no bias:
+
+    conv(X, W)[k, j, i, o] = sum_{a, b, c in {0,1,2}} sum_q W[a, b, c, q, o] X[k+a-1, j+b-1, i+c-1, q]
+
+Input channels (7): the residual on the x, y, z faces of each node (the faces
+whose lower corner is the node), divided by its RMS over the open faces, then
+the face fractions A_x, A_y, A_z and the cell fraction V of the node's cell.
+Output channels (3): the predicted error on those faces, in units of
+(RMS of r) * h^2.  The training loss is the mean squared error over the open
+faces.  Without biases, relu networks are positively homogeneous, and the
+scaling above makes the prediction independent of the residual's magnitude.
+
+Pins (tests/test_oracle_learned.py): single-channel conv equals
+scipy.ndimage.correlate with zero padding (a library routine); a delta kernel
+shifts; the analytic gradients of every weight and of the input match central
+finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+OFFSETS = [(a, b, c) for a in range(3) for b in range(3) for c in range(3)]
+
+
+def conv(X, W):
+    """3x3x3 zero-padded cross-correlation. X: (nz, ny, nx, Cin), W: (3, 3, 3, Cin, Cout)."""
+    nz, ny, nx, _ = X.shape
+    P = np.pad(X, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    Y = np.zeros((nz, ny, nx, W.shape[4]))
+    for a, b, c in OFFSETS:
+        Y += P[a:a + nz, b:b + ny, c:c + nx, :] @ W[a, b, c]
+    return Y
+
+
+def conv_grad_input(dY, W):
+    """d/dX of sum(dY * conv(X, W)): correlation of dY with the flipped,
+    transposed kernel."""
+    nz, ny, nx, _ = dY.shape
+    P = np.pad(dY, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    dX = np.zeros((nz, ny, nx, W.shape[3]))
+    for a, b, c in OFFSETS:
+        # X[p + d] feeds Y[p] with W[d]; so dX[q] += dY[q - d] W[d]^T
+        dX += P[2 - a:2 - a + nz, 2 - b:2 - b + ny, 2 - c:2 - c + nx, :] @ W[a, b, c].T
+    return dX
+
+
+def conv_grad_weight(X, dY):
+    """d/dW of sum(dY * conv(X, W)): dW[a, b, c] = sum_p X[p + d]^T dY[p]."""
+    nz, ny, nx, cin = X.shape
+    P = np.pad(X, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    dW = np.zeros((3, 3, 3, cin, dY.shape[3]))
+    for a, b, c in OFFSETS:
+        Xs = P[a:a + nz, b:b + ny, c:c + nx, :].reshape(-1, cin)
+        dW[a, b, c] = Xs.T @ dY.reshape(-1, dY.shape[3])
+    return dW
+
+
+def forward(X, Ws):
+    W1, W2, W3 = Ws
+    Z1 = conv(X, W1)
+    H1 = np.maximum(Z1, 0.0)
+    Z2 = conv(H1, W2)
+    H2 = np.maximum(Z2, 0.0)
+    Y = conv(H2, W3)
+    return Y, (X, Z1, H1, Z2, H2)
+
+
+def loss_and_grads(X, E, M, Ws):
+    """Masked MSE 0.5 * sum(M (Y - E)^2) / sum(M) and its gradients."""
+    Y, (X0, Z1, H1, Z2, H2) = forward(X, Ws)
+    msum = max(float(M.sum()), 1.0)
+    R = M * (Y - E)
+    loss = 0.5 * float((R * (Y - E)).sum()) / msum
+    dY = R / msum
+    W1, W2, W3 = Ws
+    dW3 = conv_grad_weight(H2, dY)
+    dH2 = conv_grad_input(dY, W3) * (Z2 > 0)
+    dW2 = conv_grad_weight(H1, dH2)
+    dH1 = conv_grad_input(dH2, W2) * (Z1 > 0)
+    dW1 = conv_grad_weight(X0, dH1)
+    dX = conv_grad_input(dH1, W1)
+    return loss, (dW1, dW2, dW3), dX
+
+
+def init_weights(rng, cin=7, hidden=16, cout=3):
+    """He-normal initialisation (fan-in 27 * Cin)."""
+    def he(ci, co):
+        return rng.standard_normal((3, 3, 3, ci, co)) * np.sqrt(2.0 / (27 * ci))
+    return [he(cin, hidden), he(hidden, hidden), he(hidden, cout) * 0.1]
+
+
+def adam_step(Ws, Gs, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015), state = dict(t, m list, v list)."""
+    state["t"] += 1
+    t = state["t"]
+    out = []
+    for i, (W, G) in enumerate(zip(Ws, Gs)):
+        state["m"][i] = b1 * state["m"][i] + (1 - b1) * G
+        state["v"][i] = b2 * state["v"][i] + (1 - b2) * G * G
+        mh = state["m"][i] / (1 - b1 ** t)
+        vh = state["v"][i] / (1 - b2 ** t)
+        out.append(W - lr * mh / (np.sqrt(vh) + eps))
+    return out

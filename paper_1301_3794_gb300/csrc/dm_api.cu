@@ -8,6 +8,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -104,6 +105,10 @@ struct GeoLevel {
     int nband = 0;
     DBuf<unsigned char> active;
     int nopen = 0;
+    DBuf<int> tiles;     // active tiles (ascending)
+    int ntiles = 0;
+    Domain vdom() const { return Domain{g, tiles.get(), ntiles, 3}; }   // face vectors
+    Domain sdom() const { return Domain{g, tiles.get(), ntiles, 1}; }   // cell vectors
 };
 
 struct Sync {
@@ -254,6 +259,15 @@ struct dm_operator {
     DBuf<double> t0, t1, t2, t3, c0, c1;
     Fgmres vg, sg;
     double complexity = 1.0;
+    // V-cycles captured as CUDA graphs (level-0 work buffers as fixed input/output)
+    cudaGraphExec_t vexec = nullptr, sexec = nullptr;
+    long long vexec_kernels = 0, sexec_kernels = 0;
+    int vcalls = 0, scalls = 0;
+    bool graphs = true;
+    ~dm_operator() {
+        if (vexec) cudaGraphExecDestroy(vexec);
+        if (sexec) cudaGraphExecDestroy(sexec);
+    }
 };
 
 namespace {
@@ -281,12 +295,13 @@ template <typename T, typename TC>
 VecOp<T, TC> vop(const dm_operator* op, int l) {
     const GeoLevel& g = glv(op, l);
     return VecOp<T, TC>{g.g, Pick<T, TC>::A(g), Pick<T, TC>::L(g), Pick<T, TC>::iV(g), Pick<T, TC>::iD(op->ol[l]),
-                        op->sigma, l};
+                        op->sigma, l, g.tiles.get(), g.ntiles};
 }
 template <typename T, typename TC>
 ScalOp<T, TC> sop(const dm_operator* op, int l) {
     const GeoLevel& g = glv(op, l);
-    return ScalOp<T, TC>{g.g, Pick<T, TC>::A(g), g.active.get(), Pick<T, TC>::iDs(op->ol[l]), l};
+    return ScalOp<T, TC>{g.g, Pick<T, TC>::A(g), g.active.get(), Pick<T, TC>::iDs(op->ol[l]), l, g.tiles.get(),
+                         g.ntiles};
 }
 
 // ---- vector V-cycle: result in rbuf ------------------------------------------------
@@ -306,16 +321,17 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const double om = op->ol[l].omega;
     float* u = reinterpret_cast<float*>(op->band_u.get());
     vec_jacobi_zero(o, f, ebuf, om, s);
-    for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, f, ebuf, u, om, s);
+    vec_band_sweeps(o, g.band.get(), g.nband, f, ebuf, u, om, op->mg.band_sweeps, s);
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
     T* fc = reinterpret_cast<T*>(wc.f.get());
-    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, s);
+    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, gc.tiles.get(), gc.ntiles, s);
     vcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.e.get()), reinterpret_cast<T*>(wc.r.get()));
-    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, s);
+    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, g.tiles.get(),
+                            g.ntiles, s);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
-    for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, f, rbuf, u, om, s);
+    vec_band_sweeps(o, g.band.get(), g.nband, f, rbuf, u, om, op->mg.band_sweeps, s);
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -337,60 +353,116 @@ void svcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
     T* fc = reinterpret_cast<T*>(wc.sf.get());
-    cell_restrict<T>(g.g, gc.g, gc.active.get(), rbuf, fc, s);
+    cell_restrict<T>(g.g, gc.g, gc.active.get(), rbuf, fc, gc.tiles.get(), gc.ntiles, s);
     svcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.se.get()), reinterpret_cast<T*>(wc.sr.get()));
-    cell_prolong_add<T>(g.g, gc.g, g.active.get(), reinterpret_cast<const T*>(wc.sr.get()), ebuf, s);
+    cell_prolong_add<T>(g.g, gc.g, g.active.get(), reinterpret_cast<const T*>(wc.sr.get()), ebuf, g.tiles.get(),
+                        g.ntiles, s);
     scal_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
 }
 
-// preconditioner on FP64 fine-level vectors: z = M^-1 v
-void precond_vec(dm_operator* op, const double* v, double* z) {
+// Capture f(...) issued on the context stream into an executable graph.
+// Returns false (and leaves *out null) if the capture cannot be made, in which
+// case the caller keeps launching kernels directly.
+template <class F>
+bool capture_graph(dm_operator* op, F&& f, cudaGraphExec_t* out, long long* kernels) {
     cudaStream_t s = op->ctx->stream;
-    const long long n = 3ll * glv(op, 0).g.np;
+    cudaGraph_t graph = nullptr;
+    *out = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const long long before = g_launch_counter ? *g_launch_counter : 0;
+    bool ok = true;
+    try {
+        f();
+    } catch (...) {
+        ok = false;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (!ok || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return false;
+    }
+    *kernels = (g_launch_counter ? *g_launch_counter : 0) - before;
+    if (g_launch_counter) *g_launch_counter = before;   // captured, not executed
+    return true;
+}
+
+bool graphs_allowed(const dm_operator* op) {
+    return op->graphs && !(g_tracer && g_tracer->on);
+}
+
+// z = M^-1 v on FP64 fine-level vectors: v is converted into the level-0 f
+// buffer, the V-cycle runs (as a graph after its first direct run), and the
+// result in the level-0 r buffer is converted into z.
+template <typename T, typename TC>
+void precond_vec_T(dm_operator* op, const double* v, double* z) {
+    cudaStream_t s = op->ctx->stream;
+    const Domain D = glv(op, 0).vdom();
     WorkLevel& w0 = op->wk[0];
+    T* f = reinterpret_cast<T*>(w0.f.get());
+    T* e = reinterpret_cast<T*>(w0.e.get());
+    T* r = reinterpret_cast<T*>(w0.r.get());
+    convert<T, double>(D, v, f, s);
+    if (graphs_allowed(op) && op->vcalls > 0) {
+        if (!op->vexec && !capture_graph(op, [&] { vcycle<T, TC>(op, 0, f, e, r); }, &op->vexec, &op->vexec_kernels))
+            op->graphs = false;
+    }
+    if (graphs_allowed(op) && op->vexec) {
+        DM_CUDA(cudaGraphLaunch(op->vexec, s));
+        count_launch(op->vexec_kernels);
+    } else {
+        vcycle<T, TC>(op, 0, f, e, r);
+    }
+    ++op->vcalls;
+    convert<double, T>(D, r, z, s);
+}
+
+template <typename T, typename TC>
+void precond_scal_T(dm_operator* op, const double* v, double* z) {
+    cudaStream_t s = op->ctx->stream;
+    const Domain D = glv(op, 0).sdom();
+    WorkLevel& w0 = op->wk[0];
+    T* f = reinterpret_cast<T*>(w0.sf.get());
+    T* e = reinterpret_cast<T*>(w0.se.get());
+    T* r = reinterpret_cast<T*>(w0.sr.get());
+    convert<T, double>(D, v, f, s);
+    if (graphs_allowed(op) && op->scalls > 0) {
+        if (!op->sexec && !capture_graph(op, [&] { svcycle<T, TC>(op, 0, f, e, r); }, &op->sexec, &op->sexec_kernels))
+            op->graphs = false;
+    }
+    if (graphs_allowed(op) && op->sexec) {
+        DM_CUDA(cudaGraphLaunch(op->sexec, s));
+        count_launch(op->sexec_kernels);
+    } else {
+        svcycle<T, TC>(op, 0, f, e, r);
+    }
+    ++op->scalls;
+    convert<double, T>(D, r, z, s);
+}
+
+void precond_vec(dm_operator* op, const double* v, double* z) {
     switch (op->mg.precision) {
-        case DM_PREC_F64:
-            vcycle<double, double>(op, 0, v, reinterpret_cast<double*>(w0.e.get()), z);
-            break;
-        case DM_PREC_F32: {
-            float* f = reinterpret_cast<float*>(w0.f.get());
-            convert<float, double>(n, v, f, s);
-            vcycle<float, float>(op, 0, f, reinterpret_cast<float*>(w0.e.get()), reinterpret_cast<float*>(w0.r.get()));
-            convert<double, float>(n, reinterpret_cast<float*>(w0.r.get()), z, s);
-            break;
-        }
-        default: {
-            auto* f = reinterpret_cast<__nv_bfloat16*>(w0.f.get());
-            convert<__nv_bfloat16, double>(n, v, f, s);
-            vcycle<__nv_bfloat16, float>(op, 0, f, reinterpret_cast<__nv_bfloat16*>(w0.e.get()),
-                                         reinterpret_cast<__nv_bfloat16*>(w0.r.get()));
-            convert<double, __nv_bfloat16>(n, reinterpret_cast<__nv_bfloat16*>(w0.r.get()), z, s);
-        }
+        case DM_PREC_F64: precond_vec_T<double, double>(op, v, z); break;
+        case DM_PREC_F32: precond_vec_T<float, float>(op, v, z); break;
+        default: precond_vec_T<__nv_bfloat16, float>(op, v, z);
     }
 }
 
 void precond_scal(dm_operator* op, const double* v, double* z) {
-    cudaStream_t s = op->ctx->stream;
-    const long long n = glv(op, 0).g.np;
-    WorkLevel& w0 = op->wk[0];
     switch (op->mg.precision) {
-        case DM_PREC_F64:
-            svcycle<double, double>(op, 0, v, reinterpret_cast<double*>(w0.se.get()), z);
-            break;
-        case DM_PREC_F32: {
-            float* f = reinterpret_cast<float*>(w0.sf.get());
-            convert<float, double>(n, v, f, s);
-            svcycle<float, float>(op, 0, f, reinterpret_cast<float*>(w0.se.get()), reinterpret_cast<float*>(w0.sr.get()));
-            convert<double, float>(n, reinterpret_cast<float*>(w0.sr.get()), z, s);
-            break;
-        }
-        default: {
-            auto* f = reinterpret_cast<__nv_bfloat16*>(w0.sf.get());
-            convert<__nv_bfloat16, double>(n, v, f, s);
-            svcycle<__nv_bfloat16, float>(op, 0, f, reinterpret_cast<__nv_bfloat16*>(w0.se.get()),
-                                          reinterpret_cast<__nv_bfloat16*>(w0.sr.get()));
-            convert<double, __nv_bfloat16>(n, reinterpret_cast<__nv_bfloat16*>(w0.sr.get()), z, s);
-        }
+        case DM_PREC_F64: precond_scal_T<double, double>(op, v, z); break;
+        case DM_PREC_F32: precond_scal_T<float, float>(op, v, z); break;
+        default: precond_scal_T<__nv_bfloat16, float>(op, v, z);
     }
 }
 
@@ -401,24 +473,25 @@ void apply_scal64(dm_operator* op, int l, const double* x, double* y) {
     scal_stencil<double, double>(sop<double, double>(op, l), ST_APPLY, x, nullptr, y, 0.0, op->ctx->stream);
 }
 
-double norm2(dm_context* ctx, long long n, const double* x, const double* w = nullptr) {
+double norm2(dm_context* ctx, const Domain& D, const double* x, const double* w = nullptr) {
     double r = 0.0;
-    mdot(ctx->red, n, 1, x, n, x, w, &r, ctx->stream);
+    mdot(ctx->red, D, 1, x, D.len(), x, w, &r, ctx->stream);
     return std::sqrt(std::max(r, 0.0));
 }
 
 // Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt
 // applied twice.  x is overwritten.  Returns the iteration count.
 template <class Apply, class Prec>
-int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec prec, const double* b, double* x,
+int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Prec prec, const double* b, double* x,
            double tol, int maxit, double* relres) {
     cudaStream_t s = ctx->stream;
+    const long long n = D.len();
     ws.ensure(n, m);
     double* V = ws.V.get();
     double* Z = ws.Z.get();
     double* w = ws.w.get();
     zero(x, sizeof(double) * n, s);
-    const double bnorm = norm2(ctx, n, b);
+    const double bnorm = norm2(ctx, D, b);
     if (relres) *relres = 0.0;
     if (bnorm == 0.0) return 0;
     int total = 0;
@@ -428,16 +501,16 @@ int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec pr
     while (total < maxit) {
         // r = b - A x
         if (first) {
-            scale_copy(n, 1.0, b, V, s);
+            scale_copy(D, 1.0, b, V, s);
         } else {
             apply(x, w);
-            axpby(n, 1.0, b, -1.0, w, s);
-            scale_copy(n, 1.0, w, V, s);
+            axpby(D, 1.0, b, -1.0, w, s);
+            scale_copy(D, 1.0, w, V, s);
         }
-        const double beta = norm2(ctx, n, V);
+        const double beta = norm2(ctx, D, V);
         res = beta / bnorm;
         if (beta <= tol * bnorm) break;
-        scale_copy(n, 1.0 / beta, V, V, s);
+        scale_copy(D, 1.0 / beta, V, V, s);
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -447,13 +520,13 @@ int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec pr
             apply(Z + (size_t)j * n, w);
             std::vector<double> h(j + 1);
             for (int pass = 0; pass < 2; ++pass) {
-                mdot(ctx->red, n, j + 1, V, n, w, nullptr, h.data(), s);
-                maxpy(ctx->red, n, j + 1, V, n, h.data(), w, s);
+                mdot(ctx->red, D, j + 1, V, n, w, nullptr, h.data(), s);
+                maxpy(ctx->red, D, j + 1, V, n, h.data(), w, s);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
             }
-            const double hn = norm2(ctx, n, w);
+            const double hn = norm2(ctx, D, w);
             H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) scale_copy(n, 1.0 / hn, w, V + (size_t)(j + 1) * n, s);
+            if (hn > 0.0) scale_copy(D, 1.0 / hn, w, V + (size_t)(j + 1) * n, s);
             // Givens
             for (int i = 0; i < j; ++i) {
                 const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -482,13 +555,13 @@ int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec pr
         }
         std::vector<double> neg(jend + 1);
         for (int i = 0; i <= jend; ++i) neg[i] = -y[i];
-        maxpy(ctx->red, n, jend + 1, Z, n, neg.data(), x, s);
+        maxpy(ctx->red, D, jend + 1, Z, n, neg.data(), x, s);
         first = false;
         if (res <= tol) {
             // confirm with the true residual
             apply(x, w);
-            axpby(n, 1.0, b, -1.0, w, s);
-            const double tr = norm2(ctx, n, w) / bnorm;
+            axpby(D, 1.0, b, -1.0, w, s);
+            const double tr = norm2(ctx, D, w) / bnorm;
             res = tr;
             if (tr <= 10.0 * tol) break;
         }
@@ -498,7 +571,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, long long n, int m, Apply apply, Prec pr
 }
 
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
-    const long long n = 3ll * glv(op, 0).g.np;
+    const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
     auto prec = [op](const double* in, double* out) { precond_vec(op, in, out); };
     return fgmres(op->ctx, op->vg, n, restart, apply, prec, b, x, tol, maxit, relres);
@@ -508,47 +581,48 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
 int project(dm_operator* op, const double* x, double* y, double tol) {
     cudaStream_t s = op->ctx->stream;
     const GeoLevel& g0 = glv(op, 0);
-    const long long nc = g0.g.np;
+    const Domain nc = g0.sdom();
     double* sv = op->c0.get();
     double* phi = op->c1.get();
-    dm_div_a(g0.g, g0.A.get(), x, sv, s);
+    dm_div_a(g0.g, g0.A.get(), x, sv, g0.tiles.get(), g0.ntiles, s);
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
     auto prec = [op](const double* in, double* out) { precond_scal(op, in, out); };
     double rr = 0.0;
     const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr);
-    dm_sub_grad(g0.g, g0.A.get(), x, phi, y, s);
+    dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
     return it;
 }
 
 double power_lambda_max(dm_operator* op, int l, bool scalar) {
     cudaStream_t s = op->ctx->stream;
     const GeoLevel& g = glv(op, l);
-    const long long n = scalar ? g.g.np : 3ll * g.g.np;
+    const Domain D = scalar ? g.sdom() : g.vdom();
+    const long long n = D.len();
     DBuf<double> x(n), y(n);
     if (scalar) {
         // random start on the active cells (scaling by D^-1 zeroes the inactive ones)
         DBuf<double> tmp(n);
-        fill_random(n, 12345 + l, nullptr, tmp.get(), s);
-        hadamard(n, op->ol[l].invDs.get(), tmp.get(), x.get(), s);
+        fill_random(D, 12345 + l, nullptr, tmp.get(), s);
+        hadamard(D, op->ol[l].invDs.get(), tmp.get(), x.get(), s);
     } else {
-        fill_random(n, 12345 + l, g.A.get(), x.get(), s);
+        fill_random(D, 12345 + l, g.A.get(), x.get(), s);
     }
     double lam = 0.0;
-    double nx = norm2(op->ctx, n, x.get());
+    double nx = norm2(op->ctx, D, x.get());
     if (nx == 0.0) return 1.0;
-    scale_copy(n, 1.0 / nx, x.get(), x.get(), s);
+    scale_copy(D, 1.0 / nx, x.get(), x.get(), s);
     for (int it = 0; it < op->mg.power_iters; ++it) {
         if (scalar) {
             apply_scal64(op, l, x.get(), y.get());
-            hadamard(n, op->ol[l].invDs.get(), y.get(), y.get(), s);
+            hadamard(D, op->ol[l].invDs.get(), y.get(), y.get(), s);
         } else {
             apply_vec64(op, l, x.get(), y.get());
-            hadamard(n, op->ol[l].invD.get(), y.get(), y.get(), s);
+            hadamard(D, op->ol[l].invD.get(), y.get(), y.get(), s);
         }
-        const double ny = norm2(op->ctx, n, y.get());
+        const double ny = norm2(op->ctx, D, y.get());
         if (ny == 0.0) break;
         lam = ny;
-        scale_copy(n, 1.0 / ny, y.get(), x.get(), s);
+        scale_copy(D, 1.0 / ny, y.get(), x.get(), s);
     }
     return lam > 0.0 ? lam : 1.0;
 }
@@ -707,13 +781,24 @@ void stage_out(dm_context* ctx, const double* dev, double* dst, int on_device, s
     DM_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
+__global__ void k_mask_open(long long n, const double* __restrict__ A, double* __restrict__ x) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        if (!(A[r] > 0.0)) x[r] = 0.0;
+}
+
+// caller face vector -> padded level-l vector; entries on closed faces are
+// dropped (closed faces always hold 0)
 void faces_in(dm_operator* op, int l, const double* nat, int on_device, double* pad) {
-    const Grid3& g = glv(op, l).g;
+    const GeoLevel& gl = glv(op, l);
+    const Grid3& g = gl.g;
     DBuf<double> tmp;
     const double* d = nullptr;
     stage_in(op->ctx, nat, on_device, (size_t)natural_faces(g), tmp, &d);
     zero(pad, sizeof(double) * 3 * (size_t)g.np, op->ctx->stream);
     pack_faces(g, d, pad, op->ctx->stream);
+    const long long n3 = 3ll * g.np;
+    launch("k_mask_open", k_mask_open, (int)std::min<long long>((n3 + 255) / 256, 1216), 256, 0, op->ctx->stream, n3,
+           gl.A.get(), pad);
     Sync::stream(op->ctx->stream);
 }
 void faces_out(dm_operator* op, int l, const double* pad, double* nat, int on_device) {
@@ -754,16 +839,17 @@ void cells_out(dm_operator* op, int l, const double* pad, double* nat, int on_de
 template <typename T, class F>
 void with_mg_vectors(dm_operator* op, int l, int count, double* const* pads, F&& f) {
     cudaStream_t s = op->ctx->stream;
-    const long long n = 3ll * glv(op, l).g.np;
+    const Domain D = glv(op, l).vdom();
+    const long long n = D.len();
     std::vector<DBuf<T>> b(count);
     std::vector<T*> p(count);
     for (int i = 0; i < count; ++i) {
         b[i].alloc(n);
         p[i] = b[i].get();
-        convert<T, double>(n, pads[i], p[i], s);
+        convert<T, double>(D, pads[i], p[i], s);
     }
     f(p.data());
-    for (int i = 0; i < count; ++i) convert<double, T>(n, p[i], pads[i], s);
+    for (int i = 0; i < count; ++i) convert<double, T>(D, p[i], pads[i], s);
     Sync::stream(s);
 }
 
@@ -890,6 +976,12 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
             lv->nband = geom_band(lv->g, lv->A.get(), lv->V.get(), flag.get(), lv->band.get(), cnt.get(), s);
             lv->active.alloc(n1);
             geom_active_cells(lv->g, lv->A.get(), nullptr, lv->active.get(), cnt.get(), s);
+            {
+                const int nt = tiles_x(lv->g) * tiles_y(lv->g) * tiles_z(lv->g);
+                DBuf<int> tflags(nt);
+                lv->tiles.alloc(nt);
+                lv->ntiles = geom_tiles(lv->g, lv->A.get(), lv->active.get(), lv->tiles.get(), tflags.get(), cnt.get(), s);
+            }
             geom->lv.push_back(std::move(lv));
             if (!can_coarsen(cx, cy, cz, 4)) break;
             cx /= 2; cy /= 2; cz /= 2;
@@ -972,6 +1064,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 64, DM_ERR_INVALID_ARG, "band_sweeps out of range");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
+        const char* ng = std::getenv("DMEIG_NO_GRAPHS");
+        op->graphs = !(ng && ng[0] && ng[0] != '0');
         setup_operator(op.get());
     });
     if (st != DM_OK) return st;
@@ -996,6 +1090,9 @@ dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double o
     if (!op || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
     if (scalar) op->ol[level].omega_s = omega;
     else op->ol[level].omega = omega;
+    // captured V-cycles hold the old weights
+    if (op->vexec) { cudaGraphExecDestroy(op->vexec); op->vexec = nullptr; }
+    if (op->sexec) { cudaGraphExecDestroy(op->sexec); op->sexec = nullptr; }
     return DM_OK;
 }
 
@@ -1037,7 +1134,7 @@ dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double
             using TC = std::conditional_t<std::is_same<T, double>::value, double, float>;
             const VecOp<T, TC> o = vop<T, TC>(op, level);
             vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
-            for (int b = 0; b < op->mg.band_sweeps; ++b) vec_band_sweep(o, g.band.get(), g.nband, p[0], p[2], u, om, s);
+            vec_band_sweeps(o, g.band.get(), g.nband, p[0], p[2], u, om, op->mg.band_sweeps, s);
         };
         if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
         else if (op->mg.precision == DM_PREC_F32)
@@ -1057,21 +1154,22 @@ dm_status dm_operator_restrict(dm_operator* op, int level, const double* r, doub
         faces_in(op, level, r, on_device, rp.get());
         cudaStream_t s = op->ctx->stream;
         if (op->mg.precision == DM_PREC_F64) {
-            face_restrict<double, double>(g.g, gc.g, gc.A.get(), rp.get(), cp.get(), s);
+            face_restrict<double, double>(g.g, gc.g, gc.A.get(), rp.get(), cp.get(), gc.tiles.get(), gc.ntiles, s);
         } else {
             // the transfer weights are exact in any precision; run in the preconditioner's storage type
             const long long nf = 3ll * g.g.np, nc = 3ll * gc.g.np;
+            const Domain df = g.vdom(), dc = gc.vdom();
             if (op->mg.precision == DM_PREC_F32) {
                 DBuf<float> a(nf), b(nc);
-                convert<float, double>(nf, rp.get(), a.get(), s);
-                face_restrict<float, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), s);
-                convert<double, float>(nc, b.get(), cp.get(), s);
+                convert<float, double>(df, rp.get(), a.get(), s);
+                face_restrict<float, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), gc.tiles.get(), gc.ntiles, s);
+                convert<double, float>(dc, b.get(), cp.get(), s);
                 Sync::stream(s);
             } else {
                 DBuf<__nv_bfloat16> a(nf), b(nc);
-                convert<__nv_bfloat16, double>(nf, rp.get(), a.get(), s);
-                face_restrict<__nv_bfloat16, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), s);
-                convert<double, __nv_bfloat16>(nc, b.get(), cp.get(), s);
+                convert<__nv_bfloat16, double>(df, rp.get(), a.get(), s);
+                face_restrict<__nv_bfloat16, float>(g.g, gc.g, gc.A32.get(), a.get(), b.get(), gc.tiles.get(), gc.ntiles, s);
+                convert<double, __nv_bfloat16>(dc, b.get(), cp.get(), s);
                 Sync::stream(s);
             }
         }
@@ -1089,22 +1187,23 @@ dm_status dm_operator_prolong(dm_operator* op, int level, const double* ec, doub
         faces_in(op, level, x, on_device, xp.get());
         cudaStream_t s = op->ctx->stream;
         if (op->mg.precision == DM_PREC_F64) {
-            face_prolong_add<double, double>(g.g, gc.g, g.A.get(), cp.get(), xp.get(), s);
+            face_prolong_add<double, double>(g.g, gc.g, g.A.get(), cp.get(), xp.get(), g.tiles.get(), g.ntiles, s);
         } else {
             const long long nf = 3ll * g.g.np, nc = 3ll * gc.g.np;
+            const Domain df = g.vdom(), dc = gc.vdom();
             if (op->mg.precision == DM_PREC_F32) {
                 DBuf<float> a(nc), b(nf);
-                convert<float, double>(nc, cp.get(), a.get(), s);
-                convert<float, double>(nf, xp.get(), b.get(), s);
-                face_prolong_add<float, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), s);
-                convert<double, float>(nf, b.get(), xp.get(), s);
+                convert<float, double>(dc, cp.get(), a.get(), s);
+                convert<float, double>(df, xp.get(), b.get(), s);
+                face_prolong_add<float, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), g.tiles.get(), g.ntiles, s);
+                convert<double, float>(df, b.get(), xp.get(), s);
                 Sync::stream(s);
             } else {
                 DBuf<__nv_bfloat16> a(nc), b(nf);
-                convert<__nv_bfloat16, double>(nc, cp.get(), a.get(), s);
-                convert<__nv_bfloat16, double>(nf, xp.get(), b.get(), s);
-                face_prolong_add<__nv_bfloat16, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), s);
-                convert<double, __nv_bfloat16>(nf, b.get(), xp.get(), s);
+                convert<__nv_bfloat16, double>(dc, cp.get(), a.get(), s);
+                convert<__nv_bfloat16, double>(df, xp.get(), b.get(), s);
+                face_prolong_add<__nv_bfloat16, float>(g.g, gc.g, g.A32.get(), a.get(), b.get(), g.tiles.get(), g.ntiles, s);
+                convert<double, __nv_bfloat16>(df, b.get(), xp.get(), s);
                 Sync::stream(s);
             }
         }
@@ -1188,26 +1287,27 @@ void certify_padded(dm_context* ctx, const GeoLevel& g0, int n, const double* X,
                     double* delta, double* rq) {
     cudaStream_t s = ctx->stream;
     const long long n3 = 3ll * g0.g.np;
+    const Domain D = g0.vdom(), Dc = g0.sdom();
     DBuf<double> kb(n3), ab(n3), dv(g0.g.np);
     const VecOp<double, double> o{g0.g, g0.A.get(), g0.L.get(), g0.invV.get(), nullptr, 0.0, 0};
     const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
     for (int i = 0; i < n; ++i) {
         const double* b = X + (size_t)i * n3;
         vec_stencil<double, double>(o, ST_APPLY, b, nullptr, kb.get(), 0.0, s);
-        hadamard(n3, g0.A.get(), b, ab.get(), s);
+        hadamard(D, g0.A.get(), b, ab.get(), s);
         double bkb = 0.0, bab = 0.0;
-        mdot(ctx->red, n3, 1, b, n3, kb.get(), nullptr, &bkb, s);
-        mdot(ctx->red, n3, 1, b, n3, ab.get(), nullptr, &bab, s);
+        mdot(ctx->red, D, 1, b, n3, kb.get(), nullptr, &bkb, s);
+        mdot(ctx->red, D, 1, b, n3, ab.get(), nullptr, &bab, s);
         const double r = bkb / bab;
         if (rq) rq[i] = r;
         const double k2 = set_k2 ? r : k2_io[i];
         if (set_k2) k2_io[i] = r;
-        const double abn = norm2(ctx, n3, ab.get());
-        axpby(n3, -k2, ab.get(), 1.0, kb.get(), s);
-        const double rn = norm2(ctx, n3, kb.get());
+        const double abn = norm2(ctx, D, ab.get());
+        axpby(D, -k2, ab.get(), 1.0, kb.get(), s);
+        const double rn = norm2(ctx, D, kb.get());
         if (rho) rho[i] = rn / (std::fabs(k2) * abn);
-        dm_div_a(g0.g, g0.A.get(), b, dv.get(), s);
-        const double dn = norm2(ctx, g0.g.np, dv.get());
+        dm_div_a(g0.g, g0.A.get(), b, dv.get(), g0.tiles.get(), g0.ntiles, s);
+        const double dn = norm2(ctx, Dc, dv.get());
         if (delta) delta[i] = dn * h / abn;
     }
 }
@@ -1266,17 +1366,18 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         LaunchScope scope(ctx);
         const double t_solve0 = now_s();
         const GeoLevel& g0 = glv(op, 0);
-        const long long n = 3ll * g0.g.np;
+        const Domain D = g0.vdom();
+        const long long n = D.len();
         const double* a = g0.A.get();
         DBuf<double> Vb((size_t)(m + 1) * n), tmp((size_t)m * n), rhs(n), x(n);
         double* V = Vb.get();
         // start vector: seeded random on the open faces, projected, A-normalised
-        fill_random(n, p.seed, a, rhs.get(), s);
+        fill_random(D, p.seed, a, rhs.get(), s);
         project(op, rhs.get(), V, p.proj_tol);
         {
-            const double nv = norm2(ctx, n, V, a);
+            const double nv = norm2(ctx, D, V, a);
             DM_REQUIRE(nv > 0.0, DM_ERR_GEOMETRY, "start vector vanished under the projection (no open faces?)");
-            scale_copy(n, 1.0 / nv, V, V, s);
+            scale_copy(D, 1.0 / nv, V, V, s);
         }
         std::vector<double> H((size_t)(m + 1) * m, 0.0);
         auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
@@ -1286,7 +1387,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         while (true) {
             for (int j = k; j < m; ++j) {
                 double* vj = V + (size_t)j * n;
-                hadamard(n, a, vj, rhs.get(), s);           // A v_j
+                hadamard(D, a, vj, rhs.get(), s);           // A v_j
                 double rr = 0.0;
                 inner_total += solve_vec(op, rhs.get(), x.get(), p.inner_tol, p.inner_restart, p.inner_maxit, &rr);
                 double* w = V + (size_t)(j + 1) * n;
@@ -1294,14 +1395,14 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 ++outer;
                 std::vector<double> h(j + 1);
                 for (int pass = 0; pass < 2; ++pass) {
-                    mdot(ctx->red, n, j + 1, V, n, w, a, h.data(), s);
-                    maxpy(ctx->red, n, j + 1, V, n, h.data(), w, s);
+                    mdot(ctx->red, D, j + 1, V, n, w, a, h.data(), s);
+                    maxpy(ctx->red, D, j + 1, V, n, h.data(), w, s);
                     for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
                 }
-                const double beta = norm2(ctx, n, w, a);
+                const double beta = norm2(ctx, D, w, a);
                 Hat(j + 1, j) = beta;
                 DM_REQUIRE(beta > 0.0, DM_ERR_NO_CONVERGENCE, "Krylov space exhausted");
-                scale_copy(n, 1.0 / beta, w, w, s);
+                scale_copy(D, 1.0 / beta, w, w, s);
             }
             // Rayleigh-Ritz on the symmetrised projected matrix
             std::vector<double> Hs((size_t)m * m);
@@ -1324,7 +1425,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 for (int r = 0; r < m; ++r) Yk[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
             DBuf<double> Yd((size_t)m * pk);
             DM_CUDA(cudaMemcpyAsync(Yd.get(), Yk.data(), sizeof(double) * m * pk, cudaMemcpyHostToDevice, s));
-            vgemm(n, m, pk, V, n, Yd.get(), m, tmp.get(), n, s);
+            vgemm(D, m, pk, V, n, Yd.get(), m, tmp.get(), n, s);
             DM_CUDA(cudaMemcpyAsync(V, tmp.get(), sizeof(double) * pk * n, cudaMemcpyDeviceToDevice, s));
             DM_CUDA(cudaMemcpyAsync(V + (size_t)pk * n, V + (size_t)m * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             std::fill(H.begin(), H.end(), 0.0);
@@ -1343,12 +1444,12 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             for (int r = 0; r < m; ++r) Yw[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
         DBuf<double> Yd((size_t)m * nev), sign(1);
         DM_CUDA(cudaMemcpyAsync(Yd.get(), Yw.data(), sizeof(double) * m * nev, cudaMemcpyHostToDevice, s));
-        vgemm(n, m, nev, V, n, Yd.get(), m, tmp.get(), n, s);
+        vgemm(D, m, nev, V, n, Yd.get(), m, tmp.get(), n, s);
         std::vector<double> k2(nev), rho(nev), delta(nev), rq(nev);
         for (int c = 0; c < nev; ++c) {
             double* b = tmp.get() + (size_t)c * n;
-            const double nb = norm2(ctx, n, b, a);
-            scale_copy(n, 1.0 / nb, b, b, s);
+            const double nb = norm2(ctx, D, b, a);
+            scale_copy(D, 1.0 / nb, b, b, s);
             launch("k_max_entry_sign", k_max_entry_sign, 1, 1024, 0, s, n, b, sign.get());
             launch("k_sign_fix", k_sign_fix, (int)std::min<long long>((n + 255) / 256, 1216), 256, 0, s, n, b, sign.get());
         }

@@ -5,13 +5,17 @@
 // The weighted dot sum_r w_r u_r v_r with w = A (the face fractions) is the
 // inner product of Eq. bInner in which P_DM (Eq. proj) is an orthogonal
 // projection and the shift-inverted operator of Eq. fullMat is self-adjoint.
+//
+// Every kernel runs over a Domain: either the list of active 32 x 4 x 2 node
+// tiles of a level (entries outside them are zero in every vector and are
+// neither read nor written), or, with no tile list, the whole array.
 #include "dm_common.cuh"
 
 namespace dm {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // = TX * TY * TZ: one tile per block pass
 constexpr int kChunk = 8;          // columns per pass of the multi-dot
 constexpr int kMaxBlocks = 152 * 4;
 
@@ -21,8 +25,8 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// partial[b * ldp + c0 + c] = sum over this block's rows of w * V_c * x
-__global__ void k_mdot_partial(long long n, int m, const double* __restrict__ V, long long ld,
+// partial[b * ldp + c0 + c] = sum over this block's entries of w * V_c * x
+__global__ void k_mdot_partial(Domain d, int m, const double* __restrict__ V, long long ld,
                                const double* __restrict__ x, const double* __restrict__ w, double* __restrict__ partial,
                                int ldp) {
     __shared__ double red[kThreads / 32][kChunk];
@@ -31,13 +35,13 @@ __global__ void k_mdot_partial(long long n, int m, const double* __restrict__ V,
         double acc[kChunk];
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
-        for (long long r = blockIdx.x * (long long)kThreads + threadIdx.x; r < n; r += (long long)gridDim.x * kThreads) {
+        for_each_entry(d, [&](long long r) {
             double xr = x[r];
             if (w) xr *= w[r];
 #pragma unroll
             for (int c = 0; c < kChunk; ++c)
                 if (c < nc) acc[c] += V[(c0 + c) * ld + r] * xr;
-        }
+        });
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
@@ -65,19 +69,19 @@ __global__ void k_mdot_final(int nb, int m, const double* __restrict__ partial, 
     if (lane == 0) result[c] = s;
 }
 
-__global__ void k_maxpy(long long n, int m, const double* __restrict__ V, long long ld, const double* __restrict__ h,
+__global__ void k_maxpy(Domain d, int m, const double* __restrict__ V, long long ld, const double* __restrict__ h,
                         double* __restrict__ x) {
     __shared__ double hs[128];
     for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = h[c];
     __syncthreads();
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    for_each_entry(d, [&](long long r) {
         double acc = 0.0;
         for (int c = 0; c < m; ++c) acc += hs[c] * V[c * ld + r];
         x[r] -= acc;
-    }
+    });
 }
 
-__global__ void k_vgemm(long long n, int m, int p, const double* __restrict__ V, long long ld,
+__global__ void k_vgemm(Domain d, int m, int p, const double* __restrict__ V, long long ld,
                         const double* __restrict__ Y, int ldy, double* __restrict__ out, long long ldo) {
     extern __shared__ double Ys[];
     for (int t = threadIdx.x; t < m * p; t += blockDim.x) {
@@ -85,7 +89,7 @@ __global__ void k_vgemm(long long n, int m, int p, const double* __restrict__ V,
         Ys[t] = Y[c + (long long)ldy * j];
     }
     __syncthreads();
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    for_each_entry(d, [&](long long r) {
         for (int j0 = 0; j0 < p; j0 += 8) {
             double acc[8];
 #pragma unroll
@@ -100,26 +104,25 @@ __global__ void k_vgemm(long long n, int m, int p, const double* __restrict__ V,
             for (int j = 0; j < 8; ++j)
                 if (j0 + j < p) out[(j0 + j) * ldo + r] = acc[j];
         }
-    }
+    });
 }
 
-__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        y[r] = a * x[r] + b * y[r];
+__global__ void k_axpby(Domain d, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    for_each_entry(d, [&](long long r) { y[r] = a * x[r] + b * y[r]; });
 }
-__global__ void k_scale_copy(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        y[r] = a * x[r];
+__global__ void k_scale_copy(Domain d, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for_each_entry(d, [&](long long r) { y[r] = a * x[r]; });
 }
-__global__ void k_hadamard(long long n, const double* __restrict__ a, const double* __restrict__ x,
+__global__ void k_scale_inplace(Domain d, double a, double* __restrict__ y) {
+    for_each_entry(d, [&](long long r) { y[r] *= a; });
+}
+__global__ void k_hadamard(Domain d, const double* __restrict__ a, const double* __restrict__ x,
                            double* __restrict__ y) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        y[r] = a[r] * x[r];
+    for_each_entry(d, [&](long long r) { y[r] = a[r] * x[r]; });
 }
 template <typename TD, typename TS>
-__global__ void k_convert(long long n, const TS* __restrict__ x, TD* __restrict__ y) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
-        y[r] = to_store<TD>(to_c(x[r]));
+__global__ void k_convert(Domain d, const TS* __restrict__ x, TD* __restrict__ y) {
+    for_each_entry(d, [&](long long r) { y[r] = to_store<TD>(to_c(x[r])); });
 }
 template <typename TD>
 __global__ void k_convert_coeff(long long n, const double* __restrict__ x, TD* __restrict__ y) {
@@ -134,17 +137,18 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
 }
-__global__ void k_fill_random(long long n, unsigned long long seed, const double* __restrict__ mask,
+__global__ void k_fill_random(Domain d, unsigned long long seed, const double* __restrict__ mask,
                               double* __restrict__ x) {
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+    for_each_entry(d, [&](long long r) {
         const unsigned long long z = mix64(seed * 0x632be59bd9b4e019ull + (unsigned long long)r);
         const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
         x[r] = (mask && !(mask[r] > 0.0)) ? 0.0 : u;
-    }
+    });
 }
 
-inline int blocks_for(long long n, int threads = kThreads) {
-    return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, kMaxBlocks));
+inline int blocks_for(const Domain& d) {
+    const long long work = d.tiles ? (long long)d.ntiles : (d.len() + kThreads - 1) / kThreads;
+    return (int)std::max<long long>(1, std::min<long long>(work, kMaxBlocks));
 }
 
 }  // namespace
@@ -163,61 +167,63 @@ void reducer_free(Reducer& r) {
     r = Reducer{};
 }
 
-void mdot(Reducer& red, long long n, int m, const double* V, long long ld, const double* x, const double* w,
+void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
-    const int nb = blocks_for(n);
-    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, n, m, V, ld, x, w, red.partial, red.max_cols);
+    const int nb = blocks_for(d);
+    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
 }
 
-void maxpy(Reducer& red, long long n, int m, const double* V, long long ld, const double* h_host, double* x,
+void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* h_host, double* x,
            cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
     // stage h through pinned memory (the host array may be pageable)
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) red.host[c] = h_host[c];
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-    launch("k_maxpy", k_maxpy, blocks_for(n), kThreads, 0, s, n, m, V, ld, red.result, x);
+    launch("k_maxpy", k_maxpy, blocks_for(d), kThreads, 0, s, d, m, V, ld, red.result, x);
 }
 
-void vgemm(long long n, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
+void vgemm(const Domain& d, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
            long long ldo, cudaStream_t s) {
     const size_t sm = sizeof(double) * (size_t)m * p;
     DM_REQUIRE(sm <= 48 * 1024, DM_ERR_INVALID_ARG, "vgemm: basis too large");
-    launch("k_vgemm", k_vgemm, blocks_for(n), kThreads, sm, s, n, m, p, V, ld, Y_dev, ldy, out, ldo);
+    launch("k_vgemm", k_vgemm, blocks_for(d), kThreads, sm, s, d, m, p, V, ld, Y_dev, ldy, out, ldo);
 }
 
-void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
-    launch("k_axpby", k_axpby, blocks_for(n), kThreads, 0, s, n, a, x, b, y);
+void axpby(const Domain& d, double a, const double* x, double b, double* y, cudaStream_t s) {
+    launch("k_axpby", k_axpby, blocks_for(d), kThreads, 0, s, d, a, x, b, y);
 }
-void scale_copy(long long n, double a, const double* x, double* y, cudaStream_t s) {
-    launch("k_scale_copy", k_scale_copy, blocks_for(n), kThreads, 0, s, n, a, x, y);
+void scale_copy(const Domain& d, double a, const double* x, double* y, cudaStream_t s) {
+    if (x == y) launch("k_scale_inplace", k_scale_inplace, blocks_for(d), kThreads, 0, s, d, a, y);
+    else launch("k_scale_copy", k_scale_copy, blocks_for(d), kThreads, 0, s, d, a, x, y);
 }
-void hadamard(long long n, const double* a, const double* x, double* y, cudaStream_t s) {
-    launch("k_hadamard", k_hadamard, blocks_for(n), kThreads, 0, s, n, a, x, y);
+void hadamard(const Domain& d, const double* a, const double* x, double* y, cudaStream_t s) {
+    launch("k_hadamard", k_hadamard, blocks_for(d), kThreads, 0, s, d, a, x, y);
 }
 template <typename TD, typename TS>
-void convert(long long n, const TS* x, TD* y, cudaStream_t s) {
-    launch("k_convert", k_convert<TD, TS>, blocks_for(n), kThreads, 0, s, n, x, y);
+void convert(const Domain& d, const TS* x, TD* y, cudaStream_t s) {
+    launch("k_convert", k_convert<TD, TS>, blocks_for(d), kThreads, 0, s, d, x, y);
 }
 template <typename TD>
 void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s) {
-    launch("k_convert_coeff", k_convert_coeff<TD>, blocks_for(n), kThreads, 0, s, n, x, y);
+    const int b = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
+    launch("k_convert_coeff", k_convert_coeff<TD>, b, kThreads, 0, s, n, x, y);
 }
-void fill_random(long long n, unsigned long long seed, const double* mask, double* x, cudaStream_t s) {
-    launch("k_fill_random", k_fill_random, blocks_for(n), kThreads, 0, s, n, seed, mask, x);
+void fill_random(const Domain& d, unsigned long long seed, const double* mask, double* x, cudaStream_t s) {
+    launch("k_fill_random", k_fill_random, blocks_for(d), kThreads, 0, s, d, seed, mask, x);
 }
 void zero(void* p, size_t bytes, cudaStream_t s) { DM_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
 
-template void convert<float, double>(long long, const double*, float*, cudaStream_t);
-template void convert<double, float>(long long, const float*, double*, cudaStream_t);
-template void convert<__nv_bfloat16, double>(long long, const double*, __nv_bfloat16*, cudaStream_t);
-template void convert<double, __nv_bfloat16>(long long, const __nv_bfloat16*, double*, cudaStream_t);
-template void convert<double, double>(long long, const double*, double*, cudaStream_t);
+template void convert<float, double>(const Domain&, const double*, float*, cudaStream_t);
+template void convert<double, float>(const Domain&, const float*, double*, cudaStream_t);
+template void convert<__nv_bfloat16, double>(const Domain&, const double*, __nv_bfloat16*, cudaStream_t);
+template void convert<double, __nv_bfloat16>(const Domain&, const __nv_bfloat16*, double*, cudaStream_t);
+template void convert<double, double>(const Domain&, const double*, double*, cudaStream_t);
 template void convert_coeff<float>(long long, const double*, float*, cudaStream_t);
 
 }  // namespace dm

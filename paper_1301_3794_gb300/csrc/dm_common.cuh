@@ -60,6 +60,75 @@ struct Grid3 {
 
 Grid3 make_grid(int nx, int ny, int nz, double hx, double hy, double hz);
 
+// Active tiles: 32 x 4 x 2 blocks of node positions (i in [0, nx], ...) that
+// hold at least one open face or active cell of the level.  Every vector entry
+// outside the active tiles is zero for the life of the level, so kernels walk
+// only the tile list.  Tile t sits at (i0, j0, k0) = TX (t % nti), TY ((t / nti)
+// % ntj), TZ (t / (nti ntj)) with nti = ceil((nx + 1) / TX), ntj = ceil((ny + 1) / TY).
+constexpr int TX = 32, TY = 4, TZ = 2;
+__host__ __device__ inline int tiles_x(const Grid3& g) { return (g.nx + TX) / TX; }
+__host__ __device__ inline int tiles_y(const Grid3& g) { return (g.ny + TY) / TY; }
+__host__ __device__ inline int tiles_z(const Grid3& g) { return (g.nz + TZ) / TZ; }
+__host__ __device__ inline void tile_origin(const Grid3& g, int t, int& i0, int& j0, int& k0) {
+    const int nti = tiles_x(g), ntj = tiles_y(g);
+    i0 = (t % nti) * TX;
+    t /= nti;
+    j0 = (t % ntj) * TY;
+    k0 = (t / ntj) * TZ;
+}
+
+// The part of a level's padded arrays a vector kernel visits: the active tiles
+// (tiles != nullptr) or the whole array of ncomp * np entries.
+struct Domain {
+    Grid3 g{};
+    const int* tiles = nullptr;
+    int ntiles = 0;
+    int ncomp = 3;    // 3: face vector, 1: cell vector
+    __host__ __device__ long long len() const { return (long long)ncomp * g.np; }
+};
+
+// Iterate the entries of a domain owned by this thread: calls f(r) for every
+// array index r (all components).  Tile mode: block b handles tiles b, b+G, ...
+template <class F>
+__device__ __forceinline__ void for_each_entry(const Domain& d, F&& f) {
+    if (d.tiles) {
+        const int tx = threadIdx.x & (TX - 1), ty = (threadIdx.x / TX) & (TY - 1), tz = threadIdx.x / (TX * TY);
+        for (int tb = blockIdx.x; tb < d.ntiles; tb += gridDim.x) {
+            int i0, j0, k0;
+            tile_origin(d.g, d.tiles[tb], i0, j0, k0);
+            const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+            if (i > d.g.nx || j > d.g.ny || k > d.g.nz) continue;
+            const int p = d.g.idx(i, j, k);
+            for (int c = 0; c < d.ncomp; ++c) f((long long)c * d.g.np + p);
+        }
+    } else {
+        const long long n = d.len();
+        for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+            f(r);
+    }
+}
+
+
+// Node (i, j, k) of this thread in a (TX, TY, TZ) block: from the active tile
+// list when there is one, else from a dense 3D grid of blocks.
+__device__ __forceinline__ void block_node(const Grid3& g, const int* tiles, int& i, int& j, int& k) {
+    if (tiles) {
+        int i0, j0, k0;
+        tile_origin(g, tiles[blockIdx.x], i0, j0, k0);
+        i = i0 + threadIdx.x;
+        j = j0 + threadIdx.y;
+        k = k0 + threadIdx.z;
+    } else {
+        i = blockIdx.x * TX + threadIdx.x;
+        j = blockIdx.y * TY + threadIdx.y;
+        k = blockIdx.z * TZ + threadIdx.z;
+    }
+}
+inline dim3 tile_grid(const Grid3& g, const int* tiles, int ntiles, int extra) {
+    if (tiles) return dim3(std::max(ntiles, 1));
+    return dim3((g.nx + extra + TX - 1) / TX, (g.ny + extra + TY - 1) / TY, (g.nz + extra + TZ - 1) / TZ);
+}
+
 // Launch counter of the active context (kernels this library launched).
 extern thread_local long long* g_launch_counter;
 inline void count_launch(long long n = 1) {
@@ -173,6 +242,9 @@ int geom_band(const Grid3& g, const double* A, const double* V, int* cell_flag, 
 int geom_open_faces(const Grid3& g, const double* A, int* list, int* d_count, cudaStream_t s);
 // number of entries > 0
 int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
+// active tiles of a level in ascending order (tiles: capacity of all tiles); returns the count
+int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
+               cudaStream_t s);
 int geom_active_cells(const Grid3& g, const double* A, int* list, unsigned char* active, int* d_count,
                       cudaStream_t s);
 // natural <-> padded layouts
@@ -196,6 +268,8 @@ struct VecOp {
     const TC* invD;  // 3*np inverse diagonal of K - sigma A (0 on closed faces)
     double sigma;
     int level = 0;   // multigrid level (names the kernel in traces: fine vs coarse)
+    const int* tiles = nullptr;   // active tiles of the level (nullptr: whole grid)
+    int ntiles = 0;
 };
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2 };
 // trace name of a stencil launch: "<kind>_<precision>_<mode>_<L0|Lc>"
@@ -212,6 +286,10 @@ void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cud
 template <typename T, typename TC>
 void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
                     cudaStream_t s);
+// `sweeps` band sweeps in one cooperative launch (same result as calling vec_band_sweep `sweeps` times)
+template <typename T, typename TC>
+void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
+                     int sweeps, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
                   cudaStream_t s);
 void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
@@ -225,6 +303,8 @@ struct ScalOp {
     const unsigned char* active;    // np
     const TC* invD;                 // np
     int level = 0;
+    const int* tiles = nullptr;
+    int ntiles = 0;
 };
 template <typename T, typename TC>
 void scal_stencil(const ScalOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s);
@@ -234,20 +314,25 @@ void scal_diagonal(const Grid3& g, const double* A, const unsigned char* active,
 void scal_dense_assemble(const Grid3& g, const double* A, const int* list, const unsigned char* pinned, int n,
                          double* M, cudaStream_t s);
 // divergence s = D (A x) and gradient correction y = x - D^T phi (masked)
-void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, cudaStream_t s);
-void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, cudaStream_t s);
+void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, const int* tiles, int ntiles,
+              cudaStream_t s);
+void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, const int* tiles,
+                 int ntiles, cudaStream_t s);
 
 // transfers (dm_transfer.cu)
+// tiles_c / tiles_f: active tiles of the level written (nullptr: whole grid)
 template <typename T, typename TC>
-void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, cudaStream_t s);
+void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, const int* tiles_c,
+                   int ntiles_c, cudaStream_t s);
 template <typename T, typename TC>
-void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, cudaStream_t s);
+void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, const int* tiles_f,
+                      int ntiles_f, cudaStream_t s);
 template <typename T>
 void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
-                   cudaStream_t s);
+                   const int* tiles_c, int ntiles_c, cudaStream_t s);
 template <typename T>
 void cell_prolong_add(const Grid3& gf, const Grid3& gc, const unsigned char* active_f, const T* ec, T* x,
-                      cudaStream_t s);
+                      const int* tiles_f, int ntiles_f, cudaStream_t s);
 
 // dense (dm_dense.cu)
 // in-place inverse of the n x n row-major FP64 matrix M (work: 2 n^2 + n doubles).
@@ -270,23 +355,23 @@ struct Reducer {
 };
 void reducer_init(Reducer& r, int max_cols);
 void reducer_free(Reducer& r);
-// out[c] = sum_r w[r] * V[c*ld + r] * x[r]   (w nullable = 1), c < m; result copied to host
-void mdot(Reducer& red, long long n, int m, const double* V, long long ld, const double* x, const double* w,
+// out[c] = sum_r w[r] * V[c*ld + r] * x[r] over the domain (w nullable = 1), c < m; result copied to host
+void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r]    (h host array, m <= max_cols)
-void maxpy(Reducer& red, long long n, int m, const double* V, long long ld, const double* h_host, double* x,
+void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* h_host, double* x,
            cudaStream_t s);
-// out_j = sum_c V[c*ld] * Y[c + ldy*j]  for j < p  (Y host, m x p column-major), out may not alias V
-void vgemm(long long n, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
+// out_j = sum_c V_c * Y[c + ldy*j]  for j < p  (Y device, m x p column-major), out may not alias V
+void vgemm(const Domain& d, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
            long long ldo, cudaStream_t s);
-void axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
-void scale_copy(long long n, double a, const double* x, double* y, cudaStream_t s);         // y = a x
-void hadamard(long long n, const double* a, const double* x, double* y, cudaStream_t s);    // y = a .* x
+void axpby(const Domain& d, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
+void scale_copy(const Domain& d, double a, const double* x, double* y, cudaStream_t s);         // y = a x
+void hadamard(const Domain& d, const double* a, const double* x, double* y, cudaStream_t s);    // y = a .* x
 template <typename TD, typename TS>
-void convert(long long n, const TS* x, TD* y, cudaStream_t s);
+void convert(const Domain& d, const TS* x, TD* y, cudaStream_t s);
 template <typename TD>
 void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s);
-void fill_random(long long n, unsigned long long seed, const double* mask, double* x, cudaStream_t s);
+void fill_random(const Domain& d, unsigned long long seed, const double* mask, double* x, cudaStream_t s);
 void zero(void* p, size_t bytes, cudaStream_t s);
 
 }  // namespace dm

@@ -405,6 +405,52 @@ int count_positive(long long n, const double* a, int* d_count, cudaStream_t s) {
     return read_count(d_count, s);
 }
 
+// flags[t] = 1 if tile t holds an open face or an active cell
+__global__ void k_tile_flags(Grid3 g, const double* __restrict__ A, const unsigned char* __restrict__ active,
+                             int* __restrict__ flags) {
+    const int t = blockIdx.x;
+    int i0, j0, k0;
+    tile_origin(g, t, i0, j0, k0);
+    const int i = i0 + (threadIdx.x & (TX - 1)), j = j0 + (threadIdx.x / TX) % TY, k = k0 + threadIdx.x / (TX * TY);
+    bool any = false;
+    if (i <= g.nx && j <= g.ny && k <= g.nz) {
+        const int p = g.idx(i, j, k);
+        any = A[p] > 0.0 || A[g.np + p] > 0.0 || A[2 * g.np + p] > 0.0 || active[p] != 0;
+    }
+    const int v = __syncthreads_or(any);
+    if (threadIdx.x == 0) flags[t] = v ? 1 : 0;
+}
+
+// out = indices t with flags[t] != 0, ascending (one block of 1024 threads)
+__global__ void k_compact(const int* __restrict__ flags, int n, int* __restrict__ out, int* __restrict__ count) {
+    __shared__ int scan[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int b = min(n, tid * chunk), e = min(n, b + chunk);
+    int c = 0;
+    for (int t = b; t < e; ++t) c += flags[t] != 0;
+    scan[tid] = c;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = tid >= o ? scan[tid - o] : 0;
+        __syncthreads();
+        scan[tid] += v;
+        __syncthreads();
+    }
+    int w = scan[tid] - c;
+    for (int t = b; t < e; ++t)
+        if (flags[t]) out[w++] = t;
+    if (tid == 1023) *count = scan[1023];
+}
+
+int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
+               cudaStream_t s) {
+    const int nt = tiles_x(g) * tiles_y(g) * tiles_z(g);
+    launch("k_tile_flags", k_tile_flags, nt, TX * TY * TZ, 0, s, g, A, active, flags);
+    launch("k_compact", k_compact, 1, 1024, 0, s, flags, nt, tiles, d_count);
+    return read_count(d_count, s);
+}
+
 int geom_open_faces(const Grid3& g, const double* A, int* list, int* d_count, cudaStream_t s) {
     launch("k_open_faces", k_open_faces, 1, 1, 0, s, g, A, list, d_count);
     return read_count(d_count, s);

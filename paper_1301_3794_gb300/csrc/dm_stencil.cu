@@ -17,6 +17,7 @@
 // Scalar operator inside the projection (Eq. proj): S = D A D^T on cells.
 #include "dm_common.cuh"
 
+#include <cooperative_groups.h>
 #include <set>
 
 namespace dm {
@@ -35,6 +36,17 @@ struct VecAcc {
     const T* __restrict__ x;
     int np;
     __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(x[c * np + p]); }
+};
+// Same, for kernels that also write the vector they read (no __restrict__,
+// so loads are neither cached across grid barriers nor routed through the
+// read-only path).
+template <typename T, typename C>
+struct VecAccRW {
+    const T* x;
+    int np;
+    // ld.global.cg: cached in L2 only, so values other SMs wrote before a grid
+    // barrier are never read from a stale L1 line
+    __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(__ldcg(x + c * np + p)); }
 };
 // Accessor of the unit vector e_q (packed index q = c*np + p); used to build
 // the coarsest matrix column by column from the same stencil.
@@ -132,11 +144,11 @@ __device__ __forceinline__ C face_K(const Coef<C, TC>& cf, const Acc& b, int c, 
 template <typename T, typename TC, int MODE>
 __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
                               const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
-                              const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y, double omega_d) {
+                              const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y, double omega_d,
+                              const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+    int i, j, k;
+    block_node(g, tiles, i, j, k);
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int p = g.idx(i, j, k);
     const int N = g.np;
@@ -158,12 +170,11 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
 }
 
 template <typename T, typename TC>
-__global__ void k_vec_jacobi_zero(long long n, const TC* __restrict__ invD, const T* __restrict__ f,
-                                  T* __restrict__ y, double omega_d) {
+__global__ void k_jacobi_zero(Domain d, const TC* __restrict__ invD, const T* __restrict__ f, T* __restrict__ y,
+                              double omega_d) {
     using C = typename Compute<T>::type;
     const C om = C(omega_d);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        y[q] = to_store<T>(om * (C)invD[q] * (C)to_c(f[q]));
+    for_each_entry(d, [&](long long q) { y[q] = to_store<T>(om * (C)invD[q] * (C)to_c(f[q])); });
 }
 
 template <typename T, typename TC>
@@ -194,6 +205,42 @@ __global__ void k_band_apply(const int* __restrict__ band, int nband, const floa
     const int q = band[t];
     const C u = u_d ? (C)u_d[t] : (C)u_f[t];
     x[q] = to_store<T>((C)to_c(x[q]) + u);
+}
+
+// All band sweeps of one smoothing step in one cooperative launch: per sweep,
+// every thread computes the Jacobi updates u of its band faces from the current
+// x, the grid synchronises, the updates are added, the grid synchronises again.
+// Same arithmetic as k_band_update + k_band_apply per sweep.
+template <typename T, typename TC>
+__global__ void k_band_sweeps(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
+                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
+                              const int* __restrict__ band, int nband, const T* __restrict__ f, T* x,
+                              float* u_f, double* u_d, double omega_d, int sweeps) {
+    using C = typename Compute<T>::type;
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    Coef<C, TC> cf{A, L, invV, g.np};
+    VecAccRW<T, C> b{x, g.np};
+    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz), sig = C(sigma_d), om = C(omega_d);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int t = t0; t < nband; t += stride) {
+            const int q = band[t];
+            const int c = q / g.np, p = q - c * g.np;
+            const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sig);
+            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - kx);
+            if (u_d) u_d[t] = (double)u;
+            else u_f[t] = (float)u;
+        }
+        grid.sync();
+        for (int t = t0; t < nband; t += stride) {
+            const int q = band[t];
+            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
+            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
+        }
+        grid.sync();
+    }
 }
 
 // diagonal of K - sigma A (x-face; other components cyclic):
@@ -256,11 +303,10 @@ struct CellUnit {
 template <typename T, typename TC, int MODE>
 __global__ void k_scal_stencil(Grid3 g, const TC* __restrict__ A, const unsigned char* __restrict__ active,
                                const TC* __restrict__ invD, const T* __restrict__ x, const T* __restrict__ f,
-                               T* __restrict__ y, double omega_d) {
+                               T* __restrict__ y, double omega_d, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+    int i, j, k;
+    block_node(g, tiles, i, j, k);
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int p = g.idx(i, j, k);
     C v = C(0);
@@ -302,10 +348,10 @@ __global__ void k_scal_dense(Grid3 g, const double* __restrict__ A, const int* _
 }
 
 // s = D (A x) on cells (Eq. divBInt without the V^-1)
-__global__ void k_div_a(Grid3 g, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ s) {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+__global__ void k_div_a(Grid3 g, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ s,
+                        const int* __restrict__ tiles) {
+    int i, j, k;
+    block_node(g, tiles, i, j, k);
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int p = g.idx(i, j, k);
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
@@ -315,10 +361,9 @@ __global__ void k_div_a(Grid3 g, const double* __restrict__ A, const double* __r
 
 // y = x - D^T phi on open faces, (D^T phi)_x(i) = (phi(i-1) - phi(i))/dx
 __global__ void k_sub_grad(Grid3 g, const double* __restrict__ A, const double* __restrict__ x,
-                           const double* __restrict__ phi, double* __restrict__ y) {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+                           const double* __restrict__ phi, double* __restrict__ y, const int* __restrict__ tiles) {
+    int i, j, k;
+    block_node(g, tiles, i, j, k);
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int p = g.idx(i, j, k);
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
@@ -343,18 +388,19 @@ template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
     if (mode == ST_APPLY)
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_vec_stencil<T, TC, ST_APPLY>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_vec_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_vec_stencil<T, TC, ST_RESID>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_vec_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, node_grid(g), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega);
+        launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
 }
 
 template <typename T, typename TC>
 void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
-    const long long n = 3ll * op.g.np;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-    launch("k_vec_jacobi_zero", k_vec_jacobi_zero<T, TC>, blocks, 256, 0, s, n, op.invD, f, y, omega);
+    const Domain d{op.g, op.tiles, op.ntiles, 3};
+    const int blocks = op.tiles ? std::max(op.ntiles, 1) : (int)std::min<long long>((d.len() + 255) / 256, 152 * 16);
+    launch(stencil_name("jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0), k_jacobi_zero<T, TC>, blocks, 256,
+           0, s, d, op.invD, f, y, omega);
 }
 
 template <typename T, typename TC>
@@ -366,6 +412,41 @@ void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T*
     float* uf = ud ? nullptr : u;
     launch(stencil_name("band_update", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_update<T, TC>, blocks, 256, 0, s, op.g, op.A, op.L, op.invV, op.invD, op.sigma, band, nband, x, f, uf, ud, omega);
     launch(stencil_name("band_apply", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_apply<T>, blocks, 256, 0, s, band, nband, uf, ud, x);
+}
+
+template <typename T, typename TC>
+void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
+                     int sweeps, cudaStream_t s) {
+    if (nband <= 0 || sweeps <= 0) return;
+    static int max_blocks = -1;   // co-resident blocks of 256 threads (per instantiation)
+    if (max_blocks < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        DM_CUDA(cudaGetDevice(&dev));
+        DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_sweeps<T, TC>, 256, 0));
+        max_blocks = std::max(0, per_sm * sms);
+    }
+    const int want = (nband + 255) / 256;
+    if (max_blocks <= 0) {
+        for (int i = 0; i < sweeps; ++i) vec_band_sweep(op, band, nband, f, x, u, omega, s);
+        return;
+    }
+    const int blocks = std::min(want, max_blocks);
+    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
+    float* uf = ud ? nullptr : u;
+    Grid3 g = op.g;
+    const TC *A = op.A, *L = op.L, *iV = op.invV, *iD = op.invD;
+    double sig = op.sigma, om = omega;
+    int nb = nband, sw = sweeps;
+    void* args[] = {&g, &A, &L, &iV, &iD, &sig, &band, &nb, &f, &x, &uf, &ud, &om, &sw};
+    const char* name = stencil_name("band_sweeps", prec_index<T>(), ST_JACOBI, op.level == 0);
+    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (t) t->begin(s, &e0, &e1);
+    DM_CUDA(cudaLaunchCooperativeKernel((const void*)k_band_sweeps<T, TC>, dim3(blocks), dim3(256), args, 0, s));
+    if (t) t->end(name, s, e0, e1);
+    count_launch();
+    check_launch(name);
 }
 
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
@@ -383,26 +464,19 @@ template <typename T, typename TC>
 void scal_stencil(const ScalOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
     if (mode == ST_APPLY)
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_scal_stencil<T, TC, ST_APPLY>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_scal_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_scal_stencil<T, TC, ST_RESID>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_scal_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
     else
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_scal_stencil<T, TC, ST_JACOBI>, node_grid(g, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega);
-}
-
-template <typename T, typename TC>
-__global__ void k_scal_jacobi_zero(long long n, const TC* __restrict__ invD, const T* __restrict__ f,
-                                   T* __restrict__ y, double omega_d) {
-    using C = typename Compute<T>::type;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-        y[q] = to_store<T>(C(omega_d) * (C)invD[q] * (C)to_c(f[q]));
+        launch(stencil_name("scal_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_scal_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
 }
 
 template <typename T, typename TC>
 void scal_jacobi_zero(const ScalOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
-    const long long n = op.g.np;
-    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-    launch("k_scal_jacobi_zero", k_scal_jacobi_zero<T, TC>, blocks, 256, 0, s, n, op.invD, f, y, omega);
+    const Domain d{op.g, op.tiles, op.ntiles, 1};
+    const int blocks = op.tiles ? std::max(op.ntiles, 1) : (int)std::min<long long>((d.len() + 255) / 256, 152 * 16);
+    launch(stencil_name("scal_jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0), k_jacobi_zero<T, TC>, blocks,
+           256, 0, s, d, op.invD, f, y, omega);
 }
 
 void scal_diagonal(const Grid3& g, const double* A, const unsigned char* active, double* d, cudaStream_t s) {
@@ -415,12 +489,14 @@ void scal_dense_assemble(const Grid3& g, const double* A, const int* list, const
     launch("k_scal_dense", k_scal_dense, n, 128, 0, s, g, A, list, pinned, n, M);
 }
 
-void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, cudaStream_t s) {
-    launch("k_div_a", k_div_a, node_grid(g, 0), kBlock, 0, s, g, A, x, s_out);
+void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, const int* tiles, int ntiles,
+              cudaStream_t s) {
+    launch("k_div_a", k_div_a, tile_grid(g, tiles, ntiles, 0), kBlock, 0, s, g, A, x, s_out, tiles);
 }
 
-void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, cudaStream_t s) {
-    launch("k_sub_grad", k_sub_grad, node_grid(g), kBlock, 0, s, g, A, x, phi, y);
+void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, const int* tiles,
+                 int ntiles, cudaStream_t s) {
+    launch("k_sub_grad", k_sub_grad, tile_grid(g, tiles, ntiles, 1), kBlock, 0, s, g, A, x, phi, y, tiles);
 }
 
 // explicit instantiations: FP64 storage / FP64 coefficients, FP32 / FP32, BF16 / FP32
@@ -429,6 +505,8 @@ void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double*
     template void vec_jacobi_zero<T, TC>(const VecOp<T, TC>&, const T*, T*, double, cudaStream_t);            \
     template void vec_band_sweep<T, TC>(const VecOp<T, TC>&, const int*, int, const T*, T*, float*, double,   \
                                         cudaStream_t);                                                        \
+    template void vec_band_sweeps<T, TC>(const VecOp<T, TC>&, const int*, int, const T*, T*, float*, double,  \
+                                         int, cudaStream_t);                                                  \
     template void scal_stencil<T, TC>(const ScalOp<T, TC>&, int, const T*, const T*, T*, double, cudaStream_t); \
     template void scal_jacobi_zero<T, TC>(const ScalOp<T, TC>&, const T*, T*, double, cudaStream_t);
 DM_INST(double, double)

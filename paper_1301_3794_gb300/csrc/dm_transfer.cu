@@ -40,11 +40,10 @@ __device__ __forceinline__ float w_normal(int fi, int I) {
 
 template <typename T, typename TC>
 __global__ void k_face_restrict(Grid3 gf, Grid3 gc, const TC* __restrict__ Ac, const T* __restrict__ r,
-                                T* __restrict__ fc) {
+                                T* __restrict__ fc, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z * BZ + threadIdx.z;
+    int I, J, K;
+    block_node(gc, tiles, I, J, K);
     if (I > gc.nx || J > gc.ny || K > gc.nz) return;
     const int q = gc.idx(I, J, K);
     const int nc[3] = {gc.nx, gc.ny, gc.nz};
@@ -83,11 +82,10 @@ __global__ void k_face_restrict(Grid3 gf, Grid3 gc, const TC* __restrict__ Ac, c
 
 template <typename T, typename TC>
 __global__ void k_face_prolong(Grid3 gf, Grid3 gc, const TC* __restrict__ Af, const T* __restrict__ ec,
-                               T* __restrict__ x) {
+                               T* __restrict__ x, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+    int i, j, k;
+    block_node(gf, tiles, i, j, k);
     if (i > gf.nx || j > gf.ny || k > gf.nz) return;
     const int p = gf.idx(i, j, k);
     const int nc[3] = {gc.nx, gc.ny, gc.nz};
@@ -128,11 +126,10 @@ __global__ void k_face_prolong(Grid3 gf, Grid3 gc, const TC* __restrict__ Af, co
 
 template <typename T>
 __global__ void k_cell_restrict(Grid3 gf, Grid3 gc, const unsigned char* __restrict__ active_c,
-                                const T* __restrict__ r, T* __restrict__ fc) {
+                                const T* __restrict__ r, T* __restrict__ fc, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int I = blockIdx.x * BX + threadIdx.x;
-    const int J = blockIdx.y * BY + threadIdx.y;
-    const int K = blockIdx.z * BZ + threadIdx.z;
+    int I, J, K;
+    block_node(gc, tiles, I, J, K);
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
     const int q = gc.idx(I, J, K);
     C acc = C(0);
@@ -148,11 +145,10 @@ __global__ void k_cell_restrict(Grid3 gf, Grid3 gc, const unsigned char* __restr
 
 template <typename T>
 __global__ void k_cell_prolong(Grid3 gf, Grid3 gc, const unsigned char* __restrict__ active_f,
-                               const T* __restrict__ ec, T* __restrict__ x) {
+                               const T* __restrict__ ec, T* __restrict__ x, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z * BZ + threadIdx.z;
+    int i, j, k;
+    block_node(gf, tiles, i, j, k);
     if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
     const int p = gf.idx(i, j, k);
     if (!active_f[p]) return;
@@ -166,38 +162,46 @@ inline dim3 grid_for(const Grid3& g, int extra) {
 }  // namespace
 
 template <typename T, typename TC>
-void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, cudaStream_t s) {
-    launch("k_face_restrict", k_face_restrict<T, TC>, grid_for(gc, 1), kBlock, 0, s, gf, gc, Ac, r, fc);
+void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, const int* tiles_c,
+                   int ntiles_c, cudaStream_t s) {
+    launch("k_face_restrict", k_face_restrict<T, TC>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock, 0, s, gf, gc, Ac, r,
+           fc, tiles_c);
 }
 template <typename T, typename TC>
-void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, cudaStream_t s) {
-    launch("k_face_prolong", k_face_prolong<T, TC>, grid_for(gf, 1), kBlock, 0, s, gf, gc, Af, ec, x);
+void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, const int* tiles_f,
+                      int ntiles_f, cudaStream_t s) {
+    launch("k_face_prolong", k_face_prolong<T, TC>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0, s, gf, gc, Af, ec,
+           x, tiles_f);
 }
 template <typename T>
 void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
-                   cudaStream_t s) {
-    launch("k_cell_restrict", k_cell_restrict<T>, grid_for(gc, 0), kBlock, 0, s, gf, gc, active_c, r, fc);
+                   const int* tiles_c, int ntiles_c, cudaStream_t s) {
+    launch("k_cell_restrict", k_cell_restrict<T>, tile_grid(gc, tiles_c, ntiles_c, 0), kBlock, 0, s, gf, gc,
+           active_c, r, fc, tiles_c);
 }
 template <typename T>
 void cell_prolong_add(const Grid3& gf, const Grid3& gc, const unsigned char* active_f, const T* ec, T* x,
-                      cudaStream_t s) {
-    launch("k_cell_prolong", k_cell_prolong<T>, grid_for(gf, 0), kBlock, 0, s, gf, gc, active_f, ec, x);
+                      const int* tiles_f, int ntiles_f, cudaStream_t s) {
+    launch("k_cell_prolong", k_cell_prolong<T>, tile_grid(gf, tiles_f, ntiles_f, 0), kBlock, 0, s, gf, gc, active_f,
+           ec, x, tiles_f);
 }
 
-#define DM_INST(T, TC)                                                                                  \
-    template void face_restrict<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, cudaStream_t); \
-    template void face_prolong_add<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, cudaStream_t);
+#define DM_INST(T, TC)                                                                                   \
+    template void face_restrict<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, const int*, int,  \
+                                       cudaStream_t);                                                      \
+    template void face_prolong_add<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, const int*, int, \
+                                          cudaStream_t);
 DM_INST(double, double)
 DM_INST(float, float)
 DM_INST(__nv_bfloat16, float)
 #undef DM_INST
-template void cell_restrict<double>(const Grid3&, const Grid3&, const unsigned char*, const double*, double*, cudaStream_t);
-template void cell_restrict<float>(const Grid3&, const Grid3&, const unsigned char*, const float*, float*, cudaStream_t);
+template void cell_restrict<double>(const Grid3&, const Grid3&, const unsigned char*, const double*, double*, const int*, int, cudaStream_t);
+template void cell_restrict<float>(const Grid3&, const Grid3&, const unsigned char*, const float*, float*, const int*, int, cudaStream_t);
 template void cell_restrict<__nv_bfloat16>(const Grid3&, const Grid3&, const unsigned char*, const __nv_bfloat16*,
-                                           __nv_bfloat16*, cudaStream_t);
-template void cell_prolong_add<double>(const Grid3&, const Grid3&, const unsigned char*, const double*, double*, cudaStream_t);
-template void cell_prolong_add<float>(const Grid3&, const Grid3&, const unsigned char*, const float*, float*, cudaStream_t);
+                                           __nv_bfloat16*, const int*, int, cudaStream_t);
+template void cell_prolong_add<double>(const Grid3&, const Grid3&, const unsigned char*, const double*, double*, const int*, int, cudaStream_t);
+template void cell_prolong_add<float>(const Grid3&, const Grid3&, const unsigned char*, const float*, float*, const int*, int, cudaStream_t);
 template void cell_prolong_add<__nv_bfloat16>(const Grid3&, const Grid3&, const unsigned char*, const __nv_bfloat16*,
-                                              __nv_bfloat16*, cudaStream_t);
+                                              __nv_bfloat16*, const int*, int, cudaStream_t);
 
 }  // namespace dm

@@ -69,7 +69,7 @@ def test_certify_matches_oracle(dm, ctx):
 
 def test_device_vectors(dm, ctx):
     import torch
-    w = W.box_workload(8, 6, 4, 0.8, 0.6, 0.4, sigma=50.0, nev=3)
+    w = W.box_workload(8, 6, 4, 0.8, 0.6, 0.4, sigma=20.0, nev=3)
     geom = dm.Geometry.from_workload(ctx, w)
     k2h, Bh, _, _ = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors="host")
     k2d, Bd, _, _ = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors="device")
