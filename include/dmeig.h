@@ -72,7 +72,7 @@ typedef struct dm_eig_params {
     int nev;               /* number of eigenpairs wanted */
     double tol;            /* Ritz residual tolerance, relative to |theta| (1e-10) */
     double inner_tol;      /* relative residual of each shifted solve (1e-10) */
-    double proj_tol;       /* relative residual of each scalar solve inside P_DM (1e-12) */
+    double proj_tol;       /* scalar-solve tolerance inside P_DM, see dm_operator_project (1e-12) */
     int basis;             /* Krylov-Schur basis size m; 0 = max(2 nev + 10, 24) capped at 64 */
     int max_restarts;      /* (100) */
     int inner_restart;     /* FGMRES basis size (40) */
@@ -173,7 +173,9 @@ dm_status dm_operator_vcycle(dm_operator* op, const double* f, double* e, int on
 dm_status dm_operator_solve(dm_operator* op, const double* b, double* x, int on_device,
                             double tol, int restart, int maxit, int* iters, double* relres);
 /* y = P_DM x = x - D^T (D A D^T)^-1 D A x (Eq. proj); the scalar Laplacian is
- * solved by FGMRES + cell multigrid to relative residual tol. */
+ * solved by FGMRES + cell multigrid until its residual is below
+ * tol * max(||D A x||, ||x|| / h_min): for a nearly divergence-free x the
+ * divergence is rounding noise and only the field's own scale is meaningful. */
 dm_status dm_operator_project(dm_operator* op, const double* x, double* y, int on_device,
                               double tol, int* iters);
 /* One scalar V-cycle e ~= (D A D^T)^-1 f on cells (natural cell layout). */

@@ -16,6 +16,7 @@
 namespace dm {
 
 thread_local long long* g_launch_counter = nullptr;
+thread_local cudaStream_t g_stream = nullptr;
 thread_local Tracer* g_tracer = nullptr;
 
 cudaEvent_t Tracer::get_event() {
@@ -118,13 +119,16 @@ struct Sync {
 struct LaunchScope {
     long long* prev;
     Tracer* prev_t;
-    explicit LaunchScope(dm_context* ctx) : prev(g_launch_counter), prev_t(g_tracer) {
+    cudaStream_t prev_s;
+    explicit LaunchScope(dm_context* ctx) : prev(g_launch_counter), prev_t(g_tracer), prev_s(g_stream) {
         g_launch_counter = ctx ? &ctx->launches : nullptr;
         g_tracer = ctx ? &ctx->tracer : nullptr;
+        g_stream = ctx ? ctx->stream : nullptr;
     }
     ~LaunchScope() {
         g_launch_counter = prev;
         g_tracer = prev_t;
+        g_stream = prev_s;
     }
 };
 
@@ -483,7 +487,7 @@ double norm2(dm_context* ctx, const Domain& D, const double* x, const double* w 
 // applied twice.  x is overwritten.  Returns the iteration count.
 template <class Apply, class Prec>
 int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Prec prec, const double* b, double* x,
-           double tol, int maxit, double* relres) {
+           double tol, int maxit, double* relres, double abs_tol = 0.0) {
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
     ws.ensure(n, m);
@@ -494,6 +498,9 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
     const double bnorm = norm2(ctx, D, b);
     if (relres) *relres = 0.0;
     if (bnorm == 0.0) return 0;
+    // converged when ||b - A x|| <= thr: relative to ||b||, or the absolute
+    // floor abs_tol when the caller knows a better scale than ||b||
+    const double thr = std::max(tol * bnorm, abs_tol);
     int total = 0;
     bool first = true;
     double res = 1.0;
@@ -509,7 +516,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         }
         const double beta = norm2(ctx, D, V);
         res = beta / bnorm;
-        if (beta <= tol * bnorm) break;
+        if (beta <= thr) break;
         scale_copy(D, 1.0 / beta, V, V, s);
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(g.begin(), g.end(), 0.0);
@@ -518,13 +525,19 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         for (int j = 0; j < m && total < maxit; ++j) {
             prec(V + (size_t)j * n, Z + (size_t)j * n);
             apply(Z + (size_t)j * n, w);
+            // classical Gram-Schmidt, repeated only when the pass cancelled most
+            // of w (Kahan: ||w'|| < 0.7 ||w||), norms fused into the passes
             std::vector<double> h(j + 1);
-            for (int pass = 0; pass < 2; ++pass) {
+            double wn2 = 0.0;
+            mdot_self(ctx->red, D, j + 1, V, n, w, nullptr, h.data(), &wn2, s);
+            double hn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, nullptr, s);
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
+            if (hn2 < 0.49 * wn2) {
                 mdot(ctx->red, D, j + 1, V, n, w, nullptr, h.data(), s);
-                maxpy(ctx->red, D, j + 1, V, n, h.data(), w, s);
+                hn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, nullptr, s);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
             }
-            const double hn = norm2(ctx, D, w);
+            const double hn = std::sqrt(std::max(hn2, 0.0));
             H[(size_t)(j + 1) * m + j] = hn;
             if (hn > 0.0) scale_copy(D, 1.0 / hn, w, V + (size_t)(j + 1) * n, s);
             // Givens
@@ -544,7 +557,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
             ++total;
             jend = j;
             res = std::fabs(g[j + 1]) / bnorm;
-            if (res <= tol || hn == 0.0) break;
+            if (std::fabs(g[j + 1]) <= thr || hn == 0.0) break;
         }
         if (jend < 0) break;
         // y = H^-1 g (upper triangular)
@@ -557,13 +570,13 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         for (int i = 0; i <= jend; ++i) neg[i] = -y[i];
         maxpy(ctx->red, D, jend + 1, Z, n, neg.data(), x, s);
         first = false;
-        if (res <= tol) {
+        if (res * bnorm <= thr) {
             // confirm with the true residual
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
             const double tr = norm2(ctx, D, w) / bnorm;
             res = tr;
-            if (tr <= 10.0 * tol) break;
+            if (tr * bnorm <= 10.0 * thr) break;
         }
     }
     if (relres) *relres = res;
@@ -585,10 +598,17 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     double* sv = op->c0.get();
     double* phi = op->c1.get();
     dm_div_a(g0.g, g0.A.get(), x, sv, g0.tiles.get(), g0.ntiles, s);
+    // The divergence of a nearly divergence-free x (the shifted solve of a
+    // divergence-free vector) is mostly rounding noise, which is not in the
+    // range of D A D^T (its component sums are not zero), so a tolerance
+    // relative to ||D A x|| cannot be met.  The solve is accurate enough once
+    // the residual is tol times the divergence scale of x itself, ||x|| / h.
+    const double hmin = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+    const double xscale = norm2(op->ctx, g0.vdom(), x) / hmin;
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
     auto prec = [op](const double* in, double* out) { precond_scal(op, in, out); };
     double rr = 0.0;
-    const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr);
+    const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
     return it;
 }
@@ -1393,13 +1413,19 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 double* w = V + (size_t)(j + 1) * n;
                 proj_total += project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
                 ++outer;
+                // A-orthogonalise against the basis: classical Gram-Schmidt,
+                // repeated when the first pass cancelled most of w
                 std::vector<double> h(j + 1);
-                for (int pass = 0; pass < 2; ++pass) {
+                double wn2 = 0.0;
+                mdot_self(ctx->red, D, j + 1, V, n, w, a, h.data(), &wn2, s);
+                double bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
+                for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
+                if (bn2 < 0.49 * wn2) {
                     mdot(ctx->red, D, j + 1, V, n, w, a, h.data(), s);
-                    maxpy(ctx->red, D, j + 1, V, n, h.data(), w, s);
+                    bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
                     for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
                 }
-                const double beta = norm2(ctx, D, w, a);
+                const double beta = std::sqrt(std::max(bn2, 0.0));
                 Hat(j + 1, j) = beta;
                 DM_REQUIRE(beta > 0.0, DM_ERR_NO_CONVERGENCE, "Krylov space exhausted");
                 scale_copy(D, 1.0 / beta, w, w, s);

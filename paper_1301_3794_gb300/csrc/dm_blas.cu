@@ -28,16 +28,20 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial[b * ldp + c0 + c] = sum over this block's entries of w * V_c * x
 __global__ void k_mdot_partial(Domain d, int m, const double* __restrict__ V, long long ld,
                                const double* __restrict__ x, const double* __restrict__ w, double* __restrict__ partial,
-                               int ldp) {
+                               int ldp, int self) {
     __shared__ double red[kThreads / 32][kChunk];
+    __shared__ double red_self[kThreads / 32];
+    double acc_self = 0.0;
     for (int c0 = 0; c0 < m; c0 += kChunk) {
         const int nc = min(kChunk, m - c0);
         double acc[kChunk];
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) acc[c] = 0.0;
+        const bool first = c0 == 0 && self;
         for_each_entry(d, [&](long long r) {
-            double xr = x[r];
-            if (w) xr *= w[r];
+            const double x0 = x[r];
+            const double xr = w ? x0 * w[r] : x0;
+            if (first) acc_self += xr * x0;
 #pragma unroll
             for (int c = 0; c < kChunk; ++c)
                 if (c < nc) acc[c] += V[(c0 + c) * ld + r] * xr;
@@ -55,6 +59,42 @@ __global__ void k_mdot_partial(Domain d, int m, const double* __restrict__ V, lo
             partial[(long long)blockIdx.x * ldp + c0 + threadIdx.x] = s;
         }
         __syncthreads();
+    }
+    if (self) {
+        const double v = warp_sum(acc_self);
+        if ((threadIdx.x & 31) == 0) red_self[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) t += red_self[k];
+            partial[(long long)blockIdx.x * ldp + m] = t;
+        }
+    }
+}
+
+// x -= sum_c h[c] V_c (h on the device) and the block partial of sum w x^2 of the result
+__global__ void k_maxpy_norm(Domain d, int m, const double* __restrict__ V, long long ld,
+                             const double* __restrict__ h, double* __restrict__ x, const double* __restrict__ w,
+                             double* __restrict__ partial) {
+    __shared__ double hs[128];
+    __shared__ double red[kThreads / 32];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    double acc_self = 0.0;
+    for_each_entry(d, [&](long long r) {
+        double acc = 0.0;
+        for (int c = 0; c < m; ++c) acc += hs[c] * V[c * ld + r];
+        const double v = x[r] - acc;
+        x[r] = v;
+        acc_self += (w ? w[r] * v : v) * v;
+    });
+    const double v = warp_sum(acc_self);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) t += red[k];
+        partial[blockIdx.x] = t;
     }
 }
 
@@ -171,11 +211,36 @@ void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, c
           double* host_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
     const int nb = blocks_for(d);
-    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols);
+    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 0);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
+}
+
+void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
+               double* host_out, double* self_out, cudaStream_t s) {
+    DM_REQUIRE(m >= 1 && m + 1 <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
+    const int nb = blocks_for(d);
+    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 1);
+    launch("k_mdot_final", k_mdot_final, (m + 1 + 7) / 8, 256, 0, s, nb, m + 1, red.partial, red.max_cols, red.result);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
+    *self_out = red.host[m];
+}
+
+double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long long ld, double* x, const double* w,
+                  cudaStream_t s) {
+    DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
+    const int nb = blocks_for(d);
+    // h = red.result (written by the preceding mdot on this stream); partials in a separate stripe
+    double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
+    launch("k_maxpy_norm", k_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld, red.result, x, w, part);
+    launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return red.host[0];
 }
 
 void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* h_host, double* x,

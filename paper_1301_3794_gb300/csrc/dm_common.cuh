@@ -129,6 +129,9 @@ inline dim3 tile_grid(const Grid3& g, const int* tiles, int ntiles, int extra) {
     return dim3((g.nx + extra + TX - 1) / TX, (g.ny + extra + TY - 1) / TY, (g.nz + extra + TZ - 1) / TZ);
 }
 
+// Stream of the active context: buffers are zero-filled on it, so the fill is
+// ordered with the context's kernels whatever kind of stream it is.
+extern thread_local cudaStream_t g_stream;
 // Launch counter of the active context (kernels this library launched).
 extern thread_local long long* g_launch_counter;
 inline void count_launch(long long n = 1) {
@@ -193,7 +196,7 @@ struct DBuf {
         n = count;
         if (count) {
             DM_CUDA(cudaMalloc(&p, count * sizeof(T)));
-            if (zero) DM_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+            if (zero) DM_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), g_stream));
         }
     }
     void release() {
@@ -245,6 +248,9 @@ int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
 // active tiles of a level in ascending order (tiles: capacity of all tiles); returns the count
 int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
                cudaStream_t s);
+// same for tiles of TX x sy x sz nodes (index t = ti + nti (tj + ntj tk), nti = ceil((nx+1)/TX), ntj = ceil((ny+1)/sy))
+int geom_tiles_shape(const Grid3& g, int sy, int sz, const double* A, const unsigned char* active, int* tiles,
+                     int* flags, int* d_count, cudaStream_t s);
 int geom_active_cells(const Grid3& g, const double* A, int* list, unsigned char* active, int* d_count,
                       cudaStream_t s);
 // natural <-> padded layouts
@@ -270,7 +276,15 @@ struct VecOp {
     int level = 0;   // multigrid level (names the kernel in traces: fine vs coarse)
     const int* tiles = nullptr;   // active tiles of the level (nullptr: whole grid)
     int ntiles = 0;
+    int shape = 0;                // tile shape of `tiles` for the vector stencil (see stencil_shape_dims)
 };
+// tile shapes of the tiled vector stencil: TX x SY x SZ with (SY, SZ) = (4,2), (2,4), (8,1)
+constexpr int kStencilShapes = 3;
+inline void stencil_shape_dims(int shape, int& sy, int& sz) {
+    static const int d[kStencilShapes][2] = {{4, 2}, {2, 4}, {8, 1}};
+    sy = d[shape][0];
+    sz = d[shape][1];
+}
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2 };
 // trace name of a stencil launch: "<kind>_<precision>_<mode>_<L0|Lc>"
 template <typename T> constexpr int prec_index() {
@@ -358,6 +372,13 @@ void reducer_free(Reducer& r);
 // out[c] = sum_r w[r] * V[c*ld + r] * x[r] over the domain (w nullable = 1), c < m; result copied to host
 void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s);
+// as mdot, and also returns sum_r w[r] x[r]^2 in *self_out (one pass, one sync)
+void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
+               double* host_out, double* self_out, cudaStream_t s);
+// x -= sum_c h[c] V[c*ld + r] using the h the preceding mdot left on the device (red.result),
+// and returns sum_r w[r] x[r]^2 of the updated x (one pass, one sync)
+double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long long ld, double* x, const double* w,
+                  cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r]    (h host array, m <= max_cols)
 void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* h_host, double* x,
            cudaStream_t s);

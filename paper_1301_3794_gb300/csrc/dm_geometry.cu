@@ -220,24 +220,54 @@ __device__ __forceinline__ bool valid_cell(const Grid3& g, int i, int j, int k) 
 
 __global__ void k_band(Grid3 g, const double* __restrict__ A, const int* __restrict__ flag, int* __restrict__ band,
                        int* __restrict__ count) {
+    // one block = one 32 x 4 x 2 node block; its band faces are written as one
+    // contiguous chunk (node order, x/y/z within a node) so that the sweeps
+    // read spatially close faces together
+    __shared__ int warp_tot[8];
+    __shared__ int base;
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     const int k = blockIdx.z * BZ + threadIdx.z;
-    if (i > g.nx || j > g.ny || k > g.nz) return;
-    const int p = g.idx(i, j, k);
+    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    const bool node = i <= g.nx && j <= g.ny && k <= g.nz;
+    const int p = node ? g.idx(i, j, k) : 0;
     // face of component c at (i,j,k) touches cells (i,j,k) and (i,j,k) - e_c
     const int di[3] = {1, 0, 0}, dj[3] = {0, 1, 0}, dk[3] = {0, 0, 1};
-    for (int c = 0; c < 3; ++c) {
-        if (!(A[c * g.np + p] > 0.0)) continue;
-        bool in = false;
-        if (valid_cell(g, i, j, k)) in = near_cut(g, flag, i, j, k);
-        if (!in && valid_cell(g, i - di[c], j - dj[c], k - dk[c]))
-            in = near_cut(g, flag, i - di[c], j - dj[c], k - dk[c]);
-        if (in) {
-            const int slot = atomicAdd(count, 1);
-            band[slot] = c * g.np + p;
+    bool in[3] = {false, false, false};
+    int mine = 0;
+    if (node) {
+        for (int c = 0; c < 3; ++c) {
+            if (!(A[c * g.np + p] > 0.0)) continue;
+            bool b = false;
+            if (valid_cell(g, i, j, k)) b = near_cut(g, flag, i, j, k);
+            if (!b && valid_cell(g, i - di[c], j - dj[c], k - dk[c])) b = near_cut(g, flag, i - di[c], j - dj[c], k - dk[c]);
+            in[c] = b;
+            mine += b ? 1 : 0;
         }
     }
+    // block-exclusive prefix of `mine`
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) {
+            const int t = warp_tot[w];
+            warp_tot[w] = tot;
+            tot += t;
+        }
+        base = tot > 0 ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    int slot = base + warp_tot[wid] + incl - mine;
+    for (int c = 0; c < 3; ++c)
+        if (in[c]) band[slot++] = c * g.np + p;
 }
 
 __global__ void k_open_faces(Grid3 g, const double* __restrict__ A, int* __restrict__ list, int* __restrict__ count) {
@@ -441,6 +471,29 @@ __global__ void k_compact(const int* __restrict__ flags, int n, int* __restrict_
     for (int t = b; t < e; ++t)
         if (flags[t]) out[w++] = t;
     if (tid == 1023) *count = scan[1023];
+}
+
+__global__ void k_tile_flags_shape(Grid3 g, int sy, int sz, const double* __restrict__ A,
+                                   const unsigned char* __restrict__ active, int* __restrict__ flags) {
+    const int t = blockIdx.x;
+    const int nti = (g.nx + TX) / TX, ntj = (g.ny + sy) / sy;
+    const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * sy, k0 = (t / (nti * ntj)) * sz;
+    const int i = i0 + (threadIdx.x & (TX - 1)), j = j0 + (threadIdx.x / TX) % sy, k = k0 + threadIdx.x / (TX * sy);
+    bool any = false;
+    if (i <= g.nx && j <= g.ny && k <= g.nz) {
+        const int p = g.idx(i, j, k);
+        any = A[p] > 0.0 || A[g.np + p] > 0.0 || A[2 * g.np + p] > 0.0 || active[p] != 0;
+    }
+    const int v = __syncthreads_or(any);
+    if (threadIdx.x == 0) flags[t] = v ? 1 : 0;
+}
+
+int geom_tiles_shape(const Grid3& g, int sy, int sz, const double* A, const unsigned char* active, int* tiles,
+                     int* flags, int* d_count, cudaStream_t s) {
+    const int nt = ((g.nx + TX) / TX) * ((g.ny + sy) / sy) * ((g.nz + sz) / sz);
+    launch("k_tile_flags", k_tile_flags_shape, nt, TX * sy * sz, 0, s, g, sy, sz, A, active, flags);
+    launch("k_compact", k_compact, 1, 1024, 0, s, flags, nt, tiles, d_count);
+    return read_count(d_count, s);
 }
 
 int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,

@@ -169,6 +169,96 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
     }
 }
 
+// Tiled form of k_vec_stencil: one active tile of TX x SY x SZ nodes per
+// block.  The L-weighted edge curls and cell divergences the tile's faces need
+// are computed once into shared memory (ex, ey, ez on the tile plus one layer
+// above, psi on the tile plus one layer below), then every thread forms its
+// node's three face outputs from them.  Same arithmetic as node_K.  The tile
+// shape (SY, SZ) is chosen per level by the autotuner.
+template <typename T, typename TC, int MODE, int SY, int SZ>
+__global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
+    Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L, const TC* __restrict__ invV,
+    const TC* __restrict__ invD, double sigma_d, const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y,
+    double omega_d, const int* __restrict__ tiles) {
+    using C = typename Compute<T>::type;
+    constexpr int PSI_X = TX + 1, PSI_Y = SY + 1, PSI_Z = SZ + 1;   // psi: i0-1 .. i0+TX-1 (and j, k alike)
+    constexpr int EX_X = TX, EX_Y = SY + 1, EX_Z = SZ + 1;          // ex:  i0 .. i0+TX-1, j0 .. j0+SY, k0 .. k0+SZ
+    constexpr int EY_X = TX + 1, EY_Y = SY, EY_Z = SZ + 1;
+    constexpr int EZ_X = TX + 1, EZ_Y = SY + 1, EZ_Z = SZ;
+    constexpr int N_PSI = PSI_X * PSI_Y * PSI_Z, N_EX = EX_X * EX_Y * EX_Z, N_EY = EY_X * EY_Y * EY_Z,
+                  N_EZ = EZ_X * EZ_Y * EZ_Z;
+    constexpr int NT = TX * SY * SZ;
+    __shared__ C s_psi[N_PSI], s_ex[N_EX], s_ey[N_EY], s_ez[N_EZ];
+    const int t = tiles[blockIdx.x];
+    const int nti = (g.nx + TX) / TX, ntj = (g.ny + SY) / SY;
+    const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * SY, k0 = (t / (nti * ntj)) * SZ;
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz);
+    Coef<C, TC> cf{A, L, invV, N};
+    VecAcc<T, C> b{x, N};
+    const int tid = threadIdx.x + TX * (threadIdx.y + SY * threadIdx.z);
+    for (int e = tid; e < N_PSI; e += NT) {
+        const int li = e % PSI_X, lj = (e / PSI_X) % PSI_Y, lk = e / (PSI_X * PSI_Y);
+        const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
+        C v = C(0);
+        if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz)
+            v = cell_psi(cf, b, g.idx(i, j, k), X, Y, Z, rdx, rdy, rdz);
+        s_psi[e] = v;
+    }
+    for (int e = tid; e < N_EX; e += NT) {
+        const int li = e % EX_X, lj = (e / EX_X) % EX_Y, lk = e / (EX_X * EX_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        C v = C(0);
+        if (i < g.nx && j <= g.ny && k <= g.nz) v = edge_x(cf, b, g.idx(i, j, k), Y, Z, rdy, rdz);
+        s_ex[e] = v;
+    }
+    for (int e = tid; e < N_EY; e += NT) {
+        const int li = e % EY_X, lj = (e / EY_X) % EY_Y, lk = e / (EY_X * EY_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        C v = C(0);
+        if (i <= g.nx && j < g.ny && k <= g.nz) v = edge_y(cf, b, g.idx(i, j, k), X, Z, rdx, rdz);
+        s_ey[e] = v;
+    }
+    for (int e = tid; e < N_EZ; e += NT) {
+        const int li = e % EZ_X, lj = (e / EZ_X) % EZ_Y, lk = e / (EZ_X * EZ_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        C v = C(0);
+        if (i <= g.nx && j <= g.ny && k < g.nz) v = edge_z(cf, b, g.idx(i, j, k), X, Y, rdx, rdy);
+        s_ez[e] = v;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    auto PSI = [&](int a, int b_, int c) { return s_psi[(c * PSI_Y + b_) * PSI_X + a]; };
+    auto EXS = [&](int a, int b_, int c) { return s_ex[(c * EX_Y + b_) * EX_X + a]; };
+    auto EYS = [&](int a, int b_, int c) { return s_ey[(c * EY_Y + b_) * EY_X + a]; };
+    auto EZS = [&](int a, int b_, int c) { return s_ez[(c * EZ_Y + b_) * EZ_X + a]; };
+    const C ps0 = PSI(tx + 1, ty + 1, tz + 1);
+    const C ax = cf.a(0, p), ay = cf.a(1, p), az = cf.a(2, p);
+    const C sigma = C(sigma_d);
+    C out[3];
+    out[0] = (EZS(tx, ty + 1, tz) - EZS(tx, ty, tz)) * rdy - (EYS(tx, ty, tz + 1) - EYS(tx, ty, tz)) * rdz +
+             ax * ((PSI(tx, ty + 1, tz + 1) - ps0) * rdx - sigma * b(0, p));
+    out[1] = (EXS(tx, ty, tz + 1) - EXS(tx, ty, tz)) * rdz - (EZS(tx + 1, ty, tz) - EZS(tx, ty, tz)) * rdx +
+             ay * ((PSI(tx + 1, ty, tz + 1) - ps0) * rdy - sigma * b(1, p));
+    out[2] = (EYS(tx + 1, ty, tz) - EYS(tx, ty, tz)) * rdx - (EXS(tx, ty + 1, tz) - EXS(tx, ty, tz)) * rdy +
+             az * ((PSI(tx + 1, ty + 1, tz) - ps0) * rdz - sigma * b(2, p));
+    const C av[3] = {ax, ay, az};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int q = c * N + p;
+        C v = av[c] > C(0) ? out[c] : C(0);
+        if (MODE == ST_RESID) {
+            v = (C)to_c(f[q]) - v;
+        } else if (MODE == ST_JACOBI) {
+            v = (C)to_c(x[q]) + C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - v);
+        }
+        y[q] = to_store<T>(v);
+    }
+}
+
 template <typename T, typename TC>
 __global__ void k_jacobi_zero(Domain d, const TC* __restrict__ invD, const T* __restrict__ f, T* __restrict__ y,
                               double omega_d) {
@@ -240,6 +330,35 @@ __global__ void k_band_sweeps(Grid3 g, const TC* __restrict__ A, const TC* __res
             x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
         }
         grid.sync();
+    }
+}
+
+// Small bands (coarse levels): all sweeps in one block, block barriers only.
+template <typename T, typename TC>
+__global__ void __launch_bounds__(1024) k_band_sweeps_block(
+    Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L, const TC* __restrict__ invV,
+    const TC* __restrict__ invD, double sigma_d, const int* __restrict__ band, int nband, const T* __restrict__ f,
+    T* x, float* u_f, double* u_d, double omega_d, int sweeps) {
+    using C = typename Compute<T>::type;
+    Coef<C, TC> cf{A, L, invV, g.np};
+    VecAccRW<T, C> b{x, g.np};
+    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz), sig = C(sigma_d), om = C(omega_d);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int t = threadIdx.x; t < nband; t += blockDim.x) {
+            const int q = band[t];
+            const int c = q / g.np, p = q - c * g.np;
+            const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sig);
+            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - kx);
+            if (u_d) u_d[t] = (double)u;
+            else u_f[t] = (float)u;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nband; t += blockDim.x) {
+            const int q = band[t];
+            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
+            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
+        }
+        __syncthreads();
     }
 }
 
@@ -387,6 +506,25 @@ const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
 template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
+    if (op.tiles) {
+        if (op.ntiles <= 0) return;
+        const char* nm = stencil_name("vec_stencil", prec_index<T>(), mode, op.level == 0);
+        // tile shape: 0 = 32x4x2 (the level's active tiles), 1 = 32x2x4, 2 = 32x8x1 (op.tiles is the
+        // active-tile list of that shape)
+        switch (op.shape * 3 + mode) {
+#define DM_TILED(SH, MD, SY, SZ)                                                                              \
+    case SH * 3 + MD:                                                                                         \
+        launch(nm, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, op.ntiles, dim3(TX, SY, SZ), 0, s, g, op.A, op.L, \
+               op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);                                         \
+        break;
+            DM_TILED(0, ST_APPLY, 4, 2) DM_TILED(0, ST_RESID, 4, 2) DM_TILED(0, ST_JACOBI, 4, 2)
+            DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4)
+            DM_TILED(2, ST_APPLY, 8, 1) DM_TILED(2, ST_RESID, 8, 1) DM_TILED(2, ST_JACOBI, 8, 1)
+#undef DM_TILED
+            default: throw Error(DM_ERR_INVALID_ARG, "unknown stencil tile shape");
+        }
+        return;
+    }
     if (mode == ST_APPLY)
         launch(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_vec_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
@@ -426,14 +564,20 @@ void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T
         DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_sweeps<T, TC>, 256, 0));
         max_blocks = std::max(0, per_sm * sms);
     }
-    const int want = (nband + 255) / 256;
+    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
+    float* uf = ud ? nullptr : u;
+    if (nband <= 16384) {
+        launch(stencil_name("band_sweeps", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_sweeps_block<T, TC>, 1,
+               1024, 0, s, op.g, op.A, op.L, op.invV, op.invD, op.sigma, band, nband, f, x, uf, ud, omega, sweeps);
+        return;
+    }
+    // every thread takes several band faces: fewer blocks make each grid barrier cheaper
+    const int want = (nband + 4 * 256 - 1) / (4 * 256);
     if (max_blocks <= 0) {
         for (int i = 0; i < sweeps; ++i) vec_band_sweep(op, band, nband, f, x, u, omega, s);
         return;
     }
     const int blocks = std::min(want, max_blocks);
-    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
-    float* uf = ud ? nullptr : u;
     Grid3 g = op.g;
     const TC *A = op.A, *L = op.L, *iV = op.invV, *iD = op.invD;
     double sig = op.sigma, om = omega;
