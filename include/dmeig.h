@@ -55,6 +55,7 @@ typedef enum dm_precision {
 typedef struct dm_context dm_context;
 typedef struct dm_geometry dm_geometry;
 typedef struct dm_operator dm_operator;
+typedef struct dm_learned dm_learned;
 
 /* Multigrid preconditioner settings (a design of this library: the paper used
  * an algebraic V-cycle with one order-1 polynomial smoother step per level and
@@ -65,6 +66,8 @@ typedef struct dm_mg_params {
     double omega_scale;    /* Jacobi weight = omega_scale / lambda_max(D^-1 (K - sigma A)) (1.7) */
     int power_iters;       /* power iterations for lambda_max (30) */
     int precision;         /* dm_precision of the V-cycle (DM_PREC_F64) */
+    int autotune;          /* 1: time the stencil tile shapes per level at setup and keep the fastest;
+                              results are cached in the context by level size and precision (1) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
@@ -79,6 +82,7 @@ typedef struct dm_eig_params {
     int inner_maxit;       /* FGMRES iteration cap per solve (400) */
     unsigned long long seed; /* start vector seed */
     dm_mg_params mg;
+    const dm_learned* learned; /* nullable: learned correction after each V-cycle (see dm_learned_*) */
 } dm_eig_params;
 
 typedef struct dm_eig_report {
@@ -94,6 +98,8 @@ typedef struct dm_eig_report {
     double setup_seconds;  /* operator setup (diagonals, weights, coarsest factorisation) */
     double solve_seconds;  /* eigensolver iterations and certification */
     long long kernel_launches;  /* kernels this library launched during the call */
+    int learned_applied;   /* preconditioner applications that used the learned correction */
+    int learned_fallbacks; /* shifted solves in which it was switched off (residual stalled) */
 } dm_eig_report;
 
 /* ---- context ------------------------------------------------------------ */
@@ -149,6 +155,9 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
                              const dm_mg_params* mg, dm_operator** out);
 void dm_operator_destroy(dm_operator* op);
 int dm_operator_num_levels(const dm_operator* op);
+/* Tile shape the vector stencil of `level` uses: 0 = 32x4x2, 1 = 32x2x4, 2 = 32x8x1 nodes
+ * (chosen by the autotuner), -1 on a bad argument.  No counterpart in the paper. */
+int dm_operator_stencil_shape(const dm_operator* op, int level);
 /* Jacobi weight of `level` for the vector (scalar = 0) or the scalar (scalar = 1) cycle. */
 double dm_operator_get_omega(const dm_operator* op, int level, int scalar);
 dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double omega);
@@ -194,6 +203,60 @@ void dm_eig_params_default(dm_eig_params* p);
  * and report->n_converged. */
 dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_params* p,
                         double* k2_out, double* b_out, int b_on_device, dm_eig_report* report);
+
+/* ---- learned smoother (no counterpart in the paper) -----------------------
+ * A 3-layer 3x3x3 convolutional network without biases on the fine node grid
+ * (8 -> 16 -> 16 -> 3 channels, relu between layers; BF16 activations, FP32
+ * weights and accumulation).  Input per node: the residual on the node's x, y,
+ * z faces divided by its RMS over the open faces, A_x, A_y, A_z, the node
+ * cell's V, and 0.  Output: the error on those faces in units of RMS(r) h^2
+ * (h = smallest spacing).  Inside the preconditioner it corrects the V-cycle
+ * result z by N(f - (K - sigma A) z); the FP64 FGMRES residual judges it.
+ * Weights: [W1 | W2 | W3], each W[a][b][c][cin][cout] (a along k, b along j,
+ * c along i), FP32. */
+dm_status dm_learned_create(dm_context* ctx, unsigned long long seed, dm_learned** out);
+void dm_learned_destroy(dm_learned* net);
+long long dm_learned_num_params(void);
+dm_status dm_learned_get_weights(const dm_learned* net, float* w);        /* host */
+dm_status dm_learned_set_weights(dm_learned* net, const float* w);        /* host */
+/* y = RMS(r) h^2 N(r / RMS(r), A, V) on the open faces of the geometry's fine grid
+ * (natural face layouts, host or device per on_device). */
+dm_status dm_learned_apply(dm_learned* net, const dm_geometry* geom, const double* r, double* y, int on_device);
+/* Masked MSE 0.5 sum_open (Y - E)^2 / #open and its gradient for explicit
+ * features X [(nz+1)(ny+1)(nx+1)][8] and targets E [...][3] (host, node order
+ * i fastest, channel last).  grad: host, dm_learned_num_params() floats. */
+dm_status dm_learned_loss_grad(dm_learned* net, const dm_geometry* geom, const float* X, const float* E, float* loss,
+                               float* grad);
+/* Train with Adam on (residual, error) pairs the operator's V-cycle produces:
+ * `runs` seeded random right-hand sides, 8 Krylov directions each; the error
+ * of each V-cycle result comes from an accurate shifted solve.  loss_history
+ * (nullable, host, epochs floats) receives the mean loss of every epoch. */
+dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epochs, float lr, unsigned long long seed,
+                           float* loss_history);
+/* Use (net) or stop using (NULL) the learned correction in op's preconditioner. */
+dm_status dm_operator_set_learned(dm_operator* op, const dm_learned* net);
+
+/* ---- batched eigensolves (many cavities and shifts; no counterpart in the paper) */
+
+/* One work item: a cavity (geometry) with one shift and mode count.  k2_out
+ * [params.nev] is host memory; b_out (nullable) is params.nev x F of that
+ * cavity, host or device per b_on_device.  report and status are outputs. */
+typedef struct dm_batch_item {
+    const dm_geometry* geom;
+    dm_eig_params params;
+    double* k2_out;
+    double* b_out;
+    int b_on_device;
+    dm_eig_report report;
+    int status;
+} dm_batch_item;
+
+/* Solve every item; `streams` worker streams (>= 1) take items largest-first,
+ * so the kernels of small cavities overlap on the GPU.  Each item's result is
+ * the same as dm_eigensolve on it.  Returns DM_OK when every item returned
+ * DM_OK, else the first non-OK item status (all items are still attempted).
+ * Geometries must not be destroyed or shared with other calls meanwhile. */
+dm_status dm_eigensolve_batched(dm_context* ctx, int n, dm_batch_item* items, int streams);
 
 /* Residual certificate of n given eigenpairs (b: n x F natural layout):
  * rho = ||K b - k2 A b|| / (k2 ||A b||), delta = ||D A b|| h / ||A b||,

@@ -18,7 +18,9 @@ import numpy as np
 from . import _lib
 from ._lib import EigParams, EigReport, MGParams, PREC, STATUS
 
-__all__ = ["Context", "Geometry", "Operator", "eigensolve", "certify", "DMError", "lib", "face_count",
+__all__ = ["Context", "Geometry", "Operator", "Learned", "eigensolve", "eigensolve_batched", "certify", "DMError",
+           "lib",
+           "face_count",
            "edge_count", "cell_count"]
 
 lib = _lib.load()
@@ -178,7 +180,7 @@ class Geometry:
             pass
 
 
-def mg_params(max_coarse=4, band_sweeps=8, omega_scale=1.7, power_iters=30, precision="f64"):
+def mg_params(max_coarse=4, band_sweeps=8, omega_scale=1.7, power_iters=30, precision="f64", autotune=1):
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -186,6 +188,7 @@ def mg_params(max_coarse=4, band_sweeps=8, omega_scale=1.7, power_iters=30, prec
     p.omega_scale = omega_scale
     p.power_iters = power_iters
     p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    p.autotune = int(autotune)
     return p
 
 
@@ -205,6 +208,9 @@ class Operator:
     @property
     def num_levels(self):
         return lib.dm_operator_num_levels(self.h)
+
+    def stencil_shape(self, level):
+        return lib.dm_operator_stencil_shape(self.h, level)
 
     def omega(self, level, scalar=False):
         return lib.dm_operator_get_omega(self.h, level, int(scalar))
@@ -280,6 +286,10 @@ class Operator:
         self.ctx.check(lib.dm_operator_project(self.h, a.ptr, yp, a.device, tol, C.byref(it)), "dm_operator_project")
         return y, it.value
 
+    def set_learned(self, net):
+        """Use (net) or stop using (None) the learned correction in the preconditioner."""
+        self.ctx.check(lib.dm_operator_set_learned(self.h, net.h if net is not None else None), "set_learned")
+
     def close(self):
         if getattr(self, "h", None):
             lib.dm_operator_destroy(self.h)
@@ -292,8 +302,65 @@ class Operator:
             pass
 
 
+class Learned:
+    """The learned smoother's network (3 conv layers, 8 -> 16 -> 16 -> 3 channels)."""
+
+    def __init__(self, ctx, seed=0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(lib.dm_learned_create(ctx.h, int(seed), C.byref(h)), "dm_learned_create")
+        self.h = h
+
+    @staticmethod
+    def num_params():
+        return lib.dm_learned_num_params()
+
+    def get_weights(self):
+        w = np.empty(self.num_params(), dtype=np.float32)
+        self.ctx.check(lib.dm_learned_get_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float))), "get_weights")
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.num_params()
+        self.ctx.check(lib.dm_learned_set_weights(self.h, w.ctypes.data_as(C.POINTER(C.c_float))), "set_weights")
+
+    def apply(self, geom, r):
+        a = _Arg(r, geom.level_info(0)["faces"])
+        y, yp = _out_like(a, geom.level_info(0)["faces"])
+        self.ctx.check(lib.dm_learned_apply(self.h, geom.h, a.ptr, yp, a.device), "dm_learned_apply")
+        return y
+
+    def loss_grad(self, geom, X, E):
+        fp = C.POINTER(C.c_float)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        E = np.ascontiguousarray(E, dtype=np.float32)
+        loss = C.c_float()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        self.ctx.check(lib.dm_learned_loss_grad(self.h, geom.h, X.ctypes.data_as(fp), E.ctypes.data_as(fp),
+                                                C.byref(loss), g.ctypes.data_as(fp)), "dm_learned_loss_grad")
+        return loss.value, g
+
+    def train(self, op, runs=4, epochs=20, lr=1e-3, seed=1):
+        hist = np.empty(epochs, dtype=np.float32)
+        self.ctx.check(lib.dm_learned_train(self.h, op.h, runs, epochs, lr, int(seed),
+                                            hist.ctypes.data_as(C.POINTER(C.c_float))), "dm_learned_train")
+        return hist
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.dm_learned_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
-               inner_restart=40, inner_maxit=400, seed=1301, **mg):
+               inner_restart=40, inner_maxit=400, seed=1301, learned=None, **mg):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     p.sigma = float(sigma)
@@ -307,6 +374,7 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.inner_maxit = inner_maxit
     p.seed = seed
     p.mg = mg_params(**mg)
+    p.learned = learned.h if learned is not None else None
     return p
 
 
@@ -336,6 +404,32 @@ def eigensolve(ctx, geom, sigma, nev, vectors="host", out=None, **kw):
         # DM_ERR_NO_CONVERGENCE with a filled report is a partial result; anything else is an error
         ctx.check(st, "dm_eigensolve")
     return k2, B, rep.as_dict(), st
+
+
+def eigensolve_batched(ctx, jobs, streams=8):
+    """Solve many (geometry, sigma, nev, options) jobs in one call.
+
+    jobs: list of dicts with keys geom, sigma, nev and optional eigensolve
+    options (precision, tol, ...).  Returns a list of (k2, report, status)."""
+    from ._lib import BatchItem
+    n = len(jobs)
+    arr = (BatchItem * n)()
+    keep = []
+    for i, job in enumerate(jobs):
+        opts = {k: v for k, v in job.items() if k not in ("geom", "sigma", "nev")}
+        p = eig_params(job["sigma"], job["nev"], **opts)
+        k2 = np.empty(job["nev"])
+        keep.append(k2)
+        arr[i].geom = job["geom"].h
+        arr[i].params = p
+        arr[i].k2_out = k2.ctypes.data_as(C.POINTER(C.c_double))
+        arr[i].b_out = None
+        arr[i].b_on_device = 0
+        arr[i].status = -1
+    st = lib.dm_eigensolve_batched(ctx.h, n, arr, int(streams))
+    if st not in (0, 2):
+        ctx.check(st, "dm_eigensolve_batched")
+    return [(keep[i], arr[i].report.as_dict(), arr[i].status) for i in range(n)]
 
 
 def certify(ctx, geom, k2, B):

@@ -24,7 +24,7 @@ COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # per-file extra flags: the geometry is compiled without FMA contraction so that
 # fraction sums (and the 0 < V < 1 band tests) round identically on every build
 EXTRA = {"dm_geometry.cu": ["-fmad=false"]}
-SOURCES = ["dm_geometry.cu", "dm_stencil.cu", "dm_transfer.cu", "dm_blas.cu", "dm_dense.cu", "dm_api.cu"]
+SOURCES = ["dm_geometry.cu", "dm_stencil.cu", "dm_transfer.cu", "dm_blas.cu", "dm_dense.cu", "dm_learned.cu", "dm_api.cu"]
 
 
 def nvcc():
@@ -44,7 +44,7 @@ def _stale(obj, deps):
 def build(verbose=False, force=False, jobs=None):
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, "dm_common.cuh"), os.path.join(INCLUDE, "dmeig.h")]
+    headers = [os.path.join(CSRC, "dm_common.cuh"), os.path.join(CSRC, "dm_learned.cuh"), os.path.join(INCLUDE, "dmeig.h")]
     cmds = []
     objs = []
     for src in SOURCES:

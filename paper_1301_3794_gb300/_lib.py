@@ -15,24 +15,30 @@ PREC = {"f64": 0, "f32": 1, "bf16": 2}
 
 class MGParams(C.Structure):
     _fields_ = [("max_coarse", C.c_int), ("band_sweeps", C.c_int), ("omega_scale", C.c_double),
-                ("power_iters", C.c_int), ("precision", C.c_int)]
+                ("power_iters", C.c_int), ("precision", C.c_int), ("autotune", C.c_int)]
 
 
 class EigParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("nev", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("proj_tol", C.c_double), ("basis", C.c_int), ("max_restarts", C.c_int),
                 ("inner_restart", C.c_int), ("inner_maxit", C.c_int), ("seed", C.c_ulonglong),
-                ("mg", MGParams)]
+                ("mg", MGParams), ("learned", C.c_void_p)]
 
 
 class EigReport(C.Structure):
     _fields_ = [("n_converged", C.c_int), ("outer_iters", C.c_int), ("restarts", C.c_int),
                 ("inner_iters", C.c_int), ("proj_iters", C.c_int), ("mg_levels", C.c_int),
                 ("mg_complexity", C.c_double), ("rho_max", C.c_double), ("delta_max", C.c_double),
-                ("setup_seconds", C.c_double), ("solve_seconds", C.c_double), ("kernel_launches", C.c_longlong)]
+                ("setup_seconds", C.c_double), ("solve_seconds", C.c_double), ("kernel_launches", C.c_longlong),
+                ("learned_applied", C.c_int), ("learned_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("geom", C.c_void_p), ("params", EigParams), ("k2_out", C.POINTER(C.c_double)),
+                ("b_out", C.c_void_p), ("b_on_device", C.c_int), ("report", EigReport), ("status", C.c_int)]
 
 
 _P = C.c_void_p
@@ -55,6 +61,7 @@ SIGNATURES = {
     "dm_operator_create": (C.c_int, [_P, _P, C.c_double, C.POINTER(MGParams), C.POINTER(_P)]),
     "dm_operator_destroy": (None, [_P]),
     "dm_operator_num_levels": (C.c_int, [_P]),
+    "dm_operator_stencil_shape": (C.c_int, [_P, C.c_int]),
     "dm_operator_get_omega": (C.c_double, [_P, C.c_int, C.c_int]),
     "dm_operator_set_omega": (C.c_int, [_P, C.c_int, C.c_int, C.c_double]),
     "dm_operator_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
@@ -70,6 +77,17 @@ SIGNATURES = {
     "dm_eig_params_default": (None, [C.POINTER(EigParams)]),
     "dm_eigensolve": (C.c_int, [_P, _P, C.POINTER(EigParams), _D, _P, C.c_int, C.POINTER(EigReport)]),
     "dm_certify": (C.c_int, [_P, _P, C.c_int, _D, _P, C.c_int, _D, _D, _D]),
+    "dm_eigensolve_batched": (C.c_int, [_P, C.c_int, C.POINTER(BatchItem), C.c_int]),
+    "dm_learned_create": (C.c_int, [_P, C.c_ulonglong, C.POINTER(_P)]),
+    "dm_learned_destroy": (None, [_P]),
+    "dm_learned_num_params": (C.c_longlong, []),
+    "dm_learned_get_weights": (C.c_int, [_P, C.POINTER(C.c_float)]),
+    "dm_learned_set_weights": (C.c_int, [_P, C.POINTER(C.c_float)]),
+    "dm_learned_apply": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "dm_learned_loss_grad": (C.c_int, [_P, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_float)]),
+    "dm_learned_train": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_float, C.c_ulonglong, C.POINTER(C.c_float)]),
+    "dm_operator_set_learned": (C.c_int, [_P, _P]),
 }
 
 

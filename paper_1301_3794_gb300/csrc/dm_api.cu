@@ -5,13 +5,19 @@
 // eigenproblem of Krylov--Schur); every vector operation runs in the kernels
 // of dm_geometry.cu, dm_stencil.cu, dm_transfer.cu, dm_blas.cu, dm_dense.cu.
 #include "dm_common.cuh"
+#include "dm_learned.cuh"
 
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <numeric>
+#include <random>
 
 namespace dm {
 
@@ -94,6 +100,8 @@ struct dm_context {
     long long launches = 0;
     Reducer red;
     Tracer tracer;
+    // autotuner cache: (nx, ny, nz, precision) -> stencil tile shape
+    std::vector<std::pair<std::array<int, 4>, int>> tuned;
 };
 
 namespace {
@@ -202,9 +210,15 @@ void jacobi_eig(int n, std::vector<double>& a, std::vector<double>& w, std::vect
 
 }  // namespace
 
+struct dm_learned {
+    dm_context* ctx = nullptr;
+    LearnedNet net;
+};
+
 struct dm_geometry {
     dm_context* ctx = nullptr;
     std::vector<std::unique_ptr<GeoLevel>> lv;
+    std::mutex mu;   // guards the lazily made FP32 coefficient copies
 };
 
 namespace {
@@ -221,6 +235,9 @@ struct OpLevel {
     DBuf<double> invDs;       // np
     DBuf<float> invDs32;
     double omega = 0.0, omega_s = 0.0;
+    int shape = 0;            // stencil tile shape (autotuned)
+    DBuf<int> stiles;         // active tiles of that shape (shape != 0)
+    int nstiles = 0;
 };
 
 struct Fgmres {
@@ -268,6 +285,11 @@ struct dm_operator {
     long long vexec_kernels = 0, sexec_kernels = 0;
     int vcalls = 0, scalls = 0;
     bool graphs = true;
+    // learned correction after the V-cycle (own copy of the network's weights and buffers)
+    std::unique_ptr<LearnedNet> lnet;
+    bool learned_active = false;
+    int learned_applied = 0, learned_fallbacks = 0;
+    long long nopen0 = 0;
     ~dm_operator() {
         if (vexec) cudaGraphExecDestroy(vexec);
         if (sexec) cudaGraphExecDestroy(sexec);
@@ -299,7 +321,8 @@ template <typename T, typename TC>
 VecOp<T, TC> vop(const dm_operator* op, int l) {
     const GeoLevel& g = glv(op, l);
     return VecOp<T, TC>{g.g, Pick<T, TC>::A(g), Pick<T, TC>::L(g), Pick<T, TC>::iV(g), Pick<T, TC>::iD(op->ol[l]),
-                        op->sigma, l, g.tiles.get(), g.ntiles};
+                        op->sigma, l, g.tiles.get(), g.ntiles,
+                        op->ol[l].shape ? op->ol[l].stiles.get() : nullptr, op->ol[l].nstiles, op->ol[l].shape};
 }
 template <typename T, typename TC>
 ScalOp<T, TC> sop(const dm_operator* op, int l) {
@@ -405,6 +428,25 @@ bool graphs_allowed(const dm_operator* op) {
     return op->graphs && !(g_tracer && g_tracer->on);
 }
 
+// z <- z + RMS(r) h^2 N(r / RMS(r), A, V) with r = f - (K - sigma A) z on the fine level
+template <typename T, typename TC>
+void learned_correct(dm_operator* op, const T* f, T* z, T* scratch) {
+    cudaStream_t s = op->ctx->stream;
+    const GeoLevel& g0 = glv(op, 0);
+    const VecOp<T, TC> o = vop<T, TC>(op, 0);
+    vec_stencil(o, ST_RESID, z, f, scratch, 0.0, s);
+    const double ss = sumsq<T>(3ll * g0.g.np, scratch, s);
+    if (!(ss > 0.0) || op->nopen0 <= 0) return;
+    const double scale = std::sqrt(ss / (double)op->nopen0);
+    const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+    LearnedNet& net = *op->lnet;
+    net.alloc(g0.g);
+    net.features(g0.A.get(), g0.V.get(), 1.0 / scale, scratch, prec_index<T>(), s);
+    net.forward(s);
+    net.add_correction<T>(g0.A.get(), scale * h * h, z, s);
+    ++op->learned_applied;
+}
+
 // z = M^-1 v on FP64 fine-level vectors: v is converted into the level-0 f
 // buffer, the V-cycle runs (as a graph after its first direct run), and the
 // result in the level-0 r buffer is converted into z.
@@ -428,6 +470,7 @@ void precond_vec_T(dm_operator* op, const double* v, double* z) {
         vcycle<T, TC>(op, 0, f, e, r);
     }
     ++op->vcalls;
+    if (op->lnet && op->learned_active) learned_correct<T, TC>(op, f, r, e);
     convert<double, T>(D, r, z, s);
 }
 
@@ -485,9 +528,14 @@ double norm2(dm_context* ctx, const Domain& D, const double* x, const double* w 
 
 // Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt
 // applied twice.  x is overwritten.  Returns the iteration count.
-template <class Apply, class Prec>
+struct NoMonitor {
+    void operator()(double) const {}
+};
+
+// monitor(ratio) is told the residual contraction of every iteration
+template <class Apply, class Prec, class Monitor = NoMonitor>
 int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Prec prec, const double* b, double* x,
-           double tol, int maxit, double* relres, double abs_tol = 0.0) {
+           double tol, int maxit, double* relres, double abs_tol = 0.0, Monitor monitor = Monitor()) {
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
     ws.ensure(n, m);
@@ -552,8 +600,10 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
             sn[j] = rr > 0 ? bb / rr : 0.0;
             H[(size_t)j * m + j] = rr;
             H[(size_t)(j + 1) * m + j] = 0.0;
+            const double gprev = std::fabs(g[j]);
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
+            if (gprev > 0.0) monitor(std::fabs(g[j + 1]) / gprev);
             ++total;
             jend = j;
             res = std::fabs(g[j + 1]) / bnorm;
@@ -587,7 +637,20 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
     auto prec = [op](const double* in, double* out) { precond_vec(op, in, out); };
-    return fgmres(op->ctx, op->vg, n, restart, apply, prec, b, x, tol, maxit, relres);
+    // the learned correction is judged by the FP64 residual: an iteration that
+    // contracts by less than 0.8 switches it off for the rest of the solve
+    op->learned_active = op->lnet != nullptr;
+    bool fell_back = false;
+    auto monitor = [op, &fell_back](double ratio) {
+        if (op->learned_active && ratio > 0.8) {
+            op->learned_active = false;
+            fell_back = true;
+        }
+    };
+    const int it = fgmres(op->ctx, op->vg, n, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
+    if (fell_back) ++op->learned_fallbacks;
+    op->learned_active = false;
+    return it;
 }
 
 // y = P_DM x (Eq. proj); x, y padded FP64 fine-level face vectors (may alias)
@@ -667,6 +730,70 @@ void invert_diag(long long n, const double* d, double* inv, cudaStream_t s) {
     launch("k_invert_diag", k_invert_diag, b, 256, 0, s, n, d, inv);
 }
 
+// Time the tiled Jacobi stencil of `level` for every tile shape and keep the
+// fastest (CUDA events on the context stream; 2 warm-up + 5 timed launches on
+// the level's work buffers).  Choices are cached in the context.
+template <typename T, typename TC>
+void autotune_level(dm_operator* op, int l) {
+    cudaStream_t s = op->ctx->stream;
+    GeoLevel& g = *const_cast<dm_geometry*>(op->geom)->lv[l];
+    OpLevel& o = op->ol[l];
+    const std::array<int, 4> key{g.g.nx, g.g.ny, g.g.nz, op->mg.precision};
+    for (const auto& kv : op->ctx->tuned)
+        if (kv.first == key) {
+            o.shape = kv.second;
+            break;
+        }
+    std::vector<DBuf<int>> lists(kStencilShapes);
+    std::vector<int> counts(kStencilShapes, 0);
+    DBuf<int> cnt(1);
+    for (int sh = 1; sh < kStencilShapes; ++sh) {
+        int sy, sz;
+        stencil_shape_dims(sh, sy, sz);
+        const int nt = ((g.g.nx + TX) / TX) * ((g.g.ny + sy) / sy) * ((g.g.nz + sz) / sz);
+        DBuf<int> flags(nt);
+        lists[sh].alloc(nt);
+        counts[sh] = geom_tiles_shape(g.g, sy, sz, g.A.get(), g.active.get(), lists[sh].get(), flags.get(), cnt.get(), s);
+    }
+    bool cached = false;
+    for (const auto& kv : op->ctx->tuned) cached |= kv.first == key;
+    if (!cached) {
+        WorkLevel& w = op->wk[l];
+        const T* x = reinterpret_cast<const T*>(w.e.get());
+        const T* f = reinterpret_cast<const T*>(w.f.get());
+        T* y = reinterpret_cast<T*>(w.r.get());
+        cudaEvent_t e0, e1;
+        DM_CUDA(cudaEventCreate(&e0));
+        DM_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int best_shape = 0;
+        for (int sh = 0; sh < kStencilShapes; ++sh) {
+            o.shape = sh;
+            o.nstiles = counts[sh];
+            VecOp<T, TC> vo = vop<T, TC>(op, l);
+            if (sh) vo.stiles = lists[sh].get();
+            for (int r = 0; r < 2; ++r) vec_stencil(vo, ST_JACOBI, x, f, y, 0.5, s);
+            DM_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 5; ++r) vec_stencil(vo, ST_JACOBI, x, f, y, 0.5, s);
+            DM_CUDA(cudaEventRecord(e1, s));
+            DM_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            DM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_shape = sh;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        o.shape = best_shape;
+        op->ctx->tuned.push_back({key, o.shape});
+    }
+    o.nstiles = counts[o.shape];
+    if (o.shape) o.stiles = std::move(lists[o.shape]);
+    zero(op->wk[l].r.get(), op->wk[l].r.n, s);
+}
+
 void setup_operator(dm_operator* op) {
     cudaStream_t s = op->ctx->stream;
     dm_geometry* geom = const_cast<dm_geometry*>(op->geom);
@@ -685,7 +812,11 @@ void setup_operator(dm_operator* op) {
     int max_band = 1;
     for (int l = 0; l < nl; ++l) {
         GeoLevel& g = *geom->lv[l];
-        if (lowp) ensure_f32(g, s);
+        if (lowp) {
+            std::lock_guard<std::mutex> lock(geom->mu);
+            ensure_f32(g, s);
+            Sync::stream(s);
+        }
         OpLevel& o = op->ol[l];
         const long long n3 = 3ll * g.g.np, n1 = g.g.np;
         DBuf<double> d(n3);
@@ -712,6 +843,15 @@ void setup_operator(dm_operator* op) {
         max_band = std::max(max_band, g.nband);
     }
     op->band_u.alloc((size_t)max_band);
+    if (op->mg.autotune) {
+        for (int l = 0; l + 1 < nl; ++l) {
+            switch (op->mg.precision) {
+                case DM_PREC_F64: autotune_level<double, double>(op, l); break;
+                case DM_PREC_F32: autotune_level<float, float>(op, l); break;
+                default: autotune_level<__nv_bfloat16, float>(op, l);
+            }
+        }
+    }
     {
         DBuf<int> cnt(1);
         long long tot = 0, fine = 0;
@@ -722,6 +862,7 @@ void setup_operator(dm_operator* op) {
             tot += c;
         }
         op->complexity = fine > 0 ? (double)tot / (double)fine : 1.0;
+        op->nopen0 = fine;
     }
     // Jacobi weights from the largest eigenvalue of D^-1 (K - sigma A)
     for (int l = 0; l + 1 < nl; ++l) {
@@ -1066,6 +1207,7 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->omega_scale = 1.7;
     p->power_iters = 30;
     p->precision = DM_PREC_F64;
+    p->autotune = 1;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1100,6 +1242,11 @@ void dm_operator_destroy(dm_operator* op) {
 }
 
 int dm_operator_num_levels(const dm_operator* op) { return op ? op->nlev : 0; }
+
+int dm_operator_stencil_shape(const dm_operator* op, int level) {
+    if (!op || level < 0 || level >= op->nlev) return -1;
+    return op->ol[level].shape;
+}
 
 double dm_operator_get_omega(const dm_operator* op, int level, int scalar) {
     if (!op || level < 0 || level >= op->nlev) return 0.0;
@@ -1296,6 +1443,7 @@ void dm_eig_params_default(dm_eig_params* p) {
     p->inner_maxit = 400;
     p->seed = 1301;
     dm_mg_params_default(&p->mg);
+    p->learned = nullptr;
 }
 
 }  // extern "C"
@@ -1383,6 +1531,10 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         const dm_status cs = dm_operator_create(ctx, geom, p.sigma, &p.mg, &op);
         if (cs != DM_OK) throw Error(cs, std::string("operator setup: ") + ctx->err);
         std::unique_ptr<dm_operator, void (*)(dm_operator*)> opg(op, dm_operator_destroy);
+        if (p.learned) {
+            const dm_status ls = dm_operator_set_learned(op, p.learned);
+            if (ls != DM_OK) throw Error(ls, std::string("learned: ") + ctx->err);
+        }
         LaunchScope scope(ctx);
         const double t_solve0 = now_s();
         const GeoLevel& g0 = glv(op, 0);
@@ -1519,9 +1671,284 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             report->setup_seconds = t_solve0 - t_setup0;
             report->solve_seconds = now_s() - t_solve0;
             report->kernel_launches = ctx->launches - launches0;
+            report->learned_applied = op->learned_applied;
+            report->learned_fallbacks = op->learned_fallbacks;
         }
     });
     return st != DM_OK ? st : conv;
+}
+
+// ---------------------------------------------------------------------------
+// learned smoother
+// ---------------------------------------------------------------------------
+
+dm_status dm_learned_create(dm_context* ctx, unsigned long long seed, dm_learned** out) {
+    if (!ctx || !out) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto net = std::make_unique<dm_learned>();
+    const dm_status st = guarded(ctx, [&] {
+        net->ctx = ctx;
+        net->net.init_params();
+        // He-normal initialisation (fan-in 27 * Cin); the last layer scaled by 0.1
+        std::mt19937_64 rng(seed);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        std::vector<float> w(LearnedNet::n_params());
+        auto fill = [&](size_t off, size_t n, int cin, double extra) {
+            const double sd = std::sqrt(2.0 / (27.0 * cin)) * extra;
+            for (size_t t = 0; t < n; ++t) w[off + t] = (float)(nd(rng) * sd);
+        };
+        fill(0, LearnedNet::n1(), LearnedNet::CIN_, 1.0);
+        fill(LearnedNet::off2(), LearnedNet::n2(), LearnedNet::HID, 1.0);
+        fill(LearnedNet::off3(), LearnedNet::n3(), LearnedNet::HID, 0.1);
+        DM_CUDA(cudaMemcpyAsync(net->net.W.get(), w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, ctx->stream));
+        Sync::stream(ctx->stream);
+    });
+    if (st != DM_OK) return st;
+    *out = net.release();
+    return DM_OK;
+}
+
+void dm_learned_destroy(dm_learned* net) {
+    if (!net) return;
+    if (net->ctx) cudaStreamSynchronize(net->ctx->stream);
+    delete net;
+}
+
+long long dm_learned_num_params(void) { return (long long)LearnedNet::n_params(); }
+
+dm_status dm_learned_get_weights(const dm_learned* net, float* w) {
+    if (!net || !w) return DM_ERR_INVALID_ARG;
+    return guarded(net->ctx, [&] {
+        DM_CUDA(cudaMemcpyAsync(w, net->net.W.get(), sizeof(float) * LearnedNet::n_params(), cudaMemcpyDeviceToHost,
+                                net->ctx->stream));
+        Sync::stream(net->ctx->stream);
+    });
+}
+
+dm_status dm_learned_set_weights(dm_learned* net, const float* w) {
+    if (!net || !w) return DM_ERR_INVALID_ARG;
+    return guarded(net->ctx, [&] {
+        DM_CUDA(cudaMemcpyAsync(net->net.W.get(), w, sizeof(float) * LearnedNet::n_params(), cudaMemcpyHostToDevice,
+                                net->ctx->stream));
+        Sync::stream(net->ctx->stream);
+        net->net.step = 0;
+        zero(net->net.M1.get(), sizeof(float) * LearnedNet::n_params(), net->ctx->stream);
+        zero(net->net.M2.get(), sizeof(float) * LearnedNet::n_params(), net->ctx->stream);
+    });
+}
+
+dm_status dm_learned_apply(dm_learned* net, const dm_geometry* geom, const double* r, double* y, int on_device) {
+    if (!net || !geom || !r || !y) return DM_ERR_INVALID_ARG;
+    return guarded(net->ctx, [&] {
+        dm_context* ctx = net->ctx;
+        cudaStream_t s = ctx->stream;
+        const GeoLevel& g0 = *geom->lv[0];
+        const long long n3 = 3ll * g0.g.np;
+        const size_t nf = (size_t)natural_faces(g0.g);
+        DBuf<double> rp(n3), yp(n3), tmp;
+        const double* d = nullptr;
+        stage_in(ctx, r, on_device, nf, tmp, &d);
+        pack_faces(g0.g, d, rp.get(), s);
+        launch("k_mask_open", k_mask_open, (int)std::min<long long>((n3 + 255) / 256, 1216), 256, 0, s, n3, g0.A.get(),
+               rp.get());
+        DBuf<int> cnt(1);
+        const long long nopen = count_positive(n3, g0.A.get(), cnt.get(), s);
+        const double ss = sumsq<double>(n3, rp.get(), s);
+        if (ss > 0.0 && nopen > 0) {
+            const double scale = std::sqrt(ss / (double)nopen);
+            const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+            net->net.alloc(g0.g);
+            net->net.features(g0.A.get(), g0.V.get(), 1.0 / scale, rp.get(), 0, s);
+            net->net.forward(s);
+            net->net.add_correction<double>(g0.A.get(), scale * h * h, yp.get(), s);
+        }
+        if (on_device) {
+            unpack_faces(g0.g, yp.get(), y, s);
+            Sync::stream(s);
+        } else {
+            DBuf<double> t(nf, false);
+            unpack_faces(g0.g, yp.get(), t.get(), s);
+            stage_out(ctx, t.get(), y, 0, nf);
+        }
+    });
+}
+
+dm_status dm_learned_loss_grad(dm_learned* net, const dm_geometry* geom, const float* X, const float* E, float* loss,
+                               float* grad) {
+    if (!net || !geom || !X || !E) return DM_ERR_INVALID_ARG;
+    return guarded(net->ctx, [&] {
+        dm_context* ctx = net->ctx;
+        cudaStream_t s = ctx->stream;
+        const GeoLevel& g0 = *geom->lv[0];
+        const size_t nn = (size_t)(g0.g.nx + 1) * (g0.g.ny + 1) * (g0.g.nz + 1);
+        DBuf<float> xd(nn * LearnedNet::CIN_, false), ed(nn * LearnedNet::COUT_, false);
+        DM_CUDA(cudaMemcpyAsync(xd.get(), X, sizeof(float) * nn * LearnedNet::CIN_, cudaMemcpyHostToDevice, s));
+        DM_CUDA(cudaMemcpyAsync(ed.get(), E, sizeof(float) * nn * LearnedNet::COUT_, cudaMemcpyHostToDevice, s));
+        LearnedNet& L = net->net;
+        L.alloc(g0.g);
+        L.set_X(xd.get(), s);
+        L.set_E(ed.get(), s);
+        L.forward(s);
+        DBuf<int> cnt(1);
+        const long long nopen = count_positive(3ll * g0.g.np, g0.A.get(), cnt.get(), s);
+        const float l = L.loss(g0.A.get(), (double)nopen, s);
+        L.backward(s);
+        if (loss) *loss = l;
+        if (grad) {
+            DM_CUDA(cudaMemcpyAsync(grad, L.G.get(), sizeof(float) * LearnedNet::n_params(), cudaMemcpyDeviceToHost, s));
+        }
+        Sync::stream(s);
+    });
+}
+
+dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epochs, float lr, unsigned long long seed,
+                           float* loss_history) {
+    if (!net || !op || runs < 1 || epochs < 1 || !(lr > 0.f)) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        dm_context* ctx = op->ctx;
+        cudaStream_t s = ctx->stream;
+        const GeoLevel& g0 = glv(op, 0);
+        const Domain D = g0.vdom();
+        const long long n3 = D.len();
+        const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+        // 1. (residual, error) pairs: for Krylov directions v of FGMRES-like
+        //    sequences, z = V-cycle(v), r = v - (K - sigma A) z, e = (K - sigma A)^-1 r
+        const int dirs = 8;
+        std::vector<DBuf<float>> R, Eg;
+        std::vector<double> scales;
+        DBuf<double> v((size_t)(dirs + 1) * n3), z(n3), r(n3), e(n3);
+        const bool had = op->lnet != nullptr;
+        std::unique_ptr<LearnedNet> keep = std::move(op->lnet);   // plain V-cycle while sampling
+        for (int run = 0; run < runs; ++run) {
+            fill_random(D, seed + 7919ull * run, g0.A.get(), v.get(), s);
+            double nv = norm2(ctx, D, v.get());
+            scale_copy(D, 1.0 / nv, v.get(), v.get(), s);
+            for (int j = 0; j < dirs; ++j) {
+                double* vj = v.get() + (size_t)j * n3;
+                precond_vec(op, vj, z.get());
+                apply_vec64(op, 0, z.get(), r.get());          // r = (K - sigma A) z
+                axpby(D, 1.0, vj, -1.0, r.get(), s);          // r = v - (K - sigma A) z
+                double rr = 0.0;
+                solve_vec(op, r.get(), e.get(), 1e-6, 40, 200, &rr);
+                const double rs = std::sqrt(sumsq<double>(n3, r.get(), s) / (double)std::max(op->nopen0, 1ll));
+                if (rs > 0.0) {
+                    R.emplace_back(n3);
+                    Eg.emplace_back(n3);
+                    convert<float, double>(D, r.get(), R.back().get(), s);
+                    convert<float, double>(D, e.get(), Eg.back().get(), s);
+                    scales.push_back(rs);
+                }
+                // next direction: (K - sigma A) z orthonormalised against the previous ones
+                double* w = v.get() + (size_t)(j + 1) * n3;
+                apply_vec64(op, 0, z.get(), w);
+                std::vector<double> hh(j + 1);
+                mdot(ctx->red, D, j + 1, v.get(), n3, w, nullptr, hh.data(), s);
+                maxpy(ctx->red, D, j + 1, v.get(), n3, hh.data(), w, s);
+                const double nw = norm2(ctx, D, w);
+                if (!(nw > 0.0)) break;
+                scale_copy(D, 1.0 / nw, w, w, s);
+            }
+        }
+        op->lnet = std::move(keep);
+        (void)had;
+        DM_REQUIRE(!R.empty(), DM_ERR_NO_CONVERGENCE, "learned training: no samples");
+        // 2. Adam on the masked MSE, samples in a seeded order every epoch
+        LearnedNet& L = net->net;
+        L.alloc(g0.g);
+        std::mt19937_64 rng(seed ^ 0x5bd1e995ull);
+        std::vector<int> order(R.size());
+        std::iota(order.begin(), order.end(), 0);
+        for (int ep = 0; ep < epochs; ++ep) {
+            std::shuffle(order.begin(), order.end(), rng);
+            double tot = 0.0;
+            for (int k : order) {
+                L.features(g0.A.get(), g0.V.get(), 1.0 / scales[k], R[k].get(), 1, s);
+                L.target_from(Eg[k].get(), g0.A.get(), 1.0 / (scales[k] * h * h), s);
+                L.forward(s);
+                tot += L.loss(g0.A.get(), (double)op->nopen0, s);
+                L.backward(s);
+                L.adam(lr, s);
+            }
+            if (loss_history) loss_history[ep] = (float)(tot / (double)order.size());
+        }
+        Sync::stream(s);
+    });
+}
+
+dm_status dm_operator_set_learned(dm_operator* op, const dm_learned* net) {
+    if (!op) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        if (!net) {
+            op->lnet.reset();
+            return;
+        }
+        auto ln = std::make_unique<LearnedNet>();
+        ln->init_params();
+        DM_CUDA(cudaMemcpyAsync(ln->W.get(), net->net.W.get(), sizeof(float) * LearnedNet::n_params(),
+                                cudaMemcpyDeviceToDevice, op->ctx->stream));
+        ln->alloc(glv(op, 0).g);
+        Sync::stream(op->ctx->stream);
+        op->lnet = std::move(ln);
+    });
+}
+
+dm_status dm_eigensolve_batched(dm_context* ctx, int n, dm_batch_item* items, int streams) {
+    if (!ctx || n < 0 || (n > 0 && !items) || streams < 1) return DM_ERR_INVALID_ARG;
+    if (n == 0) return DM_OK;
+    // largest work first: faces x modes
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    auto work = [&](int i) -> double {
+        const dm_geometry* g = items[i].geom;
+        if (!g || g->lv.empty()) return 0.0;
+        return (double)natural_faces(g->lv[0]->g) * std::max(1, items[i].params.nev);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    const int nw = std::min(streams, n);
+    std::vector<dm_context*> sub(nw, nullptr);
+    for (int w = 0; w < nw; ++w) {
+        const dm_status st = dm_context_create(ctx->device, nullptr, &sub[w]);
+        if (st != DM_OK) {
+            for (int u = 0; u < w; ++u) dm_context_destroy(sub[u]);
+            ctx->err = "batched: cannot create worker stream";
+            return st;
+        }
+        sub[w]->tuned = ctx->tuned;
+    }
+    std::atomic<int> next{0};
+    auto worker = [&](int w) {
+        cudaSetDevice(ctx->device);
+        while (true) {
+            const int k = next.fetch_add(1);
+            if (k >= n) break;
+            dm_batch_item& it = items[order[k]];
+            if (!it.geom || !it.k2_out) {
+                it.status = DM_ERR_INVALID_ARG;
+                continue;
+            }
+            it.status = dm_eigensolve(sub[w], it.geom, &it.params, it.k2_out, it.b_out, it.b_on_device, &it.report);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(worker, w);
+    worker(0);
+    for (auto& t : pool) t.join();
+    dm_status first = DM_OK;
+    std::string msg;
+    for (int w = 0; w < nw; ++w) {
+        ctx->launches += sub[w]->launches;
+        if (msg.empty() && !sub[w]->err.empty()) msg = sub[w]->err;
+        for (const auto& kv : sub[w]->tuned) {
+            bool have = false;
+            for (const auto& c : ctx->tuned) have |= c.first == kv.first;
+            if (!have) ctx->tuned.push_back(kv);
+        }
+        dm_context_destroy(sub[w]);
+    }
+    for (int i = 0; i < n; ++i)
+        if (items[i].status != DM_OK && first == DM_OK) first = (dm_status)items[i].status;
+    ctx->err = msg;
+    return first;
 }
 
 dm_status dm_certify(dm_context* ctx, const dm_geometry* geom, int n, const double* k2, const double* b, int on_device,

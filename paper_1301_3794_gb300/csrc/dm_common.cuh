@@ -276,7 +276,11 @@ struct VecOp {
     int level = 0;   // multigrid level (names the kernel in traces: fine vs coarse)
     const int* tiles = nullptr;   // active tiles of the level (nullptr: whole grid)
     int ntiles = 0;
-    int shape = 0;                // tile shape of `tiles` for the vector stencil (see stencil_shape_dims)
+    // tile list and shape used by the tiled vector stencil (chosen by the
+    // autotuner; by default the 32x4x2 active tiles above)
+    const int* stiles = nullptr;
+    int nstiles = 0;
+    int shape = 0;
 };
 // tile shapes of the tiled vector stencil: TX x SY x SZ with (SY, SZ) = (4,2), (2,4), (8,1)
 constexpr int kStencilShapes = 3;

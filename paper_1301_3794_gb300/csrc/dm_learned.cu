@@ -1,0 +1,416 @@
+// Learned smoother: a 3-layer 3x3x3 convolutional network on the node grid of
+// the fine level (a design of this library; the paper has no learned part).
+//
+//   H1 = relu(conv(X, W1)),  H2 = relu(conv(H1, W2)),  Y = conv(H2, W3)
+//
+// conv is a zero-padded 3x3x3 cross-correlation without bias:
+//   conv(X, W)[p, o] = sum_{a,b,c} sum_q W[a,b,c,q,o] X[p + (c-1, b-1, a-1), q]
+// (a along k, b along j, c along i).  X has 8 channels: the residual on the
+// node's x, y, z faces divided by its RMS, the face fractions A_x, A_y, A_z,
+// the cell fraction V, and a zero channel.  Y has 3 channels: the predicted
+// error on the node's faces in units of RMS(r) * h^2.
+//
+// Activations are BF16, channel-last ([np][C]) on the padded node grid (the
+// ghost layer gives the zero padding); weights, accumulation, losses and the
+// optimiser state are FP32.  The weight gradient is reduced in a fixed order
+// (per-block partials, then a column sum), so training is deterministic.
+#include "dm_common.cuh"
+
+#include "dm_learned.cuh"
+
+#include <atomic>
+#include <cmath>
+
+namespace dm {
+
+namespace {
+
+constexpr int LX = TX, LY = TY, LZ = TZ;                 // output tile (one block)
+constexpr int HX = LX + 2, HY = LY + 2, HZ = LZ + 2;     // input tile with halo
+constexpr int NHALO = HX * HY * HZ;
+
+template <typename T> __device__ __forceinline__ float ldf(const T* p) { return to_c(*p); }
+__device__ __forceinline__ float ldf(const float* p) { return *p; }
+
+// Generic conv over the node grid, one 32 x 4 x 2 output tile per block.
+// in: [np][CIN] (TIN), W: [27][CIN][COUT] fp32 (flip = 1 uses W[26 - o][co][ci]
+// transposed, the adjoint of the forward conv), out: [np][COUT] (TOUT).
+// relu_mask (nullable, [np][COUT] bf16): zero the output where mask <= 0
+// (backward through a relu); relu_out: apply relu to the output.
+template <int CIN, int COUT, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(LX * LY * LZ) k_conv(Grid3 g, const TIN* __restrict__ in, const float* __restrict__ W,
+                                                       int flip, int relu_out, const __nv_bfloat16* __restrict__ relu_mask,
+                                                       TOUT* __restrict__ out) {
+    extern __shared__ float smem[];
+    float* w_s = smem;                                     // 27 * CIN * COUT
+    float* in_s = smem + 27 * CIN * COUT;                  // NHALO * CIN
+    const int tid = threadIdx.x + LX * (threadIdx.y + LY * threadIdx.z);
+    for (int e = tid; e < 27 * CIN * COUT; e += LX * LY * LZ) {
+        const int o = e / (CIN * COUT), rem = e % (CIN * COUT), ci = rem / COUT, co = rem % COUT;
+        // forward: W[o][ci][co]; adjoint: the input of this conv is dY (COUT = original CIN ...):
+        // out[q][ci'] = sum_o sum_co' W[o][ci'][co'] dY[q - off(o)][co'] = sum_o' W[26 - o'][ci'][co'] dY[q + off(o')][co']
+        w_s[e] = flip ? W[(size_t)(26 - o) * CIN * COUT + (size_t)co * CIN + ci] : W[e];
+    }
+    int i0, j0, k0;
+    i0 = blockIdx.x * LX;
+    j0 = blockIdx.y * LY;
+    k0 = blockIdx.z * LZ;
+    for (int e = tid; e < NHALO; e += LX * LY * LZ) {
+        const int li = e % HX, lj = (e / HX) % HY, lk = e / (HX * HY);
+        const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
+        const bool inside = i >= -1 && j >= -1 && k >= -1 && i <= g.nx + 1 && j <= g.ny + 1 && k <= g.nz + 1;
+        const int p = inside ? g.idx(i, j, k) : 0;
+#pragma unroll
+        for (int c = 0; c < CIN; ++c) in_s[e * CIN + c] = inside ? ldf(in + (size_t)p * CIN + c) : 0.f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    float acc[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float* xin = in_s + ((tz + a) * HY * HX + (ty + b) * HX + (tx + c)) * CIN;
+                const float* wo = w_s + (a * 9 + b * 3 + c) * CIN * COUT;
+#pragma unroll
+                for (int ci = 0; ci < CIN; ++ci) {
+                    const float v = xin[ci];
+#pragma unroll
+                    for (int co = 0; co < COUT; ++co) acc[co] += v * wo[ci * COUT + co];
+                }
+            }
+    const int p = g.idx(i, j, k);
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) {
+        float v = acc[co];
+        if (relu_out) v = fmaxf(v, 0.f);
+        if (relu_mask && !(to_c(relu_mask[(size_t)p * COUT + co]) > 0.f)) v = 0.f;
+        out[(size_t)p * COUT + co] = to_store<TOUT>(v);
+    }
+}
+
+// Weight gradient partials: part[b][o][ci][co] = sum over the tiles of block b
+// of X[p + off(o)][ci] * dY[p][co].  Blocks take tiles (dense tile index)
+// b, b + G, ... so the reduction order is fixed.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_conv_dw(Grid3 g, const __nv_bfloat16* __restrict__ X,
+                                                 const __nv_bfloat16* __restrict__ dY, float* __restrict__ part) {
+    extern __shared__ float smem[];
+    constexpr int NW = 27 * CIN * COUT;
+    float* x_s = smem;                          // NHALO * CIN
+    float* dy_s = smem + NHALO * CIN;           // LX*LY*LZ * COUT
+    float* acc_s = dy_s + LX * LY * LZ * COUT;  // NW: this block's partial (entry w owned by thread w % 256)
+    const int tid = threadIdx.x;
+    for (int w = tid; w < NW; w += 256) acc_s[w] = 0.f;
+    const int ntx = (g.nx + LX) / LX, nty = (g.ny + LY) / LY, ntz = (g.nz + LZ) / LZ;
+    const int ntot = ntx * nty * ntz;
+    for (int t = blockIdx.x; t < ntot; t += gridDim.x) {
+        const int i0 = (t % ntx) * LX, j0 = ((t / ntx) % nty) * LY, k0 = (t / (ntx * nty)) * LZ;
+        __syncthreads();
+        for (int e = tid; e < NHALO; e += 256) {
+            const int li = e % HX, lj = (e / HX) % HY, lk = e / (HX * HY);
+            const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
+            const bool inside = i >= -1 && j >= -1 && k >= -1 && i <= g.nx + 1 && j <= g.ny + 1 && k <= g.nz + 1;
+            const int p = inside ? g.idx(i, j, k) : 0;
+#pragma unroll
+            for (int c = 0; c < CIN; ++c) x_s[e * CIN + c] = inside ? to_c(X[(size_t)p * CIN + c]) : 0.f;
+        }
+        for (int e = tid; e < LX * LY * LZ; e += 256) {
+            const int li = e % LX, lj = (e / LX) % LY, lk = e / (LX * LY);
+            const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+            const bool valid = i <= g.nx && j <= g.ny && k <= g.nz;
+            const int p = valid ? g.idx(i, j, k) : 0;
+#pragma unroll
+            for (int c = 0; c < COUT; ++c) dy_s[e * COUT + c] = valid ? to_c(dY[(size_t)p * COUT + c]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int w = tid; w < NW; w += 256) {
+            const int o = w / (CIN * COUT), rem = w % (CIN * COUT), ci = rem / COUT, co = rem % COUT;
+            const int a = o / 9, b = (o / 3) % 3, c = o % 3;
+            float s = 0.f;
+            for (int lk = 0; lk < LZ; ++lk)
+                for (int lj = 0; lj < LY; ++lj) {
+                    const float* xr = x_s + ((lk + a) * HY * HX + (lj + b) * HX + c) * CIN + ci;
+                    const float* dr = dy_s + ((lk * LY + lj) * LX) * COUT + co;
+#pragma unroll 8
+                    for (int li = 0; li < LX; ++li) s += xr[li * CIN] * dr[li * COUT];
+                }
+            acc_s[w] += s;
+        }
+    }
+    __syncthreads();
+    for (int w = tid; w < NW; w += 256) part[(size_t)blockIdx.x * NW + w] = acc_s[w];
+}
+
+// column sums of part[nb][n] in block order
+__global__ void k_colsum(const float* __restrict__ part, int nb, int n, float* __restrict__ out) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * n + w];
+    out[w] = s;
+}
+
+// input features of every node: residual / scale on the three faces, A_x, A_y, A_z, V, 0
+template <typename T>
+__global__ void k_features(Grid3 g, const T* __restrict__ r, const double* __restrict__ A, const double* __restrict__ V,
+                           double inv_scale, __nv_bfloat16* __restrict__ X) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    __nv_bfloat16* x = X + (size_t)p * 8;
+    for (int c = 0; c < 3; ++c) {
+        const double a = A[c * g.np + p];
+        x[c] = __float2bfloat16(a > 0.0 ? (float)(to_c(r[c * g.np + p]) * inv_scale) : 0.f);
+        x[3 + c] = __float2bfloat16((float)a);
+    }
+    x[6] = __float2bfloat16((float)V[p]);
+    x[7] = __float2bfloat16(0.f);
+}
+
+// z += scale * Y on the open faces (Y: [np][3] fp32)
+template <typename T>
+__global__ void k_add_correction(Grid3 g, const float* __restrict__ Y, const double* __restrict__ A, double scale,
+                                 T* __restrict__ z) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    for (int c = 0; c < 3; ++c) {
+        const int q = c * g.np + p;
+        if (A[q] > 0.0) z[q] = to_store<T>((float)(to_c(z[q]) + scale * (double)Y[(size_t)p * 3 + c]));
+    }
+}
+
+// loss = 0.5 sum M (Y - E)^2 / sum M (block partials) and dY = M (Y - E) / sum M (bf16)
+__global__ void k_mse(Grid3 g, const float* __restrict__ Y, const float* __restrict__ E, const double* __restrict__ A,
+                      float inv_msum, __nv_bfloat16* __restrict__ dY, float* __restrict__ part) {
+    __shared__ float red[256];
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    const int tid = threadIdx.x + LX * (threadIdx.y + LY * threadIdx.z);
+    float l = 0.f;
+    if (i <= g.nx && j <= g.ny && k <= g.nz) {
+        const int p = g.idx(i, j, k);
+        for (int c = 0; c < 3; ++c) {
+            const float m = A[c * g.np + p] > 0.0 ? 1.f : 0.f;
+            const float d = m * (Y[(size_t)p * 3 + c] - E[(size_t)p * 3 + c]);
+            l += 0.5f * d * d;
+            dY[(size_t)p * 3 + c] = __float2bfloat16(d * inv_msum);
+        }
+    }
+    red[tid] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = red[0] * inv_msum;
+}
+
+__global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ grad, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float gr = grad[t];
+    const float mt = b1 * m[t] + (1.f - b1) * gr;
+    const float vt = b2 * v[t] + (1.f - b2) * gr * gr;
+    m[t] = mt;
+    v[t] = vt;
+    w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+}
+
+// channel-last natural node array (i fastest) -> padded node grid
+template <typename TOUT>
+__global__ void k_pack_nodes_ch(Grid3 g, int C, const float* __restrict__ nat, TOUT* __restrict__ pad) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const long long n = i + (long long)(g.nx + 1) * (j + (long long)(g.ny + 1) * k);
+    const int p = g.idx(i, j, k);
+    for (int c = 0; c < C; ++c) pad[(size_t)p * C + c] = to_store<TOUT>(nat[n * C + c]);
+}
+
+// training target: E[p][c] = e_c[p] * inv on open faces (e: padded fp32 face vector)
+__global__ void k_target(Grid3 g, const float* __restrict__ e, const double* __restrict__ A, double inv,
+                         float* __restrict__ E) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    for (int c = 0; c < 3; ++c) {
+        const int q = c * g.np + p;
+        E[(size_t)p * 3 + c] = A[q] > 0.0 ? (float)(e[q] * inv) : 0.f;
+    }
+}
+
+// block partials of sum x^2 over a padded face vector of any storage type
+template <typename T>
+__global__ void k_sumsq(long long n, const T* __restrict__ x, double* __restrict__ part) {
+    __shared__ double red[256];
+    double a = 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const double v = (double)to_c(x[r]);
+        a += v * v;
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_sum_d(const double* __restrict__ part, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += part[b];
+        *out = s;
+    }
+}
+
+inline dim3 node_blocks(const Grid3& g) {
+    return dim3((g.nx + LX) / LX, (g.ny + LY) / LY, (g.nz + LZ) / LZ);
+}
+
+template <int CIN, int COUT, typename TIN, typename TOUT>
+void conv_launch(const Grid3& g, const TIN* in, const float* W, int flip, int relu_out, const __nv_bfloat16* mask,
+                 TOUT* out, cudaStream_t s) {
+    const size_t sm = sizeof(float) * (27 * CIN * COUT + NHALO * CIN);
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load()) {
+        DM_CUDA(cudaFuncSetAttribute(k_conv<CIN, COUT, TIN, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set.store(true);
+    }
+    launch("conv_fwd", k_conv<CIN, COUT, TIN, TOUT>, node_blocks(g), dim3(LX, LY, LZ), sm, s, g, in, W, flip, relu_out,
+           mask, out);
+}
+
+template <int CIN, int COUT>
+void conv_dw_launch(const Grid3& g, const __nv_bfloat16* X, const __nv_bfloat16* dY, float* part, float* dW, int nb,
+                    cudaStream_t s) {
+    const size_t sm = sizeof(float) * (NHALO * CIN + LX * LY * LZ * COUT + 27 * CIN * COUT);
+    static std::atomic<bool> attr_set{false};
+    if (!attr_set.load()) {
+        DM_CUDA(cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set.store(true);
+    }
+    launch("conv_dw", k_conv_dw<CIN, COUT>, nb, 256, sm, s, g, X, dY, part);
+    const int n = 27 * CIN * COUT;
+    launch("conv_dw_sum", k_colsum, (n + 255) / 256, 256, 0, s, part, nb, n, dW);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+void LearnedNet::alloc(const Grid3& grid) {
+    if (g.np == grid.np && g.nx == grid.nx && g.ny == grid.ny && g.nz == grid.nz && X.get()) return;
+    g = grid;
+    const size_t np = (size_t)g.np;
+    X.alloc(np * CIN_);
+    H1.alloc(np * HID);
+    H2.alloc(np * HID);
+    Y.alloc(np * COUT_);
+    dY.alloc(np * COUT_);
+    dH1.alloc(np * HID);
+    dH2.alloc(np * HID);
+    E.alloc(np * COUT_);
+    const dim3 nb = node_blocks(g);
+    loss_part.alloc((size_t)nb.x * nb.y * nb.z);
+    dw_part.alloc((size_t)kDwBlocks * 27 * HID * HID);
+}
+
+void LearnedNet::init_params() {
+    W.alloc(n_params());
+    G.alloc(n_params());
+    M1.alloc(n_params());
+    M2.alloc(n_params());
+}
+
+void LearnedNet::features(const double* A, const double* V, double inv_scale, const void* r, int r_prec,
+                          cudaStream_t s) {
+    const dim3 nb = node_blocks(g);
+    if (r_prec == 0)
+        launch("learned_features", k_features<double>, nb, dim3(LX, LY, LZ), 0, s, g, (const double*)r, A, V, inv_scale, X.get());
+    else if (r_prec == 1)
+        launch("learned_features", k_features<float>, nb, dim3(LX, LY, LZ), 0, s, g, (const float*)r, A, V, inv_scale, X.get());
+    else
+        launch("learned_features", k_features<__nv_bfloat16>, nb, dim3(LX, LY, LZ), 0, s, g, (const __nv_bfloat16*)r, A,
+               V, inv_scale, X.get());
+}
+
+void LearnedNet::forward(cudaStream_t s) {
+    conv_launch<CIN_, HID, __nv_bfloat16, __nv_bfloat16>(g, X.get(), w1(), 0, 1, nullptr, H1.get(), s);
+    conv_launch<HID, HID, __nv_bfloat16, __nv_bfloat16>(g, H1.get(), w2(), 0, 1, nullptr, H2.get(), s);
+    conv_launch<HID, COUT_, __nv_bfloat16, float>(g, H2.get(), w3(), 0, 0, nullptr, Y.get(), s);
+}
+
+void LearnedNet::backward(cudaStream_t s) {
+    // dW3 = dW(H2, dY); dH2 = conv^T(dY, W3) * (H2 > 0); dW2 = dW(H1, dH2); dH1 = conv^T(dH2, W2) * (H1 > 0);
+    // dW1 = dW(X, dH1)
+    conv_dw_launch<HID, COUT_>(g, H2.get(), dY.get(), dw_part.get(), G.get() + off3(), kDwBlocks, s);
+    conv_launch<COUT_, HID, __nv_bfloat16, __nv_bfloat16>(g, dY.get(), w3(), 1, 0, H2.get(), dH2.get(), s);
+    conv_dw_launch<HID, HID>(g, H1.get(), dH2.get(), dw_part.get(), G.get() + off2(), kDwBlocks, s);
+    conv_launch<HID, HID, __nv_bfloat16, __nv_bfloat16>(g, dH2.get(), w2(), 1, 0, H1.get(), dH1.get(), s);
+    conv_dw_launch<CIN_, HID>(g, X.get(), dH1.get(), dw_part.get(), G.get(), kDwBlocks, s);
+}
+
+float LearnedNet::loss(const double* A, double msum, cudaStream_t s) {
+    const dim3 nb = node_blocks(g);
+    launch("learned_mse", k_mse, nb, dim3(LX, LY, LZ), 0, s, g, Y.get(), E.get(), A, (float)(1.0 / std::max(msum, 1.0)),
+           dY.get(), loss_part.get());
+    const int n = nb.x * nb.y * nb.z;
+    DBuf<float> tot(1);
+    launch("learned_mse_sum", k_colsum, 1, 256, 0, s, loss_part.get(), n, 1, tot.get());
+    float h = 0.f;
+    DM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof(float), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+void LearnedNet::adam(float lr, cudaStream_t s) {
+    ++step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)step), c2 = 1.f - std::pow(b2, (float)step);
+    const int n = (int)n_params();
+    launch("learned_adam", k_adam, (n + 255) / 256, 256, 0, s, n, W.get(), G.get(), M1.get(), M2.get(), lr, b1, b2,
+           1e-8f, c1, c2);
+}
+
+void LearnedNet::set_X(const float* nat_dev, cudaStream_t s) {
+    launch("learned_pack", k_pack_nodes_ch<__nv_bfloat16>, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, CIN_, nat_dev,
+           X.get());
+}
+void LearnedNet::set_E(const float* nat_dev, cudaStream_t s) {
+    launch("learned_pack", k_pack_nodes_ch<float>, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, COUT_, nat_dev, E.get());
+}
+void LearnedNet::target_from(const float* e_pad, const double* A, double inv, cudaStream_t s) {
+    launch("learned_target", k_target, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, e_pad, A, inv, E.get());
+}
+
+template <typename T>
+double sumsq(long long n, const T* x, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 4));
+    DBuf<double> part(nb), out(1);
+    launch("learned_sumsq", k_sumsq<T>, nb, 256, 0, s, n, x, part.get());
+    launch("learned_sumsq", k_sum_d, 1, 32, 0, s, part.get(), nb, out.get());
+    double h = 0.0;
+    DM_CUDA(cudaMemcpyAsync(&h, out.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+template double sumsq<double>(long long, const double*, cudaStream_t);
+template double sumsq<float>(long long, const float*, cudaStream_t);
+template double sumsq<__nv_bfloat16>(long long, const __nv_bfloat16*, cudaStream_t);
+
+template <typename T>
+void LearnedNet::add_correction(const double* A, double scale, T* z, cudaStream_t s) {
+    launch("learned_correct", k_add_correction<T>, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, Y.get(), A, scale, z);
+}
+template void LearnedNet::add_correction<double>(const double*, double, double*, cudaStream_t);
+template void LearnedNet::add_correction<float>(const double*, double, float*, cudaStream_t);
+template void LearnedNet::add_correction<__nv_bfloat16>(const double*, double, __nv_bfloat16*, cudaStream_t);
+
+}  // namespace dm

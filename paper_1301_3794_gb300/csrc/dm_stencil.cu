@@ -18,6 +18,8 @@
 #include "dm_common.cuh"
 
 #include <cooperative_groups.h>
+#include <atomic>
+#include <mutex>
 #include <set>
 
 namespace dm {
@@ -495,8 +497,11 @@ __global__ void k_sub_grad(Grid3 g, const double* __restrict__ A, const double* 
 }  // namespace
 
 const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
-    // interned names: a node-based set keeps every c_str() pointer stable
+    // interned names: a node-based set keeps every c_str() pointer stable;
+    // batched solves call this from several host threads
     static std::set<std::string>* names = new std::set<std::string>();
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     static const char* precs[3] = {"f64", "f32", "bf16"};
     static const char* modes[3] = {"apply", "resid", "jacobi"};
     const std::string n = std::string(kind) + "_" + precs[prec] + "_" + modes[mode] + (fine ? "_L0" : "_Lc");
@@ -507,15 +512,17 @@ template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
     if (op.tiles) {
-        if (op.ntiles <= 0) return;
+        const int* tl = op.stiles ? op.stiles : op.tiles;
+        const int nt = op.stiles ? op.nstiles : op.ntiles;
+        if (nt <= 0) return;
         const char* nm = stencil_name("vec_stencil", prec_index<T>(), mode, op.level == 0);
         // tile shape: 0 = 32x4x2 (the level's active tiles), 1 = 32x2x4, 2 = 32x8x1 (op.tiles is the
         // active-tile list of that shape)
         switch (op.shape * 3 + mode) {
 #define DM_TILED(SH, MD, SY, SZ)                                                                              \
     case SH * 3 + MD:                                                                                         \
-        launch(nm, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, op.ntiles, dim3(TX, SY, SZ), 0, s, g, op.A, op.L, \
-               op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);                                         \
+        launch(nm, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, nt, dim3(TX, SY, SZ), 0, s, g, op.A, op.L, op.invV, \
+               op.invD, op.sigma, x, f, y, omega, tl);                                                        \
         break;
             DM_TILED(0, ST_APPLY, 4, 2) DM_TILED(0, ST_RESID, 4, 2) DM_TILED(0, ST_JACOBI, 4, 2)
             DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4)
@@ -556,13 +563,15 @@ template <typename T, typename TC>
 void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
                      int sweeps, cudaStream_t s) {
     if (nband <= 0 || sweeps <= 0) return;
-    static int max_blocks = -1;   // co-resident blocks of 256 threads (per instantiation)
+    static std::atomic<int> max_blocks_cache{-1};   // co-resident blocks of 256 threads (per instantiation)
+    int max_blocks = max_blocks_cache.load();
     if (max_blocks < 0) {
         int dev = 0, sms = 0, per_sm = 0;
         DM_CUDA(cudaGetDevice(&dev));
         DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_sweeps<T, TC>, 256, 0));
         max_blocks = std::max(0, per_sm * sms);
+        max_blocks_cache.store(max_blocks);
     }
     double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
     float* uf = ud ? nullptr : u;

@@ -1,0 +1,57 @@
+"""Batched eigensolves over worker streams and the stencil tile-shape autotuner."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import eigen, geometry, operators
+
+pytestmark = pytest.mark.gpu
+
+
+def _cavities():
+    return [W.sphere_workload(16, offset_seed=11, sigma=7.0, nev=4),
+            W.ellipsoid_workload(20, seed=21, sigma=6.0, nev=3),
+            W.sphere_workload(24, offset_seed=12, sigma=9.0, nev=5),
+            W.box_workload(12, 10, 8, 1.0, 0.8, 0.6, sigma=30.0, nev=4)]
+
+
+def test_batched_matches_single_solves(dm, ctx):
+    ws = _cavities()
+    geoms = [dm.Geometry.from_workload(ctx, w) for w in ws]
+    jobs = []
+    for w, g in zip(ws, geoms):
+        jobs.append({"geom": g, "sigma": w.sigma, "nev": w.nev, "precision": "f32"})
+    jobs.append({"geom": geoms[0], "sigma": 14.0, "nev": 3, "precision": "f32"})   # second shift, same cavity
+    out = dm.eigensolve_batched(ctx, jobs, streams=3)
+    for job, (k2, rep, st) in zip(jobs, out):
+        assert st == 0, rep
+        ref, _, _, st1 = dm.eigensolve(ctx, job["geom"], job["sigma"], job["nev"], vectors=None, precision="f32")
+        assert st1 == 0
+        assert np.max(np.abs(k2 - ref) / np.abs(ref)) < 1e-12
+        assert rep["rho_max"] < 1e-8
+
+
+def test_batched_item_against_oracle(dm, ctx):
+    w = W.ellipsoid_workload(20, seed=21, sigma=6.0, nev=3)
+    ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
+    kref, _, _ = eigen.shift_invert_modes(ops, w.sigma, w.nev)
+    g = dm.Geometry.from_workload(ctx, w)
+    (k2, rep, st), = dm.eigensolve_batched(ctx, [{"geom": g, "sigma": w.sigma, "nev": w.nev, "precision": "f32"}])
+    assert st == 0
+    assert np.max(np.abs(k2 - kref) / kref) < 1e-8
+
+
+def test_autotuned_shape_does_not_change_results(dm, ctx):
+    w = W.sphere_workload(32, offset_seed=5, sigma=5.0)
+    g = dm.Geometry.from_workload(ctx, w)
+    tuned = dm.Operator(ctx, g, w.sigma, precision="f32", autotune=1)
+    plain = dm.Operator(ctx, g, w.sigma, precision="f32", autotune=0)
+    for l in range(tuned.num_levels - 1):
+        assert tuned.stencil_shape(l) in (0, 1, 2)
+        assert plain.stencil_shape(l) == 0
+    _, A, _ = g.fractions(0)
+    x = np.random.default_rng(0).standard_normal(A.size) * (A > 0)
+    for l in range(tuned.num_levels - 1):
+        tuned.set_omega(l, plain.omega(l))
+    assert np.array_equal(tuned.apply(x), plain.apply(x))
+    assert np.array_equal(tuned.vcycle(x), plain.vcycle(x))
