@@ -174,10 +174,9 @@ def peaks():
 
 
 def stencil_bytes_per_cell(name):
-    """Algorithmic bytes per grid cell of one stencil launch, from its storage
-    types: vector x (3 values) read, y (3) written, f (3) read for resid and
-    jacobi, x re-read for jacobi is the same stream; coefficients A (3), L (3),
-    1/V (1) and 1/D (3, jacobi only) read."""
+    """Bytes per grid cell of one vector-stencil launch that streams every cell
+    once: x (3 values) read, y (3) written, f (3) read for resid and jacobi;
+    coefficients A (3), L (3), 1/V (1) and 1/D (3, jacobi only)."""
     parts = name.split("_")
     prec, mode = parts[2], parts[3]
     tv = {"f64": 8, "f32": 4, "bf16": 2}[prec]
@@ -187,20 +186,56 @@ def stencil_bytes_per_cell(name):
     return vec + coef
 
 
-def roofline(stats, grid_cells, hbm_peak, peak_kind, traffic=None):
-    """Dominant fine-level stencil kernel: algorithmic bytes per launch over its
-    average event-timed duration."""
-    cands = {k: v for k, v in stats.items() if "stencil" in k and k.endswith("_L0")}
-    if not cands:
-        return None
-    name, (launches, ms) = max(cands.items(), key=lambda kv: kv[1][1])
+def stencil_bytes_per_open_face(name):
+    """Algorithmic bytes per OPEN face of one vector-stencil launch (conductor
+    regions excluded): the face's x, y and (resid / jacobi) f, its A and 1/D
+    (jacobi), about one edge fraction L and a third of a 1/V per face."""
+    parts = name.split("_")
+    prec, mode = parts[2], parts[3]
+    tv = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    tc = 8 if prec == "f64" else 4
+    vec = tv * (2 + (1 if mode in ("resid", "jacobi") else 0))
+    coef = tc * (2 + (1 if mode == "jacobi" else 0)) + tc / 3.0
+    return vec + coef
+
+
+# Algorithmic FP64 operations of one K - sigma A evaluation per open face:
+# about 66 per cell of 3 faces (two curls, the grad-div and the shift).
+APPLY_FLOPS_PER_FACE = 22.0
+FP64_PEAK_TFLOPS = 1.204      # FMA probe on this pool's GB300 (see DESIGN.md)
+
+
+def roofline(stats, open_faces, hbm_peak, peak_kind, precision="f32", traffic=None):
+    """Fine-level V-cycle smoothing stencil (the metric's V-cycle kernel):
+    algorithmic bytes per launch (open faces only) over its event-timed mean
+    duration."""
+    name = f"vec_stencil_{precision}_jacobi_L0"
+    if name not in stats:
+        cands = {k: v for k, v in stats.items() if k.startswith("vec_stencil") and k.endswith("_L0")}
+        if not cands:
+            return None
+        name = max(cands.items(), key=lambda kv: kv[1][1])[0]
+    launches, ms = stats[name]
     avg_s = ms / launches * 1e-3
-    bytes_per_launch = stencil_bytes_per_cell(name) * grid_cells
+    bytes_per_launch = stencil_bytes_per_open_face(name) * open_faces
     achieved = bytes_per_launch / avg_s / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
             "bytes_per_launch": int(bytes_per_launch), "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches,
-            "peak_kind": f"{peak_kind} (copy)"}
+            "peak_kind": f"{peak_kind} (copy)", "unit_of_work": "open face"}
+
+
+def roofline_fp64_apply(stats, open_faces):
+    """The FP64 outer K - sigma A apply: bounded by GB300's FP64 pipes."""
+    name = "vec_stencil_f64_apply_L0"
+    if name not in stats:
+        return None
+    launches, ms = stats[name]
+    avg_s = ms / launches * 1e-3
+    tf = APPLY_FLOPS_PER_FACE * open_faces / avg_s / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches,
+            "peak_kind": "measured FP64 FMA probe"}
 
 
 # ---------------------------------------------------------------------------
@@ -281,7 +316,12 @@ def run_native(args):
     ctx.trace(False)
     stats = ctx.trace_stats()
     hbm, kind = peaks()
-    roof = roofline(stats, g.n_cells, hbm, kind)
+    open_faces = geom_open = None
+    g0info = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi_dev, g.origin)
+    open_faces = g0info.level_info(0)["open"]
+    g0info.close()
+    roof = roofline(stats, open_faces, hbm, kind, args.precision)
+    roof64 = roofline_fp64_apply(stats, open_faces)
     # ---- plain FP64 multigrid on the same cavity ----
     plain = None
     if not args.no_compare and args.precision != "f64":
@@ -307,6 +347,7 @@ def run_native(args):
                 "h2d_bytes_per_step": int(phi_host.nbytes), "d2h_bytes_per_step": int(args.nev * nf * 8)},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "roofline_fp64_apply": roof64,
         "clocks": clk,
         "solver": {"inner_iters_per_step": reps[-1]["inner_iters"], "outer_iters": reps[-1]["outer_iters"],
                    "restarts": reps[-1]["restarts"], "proj_iters": reps[-1]["proj_iters"],

@@ -107,6 +107,8 @@ typedef struct dm_eig_report {
 /* Bind to CUDA device `device`; `cuda_stream` (a cudaStream_t, may be NULL)
  * is used for all work, NULL makes the library create its own stream. */
 dm_status dm_context_create(int device, void* cuda_stream, dm_context** out);
+/* Every geometry, operator and network made on `ctx` must be destroyed first:
+ * their destroy functions synchronise the context's stream. */
 void dm_context_destroy(dm_context* ctx);
 /* Text of the last error on this context ("" if none).  Owned by the context. */
 const char* dm_last_error(const dm_context* ctx);

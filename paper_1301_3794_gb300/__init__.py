@@ -12,6 +12,7 @@ y-faces [nz][ny+1][nx], z-faces [nz+1][ny][nx], concatenated and flattened.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 
 import numpy as np
 
@@ -116,8 +117,21 @@ class Context:
             out[buf.value.decode()] = (cnt.value, ms.value)
         return out
 
+    def _adopt(self, obj):
+        """Record a geometry, operator or network made on this context: the C
+        objects must be destroyed before their context."""
+        if not hasattr(self, "_children"):
+            self._children = weakref.WeakSet()
+        self._children.add(obj)
+
     def close(self):
         if getattr(self, "h", None):
+            live = list(getattr(self, "_children", ()))
+            # operators point at their geometry and at a network: close them first
+            for kind in (Operator, Learned, Geometry):
+                for obj in live:
+                    if isinstance(obj, kind):
+                        obj.close()
             lib.dm_context_destroy(self.h)
             self.h = None
 
@@ -141,6 +155,7 @@ class Geometry:
         st = lib.dm_geometry_create(ctx.h, nx, ny, nz, dx, dy, dz, org, arg.ptr, arg.device, float(a_min), C.byref(h))
         ctx.check(st, "dm_geometry_create")
         self.h = h
+        ctx._adopt(self)
 
     @classmethod
     def from_workload(cls, ctx, w, a_min=0.0, phi=None):
@@ -204,6 +219,7 @@ class Operator:
         ctx.check(lib.dm_operator_create(ctx.h, geom.h, self.sigma, C.byref(self.mg), C.byref(h)),
                   "dm_operator_create")
         self.h = h
+        ctx._adopt(self)
 
     @property
     def num_levels(self):
@@ -310,6 +326,7 @@ class Learned:
         h = C.c_void_p()
         ctx.check(lib.dm_learned_create(ctx.h, int(seed), C.byref(h)), "dm_learned_create")
         self.h = h
+        ctx._adopt(self)
 
     @staticmethod
     def num_params():

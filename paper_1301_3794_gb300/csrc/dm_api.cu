@@ -238,6 +238,11 @@ struct OpLevel {
     int shape = 0;            // stencil tile shape (autotuned)
     DBuf<int> stiles;         // active tiles of that shape (shape != 0)
     int nstiles = 0;
+    // band rows of K - sigma A (ELL, slot-major) for the band sweeps
+    DBuf<int> bcols;
+    DBuf<double> bv64;
+    DBuf<float> bv32;
+    int bwidth = 0;
 };
 
 struct Fgmres {
@@ -308,6 +313,7 @@ template <> struct Pick<double, double> {
     static const double* iV(const GeoLevel& g) { return g.invV.get(); }
     static const double* iD(const OpLevel& o) { return o.invD.get(); }
     static const double* iDs(const OpLevel& o) { return o.invDs.get(); }
+    static BandRows<double> br(const OpLevel& o) { return BandRows<double>{o.bcols.get(), o.bv64.get(), o.bwidth}; }
 };
 template <typename T> struct Pick<T, float> {
     static const float* A(const GeoLevel& g) { return g.A32.get(); }
@@ -315,6 +321,7 @@ template <typename T> struct Pick<T, float> {
     static const float* iV(const GeoLevel& g) { return g.invV32.get(); }
     static const float* iD(const OpLevel& o) { return o.invD32.get(); }
     static const float* iDs(const OpLevel& o) { return o.invDs32.get(); }
+    static BandRows<float> br(const OpLevel& o) { return BandRows<float>{o.bcols.get(), o.bv32.get(), o.bwidth}; }
 };
 
 template <typename T, typename TC>
@@ -348,7 +355,8 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const double om = op->ol[l].omega;
     float* u = reinterpret_cast<float*>(op->band_u.get());
     vec_jacobi_zero(o, f, ebuf, om, s);
-    vec_band_sweeps(o, g.band.get(), g.nband, f, ebuf, u, om, op->mg.band_sweeps, s);
+    band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[l]), o.invD, g.band.get(), g.nband, f, ebuf, u, om,
+                           op->mg.band_sweeps, l == 0, s);
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
@@ -358,7 +366,8 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, g.tiles.get(),
                             g.ntiles, s);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
-    vec_band_sweeps(o, g.band.get(), g.nband, f, rbuf, u, om, op->mg.band_sweeps, s);
+    band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[l]), o.invD, g.band.get(), g.nband, f, rbuf, u, om,
+                           op->mg.band_sweeps, l == 0, s);
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -833,6 +842,25 @@ void setup_operator(dm_operator* op) {
             convert_coeff<float>(n3, o.invD.get(), o.invD32.get(), s);
             convert_coeff<float>(n1, o.invDs.get(), o.invDs32.get(), s);
         }
+        if (g.nband > 0 && l + 1 < nl) {
+            constexpr int kMaxRow = 48;
+            const size_t nb = (size_t)g.nband;
+            DBuf<int> cols(kMaxRow * nb, false), mx(1);
+            DBuf<double> vals(kMaxRow * nb, false);
+            const int w = band_rows(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, g.band.get(), g.nband, kMaxRow,
+                                    cols.get(), vals.get(), mx.get(), s);
+            DM_REQUIRE(w <= kMaxRow, DM_ERR_GEOMETRY, "band row longer than the ELL width");
+            o.bwidth = std::max(w, 1);
+            o.bcols.alloc((size_t)o.bwidth * nb, false);
+            o.bv64.alloc((size_t)o.bwidth * nb, false);
+            DM_CUDA(cudaMemcpyAsync(o.bcols.get(), cols.get(), sizeof(int) * o.bwidth * nb, cudaMemcpyDeviceToDevice, s));
+            DM_CUDA(cudaMemcpyAsync(o.bv64.get(), vals.get(), sizeof(double) * o.bwidth * nb, cudaMemcpyDeviceToDevice, s));
+            if (lowp) {
+                o.bv32.alloc((size_t)o.bwidth * nb, false);
+                convert_coeff<float>((long long)o.bwidth * nb, o.bv64.get(), o.bv32.get(), s);
+            }
+            Sync::stream(s);
+        }
         WorkLevel& w = op->wk[l];
         w.f.alloc(ts * n3);
         w.e.alloc(ts * n3);
@@ -1301,7 +1329,8 @@ dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double
             using TC = std::conditional_t<std::is_same<T, double>::value, double, float>;
             const VecOp<T, TC> o = vop<T, TC>(op, level);
             vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
-            vec_band_sweeps(o, g.band.get(), g.nband, p[0], p[2], u, om, op->mg.band_sweeps, s);
+            band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[level]), o.invD, g.band.get(), g.nband, p[0], p[2], u, om,
+                                   op->mg.band_sweeps, level == 0, s);
         };
         if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
         else if (op->mg.precision == DM_PREC_F32)

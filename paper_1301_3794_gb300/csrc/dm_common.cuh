@@ -308,6 +308,20 @@ void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T*
 template <typename T, typename TC>
 void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
                      int sweeps, cudaStream_t s);
+// Band rows of K - sigma A in ELL form (slot-major), see k_band_rows
+template <typename TC>
+struct BandRows {
+    const int* cols = nullptr;
+    const TC* vals = nullptr;
+    int width = 0;
+};
+// assemble up to `width` entries per band row; returns the largest row length
+int band_rows(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
+              int nband, int width, int* cols, double* vals, int* d_maxnz, cudaStream_t s);
+// `sweeps` Jacobi sweeps restricted to the band, from the assembled rows
+template <typename T, typename TC>
+void band_sweeps_ell(const BandRows<TC>& br, const TC* invD, const int* band, int nband, const T* f, T* x, float* u,
+                     double omega, int sweeps, bool fine, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
                   cudaStream_t s);
 void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,

@@ -182,7 +182,7 @@ __global__ void k_add_correction(Grid3 g, const float* __restrict__ Y, const dou
     const int p = g.idx(i, j, k);
     for (int c = 0; c < 3; ++c) {
         const int q = c * g.np + p;
-        if (A[q] > 0.0) z[q] = to_store<T>((float)(to_c(z[q]) + scale * (double)Y[(size_t)p * 3 + c]));
+        if (A[q] > 0.0) z[q] = to_store<T>((double)to_c(z[q]) + scale * (double)Y[(size_t)p * 3 + c]);
     }
 }
 

@@ -364,6 +364,79 @@ __global__ void __launch_bounds__(1024) k_band_sweeps_block(
     }
 }
 
+// Rows of K - sigma A for the band faces in ELL form (slot-major: entry e of
+// band face t at [e * nband + t]): every face in the 3x3x3 node neighbourhood
+// is a candidate; its coefficient is face_K of the candidate's unit vector
+// (the same arithmetic as every other use of the operator); zeros are
+// dropped, unused slots point at the row's own face with coefficient 0.
+__global__ void k_band_rows(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
+                            const double* __restrict__ invV, double sigma, const int* __restrict__ band, int nband,
+                            int width, int* __restrict__ cols, double* __restrict__ vals, int* __restrict__ maxnz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nband) return;
+    const int q = band[t];
+    const int c = q / g.np, p = q - c * g.np;
+    Coef<double, double> cf{A, L, invV, g.np};
+    const double rdx = 1.0 / g.hx, rdy = 1.0 / g.hy, rdz = 1.0 / g.hz;
+    int n = 0;
+    for (int dk = -1; dk <= 1; ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di)
+                for (int cc = 0; cc < 3; ++cc) {
+                    const int cand = cc * g.np + p + di + dj * g.sx + dk * g.sxy;
+                    UnitAcc<double> b{cand, g.np};
+                    const double v = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sigma);
+                    if (v != 0.0) {
+                        if (n < width) {
+                            cols[(size_t)n * nband + t] = cand;
+                            vals[(size_t)n * nband + t] = v;
+                        }
+                        ++n;
+                    }
+                }
+    for (int e = n; e < width; ++e) {
+        cols[(size_t)e * nband + t] = q;
+        vals[(size_t)e * nband + t] = 0.0;
+    }
+    atomicMax(maxnz, n);
+}
+
+// Band sweeps from the assembled rows: per sweep u_t = omega invD (f - row_t . x),
+// barrier, x += u, barrier.  The barrier is the grid's (coop = 1, cooperative
+// launch) or the block's (coop = 0, one block).
+template <typename T, typename TC>
+__global__ void k_band_ell(int nband, int width, const int* __restrict__ band, const int* __restrict__ cols,
+                           const TC* __restrict__ vals, const TC* __restrict__ invD, const T* __restrict__ f, T* x,
+                           float* u_f, double* u_d, double omega_d, int sweeps, int coop) {
+    using C = typename Compute<T>::type;
+    namespace cg = cooperative_groups;
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const C om = C(omega_d);
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int t = t0; t < nband; t += stride) {
+            C acc = C(0);
+            for (int e = 0; e < width; ++e) {
+                const size_t k = (size_t)e * nband + t;
+                acc += (C)vals[k] * (C)to_c(__ldcg(x + cols[k]));
+            }
+            const int q = band[t];
+            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - acc);
+            if (u_d) u_d[t] = (double)u;
+            else u_f[t] = (float)u;
+        }
+        if (coop) cg::this_grid().sync();
+        else __syncthreads();
+        for (int t = t0; t < nband; t += stride) {
+            const int q = band[t];
+            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
+            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
+        }
+        if (coop) cg::this_grid().sync();
+        else __syncthreads();
+    }
+}
+
 // diagonal of K - sigma A (x-face; other components cyclic):
 //   (L_z(j) + L_z(j+1))/dy^2 + (L_y(k) + L_y(k+1))/dz^2 + A_x^2 (V^-1(i-1) + V^-1(i))/dx^2 - sigma A_x
 __global__ void k_vec_diag(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
@@ -540,6 +613,55 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
 }
 
+int band_rows(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
+              int nband, int width, int* cols, double* vals, int* d_maxnz, cudaStream_t s) {
+    DM_CUDA(cudaMemsetAsync(d_maxnz, 0, sizeof(int), s));
+    if (nband <= 0) return 0;
+    launch("k_band_rows", k_band_rows, (nband + 127) / 128, 128, 0, s, g, A, L, invV, sigma, band, nband, width, cols,
+           vals, d_maxnz);
+    int h = 0;
+    DM_CUDA(cudaMemcpyAsync(&h, d_maxnz, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+template <typename T, typename TC>
+void band_sweeps_ell(const BandRows<TC>& br, const TC* invD, const int* band, int nband, const T* f, T* x, float* u,
+                     double omega, int sweeps, bool fine, cudaStream_t s) {
+    if (nband <= 0 || sweeps <= 0) return;
+    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
+    float* uf = ud ? nullptr : u;
+    const char* name = stencil_name("band_ell", prec_index<T>(), ST_JACOBI, fine);
+    if (nband <= 8192) {
+        launch(name, k_band_ell<T, TC>, 1, 1024, 0, s, nband, br.width, band, br.cols, br.vals, invD, f, x, uf, ud,
+               omega, sweeps, 0);
+        return;
+    }
+    static std::atomic<int> max_blocks_cache{-1};
+    int max_blocks = max_blocks_cache.load();
+    if (max_blocks < 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        DM_CUDA(cudaGetDevice(&dev));
+        DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_ell<T, TC>, 256, 0));
+        max_blocks = std::max(0, per_sm * sms);
+        max_blocks_cache.store(max_blocks);
+    }
+    const int blocks = std::max(1, std::min((nband + 2 * 256 - 1) / (2 * 256), max_blocks));
+    int nb = nband, w = br.width, sw = sweeps, coop = 1;
+    const int* cols = br.cols;
+    const TC* vals = br.vals;
+    double om = omega;
+    void* args[] = {&nb, &w, &band, &cols, &vals, &invD, &f, &x, &uf, &ud, &om, &sw, &coop};
+    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (t) t->begin(s, &e0, &e1);
+    DM_CUDA(cudaLaunchCooperativeKernel((const void*)k_band_ell<T, TC>, dim3(blocks), dim3(256), args, 0, s));
+    if (t) t->end(name, s, e0, e1);
+    count_launch();
+    check_launch(name);
+}
+
 template <typename T, typename TC>
 void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
     const Domain d{op.g, op.tiles, op.ntiles, 3};
@@ -666,5 +788,12 @@ DM_INST(double, double)
 DM_INST(float, float)
 DM_INST(__nv_bfloat16, float)
 #undef DM_INST
+template void band_sweeps_ell<double, double>(const BandRows<double>&, const double*, const int*, int, const double*,
+                                              double*, float*, double, int, bool, cudaStream_t);
+template void band_sweeps_ell<float, float>(const BandRows<float>&, const float*, const int*, int, const float*, float*,
+                                            float*, double, int, bool, cudaStream_t);
+template void band_sweeps_ell<__nv_bfloat16, float>(const BandRows<float>&, const float*, const int*, int,
+                                                    const __nv_bfloat16*, __nv_bfloat16*, float*, double, int, bool,
+                                                    cudaStream_t);
 
 }  // namespace dm

@@ -59,8 +59,12 @@ def test_stencil_byte_model():
     assert bench.stencil_bytes_per_cell("vec_stencil_f64_apply_L0") == 104
     # FP32 Jacobi: x, f, y (3 x 4 B each) + A, L, 1/V, 1/D (10 x 4 B)
     assert bench.stencil_bytes_per_cell("vec_stencil_f32_jacobi_L0") == 36 + 40
+    # per open face, FP32 Jacobi: x, f, y (4 B each) + A, 1/D (4 B each) + L (4 B) + 1/V / 3
+    assert bench.stencil_bytes_per_open_face("vec_stencil_f32_jacobi_L0") == pytest.approx(12 + 12 + 4 / 3)
     r = bench.roofline({"vec_stencil_f32_jacobi_L0": (10, 1.0), "k_mdot_partial": (5, 100.0)}, 10 ** 6, 6758.5,
-                       "measured")
+                       "measured", "f32")
     assert r["kernel"] == "vec_stencil_f32_jacobi_L0"
-    assert r["achieved"] == pytest.approx(76 * 10 ** 6 / 1e-4 / 1e9, rel=1e-3)
+    assert r["achieved"] == pytest.approx((24 + 4 / 3) * 10 ** 6 / 1e-4 / 1e9, rel=1e-3)
     assert 0 < r["frac"] < 1
+    f = bench.roofline_fp64_apply({"vec_stencil_f64_apply_L0": (4, 2.0)}, 10 ** 6)
+    assert f["bound"] == "alu" and f["achieved"] == pytest.approx(22e6 / 5e-4 / 1e12)

@@ -1,0 +1,120 @@
+"""Learned smoother on the GPU against the FP64 oracle network (oracle/learned.py),
+and its training / use inside the shifted solve."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import geometry, learned as OL, operators
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    """Round to bfloat16 (round to nearest even), as the GPU stores activations."""
+    a = np.asarray(a, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _weights(w_flat):
+    n1, n2 = 27 * 8 * 16, 27 * 16 * 16
+    W1 = w_flat[:n1].reshape(3, 3, 3, 8, 16).astype(np.float64)
+    W2 = w_flat[n1:n1 + n2].reshape(3, 3, 3, 16, 16).astype(np.float64)
+    W3 = w_flat[n1 + n2:].reshape(3, 3, 3, 16, 3).astype(np.float64)
+    return [W1, W2, W3]
+
+
+def _node_faces(fr_or_vec, g):
+    """Natural face vector -> (nz+1, ny+1, nx+1, 3) node array (face c of node = lower face)."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    sx, sy, sz = (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+    n = [int(np.prod(s)) for s in (sx, sy, sz)]
+    parts = np.split(np.asarray(fr_or_vec), np.cumsum(n)[:-1])
+    out = np.zeros((nz + 1, ny + 1, nx + 1, 3))
+    out[:nz, :ny, :, 0] = parts[0].reshape(sx)
+    out[:nz, :, :nx, 1] = parts[1].reshape(sy)
+    out[:, :ny, :nx, 2] = parts[2].reshape(sz)
+    return out
+
+
+def _faces_from_nodes(arr, g):
+    nx, ny, nz = g.nx, g.ny, g.nz
+    return np.concatenate([arr[:nz, :ny, :, 0].ravel(), arr[:nz, :, :nx, 1].ravel(), arr[:, :ny, :nx, 2].ravel()])
+
+
+def _features(w, r):
+    g = w.grid
+    fr = geometry.fractions(w.phi)
+    A = operators.face_vector(fr)
+    nopen = int((A > 0).sum())
+    scale = np.sqrt((r[A > 0] ** 2).sum() / nopen)
+    X = np.zeros((g.nz + 1, g.ny + 1, g.nx + 1, 8))
+    X[..., 0:3] = _node_faces(np.where(A > 0, r / scale, 0.0), g)
+    X[..., 3:6] = _node_faces(A, g)
+    X[:g.nz, :g.ny, :g.nx, 6] = fr["V"]
+    M = (_node_faces(A, g) > 0).astype(float)
+    return X, M, scale, A
+
+
+def test_forward_matches_oracle(dm, ctx):
+    w = W.sphere_workload(12, offset_seed=4, sigma=5.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    net = dm.Learned(ctx, seed=3)
+    Ws = _weights(net.get_weights())
+    A = operators.face_vector(geometry.fractions(w.phi))
+    r = np.random.default_rng(0).standard_normal(A.size) * (A > 0)
+    y = net.apply(geom, r)
+    X, M, scale, _ = _features(w, r)
+    Y, _ = OL.forward(_bf16(X), Ws)
+    h = min(w.grid.dx, w.grid.dy, w.grid.dz)
+    yref = _faces_from_nodes(Y, w.grid) * scale * h * h * (A > 0)
+    rel = np.linalg.norm(y - yref) / np.linalg.norm(yref)
+    assert rel < 3e-2, rel          # BF16 activations
+
+
+def test_loss_and_gradient_match_oracle(dm, ctx):
+    w = W.sphere_workload(10, offset_seed=6, sigma=5.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    net = dm.Learned(ctx, seed=5)
+    wts = net.get_weights()
+    wts[27 * 8 * 16 + 27 * 16 * 16:] *= 10.0     # last layer O(1) so every layer's gradient matters
+    net.set_weights(wts)
+    Ws = _weights(wts)
+    rng = np.random.default_rng(1)
+    A = operators.face_vector(geometry.fractions(w.phi))
+    X, M, _, _ = _features(w, rng.standard_normal(A.size) * (A > 0))
+    E = rng.standard_normal(X.shape[:3] + (3,)) * M
+    Xb = _bf16(X)
+    loss, g = net.loss_grad(geom, Xb.astype(np.float32), E.astype(np.float32))
+    lref, Gref, _ = OL.loss_and_grads(Xb, E, M, Ws)
+    assert abs(loss - lref) / lref < 2e-2, (loss, lref)
+    gref = np.concatenate([G.ravel() for G in Gref])
+    cos = float(g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert cos > 0.995, cos
+    for a, b in ((0, 27 * 8 * 16), (27 * 8 * 16, 27 * 8 * 16 + 27 * 16 * 16), (27 * 8 * 16 + 27 * 16 * 16, g.size)):
+        rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
+        assert rel < 6e-2, (a, rel)
+
+
+def test_training_lowers_loss_and_solver_uses_network(dm, ctx):
+    w = W.sphere_workload(32, offset_seed=W.SEED_BASE + 2, sigma=5.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma, precision="f32")
+    net = dm.Learned(ctx, seed=11)
+    hist = net.train(op, runs=3, epochs=12, lr=2e-3, seed=7)
+    assert hist[-1] < hist[0], hist
+    A = operators.face_vector(geometry.fractions(w.phi))
+    b = np.random.default_rng(99).standard_normal(A.size) * (A > 0)
+    x0, it0, rr0 = op.solve(b, tol=1e-10)
+    op.set_learned(net)
+    x1, it1, rr1 = op.solve(b, tol=1e-10)
+    op.set_learned(None)
+    print(f"\nlearned smoother: plain {it0} iterations, with network {it1} iterations; loss {hist[0]:.3g} -> {hist[-1]:.3g}")
+    assert rr1 < 1e-9                      # the FP64 residual still reaches the tolerance
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) < 1e-7
+    k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, 4, vectors=None, precision="f32", learned=net)
+    k2p, _, repp, stp = dm.eigensolve(ctx, geom, w.sigma, 4, vectors=None, precision="f32")
+    assert st == 0 and rep["rho_max"] < 1e-8
+    assert np.max(np.abs(k2 - k2p) / k2p) < 1e-9
+    assert rep["learned_applied"] > 0
