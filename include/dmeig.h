@@ -167,6 +167,25 @@ dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double o
 /* y = (K - sigma A) x on `level` in FP64 (Eq. discLaplDM; K = C L C^T +
  * A D^T V^-1 D A with V^-1 = 0 where V = 0).  x, y: natural face layout. */
 dm_status dm_operator_apply(dm_operator* op, int level, const double* x, double* y, int on_device);
+/* The same y = (K - sigma A) x as dm_operator_apply, for callers that must not
+ * allocate memory once they are running: a loop that may not pay the device-
+ * wide synchronisation cudaMalloc / cudaFree can cause, or an application
+ * whose device memory is owned by its own pool allocator and capped, where an
+ * extra cudaMalloc can fail or fragment the pool.  This call makes no device
+ * or host allocation (no cudaMalloc, cudaFree, event or library allocator).
+ * The paper has no counterpart; it is a service of this library.
+ *  - x, y: device pointers, natural face layout of `level`.
+ *  - Scratch: a static device array of 6,291,456 doubles (48 MiB) inside the
+ *    library, held by every GPU that loads the library until the process exits.
+ *    A call needs 6 * np doubles (np = padded node count of the level: about
+ *    1.0 M nodes, i.e. grids up to roughly 100^3); larger levels are rejected
+ *    with DM_ERR_INVALID_ARG and an explanatory dm_last_error().
+ *  - The first call on each device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current.
+ *  - Every call shares the one scratch array: calls that overlap on the GPU
+ *    (other threads, other contexts or streams) race and corrupt each other's
+ *    results; serialise them. */
+dm_status dm_operator_apply_noalloc(dm_operator* op, int level, const double* x, double* y);
 /* Diagonal of K - sigma A on `level` (natural face layout, 0 on closed faces). */
 dm_status dm_operator_diagonal(dm_operator* op, int level, double* d, int on_device);
 /* One smoothing step on `level` in the preconditioner's precision:

@@ -246,6 +246,18 @@ class Operator:
         self.ctx.check(lib.dm_operator_apply(self.h, level, a.ptr, yp, a.device), "dm_operator_apply")
         return y
 
+    def apply_noalloc(self, x, level=0, out=None):
+        """(K - sigma A) x through dm_operator_apply_noalloc: x and the result are
+        CUDA tensors; the call allocates nothing (see include/dmeig.h)."""
+        import torch
+        F = self._faces(level)
+        if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == F):
+            raise ValueError("apply_noalloc needs a contiguous float64 CUDA tensor of the level's face count")
+        y = torch.empty_like(x) if out is None else out
+        self.ctx.check(lib.dm_operator_apply_noalloc(self.h, level, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())),
+                       "dm_operator_apply_noalloc")
+        return y
+
     def diagonal(self, level=0):
         d = np.empty(self._faces(level))
         self.ctx.check(lib.dm_operator_diagonal(self.h, level, C.c_void_p(d.ctypes.data), 0), "dm_operator_diagonal")

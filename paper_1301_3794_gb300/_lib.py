@@ -66,6 +66,7 @@ SIGNATURES = {
     "dm_operator_set_omega": (C.c_int, [_P, C.c_int, C.c_int, C.c_double]),
     "dm_operator_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "dm_operator_diagonal": (C.c_int, [_P, C.c_int, _P, C.c_int]),
+    "dm_operator_apply_noalloc": (C.c_int, [_P, C.c_int, _P, _P]),
     "dm_operator_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "dm_operator_restrict": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "dm_operator_prolong": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),

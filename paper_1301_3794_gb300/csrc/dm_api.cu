@@ -1708,6 +1708,73 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
 }
 
 // ---------------------------------------------------------------------------
+// operator apply without any allocation
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// Scratch of dm_operator_apply_noalloc: the padded input and output vectors of
+// one call.  It lives in the library's own device image, so every GPU that
+// loads the library holds it until the process exits.
+constexpr long long kNoAllocDoubles = 6ll * 1024 * 1024;   // 48 MiB
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch on `dev` (the current device), looked
+// up once per device: in host code the symbol names a host-side stand-in, not
+// device memory, so it must never be passed to a kernel directly.
+double* noalloc_scratch(int dev) {
+    static std::mutex mu;
+    static double* addr[128] = {};
+    DM_REQUIRE(dev >= 0 && dev < 128, DM_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            throw Error(DM_ERR_CUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
+        addr[dev] = static_cast<double*>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_operator_apply_noalloc(dm_operator* op, int level, const double* x, double* y) {
+    if (!op || !x || !y || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        Tracer* const saved = g_tracer;
+        g_tracer = nullptr;   // event timing would create events; this call creates nothing
+        struct Restore {
+            Tracer* t;
+            ~Restore() { g_tracer = t; }
+        } restore{saved};
+        DM_CUDA(cudaSetDevice(op->ctx->device));
+        const GeoLevel& g = glv(op, level);
+        const long long n3 = 3ll * g.g.np;
+        if (2 * n3 > kNoAllocDoubles)
+            throw Error(DM_ERR_INVALID_ARG, "dm_operator_apply_noalloc: level " + std::to_string(level) + " needs " +
+                                                std::to_string(2 * n3) + " doubles of scratch; the static scratch holds " +
+                                                std::to_string(kNoAllocDoubles) + " (use dm_operator_apply)");
+        cudaStream_t s = op->ctx->stream;
+        double* xp = noalloc_scratch(op->ctx->device);
+        double* yp = xp + n3;
+        // the scratch keeps the previous call's contents: the padded input must
+        // start at zero (ghost and non-face entries are read by the stencil)
+        DM_CUDA(cudaMemsetAsync(xp, 0, sizeof(double) * (size_t)n3, s));
+        pack_faces(g.g, x, xp, s);
+        launch("k_mask_open", k_mask_open, (int)std::min<long long>((n3 + 255) / 256, 1216), 256, 0, s, n3, g.A.get(),
+               xp);
+        vec_apply_dense_f64(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, xp, yp, s);
+        unpack_faces(g.g, yp, y, s);
+        DM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+// ---------------------------------------------------------------------------
 // learned smoother
 // ---------------------------------------------------------------------------
 

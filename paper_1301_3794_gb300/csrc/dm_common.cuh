@@ -322,6 +322,8 @@ int band_rows(const Grid3& g, const double* A, const double* L, const double* in
 template <typename T, typename TC>
 void band_sweeps_ell(const BandRows<TC>& br, const TC* invD, const int* band, int nband, const T* f, T* x, float* u,
                      double omega, int sweeps, bool fine, cudaStream_t s);
+void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
+                         const double* x, double* y, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
                   cudaStream_t s);
 void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,

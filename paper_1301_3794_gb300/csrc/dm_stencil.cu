@@ -613,6 +613,14 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
 }
 
+// y = (K - sigma A) x in FP64 over every node of the level (dense grid of
+// blocks), launched under a fixed name: makes no host or device allocation.
+void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
+                         const double* x, double* y, cudaStream_t s) {
+    launch("vec_stencil_f64_apply_noalloc", k_vec_stencil<double, double, ST_APPLY>, node_grid(g), kBlock, 0, s, g, A, L,
+           invV, (const double*)nullptr, sigma, x, (const double*)nullptr, y, 0.0, (const int*)nullptr);
+}
+
 int band_rows(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
               int nband, int width, int* cols, double* vals, int* d_maxnz, cudaStream_t s) {
     DM_CUDA(cudaMemsetAsync(d_maxnz, 0, sizeof(int), s));
