@@ -357,7 +357,7 @@ def run_native(args):
                    "inner_rate": None},
         "plain_f64": plain,
         "kernels_top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in
-                        sorted(stats.items(), key=lambda kv: -kv[1][1])[:8]},
+                        sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
     }
     if reps[-1]["inner_iters"] and reps[-1]["outer_iters"]:
         it = reps[-1]["inner_iters"] / reps[-1]["outer_iters"]

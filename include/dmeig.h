@@ -62,7 +62,12 @@ typedef struct dm_learned dm_learned;
  * direction, Sec. 6). */
 typedef struct dm_mg_params {
     int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4) */
-    int band_sweeps;       /* extra Jacobi sweeps on the cut-cell band after each smoothing step (8) */
+    int band_sweeps;       /* Jacobi sweeps of the cut-cell band smoother after each smoothing step (16):
+                              a restricted additive Schwarz step over bricks of band_brick^3 nodes with
+                              one node of overlap; each subdomain sweeps on its own faces, couplings to
+                              other faces frozen, and the brick keeps the faces it owns */
+    int band_brick;        /* brick edge in nodes (8); 0 < band_brick, and the largest subdomain must fit
+                              the sweep buffers in shared memory (DM_ERR_INVALID_ARG otherwise) */
     double omega_scale;    /* Jacobi weight = omega_scale / lambda_max(D^-1 (K - sigma A)) (1.7) */
     int power_iters;       /* power iterations for lambda_max (30) */
     int precision;         /* dm_precision of the V-cycle (DM_PREC_F64) */
@@ -189,8 +194,9 @@ dm_status dm_operator_apply_noalloc(dm_operator* op, int level, const double* x,
 /* Diagonal of K - sigma A on `level` (natural face layout, 0 on closed faces). */
 dm_status dm_operator_diagonal(dm_operator* op, int level, double* d, int on_device);
 /* One smoothing step on `level` in the preconditioner's precision:
- * x <- x + omega D^-1 (f - (K - sigma A) x), then band_sweeps sweeps restricted
- * to the cut-cell band.  x is updated in place. */
+ * x <- x + omega D^-1 (f - (K - sigma A) x), then the band smoother (band_sweeps
+ * sweeps per subdomain on the cut-cell band, see dm_mg_params).  x is updated
+ * in place. */
 dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double* x, int on_device);
 /* f_c = R r = P^T r / 8 from `level` to level+1 (precision of the preconditioner). */
 dm_status dm_operator_restrict(dm_operator* op, int level, const double* r, double* fc, int on_device);

@@ -195,11 +195,13 @@ class Geometry:
             pass
 
 
-def mg_params(max_coarse=4, band_sweeps=8, omega_scale=1.7, power_iters=30, precision="f64", autotune=1):
+def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
+              autotune=1):
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
     p.band_sweeps = band_sweeps
+    p.band_brick = band_brick
     p.omega_scale = omega_scale
     p.power_iters = power_iters
     p.precision = PREC[precision] if isinstance(precision, str) else int(precision)

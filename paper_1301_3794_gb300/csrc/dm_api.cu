@@ -238,22 +238,28 @@ struct OpLevel {
     int shape = 0;            // stencil tile shape (autotuned)
     DBuf<int> stiles;         // active tiles of that shape (shape != 0)
     int nstiles = 0;
-    // band rows of K - sigma A (ELL, slot-major) for the band sweeps
-    DBuf<int> bcols;
-    DBuf<double> bv64;
-    DBuf<float> bv32;
-    int bwidth = 0;
+    // subdomains of the band smoother (see dm_band.cu) and their rows' slot coefficients
+    DBuf<int> sd_off, sd_copy, sd_pos, sd_dims;
+    DBuf<double> sd_v64;
+    DBuf<float> sd_v32;
+    int sd_nsub = 0, sd_ncopies = 0, sd_maxrows = 0, sd_maxbox = 0;
+    int sd_cls_first[kSchwarzClasses] = {}, sd_cls_count[kSchwarzClasses] = {};
 };
 
+// FGMRES workspace: the Arnoldi basis V and the work vector wf in
+// float-float (see mdot_ff), the preconditioned vectors Z and the operator
+// output w in FP64
 struct Fgmres {
     long long n = 0;
     int m = 0;
-    DBuf<double> V, Z, w;
+    DBuf<float2> V, wf;
+    DBuf<double> Z, w;
     void ensure(long long n_, int m_) {
         if (n == n_ && m >= m_) return;
         n = n_;
         m = m_;
         V.alloc((size_t)(m + 1) * n);
+        wf.alloc((size_t)n);
         Z.alloc((size_t)m * n);
         w.alloc((size_t)n);
     }
@@ -306,6 +312,25 @@ namespace {
 const GeoLevel& glv(const dm_operator* op, int l) { return *op->geom->lv[l]; }
 size_t tsize(int prec) { return prec == DM_PREC_F64 ? 8 : (prec == DM_PREC_F32 ? 4 : 2); }
 
+template <typename TC>
+BandSchwarz<TC> schwarz_view(const OpLevel& o, const TC* vals) {
+    BandSchwarz<TC> b;
+    b.off = o.sd_off.get();
+    b.copy = o.sd_copy.get();
+    b.pos = o.sd_pos.get();
+    b.dims = o.sd_dims.get();
+    b.vals = vals;
+    b.nsub = o.sd_nsub;
+    b.ncopies = o.sd_ncopies;
+    b.maxrows = o.sd_maxrows;
+    b.maxbox = o.sd_maxbox;
+    for (int k = 0; k < kSchwarzClasses; ++k) {
+        b.cls_first[k] = o.sd_cls_first[k];
+        b.cls_count[k] = o.sd_cls_count[k];
+    }
+    return b;
+}
+
 template <typename T, typename TC> struct Pick;
 template <> struct Pick<double, double> {
     static const double* A(const GeoLevel& g) { return g.A.get(); }
@@ -313,7 +338,7 @@ template <> struct Pick<double, double> {
     static const double* iV(const GeoLevel& g) { return g.invV.get(); }
     static const double* iD(const OpLevel& o) { return o.invD.get(); }
     static const double* iDs(const OpLevel& o) { return o.invDs.get(); }
-    static BandRows<double> br(const OpLevel& o) { return BandRows<double>{o.bcols.get(), o.bv64.get(), o.bwidth}; }
+    static BandSchwarz<double> bs(const OpLevel& o) { return schwarz_view<double>(o, o.sd_v64.get()); }
 };
 template <typename T> struct Pick<T, float> {
     static const float* A(const GeoLevel& g) { return g.A32.get(); }
@@ -321,7 +346,7 @@ template <typename T> struct Pick<T, float> {
     static const float* iV(const GeoLevel& g) { return g.invV32.get(); }
     static const float* iD(const OpLevel& o) { return o.invD32.get(); }
     static const float* iDs(const OpLevel& o) { return o.invDs32.get(); }
-    static BandRows<float> br(const OpLevel& o) { return BandRows<float>{o.bcols.get(), o.bv32.get(), o.bwidth}; }
+    static BandSchwarz<float> bs(const OpLevel& o) { return schwarz_view<float>(o, o.sd_v32.get()); }
 };
 
 template <typename T, typename TC>
@@ -353,10 +378,10 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     }
     const VecOp<T, TC> o = vop<T, TC>(op, l);
     const double om = op->ol[l].omega;
-    float* u = reinterpret_cast<float*>(op->band_u.get());
+    double* u = op->band_u.get();
     vec_jacobi_zero(o, f, ebuf, om, s);
-    band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[l]), o.invD, g.band.get(), g.nband, f, ebuf, u, om,
-                           op->mg.band_sweeps, l == 0, s);
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om,
+                        op->mg.band_sweeps, l == 0, s);
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
@@ -366,8 +391,8 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, g.tiles.get(),
                             g.ntiles, s);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
-    band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[l]), o.invD, g.band.get(), g.nband, f, rbuf, u, om,
-                           op->mg.band_sweeps, l == 0, s);
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om,
+                        op->mg.band_sweeps, l == 0, s);
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -459,15 +484,25 @@ void learned_correct(dm_operator* op, const T* f, T* z, T* scratch) {
 // z = M^-1 v on FP64 fine-level vectors: v is converted into the level-0 f
 // buffer, the V-cycle runs (as a graph after its first direct run), and the
 // result in the level-0 r buffer is converted into z.
-template <typename T, typename TC>
-void precond_vec_T(dm_operator* op, const double* v, double* z) {
+// MG input f (storage T) from an FP64 or a float-float vector
+template <typename T>
+void mg_input(const Domain& D, const double* v, T* f, cudaStream_t s) {
+    convert<T, double>(D, v, f, s);
+}
+template <typename T>
+void mg_input(const Domain& D, const float2* v, T* f, cudaStream_t s) {
+    ff_convert<T>(D, v, f, s);
+}
+
+template <typename T, typename TC, typename TIn>
+void precond_vec_T(dm_operator* op, const TIn* v, double* z) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).vdom();
     WorkLevel& w0 = op->wk[0];
     T* f = reinterpret_cast<T*>(w0.f.get());
     T* e = reinterpret_cast<T*>(w0.e.get());
     T* r = reinterpret_cast<T*>(w0.r.get());
-    convert<T, double>(D, v, f, s);
+    mg_input<T>(D, v, f, s);
     if (graphs_allowed(op) && op->vcalls > 0) {
         if (!op->vexec && !capture_graph(op, [&] { vcycle<T, TC>(op, 0, f, e, r); }, &op->vexec, &op->vexec_kernels))
             op->graphs = false;
@@ -483,15 +518,15 @@ void precond_vec_T(dm_operator* op, const double* v, double* z) {
     convert<double, T>(D, r, z, s);
 }
 
-template <typename T, typename TC>
-void precond_scal_T(dm_operator* op, const double* v, double* z) {
+template <typename T, typename TC, typename TIn>
+void precond_scal_T(dm_operator* op, const TIn* v, double* z) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).sdom();
     WorkLevel& w0 = op->wk[0];
     T* f = reinterpret_cast<T*>(w0.sf.get());
     T* e = reinterpret_cast<T*>(w0.se.get());
     T* r = reinterpret_cast<T*>(w0.sr.get());
-    convert<T, double>(D, v, f, s);
+    mg_input<T>(D, v, f, s);
     if (graphs_allowed(op) && op->scalls > 0) {
         if (!op->sexec && !capture_graph(op, [&] { svcycle<T, TC>(op, 0, f, e, r); }, &op->sexec, &op->sexec_kernels))
             op->graphs = false;
@@ -506,7 +541,8 @@ void precond_scal_T(dm_operator* op, const double* v, double* z) {
     convert<double, T>(D, r, z, s);
 }
 
-void precond_vec(dm_operator* op, const double* v, double* z) {
+template <typename TIn>
+void precond_vec(dm_operator* op, const TIn* v, double* z) {
     switch (op->mg.precision) {
         case DM_PREC_F64: precond_vec_T<double, double>(op, v, z); break;
         case DM_PREC_F32: precond_vec_T<float, float>(op, v, z); break;
@@ -514,7 +550,8 @@ void precond_vec(dm_operator* op, const double* v, double* z) {
     }
 }
 
-void precond_scal(dm_operator* op, const double* v, double* z) {
+template <typename TIn>
+void precond_scal(dm_operator* op, const TIn* v, double* z) {
     switch (op->mg.precision) {
         case DM_PREC_F64: precond_scal_T<double, double>(op, v, z); break;
         case DM_PREC_F32: precond_scal_T<float, float>(op, v, z); break;
@@ -548,7 +585,8 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
     ws.ensure(n, m);
-    double* V = ws.V.get();
+    float2* V = ws.V.get();
+    float2* wf = ws.wf.get();
     double* Z = ws.Z.get();
     double* w = ws.w.get();
     zero(x, sizeof(double) * n, s);
@@ -563,18 +601,16 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
     double res = 1.0;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     while (total < maxit) {
-        // r = b - A x
-        if (first) {
-            scale_copy(D, 1.0, b, V, s);
-        } else {
+        // r = b - A x (FP64); V_0 = r / beta in float-float
+        double beta = bnorm;
+        if (!first) {
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
-            scale_copy(D, 1.0, w, V, s);
+            beta = norm2(ctx, D, w);
         }
-        const double beta = norm2(ctx, D, V);
         res = beta / bnorm;
         if (beta <= thr) break;
-        scale_copy(D, 1.0 / beta, V, V, s);
+        ff_split(D, 1.0 / beta, first ? b : w, V, s);
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -582,21 +618,22 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         for (int j = 0; j < m && total < maxit; ++j) {
             prec(V + (size_t)j * n, Z + (size_t)j * n);
             apply(Z + (size_t)j * n, w);
+            ff_split(D, 1.0, w, wf, s);
             // classical Gram-Schmidt, repeated only when the pass cancelled most
             // of w (Kahan: ||w'|| < 0.7 ||w||), norms fused into the passes
             std::vector<double> h(j + 1);
             double wn2 = 0.0;
-            mdot_self(ctx->red, D, j + 1, V, n, w, nullptr, h.data(), &wn2, s);
-            double hn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, nullptr, s);
+            mdot_ff(ctx->red, D, j + 1, V, n, wf, h.data(), &wn2, s);
+            double hn2 = maxpy_norm_ff(ctx->red, D, j + 1, V, n, wf, s);
             for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
             if (hn2 < 0.49 * wn2) {
-                mdot(ctx->red, D, j + 1, V, n, w, nullptr, h.data(), s);
-                hn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, nullptr, s);
+                mdot_ff(ctx->red, D, j + 1, V, n, wf, h.data(), nullptr, s);
+                hn2 = maxpy_norm_ff(ctx->red, D, j + 1, V, n, wf, s);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
             }
             const double hn = std::sqrt(std::max(hn2, 0.0));
             H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) scale_copy(D, 1.0 / hn, w, V + (size_t)(j + 1) * n, s);
+            if (hn > 0.0) ff_scale(D, 1.0 / hn, wf, V + (size_t)(j + 1) * n, s);
             // Givens
             for (int i = 0; i < j; ++i) {
                 const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -645,7 +682,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
-    auto prec = [op](const double* in, double* out) { precond_vec(op, in, out); };
+    auto prec = [op](const float2* in, double* out) { precond_vec(op, in, out); };
     // the learned correction is judged by the FP64 residual: an iteration that
     // contracts by less than 0.8 switches it off for the rest of the solve
     op->learned_active = op->lnet != nullptr;
@@ -678,7 +715,7 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     const double hmin = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
     const double xscale = norm2(op->ctx, g0.vdom(), x) / hmin;
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
-    auto prec = [op](const double* in, double* out) { precond_scal(op, in, out); };
+    auto prec = [op](const float2* in, double* out) { precond_scal(op, in, out); };
     double rr = 0.0;
     const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
@@ -843,23 +880,39 @@ void setup_operator(dm_operator* op) {
             convert_coeff<float>(n1, o.invDs.get(), o.invDs32.get(), s);
         }
         if (g.nband > 0 && l + 1 < nl) {
-            constexpr int kMaxRow = 48;
-            const size_t nb = (size_t)g.nband;
-            DBuf<int> cols(kMaxRow * nb, false), mx(1);
-            DBuf<double> vals(kMaxRow * nb, false);
-            const int w = band_rows(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, g.band.get(), g.nband, kMaxRow,
-                                    cols.get(), vals.get(), mx.get(), s);
-            DM_REQUIRE(w <= kMaxRow, DM_ERR_GEOMETRY, "band row longer than the ELL width");
-            o.bwidth = std::max(w, 1);
-            o.bcols.alloc((size_t)o.bwidth * nb, false);
-            o.bv64.alloc((size_t)o.bwidth * nb, false);
-            DM_CUDA(cudaMemcpyAsync(o.bcols.get(), cols.get(), sizeof(int) * o.bwidth * nb, cudaMemcpyDeviceToDevice, s));
-            DM_CUDA(cudaMemcpyAsync(o.bv64.get(), vals.get(), sizeof(double) * o.bwidth * nb, cudaMemcpyDeviceToDevice, s));
-            if (lowp) {
-                o.bv32.alloc((size_t)o.bwidth * nb, false);
-                convert_coeff<float>((long long)o.bwidth * nb, o.bv64.get(), o.bv32.get(), s);
+            SchwarzLayout sl;
+            band_schwarz_setup(g.g, g.band.get(), g.nband, op->mg.band_brick, sl, s);
+            o.sd_nsub = (int)sl.off.size() - 1;
+            o.sd_ncopies = (int)sl.copy.size();
+            o.sd_maxrows = sl.maxrows;
+            o.sd_maxbox = sl.maxbox;
+            for (int k = 0; k < kSchwarzClasses; ++k) {
+                o.sd_cls_first[k] = sl.cls_first[k];
+                o.sd_cls_count[k] = sl.cls_count[k];
             }
-            Sync::stream(s);
+            switch (op->mg.precision) {
+                case DM_PREC_F64: band_schwarz_prepare<double, double>(sl); break;
+                case DM_PREC_F32: band_schwarz_prepare<float, float>(sl); break;
+                default: band_schwarz_prepare<__nv_bfloat16, float>(sl);
+            }
+            auto upload = [&](DBuf<int>& d, const std::vector<int>& h) {
+                d.alloc(h.size(), false);
+                DM_CUDA(cudaMemcpyAsync(d.get(), h.data(), sizeof(int) * h.size(), cudaMemcpyHostToDevice, s));
+            };
+            upload(o.sd_off, sl.off);
+            upload(o.sd_copy, sl.copy);
+            upload(o.sd_pos, sl.pos);
+            upload(o.sd_dims, sl.dims);
+            const size_t nb = (size_t)g.nband, nv = (size_t)kBandSlots * o.sd_ncopies;
+            DBuf<double> rows(kBandSlots * nb, false);
+            band_slots(g.g, g.A.get(), g.L.get(), g.invV.get(), op->sigma, g.band.get(), g.nband, rows.get(), s);
+            o.sd_v64.alloc(nv, false);
+            band_copy_vals(o.sd_copy.get(), o.sd_ncopies, rows.get(), g.nband, o.sd_v64.get(), s);
+            if (lowp) {
+                o.sd_v32.alloc(nv, false);
+                convert_coeff<float>((long long)nv, o.sd_v64.get(), o.sd_v32.get(), s);
+            }
+            Sync::stream(s);   // the host layout and the row buffer are released on return
         }
         WorkLevel& w = op->wk[l];
         w.f.alloc(ts * n3);
@@ -1231,7 +1284,8 @@ dm_status dm_geometry_fractions(const dm_geometry* geom, int level, double* L, d
 void dm_mg_params_default(dm_mg_params* p) {
     if (!p) return;
     p->max_coarse = 4;
-    p->band_sweeps = 8;
+    p->band_sweeps = 16;
+    p->band_brick = 8;
     p->omega_scale = 1.7;
     p->power_iters = 30;
     p->precision = DM_PREC_F64;
@@ -1251,7 +1305,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         dm_mg_params_default(&op->mg);
         if (mg) op->mg = *mg;
         DM_REQUIRE(op->mg.max_coarse >= 4, DM_ERR_INVALID_ARG, "max_coarse must be >= 4");
-        DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 64, DM_ERR_INVALID_ARG, "band_sweeps out of range");
+        DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 256, DM_ERR_INVALID_ARG, "band_sweeps out of range");
+        DM_REQUIRE(op->mg.band_brick >= 1, DM_ERR_INVALID_ARG, "band_brick must be >= 1");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
         const char* ng = std::getenv("DMEIG_NO_GRAPHS");
@@ -1323,14 +1378,14 @@ dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double
         double* pads[3] = {fp.get(), xp.get(), yp.get()};
         cudaStream_t s = op->ctx->stream;
         const double om = op->ol[level].omega;
-        float* u = reinterpret_cast<float*>(op->band_u.get());
+        double* u = op->band_u.get();
         auto run = [&](auto** p) {
             using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
             using TC = std::conditional_t<std::is_same<T, double>::value, double, float>;
             const VecOp<T, TC> o = vop<T, TC>(op, level);
             vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
-            band_sweeps_ell<T, TC>(Pick<T, TC>::br(op->ol[level]), o.invD, g.band.get(), g.nband, p[0], p[2], u, om,
-                                   op->mg.band_sweeps, level == 0, s);
+            band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[level]), o.invD, g.g, g.band.get(), g.nband, p[0], p[2], u, om,
+                                op->mg.band_sweeps, level == 0, s);
         };
         if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
         else if (op->mg.precision == DM_PREC_F32)
@@ -1513,30 +1568,47 @@ __global__ void k_sign_fix(long long n, double* __restrict__ x, const double* __
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
         x[r] *= *sign;
 }
-// sign = +1 if the entry of largest magnitude is positive (first such entry on ties)
-__global__ void k_max_entry_sign(long long n, const double* __restrict__ x, double* __restrict__ sign) {
-    __shared__ double bv[1024];
-    __shared__ long long bi[1024];
-    double best = -1.0;
-    long long idx = 0;
-    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-        const double a = fabs(x[r]);
-        if (a > best) { best = a; idx = r; }
+// sign = +1 if the entry of largest magnitude is positive (first such entry on
+// ties): per-block (value, index) maxima, then one block reduces them
+constexpr int kSignBlocks = 304;
+__device__ __forceinline__ void max_pair(double& bv, long long& bi, double v, long long i) {
+    if (v > bv || (v == bv && i < bi)) {
+        bv = v;
+        bi = i;
     }
+}
+__device__ void block_max_pair(double& best, long long& idx) {
+    __shared__ double bv[256];
+    __shared__ long long bi[256];
     bv[threadIdx.x] = best;
     bi[threadIdx.x] = idx;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            if (bv[threadIdx.x + s] > bv[threadIdx.x] ||
-                (bv[threadIdx.x + s] == bv[threadIdx.x] && bi[threadIdx.x + s] < bi[threadIdx.x])) {
-                bv[threadIdx.x] = bv[threadIdx.x + s];
-                bi[threadIdx.x] = bi[threadIdx.x + s];
-            }
-        }
+        if (threadIdx.x < s) max_pair(bv[threadIdx.x], bi[threadIdx.x], bv[threadIdx.x + s], bi[threadIdx.x + s]);
         __syncthreads();
     }
-    if (threadIdx.x == 0) *sign = x[bi[0]] < 0.0 ? -1.0 : 1.0;
+    best = bv[0];
+    idx = bi[0];
+}
+__global__ void k_max_entry_partial(long long n, const double* __restrict__ x, double* __restrict__ pv,
+                                    long long* __restrict__ pi) {
+    double best = -1.0;
+    long long idx = 0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        max_pair(best, idx, fabs(x[r]), r);
+    block_max_pair(best, idx);
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = best;
+        pi[blockIdx.x] = idx;
+    }
+}
+__global__ void k_max_entry_sign(int nb, const double* __restrict__ pv, const long long* __restrict__ pi,
+                                 const double* __restrict__ x, double* __restrict__ sign) {
+    double best = -1.0;
+    long long idx = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) max_pair(best, idx, pv[b], pi[b]);
+    block_max_pair(best, idx);
+    if (threadIdx.x == 0) *sign = x[idx] < 0.0 ? -1.0 : 1.0;
 }
 
 }  // namespace
@@ -1649,7 +1721,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         std::vector<double> Yw((size_t)m * nev);
         for (int c = 0; c < nev; ++c)
             for (int r = 0; r < m; ++r) Yw[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
-        DBuf<double> Yd((size_t)m * nev), sign(1);
+        DBuf<double> Yd((size_t)m * nev), sign(1), pv(kSignBlocks);
+        DBuf<long long> pi(kSignBlocks);
         DM_CUDA(cudaMemcpyAsync(Yd.get(), Yw.data(), sizeof(double) * m * nev, cudaMemcpyHostToDevice, s));
         vgemm(D, m, nev, V, n, Yd.get(), m, tmp.get(), n, s);
         std::vector<double> k2(nev), rho(nev), delta(nev), rq(nev);
@@ -1657,7 +1730,10 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             double* b = tmp.get() + (size_t)c * n;
             const double nb = norm2(ctx, D, b, a);
             scale_copy(D, 1.0 / nb, b, b, s);
-            launch("k_max_entry_sign", k_max_entry_sign, 1, 1024, 0, s, n, b, sign.get());
+            launch("k_max_entry_partial", k_max_entry_partial, kSignBlocks, 256, 0, s, n, (const double*)b, pv.get(),
+                   pi.get());
+            launch("k_max_entry_sign", k_max_entry_sign, 1, 256, 0, s, kSignBlocks, (const double*)pv.get(),
+                   (const long long*)pi.get(), (const double*)b, sign.get());
             launch("k_sign_fix", k_sign_fix, (int)std::min<long long>((n + 255) / 256, 1216), 256, 0, s, n, b, sign.get());
         }
         certify_padded(ctx, g0, nev, tmp.get(), k2.data(), true, rho.data(), delta.data(), rq.data());

@@ -1,0 +1,372 @@
+// Cut-cell band smoother: a restricted additive Schwarz step on the band faces.
+//
+// The band holds the open faces next to a cell within one cell of a cut cell
+// (0 < V < 1).  It is covered by bricks of b^3 nodes (a face belongs to the
+// node at its lower corner).  The subdomain of a brick is every band face whose
+// node lies within one node of the brick; the brick owns the faces whose node
+// lies inside it.  From r0 = f - (K - sigma A) x, each subdomain runs `sweeps`
+// damped Jacobi sweeps d <- d + omega D^-1 (r0 - K_SS d) from d = 0 on its own
+// rows (couplings to faces outside the subdomain stay frozen), and x takes d
+// on the owned faces.  With one brick covering the grid this is plain
+// band-restricted Jacobi.
+//
+// One thread block per subdomain.  The correction d lives in shared memory on
+// the subdomain's local box of nodes (all three components, zero wherever the
+// subdomain has no row), so a row's couplings are reached at fixed offsets:
+// the 15 slots of band_slot.  Each thread keeps the coefficients of its rows in
+// registers, so every sweep after the first touches only registers and shared
+// memory, with one block barrier per sweep and none across the grid.
+#include <algorithm>
+#include <vector>
+
+#include "dm_common.cuh"
+
+namespace dm {
+
+namespace {
+
+// Couplings of a row in the subdomain's local box: component c at local node
+// n (index within one component's box), box strides st = {1, lx, lx ly}, l3
+// nodes per component.  The 15 slots of band_slot, in order, are
+//   same component:   n, n -/+ 1, n -/+ lx, n -/+ lx ly;
+//   component c + k (k = 1, 2), its stride sk = st[(c + k) % 3]:
+//     m, m + sk, m + sc, m + sc + sk  with m = n - sc (sc = st[c]) in that component.
+struct RowAddr {
+    int b0, b1, b2;   // n, and m in components c + 1 and c + 2 (offsets into the box)
+    int sc, s1, s2;
+};
+__device__ __forceinline__ RowAddr row_addr(int p, int l3, int lx, int lxy) {
+    RowAddr a;
+    const int c = p / l3, n = p - c * l3;
+    const int st[3] = {1, lx, lxy};
+    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+    a.sc = st[c];
+    a.s1 = st[c1];
+    a.s2 = st[c2];
+    a.b0 = p;
+    a.b1 = c1 * l3 + n - a.sc;
+    a.b2 = c2 * l3 + n - a.sc;
+    return a;
+}
+template <typename C>
+__device__ __forceinline__ C row_dot(const C* v, const C* d, const RowAddr& a, int lx, int lxy) {
+    C acc = v[0] * d[a.b0];
+    acc += v[1] * d[a.b0 - 1] + v[2] * d[a.b0 + 1];
+    acc += v[3] * d[a.b0 - lx] + v[4] * d[a.b0 + lx];
+    acc += v[5] * d[a.b0 - lxy] + v[6] * d[a.b0 + lxy];
+    acc += v[7] * d[a.b1] + v[8] * d[a.b1 + a.s1] + v[9] * d[a.b1 + a.sc] + v[10] * d[a.b1 + a.sc + a.s1];
+    acc += v[11] * d[a.b2] + v[12] * d[a.b2 + a.s2] + v[13] * d[a.b2 + a.sc] + v[14] * d[a.b2 + a.sc + a.s2];
+    return acc;
+}
+
+// R > 0: each thread owns up to R rows (row r = threadIdx.x + k blockDim.x) with
+// their coefficients and addresses in registers.  R == 0: any row count; r0
+// and omega/D in shared memory and the coefficients re-read on every sweep.
+// Block b handles subdomain sub0 + b.
+template <typename T, typename TC, int R, int NT>
+__global__ void __launch_bounds__(NT)
+    k_band_schwarz(int sub0, const int* __restrict__ off, const int* __restrict__ copy, const int* __restrict__ pos,
+                   const int* __restrict__ dims, const TC* __restrict__ vals, int ncopies,
+                   const int* __restrict__ band, const TC* __restrict__ invD, const T* __restrict__ f,
+                   const T* __restrict__ x, double* __restrict__ u, typename Compute<T>::type om, int sweeps, int np,
+                   int sx, int sxy, int maxbox, int maxrows) {
+    using C = typename Compute<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* const buf0 = reinterpret_cast<C*>(smem_raw);
+    C* const buf1 = buf0 + maxbox;
+    C* s_r0 = buf1 + maxbox;          // R == 0 only
+    C* s_w = s_r0 + maxrows;
+    const int sd = sub0 + blockIdx.x;
+    const int b0 = off[sd];
+    const int nr = off[sd + 1] - b0;
+    const int dm = dims[sd];
+    const int lx = dm & 1023, ly = (dm >> 10) & 1023, lz = dm >> 20;
+    const int lxy = lx * ly, l3 = lxy * lz;
+    for (int k = threadIdx.x; k < 3 * l3; k += blockDim.x) {
+        buf0[k] = C(0);
+        buf1[k] = C(0);
+    }
+    __syncthreads();
+    constexpr int RR = R > 0 ? R : 1;
+    C v[RR][kBandSlots];
+    C r0[RR], w[RR];
+    RowAddr ad[RR];
+    // residual of the full row at the start values, and the first sweep from d = 0
+    auto start_row = [&](int r, C* ve, C& rr, C& ww) {
+        const int ct = copy[b0 + r];
+        const int t = ct >= 0 ? ct : -1 - ct;
+        const int q = band[t];
+        const int c = q / np;
+        C acc = C(0);
+#pragma unroll
+        for (int e = 0; e < kBandSlots; ++e) {
+            ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
+            acc += ve[e] * (C)to_c(x[q + band_slot_offset(c, e, np, sx, sxy)]);
+        }
+        rr = (C)to_c(f[q]) - acc;
+        ww = om * (C)invD[q];
+        buf0[pos[b0 + r]] = ww * rr;
+    };
+    if constexpr (R > 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int r = threadIdx.x + k * blockDim.x;
+            if (r < nr) {
+                start_row(r, v[k], r0[k], w[k]);
+                ad[k] = row_addr(pos[b0 + r], l3, lx, lxy);
+            }
+        }
+    } else {
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) start_row(r, v[0], s_r0[r], s_w[r]);
+    }
+    __syncthreads();
+    C* dc = buf0;
+    C* dn = buf1;
+    for (int s = 1; s < sweeps; ++s) {
+        if constexpr (R > 0) {
+#pragma unroll
+            for (int k = 0; k < RR; ++k) {
+                const int r = threadIdx.x + k * blockDim.x;
+                if (r < nr) dn[ad[k].b0] = dc[ad[k].b0] + w[k] * (r0[k] - row_dot(v[k], dc, ad[k], lx, lxy));
+            }
+        } else {
+            for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+                const RowAddr a = row_addr(pos[b0 + r], l3, lx, lxy);
+                C ve[kBandSlots];
+#pragma unroll
+                for (int e = 0; e < kBandSlots; ++e) ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
+                dn[a.b0] = dc[a.b0] + s_w[r] * (s_r0[r] - row_dot(ve, dc, a, lx, lxy));
+            }
+        }
+        __syncthreads();
+        C* const tmp = dc;
+        dc = dn;
+        dn = tmp;
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        const int ct = copy[b0 + r];
+        if (ct >= 0) u[ct] = (double)dc[pos[b0 + r]];
+    }
+}
+
+template <typename T>
+__global__ void k_band_add(const int* __restrict__ band, int nband, const double* __restrict__ u,
+                           T* __restrict__ x) {
+    using C = typename Compute<T>::type;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nband) return;
+    const int q = band[t];
+    x[q] = to_store<T>((C)to_c(x[q]) + (C)u[t]);
+}
+
+__global__ void k_band_copy_vals(const int* __restrict__ copy, int ncopies, const double* __restrict__ band_vals,
+                                 int nband, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncopies) return;
+    const int ct = copy[c];
+    const int t = ct >= 0 ? ct : -1 - ct;
+    for (int e = 0; e < kBandSlots; ++e) out[(size_t)e * ncopies + c] = band_vals[(size_t)e * nband + t];
+}
+
+template <typename T>
+size_t schwarz_smem(int maxbox, int maxrows, int R) {
+    using C = typename Compute<T>::type;
+    return sizeof(C) * (2 * (size_t)maxbox + (R == 0 ? 2 * (size_t)maxrows : 0));
+}
+
+}  // namespace
+
+// Size classes of subdomains (rows): each class is launched with its own
+// block size and rows per thread, so that small subdomains are not held to the
+// register and thread budget of the largest.
+int schwarz_class(int rows) {
+    return rows <= 256 ? 0 : (rows <= 512 ? 1 : (rows <= 1024 ? 2 : (rows <= 2048 ? 3 : 4)));
+}
+
+namespace {
+
+}  // namespace
+
+void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int brick, SchwarzLayout& out,
+                        cudaStream_t s) {
+    DM_REQUIRE(brick >= 1, DM_ERR_INVALID_ARG, "band brick must be >= 1 node");
+    out = SchwarzLayout{};
+    if (nband <= 0) return;
+    std::vector<int> band(nband);
+    DM_CUDA(cudaMemcpyAsync(band.data(), band_dev, sizeof(int) * nband, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+
+    // node (i, j, k) and component of every band face: q = c np + off0 + i + sx (j + sy k)
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int nb[3] = {(g.nx + brick) / brick, (g.ny + brick) / brick, (g.nz + brick) / brick};
+    std::vector<int> node((size_t)3 * nband);
+    std::vector<char> owner((size_t)nb[0] * nb[1] * nb[2], 0);
+    auto key = [&](int bx, int by, int bz) { return ((long long)bz * nb[1] + by) * nb[0] + bx; };
+    for (int t = 0; t < nband; ++t) {
+        const int q = band[t];
+        const int r = q % g.np - g.off0;
+        const int k = r / g.sxy, rem = r - k * g.sxy;
+        const int j = rem / g.sx, i = rem - j * g.sx;
+        node[3 * t] = i;
+        node[3 * t + 1] = j;
+        node[3 * t + 2] = k;
+        owner[key(i / brick, j / brick, k / brick)] = 1;
+    }
+    // copies (brick, face): brick B holds node P when B b - 1 <= P <= B b + b on every axis,
+    // i.e. ceil(P / b) - 1 <= B <= floor((P + 1) / b)
+    struct Copy {
+        long long brick;
+        int q, t;
+        bool owned;
+    };
+    std::vector<Copy> cp;
+    cp.reserve((size_t)nband * 2);
+    for (int t = 0; t < nband; ++t) {
+        int lo[3], hi[3], own[3];
+        for (int a = 0; a < 3; ++a) {
+            const int P = node[3 * t + a];
+            own[a] = P / brick;
+            lo[a] = std::max((P + brick - 1) / brick - 1, 0);
+            hi[a] = std::min((P + 1) / brick, nb[a] - 1);
+        }
+        for (int bz = lo[2]; bz <= hi[2]; ++bz)
+            for (int by = lo[1]; by <= hi[1]; ++by)
+                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                    const long long kb = key(bx, by, bz);
+                    if (!owner[kb]) continue;
+                    cp.push_back(Copy{kb, band[t], t, bx == own[0] && by == own[1] && bz == own[2]});
+                }
+    }
+    std::sort(cp.begin(), cp.end(), [](const Copy& a, const Copy& b) {
+        return a.brick != b.brick ? a.brick < b.brick : a.q < b.q;
+    });
+    const int nc = (int)cp.size();
+    // subdomains (runs of one brick), emitted class by class
+    std::vector<std::pair<int, int>> runs;
+    for (int c0 = 0; c0 < nc;) {
+        int c1 = c0;
+        while (c1 < nc && cp[c1].brick == cp[c0].brick) ++c1;
+        runs.push_back({c0, c1});
+        c0 = c1;
+    }
+    std::stable_sort(runs.begin(), runs.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+        return schwarz_class(a.second - a.first) < schwarz_class(b.second - b.first);
+    });
+    for (int k = 0; k < kSchwarzClasses; ++k) out.cls_first[k] = out.cls_count[k] = 0;
+    out.copy.reserve(nc);
+    out.pos.reserve(nc);
+    for (size_t rI = 0; rI < runs.size(); ++rI) {
+        const int c0 = runs[rI].first, c1 = runs[rI].second;
+        const int cl = schwarz_class(c1 - c0);
+        if (out.cls_count[cl] == 0) out.cls_first[cl] = (int)rI;
+        ++out.cls_count[cl];
+        const long long kb = cp[c0].brick;
+        const int B[3] = {(int)(kb % nb[0]), (int)((kb / nb[0]) % nb[1]), (int)(kb / ((long long)nb[0] * nb[1]))};
+        // local box: the subdomain's nodes and their neighbours, within the padded grid
+        int lo[3], l[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::max(B[a] * brick - 2, -1);
+            const int hi = std::min(B[a] * brick + brick + 1, n[a] + 1);
+            l[a] = hi - lo[a] + 1;
+        }
+        DM_REQUIRE(l[0] < 1024 && l[1] < 1024 && l[2] < 1024, DM_ERR_INVALID_ARG, "band brick too large");
+        out.off.push_back((int)out.copy.size());
+        out.dims.push_back(l[0] | (l[1] << 10) | (l[2] << 20));
+        out.maxrows = std::max(out.maxrows, c1 - c0);
+        out.maxbox = std::max(out.maxbox, 3 * l[0] * l[1] * l[2]);
+        for (int c = c0; c < c1; ++c) {
+            const int t = cp[c].t;
+            const int comp = cp[c].q / g.np;
+            const int li = node[3 * t] - lo[0], lj = node[3 * t + 1] - lo[1], lk = node[3 * t + 2] - lo[2];
+            out.copy.push_back(cp[c].owned ? t : -1 - t);
+            out.pos.push_back(((comp * l[2] + lk) * l[1] + lj) * l[0] + li);
+        }
+    }
+    out.off.push_back(nc);
+}
+
+void band_copy_vals(const int* copy, int ncopies, const double* band_vals, int nband, double* out, cudaStream_t s) {
+    if (ncopies <= 0) return;
+    launch("k_band_copy_vals", k_band_copy_vals, (ncopies + 255) / 256, 256, 0, s, copy, ncopies, band_vals, nband,
+           out);
+}
+
+// rows per thread and block size of a class (R = 0: the shared-memory variant;
+// FP64 rows hold twice the registers, so FP64 stops at R = 2)
+template <typename T>
+void class_shape(int cl, int& R, int& nt) {
+    const bool wide = sizeof(typename Compute<T>::type) == 8;
+    switch (cl) {
+        case 0: R = 1; nt = 256; break;
+        case 1: R = 1; nt = 512; break;
+        case 2: R = 2; nt = 512; break;
+        case 3: R = wide ? 0 : 4; nt = 512; break;
+        default: R = 0; nt = 512;
+    }
+}
+
+template <typename T, typename TC>
+void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, const int* band, int nband, const T* f,
+                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s) {
+    if (nband <= 0 || bs.nsub <= 0 || sweeps <= 0) return;
+    const char* name = stencil_name("band_schwarz", prec_index<T>(), ST_JACOBI, fine);
+    for (int cl = 0; cl < kSchwarzClasses; ++cl) {
+        if (bs.cls_count[cl] == 0) continue;
+        int R, nt;
+        class_shape<T>(cl, R, nt);
+        const size_t smem = schwarz_smem<T>(bs.maxbox, bs.maxrows, R);
+#define DM_SCHWARZ(RV, NV)                                                                                         \
+    launch(name, k_band_schwarz<T, TC, RV, NV>, bs.cls_count[cl], NV, smem, s, bs.cls_first[cl], bs.off, bs.copy, \
+           bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,  \
+           bs.maxbox, bs.maxrows)
+        if (nt == 256) DM_SCHWARZ(1, 256);
+        else if (R == 1) DM_SCHWARZ(1, 512);
+        else if (R == 2) DM_SCHWARZ(2, 512);
+        else if (R == 4) DM_SCHWARZ(4, 512);
+        else DM_SCHWARZ(0, 512);
+#undef DM_SCHWARZ
+    }
+    launch(stencil_name("band_add", prec_index<T>(), ST_JACOBI, fine), k_band_add<T>, (nband + 255) / 256, 256, 0, s,
+           band, nband, (const double*)u, x);
+}
+
+// Allow each variant the device's opt-in shared memory less its static share;
+// the largest subdomain box must fit in it.
+template <typename K>
+void allow_smem(K kernel, size_t need) {
+    int dev = 0, optin = 0;
+    DM_CUDA(cudaGetDevice(&dev));
+    DM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    DM_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const long long limit = (long long)optin - (long long)fa.sharedSizeBytes;
+    DM_REQUIRE((long long)need <= limit, DM_ERR_INVALID_ARG,
+               "band brick too large: a subdomain's local box exceeds shared memory (use a smaller brick)");
+    DM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
+}
+
+template <typename T, typename TC>
+void band_schwarz_prepare(const SchwarzLayout& sl) {
+    for (int cl = 0; cl < kSchwarzClasses; ++cl) {
+        if (sl.cls_count[cl] == 0) continue;
+        int R, nt;
+        class_shape<T>(cl, R, nt);
+        const size_t need = schwarz_smem<T>(sl.maxbox, sl.maxrows, R);
+        if (nt == 256) allow_smem(k_band_schwarz<T, TC, 1, 256>, need);
+        else if (R == 1) allow_smem(k_band_schwarz<T, TC, 1, 512>, need);
+        else if (R == 2) allow_smem(k_band_schwarz<T, TC, 2, 512>, need);
+        else if (R == 4) allow_smem(k_band_schwarz<T, TC, 4, 512>, need);
+        else allow_smem(k_band_schwarz<T, TC, 0, 512>, need);
+    }
+}
+
+#define DM_INST(T, TC)                                                                                           \
+    template void band_schwarz<T, TC>(const BandSchwarz<TC>&, const TC*, const Grid3&, const int*, int, const T*, \
+                                      T*, double*, double, int, bool, cudaStream_t);                             \
+    template void band_schwarz_prepare<T, TC>(const SchwarzLayout&);
+DM_INST(double, double)
+DM_INST(float, float)
+DM_INST(__nv_bfloat16, float)
+#undef DM_INST
+
+}  // namespace dm

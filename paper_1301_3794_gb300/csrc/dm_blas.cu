@@ -186,6 +186,172 @@ __global__ void k_fill_random(Domain d, unsigned long long seed, const double* _
     });
 }
 
+// ---- Krylov vectors in float-float (a pair of FP32 values per entry) -------
+// GB300 issues FP64 instructions at a small fraction of its FP32 rate, so
+// Gram-Schmidt on FP64 vectors is bound by the FP64 pipe, not by HBM.  The
+// FGMRES basis and work vector are therefore stored as hi + lo (two FP32,
+// about 48 significant bits) and every dot product, update and norm on them
+// runs on the FP32 pipes with error-free transforms (Dekker's product via FMA,
+// Knuth's two-sum).  FP64 values enter through ff_bits, which splits a double
+// with integer operations only.
+
+// hi = the double's leading 24 significant bits (truncated), lo = the rest
+// rounded to FP32; magnitudes outside the normal FP32 range give hi = 0
+// (below 2^-126) or +-inf (at and above 2^128), and lo is flushed to 0 when it
+// would fall below the normal FP32 range (so values under about 2^-100 keep
+// only FP32 precision: callers split vectors scaled to unit norm or to the
+// operator's natural scale).
+__device__ __forceinline__ float2 ff_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int sgn = (unsigned int)(b >> 32) & 0x80000000u;
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const int e = (int)(mag >> 52);                      // biased FP64 exponent
+    const int fe = e - 1023 + 127;                        // biased FP32 exponent of hi
+    if (fe <= 0) return make_float2(__uint_as_float(sgn), __uint_as_float(sgn));
+    if (fe >= 255) return make_float2(__uint_as_float(sgn | 0x7f800000u), 0.f);
+    const float hi = __uint_as_float(sgn | ((unsigned int)fe << 23) | (unsigned int)((mag >> 29) & 0x7fffffu));
+    const unsigned int rem = (unsigned int)(mag & 0x1fffffffu);   // 29 low mantissa bits, weight 2^(e - 1075)
+    if (rem == 0) return make_float2(hi, __uint_as_float(sgn));
+    const int k = 31 - __clz(rem);                        // leading bit of rem
+    const int le = k + e - 1075 + 127;                     // biased exponent of lo
+    if (le <= 0) return make_float2(hi, __uint_as_float(sgn));
+    unsigned int frac;
+    if (k <= 23) {
+        frac = (rem << (23 - k)) & 0x7fffffu;
+    } else {
+        // round to nearest, ties to even, on the k - 23 dropped bits
+        const int sh = k - 23;
+        const unsigned int keep = rem >> sh, drop = rem & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        unsigned int m = keep + ((drop > half || (drop == half && (keep & 1u))) ? 1u : 0u);
+        if (m >> 24) return make_float2(hi, __uint_as_float(sgn | ((unsigned int)(le + 1) << 23)));
+        frac = m & 0x7fffffu;
+    }
+    return make_float2(hi, __uint_as_float(sgn | ((unsigned int)le << 23) | frac));
+}
+// s + e += a * b with a = (ah, al), b = (bh, bl) (s the running sum, e the
+// collected rounding errors and low-order terms)
+__device__ __forceinline__ void ff_madd(float ah, float al, float bh, float bl, float& s, float& e) {
+    // the _rn intrinsics are never contracted into FMAs, which would break the
+    // error-free transforms
+    const float p = __fmul_rn(ah, bh);
+    float pe = fmaf(ah, bh, -p);
+    pe = fmaf(ah, bl, pe);
+    pe = fmaf(al, bh, pe);
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    e = __fadd_rn(e, __fadd_rn(err, pe));
+    s = t;
+}
+// (hi, lo) with |lo| <= ulp(hi) / 2 from an unnormalised pair (Fast2Sum, |s| >= |e|)
+__device__ __forceinline__ float2 ff_norm(float s, float e) {
+    const float hi = __fadd_rn(s, e);
+    return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+__device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
+
+// y = split(a x); a = 1 skips the FP64 multiply
+__global__ void k_ff_split(Domain d, double a, const double* __restrict__ x, float2* __restrict__ y) {
+    if (a == 1.0) for_each_entry(d, [&](long long r) { y[r] = ff_bits(x[r]); });
+    else for_each_entry(d, [&](long long r) { y[r] = ff_bits(a * x[r]); });
+}
+// y = a x, a = (ah, al)
+__global__ void k_ff_scale(Domain d, float ah, float al, const float2* __restrict__ x, float2* __restrict__ y) {
+    for_each_entry(d, [&](long long r) {
+        const float2 v = x[r];
+        float s = 0.f, e = 0.f;
+        ff_madd(ah, al, v.x, v.y, s, e);
+        y[r] = ff_norm(s, e);
+    });
+}
+template <typename T>
+__global__ void k_ff_convert(Domain d, const float2* __restrict__ x, T* __restrict__ y) {
+    for_each_entry(d, [&](long long r) {
+        const float2 v = x[r];
+        if constexpr (std::is_same<T, double>::value) y[r] = ff_to_double(v);
+        else y[r] = to_store<T>(__fadd_rn(v.x, v.y));
+    });
+}
+
+// partial[b * ldp + c0 + c] = sum over this block's entries of V_c x; with
+// self, partial[b * ldp + m] = sum x^2
+__global__ void k_ff_mdot_partial(Domain d, int m, const float2* __restrict__ V, long long ld,
+                                  const float2* __restrict__ x, double* __restrict__ partial, int ldp, int self) {
+    constexpr int kc = 8;
+    __shared__ double red[kThreads / 32][kc];
+    __shared__ double red_self[kThreads / 32];
+    float ss = 0.f, se = 0.f;
+    for (int c0 = 0; c0 < m; c0 += kc) {
+        const int nc = min(kc, m - c0);
+        float s[kc], e[kc];
+#pragma unroll
+        for (int c = 0; c < kc; ++c) s[c] = e[c] = 0.f;
+        const bool first = c0 == 0 && self;
+        for_each_entry(d, [&](long long r) {
+            const float2 xs = x[r];
+            if (first) ff_madd(xs.x, xs.y, xs.x, xs.y, ss, se);
+#pragma unroll
+            for (int c = 0; c < kc; ++c)
+                if (c < nc) {
+                    const float2 v = V[(c0 + c) * ld + r];
+                    ff_madd(v.x, v.y, xs.x, xs.y, s[c], e[c]);
+                }
+        });
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int c = 0; c < kc; ++c) {
+            const double t = warp_sum((double)s[c] + (double)e[c]);
+            if (lane == 0) red[wid][c] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            double t = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) t += red[k][threadIdx.x];
+            partial[(long long)blockIdx.x * ldp + c0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    if (self) {
+        const double v = warp_sum((double)ss + (double)se);
+        if ((threadIdx.x & 31) == 0) red_self[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kThreads / 32; ++k) t += red_self[k];
+            partial[(long long)blockIdx.x * ldp + m] = t;
+        }
+    }
+}
+
+// x -= sum_c h[c] V_c (h on the device, FP64) and the block partial of sum x^2
+__global__ void k_ff_maxpy_norm(Domain d, int m, const float2* __restrict__ V, long long ld,
+                                const double* __restrict__ h, float2* __restrict__ x, double* __restrict__ partial) {
+    __shared__ float2 hs[128];
+    __shared__ double red[kThreads / 32];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = ff_bits(-h[c]);
+    __syncthreads();
+    float ns = 0.f, ne = 0.f;
+    for_each_entry(d, [&](long long r) {
+        const float2 x0 = x[r];
+        float s = x0.x, e = x0.y;
+        for (int c = 0; c < m; ++c) {
+            const float2 v = V[c * ld + r];
+            ff_madd(hs[c].x, hs[c].y, v.x, v.y, s, e);
+        }
+        const float2 y = ff_norm(s, e);
+        x[r] = y;
+        ff_madd(y.x, y.y, y.x, y.y, ns, ne);
+    });
+    const double v = warp_sum((double)ns + (double)ne);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) t += red[k];
+        partial[blockIdx.x] = t;
+    }
+}
+
 inline int blocks_for(const Domain& d) {
     const long long work = d.tiles ? (long long)d.ntiles : (d.len() + kThreads - 1) / kThreads;
     return (int)std::max<long long>(1, std::min<long long>(work, kMaxBlocks));
@@ -251,6 +417,46 @@ void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, 
     for (int c = 0; c < m; ++c) red.host[c] = h_host[c];
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
     launch("k_maxpy", k_maxpy, blocks_for(d), kThreads, 0, s, d, m, V, ld, red.result, x);
+}
+
+void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s) {
+    launch("k_ff_split", k_ff_split, blocks_for(d), kThreads, 0, s, d, a, x, y);
+}
+void ff_scale(const Domain& d, double a, const float2* x, float2* y, cudaStream_t s) {
+    const float ah = (float)a;
+    const float al = (float)(a - (double)ah);
+    launch("k_ff_scale", k_ff_scale, blocks_for(d), kThreads, 0, s, d, ah, al, x, y);
+}
+template <typename T>
+void ff_convert(const Domain& d, const float2* x, T* y, cudaStream_t s) {
+    launch("k_ff_convert", k_ff_convert<T>, blocks_for(d), kThreads, 0, s, d, x, y);
+}
+template void ff_convert<double>(const Domain&, const float2*, double*, cudaStream_t);
+template void ff_convert<float>(const Domain&, const float2*, float*, cudaStream_t);
+template void ff_convert<__nv_bfloat16>(const Domain&, const float2*, __nv_bfloat16*, cudaStream_t);
+void mdot_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, const float2* x, double* host_out,
+             double* self_out, cudaStream_t s) {
+    const int self = self_out ? 1 : 0;
+    DM_REQUIRE(m >= 1 && m + self <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
+    const int nb = blocks_for(d);
+    launch("k_ff_mdot_partial", k_ff_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, red.partial, red.max_cols,
+           self);
+    launch("k_mdot_final", k_mdot_final, (m + self + 7) / 8, 256, 0, s, nb, m + self, red.partial, red.max_cols,
+           red.result);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * (m + self), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
+    if (self_out) *self_out = red.host[m];
+}
+double maxpy_norm_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, float2* x, cudaStream_t s) {
+    DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
+    const int nb = blocks_for(d);
+    double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
+    launch("k_ff_maxpy_norm", k_ff_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld, red.result, x, part);
+    launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return red.host[0];
 }
 
 void vgemm(const Domain& d, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,

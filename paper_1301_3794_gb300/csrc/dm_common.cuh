@@ -54,11 +54,25 @@ struct Grid3 {
     int np;                // sx * sy * sz, multiple of 4
     int off0;              // index of node (0, 0, 0)
     double hx, hy, hz;     // spacing
+    double rhx, rhy, rhz;  // 1 / spacing (computed once on the host, so kernels divide nothing)
+    float rhxf, rhyf, rhzf;
 
     __host__ __device__ int idx(int i, int j, int k) const { return off0 + i + sx * (j + sy * k); }
 };
 
 Grid3 make_grid(int nx, int ny, int nz, double hx, double hy, double hz);
+
+// 1 / h along axis a in the compute type of a kernel
+template <typename C>
+__host__ __device__ inline C inv_h(const Grid3& g, int a);
+template <>
+__host__ __device__ inline double inv_h<double>(const Grid3& g, int a) {
+    return a == 0 ? g.rhx : (a == 1 ? g.rhy : g.rhz);
+}
+template <>
+__host__ __device__ inline float inv_h<float>(const Grid3& g, int a) {
+    return a == 0 ? g.rhxf : (a == 1 ? g.rhyf : g.rhzf);
+}
 
 // Active tiles: 32 x 4 x 2 blocks of node positions (i in [0, nx], ...) that
 // hold at least one open face or active cell of the level.  Every vector entry
@@ -301,27 +315,68 @@ template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s);
 template <typename T, typename TC>
 void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s);
-template <typename T, typename TC>
-void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
-                    cudaStream_t s);
-// `sweeps` band sweeps in one cooperative launch (same result as calling vec_band_sweep `sweeps` times)
-template <typename T, typename TC>
-void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
-                     int sweeps, cudaStream_t s);
-// Band rows of K - sigma A in ELL form (slot-major), see k_band_rows
-template <typename TC>
-struct BandRows {
-    const int* cols = nullptr;
-    const TC* vals = nullptr;
-    int width = 0;
+// The couplings of one face row of K - sigma A (a face of component c at node
+// p) sit in 15 fixed slots: slot 0 the face itself, 1..6 the same component at
+// -e_x, +e_x, -e_y, +e_y, -e_z, +e_z; 7..10 component (c+1)%3 and 11..14
+// component (c+2)%3, each at offset -1 or 0 along axis c and 0 or +1 along the
+// column's own axis.
+constexpr int kBandSlots = 15;
+__host__ __device__ inline void band_slot(int c, int e, int& cc, int o[3]) {
+    o[0] = o[1] = o[2] = 0;
+    if (e < 7) {
+        cc = c;
+        if (e > 0) o[(e - 1) >> 1] = ((e - 1) & 1) ? 1 : -1;
+    } else {
+        const int k = (e - 7) & 3;
+        cc = (c + 1 + (e - 7) / 4) % 3;
+        o[c] = (k >> 1) ? 0 : -1;
+        o[cc] = k & 1;
+    }
+}
+// offset of slot e's column from the row's packed index (padded layout)
+__host__ __device__ inline int band_slot_offset(int c, int e, int np, int sx, int sxy) {
+    int cc, o[3];
+    band_slot(c, e, cc, o);
+    return (cc - c) * np + o[0] + o[1] * sx + o[2] * sxy;
+}
+// 15 slot coefficients of every band row (slot-major, FP64)
+void band_slots(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
+                int nband, double* vals, cudaStream_t s);
+
+// Subdomains of the band smoother (dm_band.cu).  Host form: copies of band
+// faces grouped by brick (off), each copy's band position (copy; -1 - t when
+// the brick does not own it) and its position in the subdomain's local box of
+// nodes (pos = ((c lz + k) ly + j) lx + i, box dims packed in dims).
+// Subdomains are stored class by class (schwarz_class of their row count):
+// class k holds subdomains cls_first[k] .. cls_first[k] + cls_count[k] - 1.
+constexpr int kSchwarzClasses = 5;
+int schwarz_class(int rows);
+struct SchwarzLayout {
+    std::vector<int> off, copy, pos, dims;
+    int maxrows = 0, maxbox = 0;
+    int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
 };
-// assemble up to `width` entries per band row; returns the largest row length
-int band_rows(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
-              int nband, int width, int* cols, double* vals, int* d_maxnz, cudaStream_t s);
-// `sweeps` Jacobi sweeps restricted to the band, from the assembled rows
+template <typename TC>
+struct BandSchwarz {
+    const int* off = nullptr;
+    const int* copy = nullptr;
+    const int* pos = nullptr;
+    const int* dims = nullptr;
+    const TC* vals = nullptr;     // [15][ncopies] slot coefficients of each copy's row
+    int nsub = 0, ncopies = 0, maxrows = 0, maxbox = 0;
+    int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
+};
+void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int brick, SchwarzLayout& out,
+                        cudaStream_t s);
+// per-copy slot coefficients from the band rows' (both slot-major)
+void band_copy_vals(const int* copy, int ncopies, const double* band_vals, int nband, double* out, cudaStream_t s);
+// checks the shared-memory need of the largest subdomain box and enables it
 template <typename T, typename TC>
-void band_sweeps_ell(const BandRows<TC>& br, const TC* invD, const int* band, int nband, const T* f, T* x, float* u,
-                     double omega, int sweeps, bool fine, cudaStream_t s);
+void band_schwarz_prepare(const SchwarzLayout& sl);
+// x <- x + (restricted additive Schwarz correction on the band); u: nband doubles of scratch
+template <typename T, typename TC>
+void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, const int* band, int nband, const T* f,
+                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s);
 void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
                          const double* x, double* y, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
@@ -397,6 +452,17 @@ void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long 
                double* host_out, double* self_out, cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r] using the h the preceding mdot left on the device (red.result),
 // and returns sum_r w[r] x[r]^2 of the updated x (one pass, one sync)
+// Krylov vectors in float-float (hi + lo FP32 pairs, about 48 significant
+// bits, arithmetic on the FP32 pipes): y = split(a x); y = a x; y = x in the
+// storage type T; h = V^T x (and sum x^2 when self_out); x -= V h with h the
+// preceding mdot_ff's device result, returning sum x^2.
+void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s);
+void ff_scale(const Domain& d, double a, const float2* x, float2* y, cudaStream_t s);
+template <typename T>
+void ff_convert(const Domain& d, const float2* x, T* y, cudaStream_t s);
+void mdot_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, const float2* x, double* host_out,
+             double* self_out, cudaStream_t s);
+double maxpy_norm_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, float2* x, cudaStream_t s);
 double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long long ld, double* x, const double* w,
                   cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r]    (h host array, m <= max_cols)

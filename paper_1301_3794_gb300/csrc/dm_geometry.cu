@@ -381,6 +381,8 @@ Grid3 make_grid(int nx, int ny, int nz, double hx, double hy, double hz) {
     g.np = (int)np;
     g.off0 = 1 + g.sx * (1 + g.sy);
     g.hx = hx; g.hy = hy; g.hz = hz;
+    g.rhx = 1.0 / hx; g.rhy = 1.0 / hy; g.rhz = 1.0 / hz;
+    g.rhxf = (float)g.rhx; g.rhyf = (float)g.rhy; g.rhzf = (float)g.rhz;
     return g;
 }
 

@@ -17,7 +17,6 @@
 // Scalar operator inside the projection (Eq. proj): S = D A D^T on cells.
 #include "dm_common.cuh"
 
-#include <cooperative_groups.h>
 #include <atomic>
 #include <mutex>
 #include <set>
@@ -38,17 +37,6 @@ struct VecAcc {
     const T* __restrict__ x;
     int np;
     __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(x[c * np + p]); }
-};
-// Same, for kernels that also write the vector they read (no __restrict__,
-// so loads are neither cached across grid barriers nor routed through the
-// read-only path).
-template <typename T, typename C>
-struct VecAccRW {
-    const T* x;
-    int np;
-    // ld.global.cg: cached in L2 only, so values other SMs wrote before a grid
-    // barrier are never read from a stale L1 line
-    __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(__ldcg(x + c * np + p)); }
 };
 // Accessor of the unit vector e_q (packed index q = c*np + p); used to build
 // the coarsest matrix column by column from the same stencil.
@@ -145,9 +133,9 @@ __device__ __forceinline__ C face_K(const Coef<C, TC>& cf, const Acc& b, int c, 
 
 template <typename T, typename TC, int MODE>
 __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
-                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
-                              const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y, double omega_d,
-                              const int* __restrict__ tiles) {
+                              const TC* __restrict__ invV, const TC* __restrict__ invD,
+                              typename Compute<T>::type sigma, const T* __restrict__ x, const T* __restrict__ f,
+                              T* __restrict__ y, typename Compute<T>::type omega, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
     int i, j, k;
     block_node(g, tiles, i, j, k);
@@ -157,7 +145,7 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
     Coef<C, TC> cf{A, L, invV, N};
     VecAcc<T, C> b{x, N};
     C out[3];
-    node_K(cf, b, p, 1, g.sx, g.sxy, C(1.0 / g.hx), C(1.0 / g.hy), C(1.0 / g.hz), C(sigma_d), out);
+    node_K(cf, b, p, 1, g.sx, g.sxy, inv_h<C>(g, 0), inv_h<C>(g, 1), inv_h<C>(g, 2), sigma, out);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int q = c * N + p;
@@ -165,7 +153,7 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
         if (MODE == ST_RESID) {
             v = (C)to_c(f[q]) - v;
         } else if (MODE == ST_JACOBI) {
-            v = (C)to_c(x[q]) + C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - v);
+            v = (C)to_c(x[q]) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
         }
         y[q] = to_store<T>(v);
     }
@@ -180,8 +168,8 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
 template <typename T, typename TC, int MODE, int SY, int SZ>
 __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
     Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L, const TC* __restrict__ invV,
-    const TC* __restrict__ invD, double sigma_d, const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ y,
-    double omega_d, const int* __restrict__ tiles) {
+    const TC* __restrict__ invD, typename Compute<T>::type sigma, const T* __restrict__ x, const T* __restrict__ f,
+    T* __restrict__ y, typename Compute<T>::type omega, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
     constexpr int PSI_X = TX + 1, PSI_Y = SY + 1, PSI_Z = SZ + 1;   // psi: i0-1 .. i0+TX-1 (and j, k alike)
     constexpr int EX_X = TX, EX_Y = SY + 1, EX_Z = SZ + 1;          // ex:  i0 .. i0+TX-1, j0 .. j0+SY, k0 .. k0+SZ
@@ -195,7 +183,7 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
     const int nti = (g.nx + TX) / TX, ntj = (g.ny + SY) / SY;
     const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * SY, k0 = (t / (nti * ntj)) * SZ;
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
-    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz);
+    const C rdx = inv_h<C>(g, 0), rdy = inv_h<C>(g, 1), rdz = inv_h<C>(g, 2);
     Coef<C, TC> cf{A, L, invV, N};
     VecAcc<T, C> b{x, N};
     const int tid = threadIdx.x + TX * (threadIdx.y + SY * threadIdx.z);
@@ -239,7 +227,6 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
     auto EZS = [&](int a, int b_, int c) { return s_ez[(c * EZ_Y + b_) * EZ_X + a]; };
     const C ps0 = PSI(tx + 1, ty + 1, tz + 1);
     const C ax = cf.a(0, p), ay = cf.a(1, p), az = cf.a(2, p);
-    const C sigma = C(sigma_d);
     C out[3];
     out[0] = (EZS(tx, ty + 1, tz) - EZS(tx, ty, tz)) * rdy - (EYS(tx, ty, tz + 1) - EYS(tx, ty, tz)) * rdz +
              ax * ((PSI(tx, ty + 1, tz + 1) - ps0) * rdx - sigma * b(0, p));
@@ -255,7 +242,7 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
         if (MODE == ST_RESID) {
             v = (C)to_c(f[q]) - v;
         } else if (MODE == ST_JACOBI) {
-            v = (C)to_c(x[q]) + C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - v);
+            v = (C)to_c(x[q]) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
         }
         y[q] = to_store<T>(v);
     }
@@ -263,177 +250,27 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
 
 template <typename T, typename TC>
 __global__ void k_jacobi_zero(Domain d, const TC* __restrict__ invD, const T* __restrict__ f, T* __restrict__ y,
-                              double omega_d) {
+                              typename Compute<T>::type om) {
     using C = typename Compute<T>::type;
-    const C om = C(omega_d);
     for_each_entry(d, [&](long long q) { y[q] = to_store<T>(om * (C)invD[q] * (C)to_c(f[q])); });
 }
 
-template <typename T, typename TC>
-__global__ void k_band_update(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
-                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
-                              const int* __restrict__ band, int nband, const T* __restrict__ x,
-                              const T* __restrict__ f, float* __restrict__ u_f, double* __restrict__ u_d,
-                              double omega_d) {
-    using C = typename Compute<T>::type;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nband) return;
-    const int q = band[t];
-    const int c = q / g.np, p = q - c * g.np;
-    Coef<C, TC> cf{A, L, invV, g.np};
-    VecAcc<T, C> b{x, g.np};
-    const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, C(1.0 / g.hx), C(1.0 / g.hy), C(1.0 / g.hz), C(sigma_d));
-    const C u = C(omega_d) * (C)invD[q] * ((C)to_c(f[q]) - kx);
-    if (u_d) u_d[t] = (double)u;
-    else u_f[t] = (float)u;
-}
-
-template <typename T>
-__global__ void k_band_apply(const int* __restrict__ band, int nband, const float* __restrict__ u_f,
-                             const double* __restrict__ u_d, T* __restrict__ x) {
-    using C = typename Compute<T>::type;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nband) return;
-    const int q = band[t];
-    const C u = u_d ? (C)u_d[t] : (C)u_f[t];
-    x[q] = to_store<T>((C)to_c(x[q]) + u);
-}
-
-// All band sweeps of one smoothing step in one cooperative launch: per sweep,
-// every thread computes the Jacobi updates u of its band faces from the current
-// x, the grid synchronises, the updates are added, the grid synchronises again.
-// Same arithmetic as k_band_update + k_band_apply per sweep.
-template <typename T, typename TC>
-__global__ void k_band_sweeps(Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L,
-                              const TC* __restrict__ invV, const TC* __restrict__ invD, double sigma_d,
-                              const int* __restrict__ band, int nband, const T* __restrict__ f, T* x,
-                              float* u_f, double* u_d, double omega_d, int sweeps) {
-    using C = typename Compute<T>::type;
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    Coef<C, TC> cf{A, L, invV, g.np};
-    VecAccRW<T, C> b{x, g.np};
-    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz), sig = C(sigma_d), om = C(omega_d);
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int t = t0; t < nband; t += stride) {
-            const int q = band[t];
-            const int c = q / g.np, p = q - c * g.np;
-            const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sig);
-            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - kx);
-            if (u_d) u_d[t] = (double)u;
-            else u_f[t] = (float)u;
-        }
-        grid.sync();
-        for (int t = t0; t < nband; t += stride) {
-            const int q = band[t];
-            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
-            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
-        }
-        grid.sync();
-    }
-}
-
-// Small bands (coarse levels): all sweeps in one block, block barriers only.
-template <typename T, typename TC>
-__global__ void __launch_bounds__(1024) k_band_sweeps_block(
-    Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L, const TC* __restrict__ invV,
-    const TC* __restrict__ invD, double sigma_d, const int* __restrict__ band, int nband, const T* __restrict__ f,
-    T* x, float* u_f, double* u_d, double omega_d, int sweeps) {
-    using C = typename Compute<T>::type;
-    Coef<C, TC> cf{A, L, invV, g.np};
-    VecAccRW<T, C> b{x, g.np};
-    const C rdx = C(1.0 / g.hx), rdy = C(1.0 / g.hy), rdz = C(1.0 / g.hz), sig = C(sigma_d), om = C(omega_d);
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int t = threadIdx.x; t < nband; t += blockDim.x) {
-            const int q = band[t];
-            const int c = q / g.np, p = q - c * g.np;
-            const C kx = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sig);
-            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - kx);
-            if (u_d) u_d[t] = (double)u;
-            else u_f[t] = (float)u;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < nband; t += blockDim.x) {
-            const int q = band[t];
-            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
-            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
-        }
-        __syncthreads();
-    }
-}
-
-// Rows of K - sigma A for the band faces in ELL form (slot-major: entry e of
-// band face t at [e * nband + t]): every face in the 3x3x3 node neighbourhood
-// is a candidate; its coefficient is face_K of the candidate's unit vector
-// (the same arithmetic as every other use of the operator); zeros are
-// dropped, unused slots point at the row's own face with coefficient 0.
-__global__ void k_band_rows(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
-                            const double* __restrict__ invV, double sigma, const int* __restrict__ band, int nband,
-                            int width, int* __restrict__ cols, double* __restrict__ vals, int* __restrict__ maxnz) {
+// Rows of K - sigma A for the band faces in the fixed 15-slot form of
+// band_slot (slot-major: slot e of band face t at [e * nband + t]); each
+// coefficient is face_K of the column's unit vector, the same arithmetic as
+// every other use of the operator.
+__global__ void k_band_slots(Grid3 g, const double* __restrict__ A, const double* __restrict__ L,
+                             const double* __restrict__ invV, double sigma, const int* __restrict__ band, int nband,
+                             double* __restrict__ vals) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nband) return;
     const int q = band[t];
     const int c = q / g.np, p = q - c * g.np;
     Coef<double, double> cf{A, L, invV, g.np};
-    const double rdx = 1.0 / g.hx, rdy = 1.0 / g.hy, rdz = 1.0 / g.hz;
-    int n = 0;
-    for (int dk = -1; dk <= 1; ++dk)
-        for (int dj = -1; dj <= 1; ++dj)
-            for (int di = -1; di <= 1; ++di)
-                for (int cc = 0; cc < 3; ++cc) {
-                    const int cand = cc * g.np + p + di + dj * g.sx + dk * g.sxy;
-                    UnitAcc<double> b{cand, g.np};
-                    const double v = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sigma);
-                    if (v != 0.0) {
-                        if (n < width) {
-                            cols[(size_t)n * nband + t] = cand;
-                            vals[(size_t)n * nband + t] = v;
-                        }
-                        ++n;
-                    }
-                }
-    for (int e = n; e < width; ++e) {
-        cols[(size_t)e * nband + t] = q;
-        vals[(size_t)e * nband + t] = 0.0;
-    }
-    atomicMax(maxnz, n);
-}
-
-// Band sweeps from the assembled rows: per sweep u_t = omega invD (f - row_t . x),
-// barrier, x += u, barrier.  The barrier is the grid's (coop = 1, cooperative
-// launch) or the block's (coop = 0, one block).
-template <typename T, typename TC>
-__global__ void k_band_ell(int nband, int width, const int* __restrict__ band, const int* __restrict__ cols,
-                           const TC* __restrict__ vals, const TC* __restrict__ invD, const T* __restrict__ f, T* x,
-                           float* u_f, double* u_d, double omega_d, int sweeps, int coop) {
-    using C = typename Compute<T>::type;
-    namespace cg = cooperative_groups;
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const C om = C(omega_d);
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int t = t0; t < nband; t += stride) {
-            C acc = C(0);
-            for (int e = 0; e < width; ++e) {
-                const size_t k = (size_t)e * nband + t;
-                acc += (C)vals[k] * (C)to_c(__ldcg(x + cols[k]));
-            }
-            const int q = band[t];
-            const C u = om * (C)invD[q] * ((C)to_c(f[q]) - acc);
-            if (u_d) u_d[t] = (double)u;
-            else u_f[t] = (float)u;
-        }
-        if (coop) cg::this_grid().sync();
-        else __syncthreads();
-        for (int t = t0; t < nband; t += stride) {
-            const int q = band[t];
-            const C u = u_d ? (C)u_d[t] : (C)u_f[t];
-            x[q] = to_store<T>((C)to_c(__ldcg(x + q)) + u);
-        }
-        if (coop) cg::this_grid().sync();
-        else __syncthreads();
+    const double rdx = g.rhx, rdy = g.rhy, rdz = g.rhz;
+    for (int e = 0; e < kBandSlots; ++e) {
+        UnitAcc<double> b{q + band_slot_offset(c, e, g.np, g.sx, g.sxy), g.np};
+        vals[(size_t)e * nband + t] = face_K(cf, b, c, p, 1, g.sx, g.sxy, rdx, rdy, rdz, sigma);
     }
 }
 
@@ -470,7 +307,7 @@ __global__ void k_vec_dense(Grid3 g, const double* __restrict__ A, const double*
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         const int q = list[r];
         const int c = q / g.np, p = q - c * g.np;
-        M[(long long)r * n + col] = face_K(cf, b, c, p, 1, g.sx, g.sxy, 1.0 / g.hx, 1.0 / g.hy, 1.0 / g.hz, sigma);
+        M[(long long)r * n + col] = face_K(cf, b, c, p, 1, g.sx, g.sxy, g.rhx, g.rhy, g.rhz, sigma);
     }
 }
 
@@ -497,7 +334,7 @@ struct CellUnit {
 template <typename T, typename TC, int MODE>
 __global__ void k_scal_stencil(Grid3 g, const TC* __restrict__ A, const unsigned char* __restrict__ active,
                                const TC* __restrict__ invD, const T* __restrict__ x, const T* __restrict__ f,
-                               T* __restrict__ y, double omega_d, const int* __restrict__ tiles) {
+                               T* __restrict__ y, typename Compute<T>::type omega, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
     int i, j, k;
     block_node(g, tiles, i, j, k);
@@ -506,11 +343,11 @@ __global__ void k_scal_stencil(Grid3 g, const TC* __restrict__ A, const unsigned
     C v = C(0);
     if (active[p]) {
         CellAcc<T, C> acc{x};
-        const C sx = cell_S<C>(A, acc, p, 1, g.sx, g.sxy, g.np, C(1.0 / (g.hx * g.hx)), C(1.0 / (g.hy * g.hy)),
-                               C(1.0 / (g.hz * g.hz)));
+        const C rx = inv_h<C>(g, 0), ry = inv_h<C>(g, 1), rz = inv_h<C>(g, 2);
+        const C sx = cell_S<C>(A, acc, p, 1, g.sx, g.sxy, g.np, rx * rx, ry * ry, rz * rz);
         if (MODE == ST_APPLY) v = sx;
         else if (MODE == ST_RESID) v = (C)to_c(f[p]) - sx;
-        else v = (C)to_c(x[p]) + C(omega_d) * (C)invD[p] * ((C)to_c(f[p]) - sx);
+        else v = (C)to_c(x[p]) + omega * (C)invD[p] * ((C)to_c(f[p]) - sx);
     }
     y[p] = to_store<T>(v);
 }
@@ -549,8 +386,8 @@ __global__ void k_div_a(Grid3 g, const double* __restrict__ A, const double* __r
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int p = g.idx(i, j, k);
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
-    s[p] = (A[p + X] * x[p + X] - A[p] * x[p]) / g.hx + (A[N + p + Y] * x[N + p + Y] - A[N + p] * x[N + p]) / g.hy +
-           (A[2 * N + p + Z] * x[2 * N + p + Z] - A[2 * N + p] * x[2 * N + p]) / g.hz;
+    s[p] = (A[p + X] * x[p + X] - A[p] * x[p]) * g.rhx + (A[N + p + Y] * x[N + p + Y] - A[N + p] * x[N + p]) * g.rhy +
+           (A[2 * N + p + Z] * x[2 * N + p + Z] - A[2 * N + p] * x[2 * N + p]) * g.rhz;
 }
 
 // y = x - D^T phi on open faces, (D^T phi)_x(i) = (phi(i-1) - phi(i))/dx
@@ -562,9 +399,9 @@ __global__ void k_sub_grad(Grid3 g, const double* __restrict__ A, const double* 
     const int p = g.idx(i, j, k);
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
     const double ph = phi[p];
-    y[p] = A[p] > 0.0 ? x[p] - (phi[p - X] - ph) / g.hx : 0.0;
-    y[N + p] = A[N + p] > 0.0 ? x[N + p] - (phi[p - Y] - ph) / g.hy : 0.0;
-    y[2 * N + p] = A[2 * N + p] > 0.0 ? x[2 * N + p] - (phi[p - Z] - ph) / g.hz : 0.0;
+    y[p] = A[p] > 0.0 ? x[p] - (phi[p - X] - ph) * g.rhx : 0.0;
+    y[N + p] = A[N + p] > 0.0 ? x[N + p] - (phi[p - Y] - ph) * g.rhy : 0.0;
+    y[2 * N + p] = A[2 * N + p] > 0.0 ? x[2 * N + p] - (phi[p - Z] - ph) * g.rhz : 0.0;
 }
 
 }  // namespace
@@ -621,53 +458,10 @@ void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const
            invV, (const double*)nullptr, sigma, x, (const double*)nullptr, y, 0.0, (const int*)nullptr);
 }
 
-int band_rows(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
-              int nband, int width, int* cols, double* vals, int* d_maxnz, cudaStream_t s) {
-    DM_CUDA(cudaMemsetAsync(d_maxnz, 0, sizeof(int), s));
-    if (nband <= 0) return 0;
-    launch("k_band_rows", k_band_rows, (nband + 127) / 128, 128, 0, s, g, A, L, invV, sigma, band, nband, width, cols,
-           vals, d_maxnz);
-    int h = 0;
-    DM_CUDA(cudaMemcpyAsync(&h, d_maxnz, sizeof(int), cudaMemcpyDeviceToHost, s));
-    DM_CUDA(cudaStreamSynchronize(s));
-    return h;
-}
-
-template <typename T, typename TC>
-void band_sweeps_ell(const BandRows<TC>& br, const TC* invD, const int* band, int nband, const T* f, T* x, float* u,
-                     double omega, int sweeps, bool fine, cudaStream_t s) {
-    if (nband <= 0 || sweeps <= 0) return;
-    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
-    float* uf = ud ? nullptr : u;
-    const char* name = stencil_name("band_ell", prec_index<T>(), ST_JACOBI, fine);
-    if (nband <= 8192) {
-        launch(name, k_band_ell<T, TC>, 1, 1024, 0, s, nband, br.width, band, br.cols, br.vals, invD, f, x, uf, ud,
-               omega, sweeps, 0);
-        return;
-    }
-    static std::atomic<int> max_blocks_cache{-1};
-    int max_blocks = max_blocks_cache.load();
-    if (max_blocks < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        DM_CUDA(cudaGetDevice(&dev));
-        DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_ell<T, TC>, 256, 0));
-        max_blocks = std::max(0, per_sm * sms);
-        max_blocks_cache.store(max_blocks);
-    }
-    const int blocks = std::max(1, std::min((nband + 2 * 256 - 1) / (2 * 256), max_blocks));
-    int nb = nband, w = br.width, sw = sweeps, coop = 1;
-    const int* cols = br.cols;
-    const TC* vals = br.vals;
-    double om = omega;
-    void* args[] = {&nb, &w, &band, &cols, &vals, &invD, &f, &x, &uf, &ud, &om, &sw, &coop};
-    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (t) t->begin(s, &e0, &e1);
-    DM_CUDA(cudaLaunchCooperativeKernel((const void*)k_band_ell<T, TC>, dim3(blocks), dim3(256), args, 0, s));
-    if (t) t->end(name, s, e0, e1);
-    count_launch();
-    check_launch(name);
+void band_slots(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, const int* band,
+                int nband, double* vals, cudaStream_t s) {
+    if (nband <= 0) return;
+    launch("k_band_slots", k_band_slots, (nband + 127) / 128, 128, 0, s, g, A, L, invV, sigma, band, nband, vals);
 }
 
 template <typename T, typename TC>
@@ -676,60 +470,6 @@ void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cud
     const int blocks = op.tiles ? std::max(op.ntiles, 1) : (int)std::min<long long>((d.len() + 255) / 256, 152 * 16);
     launch(stencil_name("jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0), k_jacobi_zero<T, TC>, blocks, 256,
            0, s, d, op.invD, f, y, omega);
-}
-
-template <typename T, typename TC>
-void vec_band_sweep(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
-                    cudaStream_t s) {
-    if (nband <= 0) return;
-    const int blocks = (nband + 255) / 256;
-    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
-    float* uf = ud ? nullptr : u;
-    launch(stencil_name("band_update", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_update<T, TC>, blocks, 256, 0, s, op.g, op.A, op.L, op.invV, op.invD, op.sigma, band, nband, x, f, uf, ud, omega);
-    launch(stencil_name("band_apply", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_apply<T>, blocks, 256, 0, s, band, nband, uf, ud, x);
-}
-
-template <typename T, typename TC>
-void vec_band_sweeps(const VecOp<T, TC>& op, const int* band, int nband, const T* f, T* x, float* u, double omega,
-                     int sweeps, cudaStream_t s) {
-    if (nband <= 0 || sweeps <= 0) return;
-    static std::atomic<int> max_blocks_cache{-1};   // co-resident blocks of 256 threads (per instantiation)
-    int max_blocks = max_blocks_cache.load();
-    if (max_blocks < 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        DM_CUDA(cudaGetDevice(&dev));
-        DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_sweeps<T, TC>, 256, 0));
-        max_blocks = std::max(0, per_sm * sms);
-        max_blocks_cache.store(max_blocks);
-    }
-    double* ud = std::is_same<T, double>::value ? reinterpret_cast<double*>(u) : nullptr;
-    float* uf = ud ? nullptr : u;
-    if (nband <= 16384) {
-        launch(stencil_name("band_sweeps", prec_index<T>(), ST_JACOBI, op.level == 0), k_band_sweeps_block<T, TC>, 1,
-               1024, 0, s, op.g, op.A, op.L, op.invV, op.invD, op.sigma, band, nband, f, x, uf, ud, omega, sweeps);
-        return;
-    }
-    // every thread takes several band faces: fewer blocks make each grid barrier cheaper
-    const int want = (nband + 4 * 256 - 1) / (4 * 256);
-    if (max_blocks <= 0) {
-        for (int i = 0; i < sweeps; ++i) vec_band_sweep(op, band, nband, f, x, u, omega, s);
-        return;
-    }
-    const int blocks = std::min(want, max_blocks);
-    Grid3 g = op.g;
-    const TC *A = op.A, *L = op.L, *iV = op.invV, *iD = op.invD;
-    double sig = op.sigma, om = omega;
-    int nb = nband, sw = sweeps;
-    void* args[] = {&g, &A, &L, &iV, &iD, &sig, &band, &nb, &f, &x, &uf, &ud, &om, &sw};
-    const char* name = stencil_name("band_sweeps", prec_index<T>(), ST_JACOBI, op.level == 0);
-    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (t) t->begin(s, &e0, &e1);
-    DM_CUDA(cudaLaunchCooperativeKernel((const void*)k_band_sweeps<T, TC>, dim3(blocks), dim3(256), args, 0, s));
-    if (t) t->end(name, s, e0, e1);
-    count_launch();
-    check_launch(name);
 }
 
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
@@ -786,22 +526,11 @@ void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double*
 #define DM_INST(T, TC)                                                                                          \
     template void vec_stencil<T, TC>(const VecOp<T, TC>&, int, const T*, const T*, T*, double, cudaStream_t);  \
     template void vec_jacobi_zero<T, TC>(const VecOp<T, TC>&, const T*, T*, double, cudaStream_t);            \
-    template void vec_band_sweep<T, TC>(const VecOp<T, TC>&, const int*, int, const T*, T*, float*, double,   \
-                                        cudaStream_t);                                                        \
-    template void vec_band_sweeps<T, TC>(const VecOp<T, TC>&, const int*, int, const T*, T*, float*, double,  \
-                                         int, cudaStream_t);                                                  \
     template void scal_stencil<T, TC>(const ScalOp<T, TC>&, int, const T*, const T*, T*, double, cudaStream_t); \
     template void scal_jacobi_zero<T, TC>(const ScalOp<T, TC>&, const T*, T*, double, cudaStream_t);
 DM_INST(double, double)
 DM_INST(float, float)
 DM_INST(__nv_bfloat16, float)
 #undef DM_INST
-template void band_sweeps_ell<double, double>(const BandRows<double>&, const double*, const int*, int, const double*,
-                                              double*, float*, double, int, bool, cudaStream_t);
-template void band_sweeps_ell<float, float>(const BandRows<float>&, const float*, const int*, int, const float*, float*,
-                                            float*, double, int, bool, cudaStream_t);
-template void band_sweeps_ell<__nv_bfloat16, float>(const BandRows<float>&, const float*, const int*, int,
-                                                    const __nv_bfloat16*, __nv_bfloat16*, float*, double, int, bool,
-                                                    cudaStream_t);
 
 }  // namespace dm

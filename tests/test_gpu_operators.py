@@ -20,6 +20,9 @@ CASES = {
 }
 
 
+SWEEPS, BRICK = 16, 8        # band smoother defaults of the library
+
+
 def _rel(a, b):
     return np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300)
 
@@ -86,7 +89,7 @@ def test_smooth_restrict_prolong(case):
         f = rng.standard_normal(lev.mask.size) * lev.mask
         x = rng.standard_normal(lev.mask.size) * lev.mask
         got = op.smooth(f, x, level=l)
-        ref = MG.smooth(lev, f, x, om, 8)
+        ref = MG.smooth(lev, f, x, om, SWEEPS, brick=BRICK)
         assert _rel(got, ref) < 1e-12, l
         r = rng.standard_normal(lev.mask.size) * lev.mask
         assert _rel(op.restrict(r, level=l), MG.restrict(levels, l, r)) < 1e-13, l
@@ -94,12 +97,40 @@ def test_smooth_restrict_prolong(case):
         assert _rel(op.prolong(ec, x, level=l), MG.prolong_add(levels, l, x, ec)) < 1e-13, l
 
 
+@pytest.mark.parametrize("case_name,brick,sweeps", [("sphere16", 2, 5), ("sphere16", 4, 16), ("sphere32", 10, 9),
+                                                   ("ragged13x11x9", 16, 7)])
+def test_band_smoother_bricks(case_name, brick, sweeps, dm, ctx):
+    """Other brick sizes and sweep counts; a 16-node brick covers the 13x11x9
+    grid (one subdomain: plain band-restricted Jacobi)."""
+    w = CASES[case_name]()
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma, band_brick=brick, band_sweeps=sweeps)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    rng = np.random.default_rng(11)
+    for l in range(len(levels) - 1):
+        lev = levels[l]
+        f = rng.standard_normal(lev.mask.size) * lev.mask
+        x = rng.standard_normal(lev.mask.size) * lev.mask
+        got = op.smooth(f, x, level=l)
+        ref = MG.smooth(lev, f, x, op.omega(l), sweeps, brick=brick)
+        assert _rel(got, ref) < 1e-12, (l, _rel(got, ref))
+
+
+def test_band_brick_too_large_is_rejected(dm, ctx):
+    """A subdomain whose local box does not fit in shared memory is an argument error."""
+    w = CASES["sphere32"]()
+    geom = dm.Geometry.from_workload(ctx, w)
+    with pytest.raises(dm.DMError) as err:
+        dm.Operator(ctx, geom, w.sigma, band_brick=64)
+    assert "brick too large" in str(err.value)
+
+
 def test_vcycle_fp64(case):
     w, geom, levels, op = case
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(6).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=8)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
 
 
@@ -122,7 +153,7 @@ def test_vcycle_low_precision(prec, tol, dm, ctx):
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(8).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=8)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
 

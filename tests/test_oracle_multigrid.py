@@ -123,3 +123,89 @@ def test_scalar_vcycle_solves_projection_system():
     # the projected field is divergence free
     y = x - (lev.ops.D.T @ psi) * lev.ops.open
     assert np.linalg.norm(lev.ops.D @ (lev.ops.a * y)) < 1e-8 * np.linalg.norm(s)
+
+
+# -- band smoother (restricted additive Schwarz over bricks) ---------------------
+
+def _level(n, seed=9):
+    w = W.sphere_workload(n, offset_seed=seed, sigma=5.0)
+    return MG.build_vector_hierarchy(w.grid, w.phi, 5.0)[0]
+
+
+def test_band_subdomains_partition_and_overlap():
+    lev = _level(12)
+    brick = 4
+    subs = MG.band_subdomains(lev, brick)
+    band = np.nonzero(lev.band > 0)[0]
+    owned = np.concatenate([r[o] for r, o in subs])
+    assert np.array_equal(np.sort(owned), band)            # every band face owned exactly once
+    # membership by brute force: face q is in brick B's subdomain iff each node
+    # coordinate lies within one node of the brick's node range
+    nodes = MG.face_nodes(lev.grid)
+    rng = np.random.default_rng(0)
+    for q in rng.choice(band, 40, replace=False):
+        P = nodes[q]
+        expect = set()
+        for bx in range(-1, 5):
+            for by in range(-1, 5):
+                for bz in range(-1, 5):
+                    B = np.array([bx, by, bz])
+                    if all(B[a] * brick - 1 <= P[a] <= B[a] * brick + brick - 1 + 1 for a in range(3)):
+                        expect.add((bx, by, bz))
+        got = set()
+        for rows, o in subs:
+            if q in rows:
+                P0 = nodes[rows[o][0]] // brick
+                got.add(tuple(int(v) for v in P0))
+        # bricks that own no band face have no subdomain
+        owners = {tuple(int(v) for v in nodes[r[o][0]] // brick) for r, o in subs}
+        assert got == expect & owners
+
+
+def test_band_schwarz_single_brick_is_band_jacobi():
+    """One brick covering the grid: the step is s sweeps of band-restricted
+    damped Jacobi on x itself."""
+    lev = _level(10)
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(lev.mask.size) * lev.mask
+    x = rng.standard_normal(lev.mask.size) * lev.mask
+    om = 0.8
+    y = x.copy()
+    for _ in range(5):
+        y = y + om * lev.band * lev.inv_d * (f - lev.K @ y)
+    got = MG.band_schwarz(lev, f, x, om, 5, brick=64)
+    assert np.max(np.abs(got - y)) < 1e-12 * np.max(np.abs(y))
+
+
+def test_band_schwarz_brute_force_loops():
+    """Literal loops over bricks, rows and couplings on a tiny grid."""
+    lev = _level(6, seed=3)
+    brick, sweeps, om = 2, 3, 0.7
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(lev.mask.size) * lev.mask
+    x = rng.standard_normal(lev.mask.size) * lev.mask
+    K = lev.K.toarray()
+    nodes = MG.face_nodes(lev.grid)
+    r0 = f - K @ x
+    out = x.copy()
+    band = [q for q in range(lev.mask.size) if lev.band[q] > 0]
+    nb = (lev.grid.nx + 1 + brick - 1) // brick
+    for bz in range(nb):
+        for by in range(nb):
+            for bx in range(nb):
+                B = (bx, by, bz)
+                sub = [q for q in band if all(B[a] * brick - 1 <= nodes[q][a] <= B[a] * brick + brick for a in range(3))]
+                if not sub:
+                    continue
+                d = {q: 0.0 for q in sub}
+                for _ in range(sweeps):
+                    new = {}
+                    for q in sub:
+                        acc = sum(K[q, p] * d[p] for p in sub)
+                        new[q] = d[q] + om * lev.inv_d[q] * (r0[q] - acc)
+                    d = new
+                for q in sub:
+                    if all(nodes[q][a] // brick == B[a] for a in range(3)):
+                        out[q] += d[q]
+    got = MG.band_schwarz(lev, f, x, om, sweeps, brick)
+    assert np.max(np.abs(got - out)) < 1e-12 * np.max(np.abs(out))
