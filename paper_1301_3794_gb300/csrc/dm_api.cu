@@ -247,7 +247,7 @@ struct OpLevel {
 };
 
 // FGMRES workspace: the Arnoldi basis V and the work vector wf in
-// float-float (see mdot_ff), the preconditioned vectors Z and the operator
+// float-float (see dcgs_dots), the preconditioned vectors Z and the operator
 // output w in FP64
 struct Fgmres {
     long long n = 0;
@@ -486,23 +486,25 @@ void learned_correct(dm_operator* op, const T* f, T* z, T* scratch) {
 // result in the level-0 r buffer is converted into z.
 // MG input f (storage T) from an FP64 or a float-float vector
 template <typename T>
-void mg_input(const Domain& D, const double* v, T* f, cudaStream_t s) {
+void mg_input(const Domain& D, const double* v, double scale, T* f, cudaStream_t s) {
+    DM_REQUIRE(scale == 1.0, DM_ERR_INVALID_ARG, "scaled FP64 preconditioner input");
     convert<T, double>(D, v, f, s);
 }
 template <typename T>
-void mg_input(const Domain& D, const float2* v, T* f, cudaStream_t s) {
-    ff_convert<T>(D, v, f, s);
+void mg_input(const Domain& D, const float2* v, double scale, T* f, cudaStream_t s) {
+    ff_convert<T>(D, scale, v, f, s);
 }
 
+// z = M^-1 (scale v): one V-cycle (graph-replayed after the first call)
 template <typename T, typename TC, typename TIn>
-void precond_vec_T(dm_operator* op, const TIn* v, double* z) {
+void precond_vec_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).vdom();
     WorkLevel& w0 = op->wk[0];
     T* f = reinterpret_cast<T*>(w0.f.get());
     T* e = reinterpret_cast<T*>(w0.e.get());
     T* r = reinterpret_cast<T*>(w0.r.get());
-    mg_input<T>(D, v, f, s);
+    mg_input<T>(D, v, scale, f, s);
     if (graphs_allowed(op) && op->vcalls > 0) {
         if (!op->vexec && !capture_graph(op, [&] { vcycle<T, TC>(op, 0, f, e, r); }, &op->vexec, &op->vexec_kernels))
             op->graphs = false;
@@ -519,14 +521,14 @@ void precond_vec_T(dm_operator* op, const TIn* v, double* z) {
 }
 
 template <typename T, typename TC, typename TIn>
-void precond_scal_T(dm_operator* op, const TIn* v, double* z) {
+void precond_scal_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).sdom();
     WorkLevel& w0 = op->wk[0];
     T* f = reinterpret_cast<T*>(w0.sf.get());
     T* e = reinterpret_cast<T*>(w0.se.get());
     T* r = reinterpret_cast<T*>(w0.sr.get());
-    mg_input<T>(D, v, f, s);
+    mg_input<T>(D, v, scale, f, s);
     if (graphs_allowed(op) && op->scalls > 0) {
         if (!op->sexec && !capture_graph(op, [&] { svcycle<T, TC>(op, 0, f, e, r); }, &op->sexec, &op->sexec_kernels))
             op->graphs = false;
@@ -542,20 +544,20 @@ void precond_scal_T(dm_operator* op, const TIn* v, double* z) {
 }
 
 template <typename TIn>
-void precond_vec(dm_operator* op, const TIn* v, double* z) {
+void precond_vec(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
     switch (op->mg.precision) {
-        case DM_PREC_F64: precond_vec_T<double, double>(op, v, z); break;
-        case DM_PREC_F32: precond_vec_T<float, float>(op, v, z); break;
-        default: precond_vec_T<__nv_bfloat16, float>(op, v, z);
+        case DM_PREC_F64: precond_vec_T<double, double>(op, v, z, scale); break;
+        case DM_PREC_F32: precond_vec_T<float, float>(op, v, z, scale); break;
+        default: precond_vec_T<__nv_bfloat16, float>(op, v, z, scale);
     }
 }
 
 template <typename TIn>
-void precond_scal(dm_operator* op, const TIn* v, double* z) {
+void precond_scal(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
     switch (op->mg.precision) {
-        case DM_PREC_F64: precond_scal_T<double, double>(op, v, z); break;
-        case DM_PREC_F32: precond_scal_T<float, float>(op, v, z); break;
-        default: precond_scal_T<__nv_bfloat16, float>(op, v, z);
+        case DM_PREC_F64: precond_scal_T<double, double>(op, v, z, scale); break;
+        case DM_PREC_F32: precond_scal_T<float, float>(op, v, z, scale); break;
+        default: precond_scal_T<__nv_bfloat16, float>(op, v, z, scale);
     }
 }
 
@@ -572,8 +574,48 @@ double norm2(dm_context* ctx, const Domain& D, const double* x, const double* w 
     return std::sqrt(std::max(r, 0.0));
 }
 
-// Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt
-// applied twice.  x is overwritten.  Returns the iteration count.
+// Residual of the least-squares problem min |beta e1 - H y| for the first k
+// columns of the (k+1) x k Hessenberg H (row stride ld), by Givens QR from
+// scratch; y (size k) receives the minimiser.
+double hessenberg_lsq(const std::vector<double>& H, int ld, int k, double beta, std::vector<double>* y) {
+    std::vector<double> R((size_t)(k + 1) * k), g(k + 1, 0.0);
+    for (int i = 0; i <= k; ++i)
+        for (int c = 0; c < k; ++c) R[(size_t)i * k + c] = H[(size_t)i * ld + c];
+    g[0] = beta;
+    for (int c = 0; c < k; ++c) {
+        const double a = R[(size_t)c * k + c], b = R[(size_t)(c + 1) * k + c];
+        const double r = std::hypot(a, b);
+        const double cs = r > 0 ? a / r : 1.0, sn = r > 0 ? b / r : 0.0;
+        for (int cc = c; cc < k; ++cc) {
+            const double u = R[(size_t)c * k + cc], v = R[(size_t)(c + 1) * k + cc];
+            R[(size_t)c * k + cc] = cs * u + sn * v;
+            R[(size_t)(c + 1) * k + cc] = -sn * u + cs * v;
+        }
+        const double gu = g[c], gv = g[c + 1];
+        g[c] = cs * gu + sn * gv;
+        g[c + 1] = -sn * gu + cs * gv;
+    }
+    if (y) {
+        y->assign(k, 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int c = i + 1; c < k; ++c) acc -= R[(size_t)i * k + c] * (*y)[c];
+            (*y)[i] = R[(size_t)i * k + i] != 0.0 ? acc / R[(size_t)i * k + i] : 0.0;
+        }
+    }
+    return std::fabs(g[k]);
+}
+
+// Right-preconditioned flexible GMRES (Saad 1993).  The Arnoldi basis is
+// orthogonalised by delayed classical Gram-Schmidt (DCGS2, after Swirydowicz,
+// Langou, Ananthan, Yang & Thomas 2020): the second Gram-Schmidt pass of each
+// basis vector is carried out in the same sweep over the basis as the first
+// pass of the next vector, so every iteration reads the basis twice (one
+// reduction, one update) instead of four times.  The newest column of H is
+// provisional until the next iteration reorthogonalises its vector; the
+// residual estimate uses it as it stands (the correction is of rounding
+// size), and the end of a cycle confirms with the true FP64 residual.
+// x is overwritten.  Returns the iteration count.
 struct NoMonitor {
     void operator()(double) const {}
 };
@@ -584,6 +626,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
            double tol, int maxit, double* relres, double abs_tol = 0.0, Monitor monitor = Monitor()) {
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
+    DM_REQUIRE(m >= 1 && 2 * m + 2 < ctx->red.max_cols, DM_ERR_INVALID_ARG, "FGMRES restart length too large");
     ws.ensure(n, m);
     float2* V = ws.V.get();
     float2* wf = ws.wf.get();
@@ -599,7 +642,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
     int total = 0;
     bool first = true;
     double res = 1.0;
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    std::vector<double> H((size_t)(m + 1) * m), dots(2 * m + 2), coef(2 * m + 2), y;
     while (total < maxit) {
         // r = b - A x (FP64); V_0 = r / beta in float-float
         double beta = bnorm;
@@ -612,59 +655,54 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         if (beta <= thr) break;
         ff_split(D, 1.0 / beta, first ? b : w, V, s);
         std::fill(H.begin(), H.end(), 0.0);
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int jend = -1;
+        double nu = 1.0;          // norm of the pending vector V_j (provisional)
+        double prev = beta;
+        int k = 0;                // columns of H built in this cycle
         for (int j = 0; j < m && total < maxit; ++j) {
-            prec(V + (size_t)j * n, Z + (size_t)j * n);
+            float2* Vj = V + (size_t)j * n;
+            prec(Vj, 1.0 / nu, Z + (size_t)j * n);
             apply(Z + (size_t)j * n, w);
             ff_split(D, 1.0, w, wf, s);
-            // classical Gram-Schmidt, repeated only when the pass cancelled most
-            // of w (Kahan: ||w'|| < 0.7 ||w||), norms fused into the passes
-            std::vector<double> h(j + 1);
-            double wn2 = 0.0;
-            mdot_ff(ctx->red, D, j + 1, V, n, wf, h.data(), &wn2, s);
-            double hn2 = maxpy_norm_ff(ctx->red, D, j + 1, V, n, wf, s);
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
-            if (hn2 < 0.49 * wn2) {
-                mdot_ff(ctx->red, D, j + 1, V, n, wf, h.data(), nullptr, s);
-                hn2 = maxpy_norm_ff(ctx->red, D, j + 1, V, n, wf, s);
-                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] += h[i];
-            }
-            const double hn = std::sqrt(std::max(hn2, 0.0));
-            H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) ff_scale(D, 1.0 / hn, wf, V + (size_t)(j + 1) * n, s);
-            // Givens
+            // one sweep: Q^T v, Q^T w, v.v, v.w with Q = V_0 .. V_{j-1} finished
+            dcgs_dots(ctx->red, D, j, V, n, Vj, wf, dots.data(), s);
+            double ss = 0.0, sc = 0.0;
             for (int i = 0; i < j; ++i) {
-                const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
-                H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
-                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+                ss += dots[i] * dots[i];
+                sc += dots[i] * dots[j + i];
             }
-            const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
-            const double rr = std::hypot(a, bb);
-            cs[j] = rr > 0 ? a / rr : 1.0;
-            sn[j] = rr > 0 ? bb / rr : 0.0;
-            H[(size_t)j * m + j] = rr;
-            H[(size_t)(j + 1) * m + j] = 0.0;
-            const double gprev = std::fabs(g[j]);
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            if (gprev > 0.0) monitor(std::fabs(g[j + 1]) / gprev);
+            const double bj = std::sqrt(std::max(dots[2 * j] - ss, 0.0));
+            if (!(bj > 0.0)) break;
+            // finish column j-1: its pending vector was Q s + bj V_j
+            if (j > 0) {
+                for (int i = 0; i < j; ++i) H[(size_t)i * m + (j - 1)] += dots[i];
+                H[(size_t)j * m + (j - 1)] = bj;
+            }
+            // new column: Q^T w and V_j . w for the finished V_j
+            const double hj = (dots[2 * j + 1] - sc) / bj;
+            for (int i = 0; i < j; ++i) {
+                coef[i] = dots[i];
+                coef[j + i] = dots[j + i] - hj / bj * dots[i];
+                H[(size_t)i * m + j] = dots[j + i];
+            }
+            H[(size_t)j * m + j] = hj;
+            coef[2 * j] = 1.0 / bj;
+            coef[2 * j + 1] = hj / bj;
+            const double nn2 = dcgs_update(ctx->red, D, j, V, n, coef.data(), Vj, wf, V + (size_t)(j + 1) * n, s);
+            nu = std::sqrt(std::max(nn2, 0.0));
+            H[(size_t)(j + 1) * m + j] = nu;   // provisional until the next iteration
+            k = j + 1;
             ++total;
-            jend = j;
-            res = std::fabs(g[j + 1]) / bnorm;
-            if (std::fabs(g[j + 1]) <= thr || hn == 0.0) break;
+            const double r = hessenberg_lsq(H, m, k, beta, nullptr);
+            if (prev > 0.0) monitor(r / prev);
+            prev = r;
+            res = r / bnorm;
+            if (r <= thr || nu == 0.0) break;
         }
-        if (jend < 0) break;
-        // y = H^-1 g (upper triangular)
-        for (int i = jend; i >= 0; --i) {
-            double acc = g[i];
-            for (int k = i + 1; k <= jend; ++k) acc -= H[(size_t)i * m + k] * y[k];
-            y[i] = acc / H[(size_t)i * m + i];
-        }
-        std::vector<double> neg(jend + 1);
-        for (int i = 0; i <= jend; ++i) neg[i] = -y[i];
-        maxpy(ctx->red, D, jend + 1, Z, n, neg.data(), x, s);
+        if (k == 0) break;
+        hessenberg_lsq(H, m, k, beta, &y);
+        std::vector<double> neg(k);
+        for (int i = 0; i < k; ++i) neg[i] = -y[i];
+        maxpy(ctx->red, D, k, Z, n, neg.data(), x, s);
         first = false;
         if (res * bnorm <= thr) {
             // confirm with the true residual
@@ -682,7 +720,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
-    auto prec = [op](const float2* in, double* out) { precond_vec(op, in, out); };
+    auto prec = [op](const float2* in, double scale, double* out) { precond_vec(op, in, out, scale); };
     // the learned correction is judged by the FP64 residual: an iteration that
     // contracts by less than 0.8 switches it off for the rest of the solve
     op->learned_active = op->lnet != nullptr;
@@ -715,7 +753,7 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     const double hmin = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
     const double xscale = norm2(op->ctx, g0.vdom(), x) / hmin;
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
-    auto prec = [op](const float2* in, double* out) { precond_scal(op, in, out); };
+    auto prec = [op](const float2* in, double scale, double* out) { precond_scal(op, in, out, scale); };
     double rr = 0.0;
     const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);

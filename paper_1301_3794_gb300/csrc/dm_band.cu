@@ -179,6 +179,9 @@ size_t schwarz_smem(int maxbox, int maxrows, int R) {
 // Size classes of subdomains (rows): each class is launched with its own
 // block size and rows per thread, so that small subdomains are not held to the
 // register and thread budget of the largest.
+// levels with at most this many subdomains are smoothed in a single launch
+constexpr int kSingleLaunchSubdomains = 304;
+
 int schwarz_class(int rows) {
     return rows <= 256 ? 0 : (rows <= 512 ? 1 : (rows <= 1024 ? 2 : (rows <= 2048 ? 3 : 4)));
 }
@@ -310,13 +313,21 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
                   T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s) {
     if (nband <= 0 || bs.nsub <= 0 || sweeps <= 0) return;
     const char* name = stencil_name("band_schwarz", prec_index<T>(), ST_JACOBI, fine);
+    // a level whose subdomains fit in one wave goes in a single launch shaped for
+    // its largest class; larger levels launch each class with its own shape
+    int top = 0;
+    for (int cl = 0; cl < kSchwarzClasses; ++cl)
+        if (bs.cls_count[cl] > 0) top = cl;
+    const bool single = bs.nsub <= kSingleLaunchSubdomains;
     for (int cl = 0; cl < kSchwarzClasses; ++cl) {
-        if (bs.cls_count[cl] == 0) continue;
+        if (bs.cls_count[cl] == 0 || (single && cl != top)) continue;
         int R, nt;
-        class_shape<T>(cl, R, nt);
+        class_shape<T>(single ? top : cl, R, nt);
+        const int first = single ? 0 : bs.cls_first[cl];
+        const int count = single ? bs.nsub : bs.cls_count[cl];
         const size_t smem = schwarz_smem<T>(bs.maxbox, bs.maxrows, R);
 #define DM_SCHWARZ(RV, NV)                                                                                         \
-    launch(name, k_band_schwarz<T, TC, RV, NV>, bs.cls_count[cl], NV, smem, s, bs.cls_first[cl], bs.off, bs.copy, \
+    launch(name, k_band_schwarz<T, TC, RV, NV>, count, NV, smem, s, first, bs.off, bs.copy,                      \
            bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,  \
            bs.maxbox, bs.maxrows)
         if (nt == 256) DM_SCHWARZ(1, 256);

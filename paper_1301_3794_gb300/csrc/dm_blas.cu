@@ -11,6 +11,9 @@
 // neither read nor written), or, with no tile list, the whole array.
 #include "dm_common.cuh"
 
+#include <map>
+#include <mutex>
+
 namespace dm {
 
 namespace {
@@ -255,106 +258,177 @@ __global__ void k_ff_split(Domain d, double a, const double* __restrict__ x, flo
     if (a == 1.0) for_each_entry(d, [&](long long r) { y[r] = ff_bits(x[r]); });
     else for_each_entry(d, [&](long long r) { y[r] = ff_bits(a * x[r]); });
 }
-// y = a x, a = (ah, al)
-__global__ void k_ff_scale(Domain d, float ah, float al, const float2* __restrict__ x, float2* __restrict__ y) {
-    for_each_entry(d, [&](long long r) {
-        const float2 v = x[r];
-        float s = 0.f, e = 0.f;
-        ff_madd(ah, al, v.x, v.y, s, e);
-        y[r] = ff_norm(s, e);
-    });
-}
+// y = a x in the storage type T
 template <typename T>
-__global__ void k_ff_convert(Domain d, const float2* __restrict__ x, T* __restrict__ y) {
+__global__ void k_ff_convert(Domain d, typename Compute<T>::type a, const float2* __restrict__ x, T* __restrict__ y) {
     for_each_entry(d, [&](long long r) {
         const float2 v = x[r];
-        if constexpr (std::is_same<T, double>::value) y[r] = ff_to_double(v);
-        else y[r] = to_store<T>(__fadd_rn(v.x, v.y));
+        if constexpr (std::is_same<T, double>::value) y[r] = a * ff_to_double(v);
+        else y[r] = to_store<T>(a * __fadd_rn(v.x, v.y));
     });
 }
 
-// partial[b * ldp + c0 + c] = sum over this block's entries of V_c x; with
-// self, partial[b * ldp + m] = sum x^2
-__global__ void k_ff_mdot_partial(Domain d, int m, const float2* __restrict__ V, long long ld,
-                                  const float2* __restrict__ x, double* __restrict__ partial, int ldp, int self) {
-    constexpr int kc = 8;
-    __shared__ double red[kThreads / 32][kc];
-    __shared__ double red_self[kThreads / 32];
-    float ss = 0.f, se = 0.f;
-    for (int c0 = 0; c0 < m; c0 += kc) {
-        const int nc = min(kc, m - c0);
-        float s[kc], e[kc];
+// One pass of delayed classical Gram-Schmidt (DCGS2): against the finished
+// basis Q (j vectors) and the pending vector v, with the new vector w:
+//   partial[b][c] = Q_c . v, [j + c] = Q_c . w (c < j), [2j] = v . v, [2j + 1] = v . w
+// Columns go in chunks of up to 8 whose size is a compile-time constant, so the
+// accumulators stay in registers and no predicated-off column is issued.
+template <int NC>
+__device__ __forceinline__ void dcgs_chunk(const Domain& d, int j, int c0, const float2* __restrict__ Q, long long ld,
+                                           const float2* __restrict__ v, const float2* __restrict__ w, bool first,
+                                           float& as, float& ae, float& ds, float& de, double* __restrict__ partial,
+                                           int ldp) {
+    __shared__ double red[kThreads / 32][16];
+    constexpr int N1 = NC > 0 ? NC : 1;
+    float ss[N1], se[N1], cs[N1], ce[N1];
 #pragma unroll
-        for (int c = 0; c < kc; ++c) s[c] = e[c] = 0.f;
-        const bool first = c0 == 0 && self;
-        for_each_entry(d, [&](long long r) {
-            const float2 xs = x[r];
-            if (first) ff_madd(xs.x, xs.y, xs.x, xs.y, ss, se);
+    for (int c = 0; c < N1; ++c) ss[c] = se[c] = cs[c] = ce[c] = 0.f;
+    for_each_entry(d, [&](long long r) {
+        const float2 vv = v[r], ww = w[r];
+        if (first) {
+            ff_madd(vv.x, vv.y, vv.x, vv.y, as, ae);
+            ff_madd(vv.x, vv.y, ww.x, ww.y, ds, de);
+        }
 #pragma unroll
-            for (int c = 0; c < kc; ++c)
-                if (c < nc) {
-                    const float2 v = V[(c0 + c) * ld + r];
-                    ff_madd(v.x, v.y, xs.x, xs.y, s[c], e[c]);
-                }
-        });
+        for (int c = 0; c < NC; ++c) {
+            const float2 q = Q[(c0 + c) * ld + r];
+            ff_madd(q.x, q.y, vv.x, vv.y, ss[c], se[c]);
+            ff_madd(q.x, q.y, ww.x, ww.y, cs[c], ce[c]);
+        }
+    });
+    if constexpr (NC > 0) {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int c = 0; c < kc; ++c) {
-            const double t = warp_sum((double)s[c] + (double)e[c]);
-            if (lane == 0) red[wid][c] = t;
+        for (int c = 0; c < NC; ++c) {
+            const double t1 = warp_sum((double)ss[c] + (double)se[c]);
+            const double t2 = warp_sum((double)cs[c] + (double)ce[c]);
+            if (lane == 0) {
+                red[wid][c] = t1;
+                red[wid][8 + c] = t2;
+            }
         }
         __syncthreads();
-        if (threadIdx.x < nc) {
+        if (threadIdx.x < 2 * NC) {
+            const bool isv = threadIdx.x < NC;
+            const int c = isv ? threadIdx.x : threadIdx.x - NC;
             double t = 0.0;
-            for (int k = 0; k < kThreads / 32; ++k) t += red[k][threadIdx.x];
-            partial[(long long)blockIdx.x * ldp + c0 + threadIdx.x] = t;
+            for (int k = 0; k < kThreads / 32; ++k) t += red[k][isv ? c : 8 + c];
+            partial[(long long)blockIdx.x * ldp + (isv ? c0 + c : j + c0 + c)] = t;
         }
         __syncthreads();
-    }
-    if (self) {
-        const double v = warp_sum((double)ss + (double)se);
-        if ((threadIdx.x & 31) == 0) red_self[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int k = 0; k < kThreads / 32; ++k) t += red_self[k];
-            partial[(long long)blockIdx.x * ldp + m] = t;
-        }
     }
 }
 
-// x -= sum_c h[c] V_c (h on the device, FP64) and the block partial of sum x^2
-__global__ void k_ff_maxpy_norm(Domain d, int m, const float2* __restrict__ V, long long ld,
-                                const double* __restrict__ h, float2* __restrict__ x, double* __restrict__ partial) {
-    __shared__ float2 hs[128];
+__global__ void k_ff_dcgs_dots(Domain d, int j, const float2* __restrict__ Q, long long ld,
+                               const float2* __restrict__ v, const float2* __restrict__ w, double* __restrict__ partial,
+                               int ldp) {
+    __shared__ double red2[kThreads / 32][2];
+    float as = 0.f, ae = 0.f, ds = 0.f, de = 0.f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < (j > 0 ? j : 1); c0 += 8) {
+        const int nc = j > 0 ? min(8, j - c0) : 0;
+        const bool first = c0 == 0;
+        switch (nc) {
+            case 0: dcgs_chunk<0>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 1: dcgs_chunk<1>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 2: dcgs_chunk<2>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 3: dcgs_chunk<3>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 4: dcgs_chunk<4>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 5: dcgs_chunk<5>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 6: dcgs_chunk<6>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 7: dcgs_chunk<7>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
+            default: dcgs_chunk<8>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp);
+        }
+    }
+    const double ta = warp_sum((double)as + (double)ae);
+    const double td = warp_sum((double)ds + (double)de);
+    if (lane == 0) {
+        red2[wid][0] = ta;
+        red2[wid][1] = td;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) t += red2[k][threadIdx.x];
+        partial[(long long)blockIdx.x * ldp + 2 * j + threadIdx.x] = t;
+    }
+}
+
+// The update pass of DCGS2, with coef = [s (j), gamma (j), 1/beta, delta]:
+//   v <- (v - Q s) / beta   (the pending vector, now finished)
+//   out <- w - Q gamma - delta v_old   and the block partial of |out|^2
+__global__ void k_ff_dcgs_update(Domain d, int j, const float2* __restrict__ Q, long long ld,
+                                 const double* __restrict__ coef, float2* __restrict__ v, const float2* __restrict__ w,
+                                 float2* __restrict__ out, double* __restrict__ partial) {
+    __shared__ float2 cs[128], cg[128];
+    __shared__ float2 rb, dl;
     __shared__ double red[kThreads / 32];
-    for (int c = threadIdx.x; c < m; c += blockDim.x) hs[c] = ff_bits(-h[c]);
+    for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        cs[c] = ff_bits(-coef[c]);
+        cg[c] = ff_bits(-coef[j + c]);
+    }
+    if (threadIdx.x == 0) {
+        rb = ff_bits(coef[2 * j]);
+        dl = ff_bits(-coef[2 * j + 1]);
+    }
     __syncthreads();
     float ns = 0.f, ne = 0.f;
     for_each_entry(d, [&](long long r) {
-        const float2 x0 = x[r];
-        float s = x0.x, e = x0.y;
-        for (int c = 0; c < m; ++c) {
-            const float2 v = V[c * ld + r];
-            ff_madd(hs[c].x, hs[c].y, v.x, v.y, s, e);
+        const float2 vv = v[r], ww = w[r];
+        float ts = vv.x, te = vv.y, us = ww.x, ue = ww.y;
+        ff_madd(dl.x, dl.y, vv.x, vv.y, us, ue);
+        for (int c = 0; c < j; ++c) {
+            const float2 q = Q[c * ld + r];
+            ff_madd(cs[c].x, cs[c].y, q.x, q.y, ts, te);
+            ff_madd(cg[c].x, cg[c].y, q.x, q.y, us, ue);
         }
-        const float2 y = ff_norm(s, e);
-        x[r] = y;
-        ff_madd(y.x, y.y, y.x, y.y, ns, ne);
+        const float2 t = ff_norm(ts, te);
+        float qs = 0.f, qe = 0.f;
+        ff_madd(rb.x, rb.y, t.x, t.y, qs, qe);
+        v[r] = ff_norm(qs, qe);
+        const float2 o = ff_norm(us, ue);
+        out[r] = o;
+        ff_madd(o.x, o.y, o.x, o.y, ns, ne);
     });
-    const double v = warp_sum((double)ns + (double)ne);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    const double t = warp_sum((double)ns + (double)ne);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int k = 0; k < kThreads / 32; ++k) t += red[k];
-        partial[blockIdx.x] = t;
+        double a = 0.0;
+        for (int k = 0; k < kThreads / 32; ++k) a += red[k];
+        partial[blockIdx.x] = a;
     }
 }
 
 inline int blocks_for(const Domain& d) {
     const long long work = d.tiles ? (long long)d.ntiles : (d.len() + kThreads - 1) / kThreads;
     return (int)std::max<long long>(1, std::min<long long>(work, kMaxBlocks));
+}
+
+// Grid of a grid-stride kernel: at most one full wave (the blocks that fit on
+// the device at once), so that no partial second wave idles most SMs.
+template <typename K>
+int blocks_for(const Domain& d, K kernel) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> wave;
+    int dev = 0;
+    DM_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_pair(dev, (const void*)kernel);
+    int full;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = wave.find(key);
+        if (it == wave.end()) {
+            int sms = 0, occ = 0;
+            DM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0));
+            const int per_sm = std::max(1, std::min(occ, kMaxBlocks / std::max(sms, 1)));
+            it = wave.emplace(key, std::max(1, std::min(sms * per_sm, kMaxBlocks))).first;
+        }
+        full = it->second;
+    }
+    const long long work = d.tiles ? (long long)d.ntiles : (d.len() + kThreads - 1) / kThreads;
+    return (int)std::max<long long>(1, std::min<long long>(work, full));
 }
 
 }  // namespace
@@ -376,7 +450,7 @@ void reducer_free(Reducer& r) {
 void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
-    const int nb = blocks_for(d);
+    const int nb = blocks_for(d, k_mdot_partial);
     launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 0);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
@@ -387,7 +461,7 @@ void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, c
 void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
                double* host_out, double* self_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m + 1 <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
-    const int nb = blocks_for(d);
+    const int nb = blocks_for(d, k_mdot_partial);
     launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 1);
     launch("k_mdot_final", k_mdot_final, (m + 1 + 7) / 8, 256, 0, s, nb, m + 1, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, s));
@@ -399,7 +473,7 @@ void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long 
 double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long long ld, double* x, const double* w,
                   cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
-    const int nb = blocks_for(d);
+    const int nb = blocks_for(d, k_maxpy_norm);
     // h = red.result (written by the preceding mdot on this stream); partials in a separate stripe
     double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
     launch("k_maxpy_norm", k_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld, red.result, x, w, part);
@@ -416,69 +490,67 @@ void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, 
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) red.host[c] = h_host[c];
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-    launch("k_maxpy", k_maxpy, blocks_for(d), kThreads, 0, s, d, m, V, ld, red.result, x);
+    launch("k_maxpy", k_maxpy, blocks_for(d, k_maxpy), kThreads, 0, s, d, m, V, ld, red.result, x);
 }
 
 void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s) {
-    launch("k_ff_split", k_ff_split, blocks_for(d), kThreads, 0, s, d, a, x, y);
-}
-void ff_scale(const Domain& d, double a, const float2* x, float2* y, cudaStream_t s) {
-    const float ah = (float)a;
-    const float al = (float)(a - (double)ah);
-    launch("k_ff_scale", k_ff_scale, blocks_for(d), kThreads, 0, s, d, ah, al, x, y);
+    launch("k_ff_split", k_ff_split, blocks_for(d, k_ff_split), kThreads, 0, s, d, a, x, y);
 }
 template <typename T>
-void ff_convert(const Domain& d, const float2* x, T* y, cudaStream_t s) {
-    launch("k_ff_convert", k_ff_convert<T>, blocks_for(d), kThreads, 0, s, d, x, y);
+void ff_convert(const Domain& d, double a, const float2* x, T* y, cudaStream_t s) {
+    launch("k_ff_convert", k_ff_convert<T>, blocks_for(d, k_ff_convert<T>), kThreads, 0, s, d, a, x, y);
 }
-template void ff_convert<double>(const Domain&, const float2*, double*, cudaStream_t);
-template void ff_convert<float>(const Domain&, const float2*, float*, cudaStream_t);
-template void ff_convert<__nv_bfloat16>(const Domain&, const float2*, __nv_bfloat16*, cudaStream_t);
-void mdot_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, const float2* x, double* host_out,
-             double* self_out, cudaStream_t s) {
-    const int self = self_out ? 1 : 0;
-    DM_REQUIRE(m >= 1 && m + self <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
-    const int nb = blocks_for(d);
-    launch("k_ff_mdot_partial", k_ff_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, red.partial, red.max_cols,
-           self);
-    launch("k_mdot_final", k_mdot_final, (m + self + 7) / 8, 256, 0, s, nb, m + self, red.partial, red.max_cols,
-           red.result);
-    DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * (m + self), cudaMemcpyDeviceToHost, s));
+template void ff_convert<double>(const Domain&, double, const float2*, double*, cudaStream_t);
+template void ff_convert<float>(const Domain&, double, const float2*, float*, cudaStream_t);
+template void ff_convert<__nv_bfloat16>(const Domain&, double, const float2*, __nv_bfloat16*, cudaStream_t);
+
+void dcgs_dots(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const float2* v, const float2* w,
+               double* host_out, cudaStream_t s) {
+    const int m = 2 * j + 2;
+    DM_REQUIRE(j >= 0 && j <= 120 && m < red.max_cols, DM_ERR_INVALID_ARG, "dcgs: too many columns");
+    const int nb = blocks_for(d, k_ff_dcgs_dots);
+    launch("k_ff_dcgs_dots", k_ff_dcgs_dots, nb, kThreads, 0, s, d, j, Q, ld, v, w, red.partial, red.max_cols);
+    launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
+    DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
-    if (self_out) *self_out = red.host[m];
 }
-double maxpy_norm_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, float2* x, cudaStream_t s) {
-    DM_REQUIRE(m >= 1 && m <= 128 && m <= red.max_cols, DM_ERR_INVALID_ARG, "maxpy: too many columns");
-    const int nb = blocks_for(d);
+
+double dcgs_update(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const double* coef_host,
+                   float2* v, const float2* w, float2* out, cudaStream_t s) {
+    DM_REQUIRE(j >= 0 && j <= 120 && 2 * j + 2 <= red.max_cols, DM_ERR_INVALID_ARG, "dcgs: too many columns");
+    // coefficients through the pinned host buffer (the preceding dots have synchronised the stream)
+    for (int c = 0; c < 2 * j + 2; ++c) red.host[c] = coef_host[c];
+    DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * (2 * j + 2), cudaMemcpyHostToDevice, s));
+    const int nb = blocks_for(d, k_ff_dcgs_update);
     double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
-    launch("k_ff_maxpy_norm", k_ff_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld, red.result, x, part);
+    launch("k_ff_dcgs_update", k_ff_dcgs_update, nb, kThreads, 0, s, d, j, Q, ld, (const double*)red.result, v, w,
+           out, part);
     launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
     return red.host[0];
 }
-
 void vgemm(const Domain& d, int m, int p, const double* V, long long ld, const double* Y_dev, int ldy, double* out,
            long long ldo, cudaStream_t s) {
     const size_t sm = sizeof(double) * (size_t)m * p;
     DM_REQUIRE(sm <= 48 * 1024, DM_ERR_INVALID_ARG, "vgemm: basis too large");
-    launch("k_vgemm", k_vgemm, blocks_for(d), kThreads, sm, s, d, m, p, V, ld, Y_dev, ldy, out, ldo);
+    launch("k_vgemm", k_vgemm, blocks_for(d, k_vgemm), kThreads, sm, s, d, m, p, V, ld, Y_dev, ldy, out, ldo);
 }
 
 void axpby(const Domain& d, double a, const double* x, double b, double* y, cudaStream_t s) {
-    launch("k_axpby", k_axpby, blocks_for(d), kThreads, 0, s, d, a, x, b, y);
+    launch("k_axpby", k_axpby, blocks_for(d, k_axpby), kThreads, 0, s, d, a, x, b, y);
 }
 void scale_copy(const Domain& d, double a, const double* x, double* y, cudaStream_t s) {
-    if (x == y) launch("k_scale_inplace", k_scale_inplace, blocks_for(d), kThreads, 0, s, d, a, y);
-    else launch("k_scale_copy", k_scale_copy, blocks_for(d), kThreads, 0, s, d, a, x, y);
+    if (x == y) launch("k_scale_inplace", k_scale_inplace, blocks_for(d, k_scale_inplace), kThreads, 0, s, d, a, y);
+    else launch("k_scale_copy", k_scale_copy, blocks_for(d, k_scale_copy), kThreads, 0, s, d, a, x, y);
 }
 void hadamard(const Domain& d, const double* a, const double* x, double* y, cudaStream_t s) {
-    launch("k_hadamard", k_hadamard, blocks_for(d), kThreads, 0, s, d, a, x, y);
+    launch("k_hadamard", k_hadamard, blocks_for(d, k_hadamard), kThreads, 0, s, d, a, x, y);
 }
 template <typename TD, typename TS>
 void convert(const Domain& d, const TS* x, TD* y, cudaStream_t s) {
-    launch("k_convert", k_convert<TD, TS>, blocks_for(d), kThreads, 0, s, d, x, y);
+    launch("k_convert", k_convert<TD, TS>, blocks_for(d, k_convert<TD, TS>), kThreads, 0, s, d, x, y);
 }
 template <typename TD>
 void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s) {
@@ -486,7 +558,7 @@ void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s) {
     launch("k_convert_coeff", k_convert_coeff<TD>, b, kThreads, 0, s, n, x, y);
 }
 void fill_random(const Domain& d, unsigned long long seed, const double* mask, double* x, cudaStream_t s) {
-    launch("k_fill_random", k_fill_random, blocks_for(d), kThreads, 0, s, d, seed, mask, x);
+    launch("k_fill_random", k_fill_random, blocks_for(d, k_fill_random), kThreads, 0, s, d, seed, mask, x);
 }
 void zero(void* p, size_t bytes, cudaStream_t s) { DM_CUDA(cudaMemsetAsync(p, 0, bytes, s)); }
 

@@ -453,16 +453,20 @@ void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long 
 // x -= sum_c h[c] V[c*ld + r] using the h the preceding mdot left on the device (red.result),
 // and returns sum_r w[r] x[r]^2 of the updated x (one pass, one sync)
 // Krylov vectors in float-float (hi + lo FP32 pairs, about 48 significant
-// bits, arithmetic on the FP32 pipes): y = split(a x); y = a x; y = x in the
-// storage type T; h = V^T x (and sum x^2 when self_out); x -= V h with h the
-// preceding mdot_ff's device result, returning sum x^2.
+// bits, arithmetic on the FP32 pipes): y = split(a x); y = a x in the storage
+// type T.
 void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s);
-void ff_scale(const Domain& d, double a, const float2* x, float2* y, cudaStream_t s);
 template <typename T>
-void ff_convert(const Domain& d, const float2* x, T* y, cudaStream_t s);
-void mdot_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, const float2* x, double* host_out,
-             double* self_out, cudaStream_t s);
-double maxpy_norm_ff(Reducer& red, const Domain& d, int m, const float2* V, long long ld, float2* x, cudaStream_t s);
+void ff_convert(const Domain& d, double a, const float2* x, T* y, cudaStream_t s);
+// Delayed classical Gram-Schmidt (DCGS2) on float-float vectors: Q = the j
+// finished basis vectors, v = the pending vector, w = the new one.
+//   dcgs_dots: out = [Q^T v (j), Q^T w (j), v.v, v.w] (one pass, one sync)
+//   dcgs_update: with coef = [s (j), gamma (j), 1/beta, delta]:
+//     v <- (v - Q s) / beta,  out <- w - Q gamma - delta v_old;  returns |out|^2
+void dcgs_dots(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const float2* v, const float2* w,
+               double* host_out, cudaStream_t s);
+double dcgs_update(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const double* coef_host,
+                   float2* v, const float2* w, float2* out, cudaStream_t s);
 double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long long ld, double* x, const double* w,
                   cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r]    (h host array, m <= max_cols)
