@@ -41,25 +41,43 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--grid", type=int, default=128)
-    ap.add_argument("--nev", type=int, default=10)
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "ellipsoid", "batch"],
+                    help="sphere: 128^3 PEC sphere, 10 modes (the headline); ellipsoid: seeded ellipsoid on 192^3, "
+                         "16 modes; batch: 48 seeded cavities of 32^3-96^3 with 1-4 shifts each, batched solve")
+    ap.add_argument("--grid", type=int, default=None)
+    ap.add_argument("--nev", type=int, default=None)
     ap.add_argument("--sigma", type=float, default=5.0)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.grid is None:
+        a.grid = {"sphere": 128, "ellipsoid": 192, "batch": 0}[a.workload]
+    if a.nev is None:
+        a.nev = {"sphere": 10, "ellipsoid": 16, "batch": 0}[a.workload]
+    return a
 
 
 def workload(args):
     import workloads as W
+    if args.workload == "ellipsoid":
+        return W.ellipsoid_workload(args.grid, seed=W.SEED_BASE + 3, sigma=args.sigma, nev=args.nev)
     return W.sphere_workload(args.grid, radius=1.0, half_width=1.1, sigma=args.sigma, nev=args.nev,
                              offset_seed=W.SEED_BASE + 2)
 
 
+def describe(args, w):
+    if args.workload == "ellipsoid":
+        ax = tuple(round(float(v), 4) for v in w.meta.get("semi_axes", ()))
+        return (f"PEC ellipsoid, seeded semi-axes {ax}, {args.grid}^3 Yee cells, sigma={args.sigma}, "
+                f"{args.nev} modes nearest sigma, residual<={RHO_TOL}")
+    return (f"PEC sphere R=1 in [-1.1,1.1]^3, {args.grid}^3 Yee cells, seeded centre offset "
+            f"{tuple(round(float(v), 5) for v in w.meta['center'])}, sigma={args.sigma}, "
+            f"{args.nev} lowest modes, residual<={RHO_TOL}")
+
+
 def config_of(args, w, extra=None):
-    c = {"workload": (f"PEC sphere R=1 in [-1.1,1.1]^3, {args.grid}^3 Yee cells, seeded centre offset "
-                      f"{tuple(round(v, 5) for v in w.meta['center'])}, sigma={args.sigma}, "
-                      f"{args.nev} lowest modes, residual<={RHO_TOL}"),
+    c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma,
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
@@ -171,6 +189,19 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), "measured"
     return 6800.0, "fallback"
+
+
+def nvtx_mark(start):
+    """Open (start) or close the NVTX range "timed" around the timed steps; a
+    no-op where NVTX is unavailable."""
+    try:
+        import torch
+        if start:
+            torch.cuda.nvtx.range_push("timed")
+        else:
+            torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
 
 
 def stencil_bytes_per_cell(name):
@@ -289,10 +320,12 @@ def run_native(args):
     e0.record(stream)
     units = 0
     reps = []
+    nvtx_mark(True)      # an NVTX range "timed", for profilers that filter on it
     for _ in range(args.steps):
         k2, rep, st = step(args.precision)
         units += converged(rep, st)
         reps.append(rep)
+    nvtx_mark(False)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -366,6 +399,95 @@ def run_native(args):
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """The batched form: 48 seeded cavities (spheres and ellipsoids, 32^3 to
+    96^3) with 1-4 shifts each, all (cavity, shift) eigensolves in one call of
+    dm_eigensolve_batched over worker streams.  One step = geometry setup of
+    every cavity + the batched solve; value = converged eigenpairs / s."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1301_3794_gb300 as dm
+
+    items = W.batch_workloads(48)
+    stream = torch.cuda.Stream()
+    ctx = dm.Context(local, stream=stream.cuda_stream)
+    phis_host = [np.ascontiguousarray(w.phi.ravel()) for w, _, _ in items]
+    with torch.cuda.stream(stream):
+        phis_dev = [torch.from_numpy(p).to(f"cuda:{local}") for p in phis_host]
+    torch.cuda.synchronize()
+    npairs = sum(len(sh) * nev for _, sh, nev in items)
+
+    def step(host_io=False):
+        geoms = []
+        jobs = []
+        for (w, shifts, nev), ph, pd in zip(items, phis_host, phis_dev):
+            g = w.grid
+            geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, ph if host_io else pd, g.origin)
+            geoms.append(geom)
+            for sg in shifts:
+                jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision})
+        out = dm.eigensolve_batched(ctx, jobs, streams=8)
+        for geom in geoms:
+            geom.close()
+        return sum(rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0 for _, rep, st in out), out
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = ctx.launches
+    t0 = time.perf_counter()
+    nvtx_mark(True)
+    units = 0
+    for _ in range(args.steps):
+        u, out = step()
+        units += u
+    nvtx_mark(False)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launches - l0
+    tot_units, max_s = aggregate(units, secs, device=f"cuda:{local}")
+    t1 = time.perf_counter()
+    units_e2e = 0
+    for _ in range(args.steps):
+        units_e2e += step(host_io=True)[0]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t1
+    tot_e2e, max_e2e = aggregate(units_e2e, e2e_s, device=f"cuda:{local}")
+    sizes = sorted({w.grid.nx for w, _, _ in items})
+    res = {
+        "metric": METRIC, "value": round(tot_units / max_s, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_s / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+" + args.precision, "data": "synthetic (seeded level sets)",
+        "config": {"workload": (f"batch of {len(items)} seeded cavities (spheres and ellipsoids, grids {sizes}), "
+                                f"{sum(len(sh) for _, sh, _ in items)} (cavity, shift) solves, {npairs} eigenpairs "
+                                f"requested per step, residual<={RHO_TOL}"),
+                   "mg_precision": args.precision, "outer_precision": "f64", "streams": 8,
+                   "l2": "inputs larger than L2 (48 cavities' solver state)", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(tot_e2e / max_e2e, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(p.nbytes for p in phis_host)),
+                "d2h_bytes_per_step": int(8 * npairs)},
+        "gpu_launches": int(launches),
+        "roofline": None,
+        "clocks": clk,
+        "solver": {"converged_per_step": units / max(args.steps, 1), "requested_per_step": npairs,
+                   "solves_per_s": round(sum(len(sh) for _, sh, _ in items) * args.steps / max_s, 3)},
+    }
+    if rank == 0:
+        print(json.dumps(res), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -443,6 +565,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_native(args)
 

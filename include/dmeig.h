@@ -238,7 +238,11 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
  * z faces divided by its RMS over the open faces, A_x, A_y, A_z, the node
  * cell's V, and 0.  Output: the error on those faces in units of RMS(r) h^2
  * (h = smallest spacing).  Inside the preconditioner it corrects the V-cycle
- * result z by N(f - (K - sigma A) z); the FP64 FGMRES residual judges it.
+ * result z: with r = f - (K - sigma A) z and c the network's correction for r,
+ * z <- z + alpha c where alpha = <r, K c> / <K c, K c> minimises the residual
+ * along c (no step when alpha <= 0); the FP64 FGMRES residual judges it and
+ * switches it off for the rest of a solve when an iteration contracts by less
+ * than 0.8.
  * Weights: [W1 | W2 | W3], each W[a][b][c][cin][cout] (a along k, b along j,
  * c along i), FP32. */
 dm_status dm_learned_create(dm_context* ctx, unsigned long long seed, dm_learned** out);
@@ -254,10 +258,12 @@ dm_status dm_learned_apply(dm_learned* net, const dm_geometry* geom, const doubl
  * i fastest, channel last).  grad: host, dm_learned_num_params() floats. */
 dm_status dm_learned_loss_grad(dm_learned* net, const dm_geometry* geom, const float* X, const float* E, float* loss,
                                float* grad);
-/* Train with Adam on (residual, error) pairs the operator's V-cycle produces:
- * `runs` seeded random right-hand sides, 8 Krylov directions each; the error
- * of each V-cycle result comes from an accurate shifted solve.  loss_history
- * (nullable, host, epochs floats) receives the mean loss of every epoch. */
+/* Train with Adam on the residuals the operator's plain V-cycle leaves: `runs`
+ * seeded random right-hand sides, 8 Krylov directions each.  The objective is
+ * the residual the correction leaves, 0.5 |r / RMS(r) - (K - sigma A) h^2 N(r)|^2
+ * over the open faces / #open faces, with the operator in FP32 (its gradient is
+ * K applied to that residual, K being symmetric).  loss_history (nullable,
+ * host, epochs floats) receives the mean loss of every epoch. */
 dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epochs, float lr, unsigned long long seed,
                            float* loss_history);
 /* Use (net) or stop using (NULL) the learned correction in op's preconditioner. */

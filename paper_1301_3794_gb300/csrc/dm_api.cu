@@ -244,6 +244,7 @@ struct OpLevel {
     DBuf<float> sd_v32;
     int sd_nsub = 0, sd_ncopies = 0, sd_maxrows = 0, sd_maxbox = 0;
     int sd_cls_first[kSchwarzClasses] = {}, sd_cls_count[kSchwarzClasses] = {};
+    bool sd_fixed = false;
 };
 
 // FGMRES workspace: the Arnoldi basis V and the work vector wf in
@@ -298,6 +299,9 @@ struct dm_operator {
     bool graphs = true;
     // learned correction after the V-cycle (own copy of the network's weights and buffers)
     std::unique_ptr<LearnedNet> lnet;
+    DBuf<char> lc_c, lc_kc;        // its correction and the operator applied to it
+    DBuf<double> lc_part;
+    std::vector<double> lc_host;
     bool learned_active = false;
     int learned_applied = 0, learned_fallbacks = 0;
     long long nopen0 = 0;
@@ -324,6 +328,7 @@ BandSchwarz<TC> schwarz_view(const OpLevel& o, const TC* vals) {
     b.ncopies = o.sd_ncopies;
     b.maxrows = o.sd_maxrows;
     b.maxbox = o.sd_maxbox;
+    b.fixed = o.sd_fixed;
     for (int k = 0; k < kSchwarzClasses; ++k) {
         b.cls_first[k] = o.sd_cls_first[k];
         b.cls_count[k] = o.sd_cls_count[k];
@@ -458,27 +463,56 @@ bool capture_graph(dm_operator* op, F&& f, cudaGraphExec_t* out, long long* kern
     return true;
 }
 
+// V-cycles replay as CUDA graphs unless the context traces kernels or the
+// environment sets DM_GRAPHS=0 (for profilers that time kernels one launch at
+// a time; the same kernels run either way).
 bool graphs_allowed(const dm_operator* op) {
-    return op->graphs && !(g_tracer && g_tracer->on);
+    static const bool env_off = [] {
+        const char* e = std::getenv("DM_GRAPHS");
+        return e && e[0] == '0';
+    }();
+    return op->graphs && !env_off && !(g_tracer && g_tracer->on);
 }
 
-// z <- z + RMS(r) h^2 N(r / RMS(r), A, V) with r = f - (K - sigma A) z on the fine level
+// Learned correction after the V-cycle on the fine level:
+//   r = f - (K - sigma A) z,  c = RMS(r) h^2 N(r / RMS(r), A, V),
+//   z <- z + alpha c  with alpha = <r, K c> / <K c, K c> (the step along c that
+// minimises the residual norm), skipped when alpha <= 0.  So the correction
+// never raises the residual of the preconditioned direction.
 template <typename T, typename TC>
 void learned_correct(dm_operator* op, const T* f, T* z, T* scratch) {
     cudaStream_t s = op->ctx->stream;
     const GeoLevel& g0 = glv(op, 0);
     const VecOp<T, TC> o = vop<T, TC>(op, 0);
+    const long long n = 3ll * g0.g.np;
+    constexpr int nb = 152 * 2;
+    if (op->lc_c.n < sizeof(T) * (size_t)n) {
+        op->lc_c.alloc(sizeof(T) * (size_t)n);
+        op->lc_kc.alloc(sizeof(T) * (size_t)n);
+        op->lc_part.alloc(2 * nb);
+        op->lc_host.assign(2 * nb, 0.0);
+    }
+    T* c = reinterpret_cast<T*>(op->lc_c.get());
+    T* kc = reinterpret_cast<T*>(op->lc_kc.get());
     vec_stencil(o, ST_RESID, z, f, scratch, 0.0, s);
-    const double ss = sumsq<T>(3ll * g0.g.np, scratch, s);
-    if (!(ss > 0.0) || op->nopen0 <= 0) return;
-    const double scale = std::sqrt(ss / (double)op->nopen0);
+    double rr[2];
+    dot2<T>(n, scratch, scratch, op->lc_part.get(), op->lc_host.data(), nb, rr, s);
+    if (!(rr[0] > 0.0) || op->nopen0 <= 0) return;
+    const double scale = std::sqrt(rr[0] / (double)op->nopen0);
     const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
     LearnedNet& net = *op->lnet;
     net.alloc(g0.g);
     net.features(g0.A.get(), g0.V.get(), 1.0 / scale, scratch, prec_index<T>(), s);
     net.forward(s);
-    net.add_correction<T>(g0.A.get(), scale * h * h, z, s);
-    ++op->learned_applied;
+    zero(c, sizeof(T) * (size_t)n, s);
+    net.add_correction<T>(g0.A.get(), scale * h * h, c, s);
+    vec_stencil(o, ST_APPLY, c, (const T*)nullptr, kc, 0.0, s);
+    double ab[2];
+    dot2<T>(n, scratch, kc, op->lc_part.get(), op->lc_host.data(), nb, ab, s);
+    if (ab[1] > 0.0 && ab[0] > 0.0) {
+        axpy_store<T>(n, ab[0] / ab[1], c, z, s);
+        ++op->learned_applied;
+    }
 }
 
 // z = M^-1 v on FP64 fine-level vectors: v is converted into the level-0 f
@@ -924,6 +958,7 @@ void setup_operator(dm_operator* op) {
             o.sd_ncopies = (int)sl.copy.size();
             o.sd_maxrows = sl.maxrows;
             o.sd_maxbox = sl.maxbox;
+            o.sd_fixed = sl.fixed;
             for (int k = 0; k < kSchwarzClasses; ++k) {
                 o.sd_cls_first[k] = sl.cls_first[k];
                 o.sd_cls_count[k] = sl.cls_count[k];
@@ -2017,17 +2052,16 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
     return guarded(op->ctx, [&] {
         dm_context* ctx = op->ctx;
         cudaStream_t s = ctx->stream;
-        const GeoLevel& g0 = glv(op, 0);
+        GeoLevel& g0 = *const_cast<dm_geometry*>(op->geom)->lv[0];
         const Domain D = g0.vdom();
         const long long n3 = D.len();
         const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
-        // 1. (residual, error) pairs: for Krylov directions v of FGMRES-like
-        //    sequences, z = V-cycle(v), r = v - (K - sigma A) z, e = (K - sigma A)^-1 r
+        // 1. residuals the plain V-cycle leaves: for Krylov directions v of
+        //    FGMRES-like sequences, z = V-cycle(v), r = v - (K - sigma A) z
         const int dirs = 8;
-        std::vector<DBuf<float>> R, Eg;
+        std::vector<DBuf<float>> R;
         std::vector<double> scales;
-        DBuf<double> v((size_t)(dirs + 1) * n3), z(n3), r(n3), e(n3);
-        const bool had = op->lnet != nullptr;
+        DBuf<double> v((size_t)(dirs + 1) * n3), z(n3), r(n3);
         std::unique_ptr<LearnedNet> keep = std::move(op->lnet);   // plain V-cycle while sampling
         for (int run = 0; run < runs; ++run) {
             fill_random(D, seed + 7919ull * run, g0.A.get(), v.get(), s);
@@ -2038,14 +2072,10 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
                 precond_vec(op, vj, z.get());
                 apply_vec64(op, 0, z.get(), r.get());          // r = (K - sigma A) z
                 axpby(D, 1.0, vj, -1.0, r.get(), s);          // r = v - (K - sigma A) z
-                double rr = 0.0;
-                solve_vec(op, r.get(), e.get(), 1e-6, 40, 200, &rr);
                 const double rs = std::sqrt(sumsq<double>(n3, r.get(), s) / (double)std::max(op->nopen0, 1ll));
                 if (rs > 0.0) {
                     R.emplace_back(n3);
-                    Eg.emplace_back(n3);
                     convert<float, double>(D, r.get(), R.back().get(), s);
-                    convert<float, double>(D, e.get(), Eg.back().get(), s);
                     scales.push_back(rs);
                 }
                 // next direction: (K - sigma A) z orthonormalised against the previous ones
@@ -2060,9 +2090,16 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
             }
         }
         op->lnet = std::move(keep);
-        (void)had;
         DM_REQUIRE(!R.empty(), DM_ERR_NO_CONVERGENCE, "learned training: no samples");
-        // 2. Adam on the masked MSE, samples in a seeded order every epoch
+        // 2. Adam on the residual objective 0.5 |r / RMS(r) - K h^2 N(r)|^2 / #open
+        //    (FP32 operator), samples in a seeded order every epoch
+        {
+            std::lock_guard<std::mutex> lock(const_cast<dm_geometry*>(op->geom)->mu);
+            ensure_f32(g0, s);
+        }
+        const VecOp<float, float> o32{g0.g, g0.A32.get(), g0.L32.get(), g0.invV32.get(), nullptr, op->sigma, 0,
+                                      g0.tiles.get(), g0.ntiles, nullptr, 0, 0};
+        DBuf<float> ybuf(n3), kbuf(n3);
         LearnedNet& L = net->net;
         L.alloc(g0.g);
         std::mt19937_64 rng(seed ^ 0x5bd1e995ull);
@@ -2073,9 +2110,9 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
             double tot = 0.0;
             for (int k : order) {
                 L.features(g0.A.get(), g0.V.get(), 1.0 / scales[k], R[k].get(), 1, s);
-                L.target_from(Eg[k].get(), g0.A.get(), 1.0 / (scales[k] * h * h), s);
                 L.forward(s);
-                tot += L.loss(g0.A.get(), (double)op->nopen0, s);
+                tot += L.residual_loss(o32, g0.A.get(), R[k].get(), 1.0 / scales[k], h * h, ybuf.get(), kbuf.get(),
+                                       (double)op->nopen0, s);
                 L.backward(s);
                 L.adam(lr, s);
             }

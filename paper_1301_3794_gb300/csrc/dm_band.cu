@@ -59,11 +59,37 @@ __device__ __forceinline__ C row_dot(const C* v, const C* d, const RowAddr& a, i
     return acc;
 }
 
+// The default brick (8 nodes) uses one fixed local box for every subdomain:
+// nodes B b - 2 .. B b + 9 on each axis (12 nodes; x padded to 13 to spread
+// shared-memory banks), so every coupling offset is a compile-time constant.
+constexpr int kFixedBrick = 8, kFX = 13, kFY = 12, kFZ = 12, kFXY = kFX * kFY, kF3 = kFXY * kFZ;
+
+template <typename C, int c>
+__device__ __forceinline__ C row_dot_fixed(const C* v, const C* d, int p) {
+    constexpr int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    constexpr int sc = c == 0 ? 1 : (c == 1 ? kFX : kFXY);
+    constexpr int s1 = c1 == 0 ? 1 : (c1 == 1 ? kFX : kFXY);
+    constexpr int s2 = c2 == 0 ? 1 : (c2 == 1 ? kFX : kFXY);
+    constexpr int o1 = (c1 - c) * kF3 - sc, o2 = (c2 - c) * kF3 - sc;
+    const C* q = d + p;
+    C acc = v[0] * q[0];
+    acc += v[1] * q[-1] + v[2] * q[1];
+    acc += v[3] * q[-kFX] + v[4] * q[kFX];
+    acc += v[5] * q[-kFXY] + v[6] * q[kFXY];
+    acc += v[7] * q[o1] + v[8] * q[o1 + s1] + v[9] * q[o1 + sc] + v[10] * q[o1 + sc + s1];
+    acc += v[11] * q[o2] + v[12] * q[o2 + s2] + v[13] * q[o2 + sc] + v[14] * q[o2 + sc + s2];
+    return acc;
+}
+template <typename C>
+__device__ __forceinline__ C row_dot_fixed(int c, const C* v, const C* d, int p) {
+    return c == 0 ? row_dot_fixed<C, 0>(v, d, p) : (c == 1 ? row_dot_fixed<C, 1>(v, d, p) : row_dot_fixed<C, 2>(v, d, p));
+}
+
 // R > 0: each thread owns up to R rows (row r = threadIdx.x + k blockDim.x) with
 // their coefficients and addresses in registers.  R == 0: any row count; r0
 // and omega/D in shared memory and the coefficients re-read on every sweep.
 // Block b handles subdomain sub0 + b.
-template <typename T, typename TC, int R, int NT>
+template <typename T, typename TC, int R, int NT, bool FIXED>
 __global__ void __launch_bounds__(NT)
     k_band_schwarz(int sub0, const int* __restrict__ off, const int* __restrict__ copy, const int* __restrict__ pos,
                    const int* __restrict__ dims, const TC* __restrict__ vals, int ncopies,
@@ -80,7 +106,7 @@ __global__ void __launch_bounds__(NT)
     const int b0 = off[sd];
     const int nr = off[sd + 1] - b0;
     const int dm = dims[sd];
-    const int lx = dm & 1023, ly = (dm >> 10) & 1023, lz = dm >> 20;
+    const int lx = FIXED ? kFX : dm & 1023, ly = FIXED ? kFY : (dm >> 10) & 1023, lz = FIXED ? kFZ : dm >> 20;
     const int lxy = lx * ly, l3 = lxy * lz;
     for (int k = threadIdx.x; k < 3 * l3; k += blockDim.x) {
         buf0[k] = C(0);
@@ -91,6 +117,7 @@ __global__ void __launch_bounds__(NT)
     C v[RR][kBandSlots];
     C r0[RR], w[RR];
     RowAddr ad[RR];
+    int cm[RR];
     // residual of the full row at the start values, and the first sweep from d = 0
     auto start_row = [&](int r, C* ve, C& rr, C& ww) {
         const int ct = copy[b0 + r];
@@ -114,6 +141,7 @@ __global__ void __launch_bounds__(NT)
             if (r < nr) {
                 start_row(r, v[k], r0[k], w[k]);
                 ad[k] = row_addr(pos[b0 + r], l3, lx, lxy);
+                cm[k] = pos[b0 + r] / l3;
             }
         }
     } else {
@@ -127,7 +155,10 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int k = 0; k < RR; ++k) {
                 const int r = threadIdx.x + k * blockDim.x;
-                if (r < nr) dn[ad[k].b0] = dc[ad[k].b0] + w[k] * (r0[k] - row_dot(v[k], dc, ad[k], lx, lxy));
+                if (r < nr) {
+                    const C acc = FIXED ? row_dot_fixed(cm[k], v[k], dc, ad[k].b0) : row_dot(v[k], dc, ad[k], lx, lxy);
+                    dn[ad[k].b0] = dc[ad[k].b0] + w[k] * (r0[k] - acc);
+                }
             }
         } else {
             for (int r = threadIdx.x; r < nr; r += blockDim.x) {
@@ -265,12 +296,18 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         ++out.cls_count[cl];
         const long long kb = cp[c0].brick;
         const int B[3] = {(int)(kb % nb[0]), (int)((kb / nb[0]) % nb[1]), (int)(kb / ((long long)nb[0] * nb[1]))};
-        // local box: the subdomain's nodes and their neighbours, within the padded grid
+        // local box: the subdomain's nodes and their neighbours (within the
+        // padded grid; the default brick uses the fixed, unclipped box)
         int lo[3], l[3];
         for (int a = 0; a < 3; ++a) {
-            lo[a] = std::max(B[a] * brick - 2, -1);
-            const int hi = std::min(B[a] * brick + brick + 1, n[a] + 1);
-            l[a] = hi - lo[a] + 1;
+            if (brick == kFixedBrick) {
+                lo[a] = B[a] * brick - 2;
+                l[a] = a == 0 ? kFX : (a == 1 ? kFY : kFZ);
+            } else {
+                lo[a] = std::max(B[a] * brick - 2, -1);
+                const int hi = std::min(B[a] * brick + brick + 1, n[a] + 1);
+                l[a] = hi - lo[a] + 1;
+            }
         }
         DM_REQUIRE(l[0] < 1024 && l[1] < 1024 && l[2] < 1024, DM_ERR_INVALID_ARG, "band brick too large");
         out.off.push_back((int)out.copy.size());
@@ -286,6 +323,7 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         }
     }
     out.off.push_back(nc);
+    out.fixed = brick == kFixedBrick;
 }
 
 void band_copy_vals(const int* copy, int ncopies, const double* band_vals, int nband, double* out, cudaStream_t s) {
@@ -327,7 +365,12 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
         const int count = single ? bs.nsub : bs.cls_count[cl];
         const size_t smem = schwarz_smem<T>(bs.maxbox, bs.maxrows, R);
 #define DM_SCHWARZ(RV, NV)                                                                                         \
-    launch(name, k_band_schwarz<T, TC, RV, NV>, count, NV, smem, s, first, bs.off, bs.copy,                      \
+    if (bs.fixed)                                                                                                  \
+        launch(name, k_band_schwarz<T, TC, RV, NV, true>, count, NV, smem, s, first, bs.off, bs.copy, bs.pos,      \
+               bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,      \
+               bs.maxbox, bs.maxrows);                                                                           \
+    else                                                                                                           \
+    launch(name, k_band_schwarz<T, TC, RV, NV, false>, count, NV, smem, s, first, bs.off, bs.copy,               \
            bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,  \
            bs.maxbox, bs.maxrows)
         if (nt == 256) DM_SCHWARZ(1, 256);
@@ -363,11 +406,17 @@ void band_schwarz_prepare(const SchwarzLayout& sl) {
         int R, nt;
         class_shape<T>(cl, R, nt);
         const size_t need = schwarz_smem<T>(sl.maxbox, sl.maxrows, R);
-        if (nt == 256) allow_smem(k_band_schwarz<T, TC, 1, 256>, need);
-        else if (R == 1) allow_smem(k_band_schwarz<T, TC, 1, 512>, need);
-        else if (R == 2) allow_smem(k_band_schwarz<T, TC, 2, 512>, need);
-        else if (R == 4) allow_smem(k_band_schwarz<T, TC, 4, 512>, need);
-        else allow_smem(k_band_schwarz<T, TC, 0, 512>, need);
+        const bool fx = sl.fixed;
+        if (nt == 256) fx ? allow_smem(k_band_schwarz<T, TC, 1, 256, true>, need)
+                          : allow_smem(k_band_schwarz<T, TC, 1, 256, false>, need);
+        else if (R == 1) fx ? allow_smem(k_band_schwarz<T, TC, 1, 512, true>, need)
+                            : allow_smem(k_band_schwarz<T, TC, 1, 512, false>, need);
+        else if (R == 2) fx ? allow_smem(k_band_schwarz<T, TC, 2, 512, true>, need)
+                            : allow_smem(k_band_schwarz<T, TC, 2, 512, false>, need);
+        else if (R == 4) fx ? allow_smem(k_band_schwarz<T, TC, 4, 512, true>, need)
+                            : allow_smem(k_band_schwarz<T, TC, 4, 512, false>, need);
+        else fx ? allow_smem(k_band_schwarz<T, TC, 0, 512, true>, need)
+                : allow_smem(k_band_schwarz<T, TC, 0, 512, false>, need);
     }
 }
 

@@ -354,6 +354,7 @@ int schwarz_class(int rows);
 struct SchwarzLayout {
     std::vector<int> off, copy, pos, dims;
     int maxrows = 0, maxbox = 0;
+    bool fixed = false;           // every subdomain uses the fixed box of the default brick
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
 };
 template <typename TC>
@@ -365,6 +366,7 @@ struct BandSchwarz {
     const TC* vals = nullptr;     // [15][ncopies] slot coefficients of each copy's row
     int nsub = 0, ncopies = 0, maxrows = 0, maxbox = 0;
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
+    bool fixed = false;
 };
 void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int brick, SchwarzLayout& out,
                         cudaStream_t s);

@@ -211,6 +211,36 @@ __global__ void k_mse(Grid3 g, const float* __restrict__ Y, const float* __restr
     if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = red[0] * inv_msum;
 }
 
+// res = mask (r inv - Ky) in place of Ky, and block partials of 0.5 |res|^2 / msum
+__global__ void k_res_loss(long long n, const float* __restrict__ r, float inv, const double* __restrict__ A,
+                           float* __restrict__ ky, float inv_msum, float* __restrict__ part) {
+    __shared__ float red[256];
+    float l = 0.f;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const float v = A[q] > 0.0 ? r[q] * inv - ky[q] : 0.f;
+        ky[q] = v;
+        l += 0.5f * v * v;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0] * inv_msum;
+}
+// dY = a g on the open faces of each node (gathered to node-channel order)
+__global__ void k_grad_gather(Grid3 g, const float* __restrict__ gv, const double* __restrict__ A, float a,
+                              __nv_bfloat16* __restrict__ dY) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    for (int c = 0; c < 3; ++c) {
+        const int q = c * g.np + p;
+        dY[(size_t)p * 3 + c] = __float2bfloat16(A[q] > 0.0 ? a * gv[q] : 0.f);
+    }
+}
+
 __global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ grad, float* __restrict__ m,
                        float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,6 +400,30 @@ float LearnedNet::loss(const double* A, double msum, cudaStream_t s) {
     return h;
 }
 
+float LearnedNet::residual_loss(const VecOp<float, float>& o, const double* A, const float* r, double inv_scale,
+                                double h2, float* ybuf, float* kbuf, double msum, cudaStream_t s) {
+    const long long n = 3ll * g.np;
+    // y = h^2 Y on the open faces, K y
+    DM_CUDA(cudaMemsetAsync(ybuf, 0, sizeof(float) * (size_t)n, s));
+    add_correction<float>(A, h2, ybuf, s);
+    vec_stencil<float, float>(o, ST_APPLY, ybuf, nullptr, kbuf, 0.0, s);
+    // res = r / RMS(r) - K y and the loss
+    const int nb = 152 * 4;
+    if (loss_part.n < (size_t)nb) loss_part.alloc(nb);
+    const float inv_m = (float)(1.0 / std::max(msum, 1.0));
+    launch("learned_res_loss", k_res_loss, nb, 256, 0, s, n, r, (float)inv_scale, A, kbuf, inv_m, loss_part.get());
+    DBuf<float> tot(1);
+    launch("learned_mse_sum", k_colsum, 1, 256, 0, s, loss_part.get(), nb, 1, tot.get());
+    // dloss/dy = -K res / msum (K symmetric), dloss/dY = h^2 dloss/dy
+    vec_stencil<float, float>(o, ST_APPLY, kbuf, nullptr, ybuf, 0.0, s);
+    launch("learned_grad_gather", k_grad_gather, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, ybuf, A,
+           (float)(-h2 * inv_m), dY.get());
+    float h = 0.f;
+    DM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof(float), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
 void LearnedNet::adam(float lr, cudaStream_t s) {
     ++step;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -404,6 +458,63 @@ double sumsq(long long n, const T* x, cudaStream_t s) {
 template double sumsq<double>(long long, const double*, cudaStream_t);
 template double sumsq<float>(long long, const float*, cudaStream_t);
 template double sumsq<__nv_bfloat16>(long long, const __nv_bfloat16*, cudaStream_t);
+
+// block partials of (x . y, y . y) over n entries of two vectors of storage type T
+template <typename T>
+__global__ void k_dot2(long long n, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ part) {
+    __shared__ double ra[256], rb[256];
+    double a = 0.0, b = 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const double xv = (double)to_c(x[r]), yv = (double)to_c(y[r]);
+        a += xv * yv;
+        b += yv * yv;
+    }
+    ra[threadIdx.x] = a;
+    rb[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            ra[threadIdx.x] += ra[threadIdx.x + s];
+            rb[threadIdx.x] += rb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = ra[0];
+        part[2 * blockIdx.x + 1] = rb[0];
+    }
+}
+// z += a c over n entries
+template <typename T>
+__global__ void k_axpy_store(long long n, double a, const T* __restrict__ c, T* __restrict__ z) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        z[r] = to_store<T>((double)to_c(z[r]) + a * (double)to_c(c[r]));
+}
+
+template <typename T>
+void dot2(long long n, const T* x, const T* y, double* part_dev, double* part_host, int nb, double out[2],
+          cudaStream_t s) {
+    launch("learned_dot2", k_dot2<T>, nb, 256, 0, s, n, x, y, part_dev);
+    DM_CUDA(cudaMemcpyAsync(part_host, part_dev, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    out[0] = out[1] = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        out[0] += part_host[2 * b];
+        out[1] += part_host[2 * b + 1];
+    }
+}
+template <typename T>
+void axpy_store(long long n, double a, const T* c, T* z, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+    launch("learned_axpy", k_axpy_store<T>, nb, 256, 0, s, n, a, c, z);
+}
+#define DM_INST(T)                                                                                              \
+    template void dot2<T>(long long, const T*, const T*, double*, double*, int, double[2], cudaStream_t);       \
+    template void axpy_store<T>(long long, double, const T*, T*, cudaStream_t);
+DM_INST(double)
+DM_INST(float)
+DM_INST(__nv_bfloat16)
+#undef DM_INST
 
 template <typename T>
 void LearnedNet::add_correction(const double* A, double scale, T* z, cudaStream_t s) {

@@ -37,10 +37,24 @@ struct LearnedNet {
     void set_X(const float* nat_dev, cudaStream_t s);       // features from a natural [nodes][8] device array
     void set_E(const float* nat_dev, cudaStream_t s);       // targets from a natural [nodes][3] device array
     void target_from(const float* e_pad, const double* A, double inv, cudaStream_t s);
+    // Residual objective on the fine level: with y = h2 Y on the open faces and
+    // r the (padded, FP32) residual, loss = 0.5 |r inv_scale - K y|^2 / msum over
+    // the open faces (K = o's operator, FP32); writes dY = dloss/dY.  ybuf, kbuf:
+    // padded FP32 face scratch.
+    float residual_loss(const VecOp<float, float>& o, const double* A, const float* r, double inv_scale, double h2,
+                        float* ybuf, float* kbuf, double msum, cudaStream_t s);
 };
 
 // sum of squares of a padded vector of n entries (host result)
 template <typename T>
 double sumsq(long long n, const T* x, cudaStream_t s);
+// (x . y, y . y) over n entries: nb block partials in part_dev / part_host
+// (pinned), summed on the host in a fixed order
+template <typename T>
+void dot2(long long n, const T* x, const T* y, double* part_dev, double* part_host, int nb, double out[2],
+          cudaStream_t s);
+// z += a c over n entries
+template <typename T>
+void axpy_store(long long n, double a, const T* c, T* z, cudaStream_t s);
 
 }  // namespace dm
