@@ -118,6 +118,10 @@ struct GeoLevel {
     int ntiles = 0;
     Domain vdom() const { return Domain{g, tiles.get(), ntiles, 3}; }   // face vectors
     Domain sdom() const { return Domain{g, tiles.get(), ntiles, 1}; }   // cell vectors
+    // ascending lists of the open faces and the active cells (the compact index
+    // spaces of the Krylov bases); built with the first operator on the level
+    DBuf<int> flist, clist;
+    int nflist = -1, nclist = -1;
 };
 
 struct Sync {
@@ -251,16 +255,17 @@ struct OpLevel {
 // float-float (see dcgs_dots), the preconditioned vectors Z and the operator
 // output w in FP64
 struct Fgmres {
-    long long n = 0;
+    long long n = 0, nc = 0;   // padded vector length, compact (basis) length
     int m = 0;
     DBuf<float2> V, wf;
     DBuf<double> Z, w;
-    void ensure(long long n_, int m_) {
-        if (n == n_ && m >= m_) return;
+    void ensure(long long n_, long long nc_, int m_) {
+        if (n == n_ && nc == nc_ && m >= m_) return;
         n = n_;
+        nc = nc_;
         m = m_;
-        V.alloc((size_t)(m + 1) * n);
-        wf.alloc((size_t)n);
+        V.alloc((size_t)(m + 1) * nc);
+        wf.alloc((size_t)nc);
         Z.alloc((size_t)m * n);
         w.alloc((size_t)n);
     }
@@ -524,14 +529,21 @@ void mg_input(const Domain& D, const double* v, double scale, T* f, cudaStream_t
     DM_REQUIRE(scale == 1.0, DM_ERR_INVALID_ARG, "scaled FP64 preconditioner input");
     convert<T, double>(D, v, f, s);
 }
+// compact float-float input: scattered into f over the level's list
+struct CompactIn {
+    const float2* v;
+    const int* list;
+    long long n;
+};
 template <typename T>
-void mg_input(const Domain& D, const float2* v, double scale, T* f, cudaStream_t s) {
-    ff_convert<T>(D, scale, v, f, s);
+void mg_input(const Domain& D, const CompactIn& v, double scale, T* f, cudaStream_t s) {
+    (void)D;
+    ff_scatter<T>(v.n, v.list, scale, v.v, f, s);
 }
 
 // z = M^-1 (scale v): one V-cycle (graph-replayed after the first call)
 template <typename T, typename TC, typename TIn>
-void precond_vec_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
+void precond_vec_T(dm_operator* op, const TIn& v, double* z, double scale = 1.0) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).vdom();
     WorkLevel& w0 = op->wk[0];
@@ -555,7 +567,7 @@ void precond_vec_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0)
 }
 
 template <typename T, typename TC, typename TIn>
-void precond_scal_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
+void precond_scal_T(dm_operator* op, const TIn& v, double* z, double scale = 1.0) {
     cudaStream_t s = op->ctx->stream;
     const Domain D = glv(op, 0).sdom();
     WorkLevel& w0 = op->wk[0];
@@ -578,7 +590,7 @@ void precond_scal_T(dm_operator* op, const TIn* v, double* z, double scale = 1.0
 }
 
 template <typename TIn>
-void precond_vec(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
+void precond_vec(dm_operator* op, const TIn& v, double* z, double scale = 1.0) {
     switch (op->mg.precision) {
         case DM_PREC_F64: precond_vec_T<double, double>(op, v, z, scale); break;
         case DM_PREC_F32: precond_vec_T<float, float>(op, v, z, scale); break;
@@ -587,7 +599,7 @@ void precond_vec(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
 }
 
 template <typename TIn>
-void precond_scal(dm_operator* op, const TIn* v, double* z, double scale = 1.0) {
+void precond_scal(dm_operator* op, const TIn& v, double* z, double scale = 1.0) {
     switch (op->mg.precision) {
         case DM_PREC_F64: precond_scal_T<double, double>(op, v, z, scale); break;
         case DM_PREC_F32: precond_scal_T<float, float>(op, v, z, scale); break;
@@ -655,13 +667,21 @@ struct NoMonitor {
 };
 
 // monitor(ratio) is told the residual contraction of every iteration
+// The basis lives in the compact index space of `list` (the nl entries of the
+// padded domain D that can be nonzero); b, x and the operator work on D.
 template <class Apply, class Prec, class Monitor = NoMonitor>
-int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Prec prec, const double* b, double* x,
-           double tol, int maxit, double* relres, double abs_tol = 0.0, Monitor monitor = Monitor()) {
+int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long long nl, int m, Apply apply, Prec prec,
+           const double* b, double* x, double tol, int maxit, double* relres, double abs_tol = 0.0,
+           Monitor monitor = Monitor()) {
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
     DM_REQUIRE(m >= 1 && 2 * m + 2 < ctx->red.max_cols, DM_ERR_INVALID_ARG, "FGMRES restart length too large");
-    ws.ensure(n, m);
+    DM_REQUIRE(nl >= 1 && nl < (1ll << 31), DM_ERR_INVALID_ARG, "FGMRES: empty basis index space");
+    ws.ensure(n, nl, m);
+    // flat domain of the compact vectors
+    Grid3 gc = D.g;
+    gc.np = (int)nl;
+    const Domain Dc{gc, nullptr, 0, 1};
     float2* V = ws.V.get();
     float2* wf = ws.wf.get();
     double* Z = ws.Z.get();
@@ -687,18 +707,18 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
         }
         res = beta / bnorm;
         if (beta <= thr) break;
-        ff_split(D, 1.0 / beta, first ? b : w, V, s);
+        ff_gather(nl, list, 1.0 / beta, first ? b : w, V, s);
         std::fill(H.begin(), H.end(), 0.0);
         double nu = 1.0;          // norm of the pending vector V_j (provisional)
         double prev = beta;
         int k = 0;                // columns of H built in this cycle
         for (int j = 0; j < m && total < maxit; ++j) {
-            float2* Vj = V + (size_t)j * n;
+            float2* Vj = V + (size_t)j * nl;
             prec(Vj, 1.0 / nu, Z + (size_t)j * n);
             apply(Z + (size_t)j * n, w);
-            ff_split(D, 1.0, w, wf, s);
+            ff_gather(nl, list, 1.0, w, wf, s);
             // one sweep: Q^T v, Q^T w, v.v, v.w with Q = V_0 .. V_{j-1} finished
-            dcgs_dots(ctx->red, D, j, V, n, Vj, wf, dots.data(), s);
+            dcgs_dots(ctx->red, Dc, j, V, nl, Vj, wf, dots.data(), s);
             double ss = 0.0, sc = 0.0;
             for (int i = 0; i < j; ++i) {
                 ss += dots[i] * dots[i];
@@ -721,7 +741,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
             H[(size_t)j * m + j] = hj;
             coef[2 * j] = 1.0 / bj;
             coef[2 * j + 1] = hj / bj;
-            const double nn2 = dcgs_update(ctx->red, D, j, V, n, coef.data(), Vj, wf, V + (size_t)(j + 1) * n, s);
+            const double nn2 = dcgs_update(ctx->red, Dc, j, V, nl, coef.data(), Vj, wf, V + (size_t)(j + 1) * nl, s);
             nu = std::sqrt(std::max(nn2, 0.0));
             H[(size_t)(j + 1) * m + j] = nu;   // provisional until the next iteration
             k = j + 1;
@@ -754,7 +774,12 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, int m, Apply apply, Pre
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
-    auto prec = [op](const float2* in, double scale, double* out) { precond_vec(op, in, out, scale); };
+    const GeoLevel& g0 = glv(op, 0);
+    const int* fl = g0.flist.get();
+    const long long nfl = g0.nflist;
+    auto prec = [op, fl, nfl](const float2* in, double scale, double* out) {
+        precond_vec(op, CompactIn{in, fl, nfl}, out, scale);
+    };
     // the learned correction is judged by the FP64 residual: an iteration that
     // contracts by less than 0.8 switches it off for the rest of the solve
     op->learned_active = op->lnet != nullptr;
@@ -765,7 +790,7 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
             fell_back = true;
         }
     };
-    const int it = fgmres(op->ctx, op->vg, n, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
+    const int it = fgmres(op->ctx, op->vg, n, fl, nfl, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
     if (fell_back) ++op->learned_fallbacks;
     op->learned_active = false;
     return it;
@@ -787,9 +812,13 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     const double hmin = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
     const double xscale = norm2(op->ctx, g0.vdom(), x) / hmin;
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
-    auto prec = [op](const float2* in, double scale, double* out) { precond_scal(op, in, out, scale); };
+    const int* cl = g0.clist.get();
+    const long long ncl = g0.nclist;
+    auto prec = [op, cl, ncl](const float2* in, double scale, double* out) {
+        precond_scal(op, CompactIn{in, cl, ncl}, out, scale);
+    };
     double rr = 0.0;
-    const int it = fgmres(op->ctx, op->sg, nc, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
+    const int it = fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
     return it;
 }
@@ -997,6 +1026,15 @@ void setup_operator(dm_operator* op) {
         max_band = std::max(max_band, g.nband);
     }
     op->band_u.alloc((size_t)max_band);
+    {
+        // compact index spaces of the fine level's Krylov bases
+        GeoLevel& g0 = *const_cast<dm_geometry*>(geom)->lv[0];
+        std::lock_guard<std::mutex> lock(const_cast<dm_geometry*>(geom)->mu);
+        if (g0.nflist < 0) {
+            g0.nflist = list_flagged<double>(3ll * g0.g.np, g0.A.get(), g0.flist, s);
+            g0.nclist = list_flagged<unsigned char>((long long)g0.g.np, g0.active.get(), g0.clist, s);
+        }
+    }
     if (op->mg.autotune) {
         for (int l = 0; l + 1 < nl; ++l) {
             switch (op->mg.precision) {

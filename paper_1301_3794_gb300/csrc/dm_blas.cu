@@ -253,21 +253,6 @@ __device__ __forceinline__ float2 ff_norm(float s, float e) {
 }
 __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
 
-// y = split(a x); a = 1 skips the FP64 multiply
-__global__ void k_ff_split(Domain d, double a, const double* __restrict__ x, float2* __restrict__ y) {
-    if (a == 1.0) for_each_entry(d, [&](long long r) { y[r] = ff_bits(x[r]); });
-    else for_each_entry(d, [&](long long r) { y[r] = ff_bits(a * x[r]); });
-}
-// y = a x in the storage type T
-template <typename T>
-__global__ void k_ff_convert(Domain d, typename Compute<T>::type a, const float2* __restrict__ x, T* __restrict__ y) {
-    for_each_entry(d, [&](long long r) {
-        const float2 v = x[r];
-        if constexpr (std::is_same<T, double>::value) y[r] = a * ff_to_double(v);
-        else y[r] = to_store<T>(a * __fadd_rn(v.x, v.y));
-    });
-}
-
 // One pass of delayed classical Gram-Schmidt (DCGS2): against the finished
 // basis Q (j vectors) and the pending vector v, with the new vector w:
 //   partial[b][c] = Q_c . v, [j + c] = Q_c . w (c < j), [2j] = v . v, [2j + 1] = v . w
@@ -319,7 +304,7 @@ __device__ __forceinline__ void dcgs_chunk(const Domain& d, int j, int c0, const
     }
 }
 
-__global__ void k_ff_dcgs_dots(Domain d, int j, const float2* __restrict__ Q, long long ld,
+__global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(Domain d, int j, const float2* __restrict__ Q, long long ld,
                                const float2* __restrict__ v, const float2* __restrict__ w, double* __restrict__ partial,
                                int ldp) {
     __shared__ double red2[kThreads / 32][2];
@@ -377,6 +362,7 @@ __global__ void k_ff_dcgs_update(Domain d, int j, const float2* __restrict__ Q, 
         const float2 vv = v[r], ww = w[r];
         float ts = vv.x, te = vv.y, us = ww.x, ue = ww.y;
         ff_madd(dl.x, dl.y, vv.x, vv.y, us, ue);
+#pragma unroll 4
         for (int c = 0; c < j; ++c) {
             const float2 q = Q[c * ld + r];
             ff_madd(cs[c].x, cs[c].y, q.x, q.y, ts, te);
@@ -397,6 +383,75 @@ __global__ void k_ff_dcgs_update(Domain d, int j, const float2* __restrict__ Q, 
         double a = 0.0;
         for (int k = 0; k < kThreads / 32; ++k) a += red[k];
         partial[blockIdx.x] = a;
+    }
+}
+
+// ---- ordered compaction: the indices r < n with flag(x[r]), ascending ----
+constexpr int kListChunk = 4096;   // entries per block (256 threads x 16)
+template <typename T>
+__device__ __forceinline__ bool list_flag(T v) { return v > T(0); }
+template <typename T>
+__global__ void k_list_count(long long n, const T* __restrict__ x, int* __restrict__ counts) {
+    __shared__ int red[kThreads / 32];
+    const long long b0 = (long long)blockIdx.x * kListChunk;
+    int c = 0;
+    for (int k = threadIdx.x; k < kListChunk; k += blockDim.x) {
+        const long long r = b0 + k;
+        if (r < n && list_flag(x[r])) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        counts[blockIdx.x] = t;
+    }
+}
+// writes the flagged indices of each chunk from offsets[b], in order: the chunk
+// goes in rounds of blockDim entries, each round ranked with a block scan
+template <typename T>
+__global__ void k_list_write(long long n, const T* __restrict__ x, const int* __restrict__ offsets,
+                             int* __restrict__ out) {
+    __shared__ int wsum[kThreads / 32];
+    __shared__ int base;
+    const long long b0 = (long long)blockIdx.x * kListChunk;
+    if (threadIdx.x == 0) base = offsets[blockIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k0 = 0; k0 < kListChunk; k0 += blockDim.x) {
+        const long long r = b0 + k0 + threadIdx.x;
+        const bool f = r < n && list_flag(x[r]);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        int woff = 0, tot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            if (w < wid) woff += wsum[w];
+            tot += wsum[w];
+        }
+        if (f) out[base + woff + before] = (int)r;
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+}
+
+// y[i] = split(a x[list[i]])   (gather into a compact float-float vector)
+__global__ void k_ff_gather(long long n, const int* __restrict__ list, double a, const double* __restrict__ x,
+                            float2* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = ff_bits(a == 1.0 ? x[list[i]] : a * x[list[i]]);
+}
+// y[list[i]] = a x[i] in storage type T   (scatter from a compact float-float vector)
+template <typename T>
+__global__ void k_ff_scatter(long long n, const int* __restrict__ list, typename Compute<T>::type a,
+                             const float2* __restrict__ x, T* __restrict__ y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = x[i];
+        if constexpr (std::is_same<T, double>::value) y[list[i]] = a * ff_to_double(v);
+        else y[list[i]] = to_store<T>(a * __fadd_rn(v.x, v.y));
     }
 }
 
@@ -493,16 +548,42 @@ void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, 
     launch("k_maxpy", k_maxpy, blocks_for(d, k_maxpy), kThreads, 0, s, d, m, V, ld, red.result, x);
 }
 
-void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s) {
-    launch("k_ff_split", k_ff_split, blocks_for(d, k_ff_split), kThreads, 0, s, d, a, x, y);
+template <typename T>
+int list_flagged(long long n, const T* x, DBuf<int>& out, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, (n + kListChunk - 1) / kListChunk);
+    DBuf<int> counts(nb, false), offsets(nb, false);
+    launch("k_list_count", k_list_count<T>, nb, kThreads, 0, s, n, x, counts.get());
+    std::vector<int> h(nb);
+    DM_CUDA(cudaMemcpyAsync(h.data(), counts.get(), sizeof(int) * nb, cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    long long tot = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int c = h[b];
+        h[b] = (int)tot;
+        tot += c;
+    }
+    DM_REQUIRE(tot < (1ll << 31), DM_ERR_INVALID_ARG, "list too long");
+    out.alloc((size_t)std::max<long long>(tot, 1), false);
+    DM_CUDA(cudaMemcpyAsync(offsets.get(), h.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    launch("k_list_write", k_list_write<T>, nb, kThreads, 0, s, n, x, (const int*)offsets.get(), out.get());
+    DM_CUDA(cudaStreamSynchronize(s));
+    return (int)tot;
+}
+template int list_flagged<double>(long long, const double*, DBuf<int>&, cudaStream_t);
+template int list_flagged<unsigned char>(long long, const unsigned char*, DBuf<int>&, cudaStream_t);
+
+void ff_gather(long long n, const int* list, double a, const double* x, float2* y, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
+    launch("k_ff_gather", k_ff_gather, nb, kThreads, 0, s, n, list, a, x, y);
 }
 template <typename T>
-void ff_convert(const Domain& d, double a, const float2* x, T* y, cudaStream_t s) {
-    launch("k_ff_convert", k_ff_convert<T>, blocks_for(d, k_ff_convert<T>), kThreads, 0, s, d, a, x, y);
+void ff_scatter(long long n, const int* list, double a, const float2* x, T* y, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
+    launch("k_ff_scatter", k_ff_scatter<T>, nb, kThreads, 0, s, n, list, (typename Compute<T>::type)a, x, y);
 }
-template void ff_convert<double>(const Domain&, double, const float2*, double*, cudaStream_t);
-template void ff_convert<float>(const Domain&, double, const float2*, float*, cudaStream_t);
-template void ff_convert<__nv_bfloat16>(const Domain&, double, const float2*, __nv_bfloat16*, cudaStream_t);
+template void ff_scatter<double>(long long, const int*, double, const float2*, double*, cudaStream_t);
+template void ff_scatter<float>(long long, const int*, double, const float2*, float*, cudaStream_t);
+template void ff_scatter<__nv_bfloat16>(long long, const int*, double, const float2*, __nv_bfloat16*, cudaStream_t);
 
 void dcgs_dots(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const float2* v, const float2* w,
                double* host_out, cudaStream_t s) {

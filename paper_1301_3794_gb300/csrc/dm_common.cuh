@@ -454,12 +454,15 @@ void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long 
                double* host_out, double* self_out, cudaStream_t s);
 // x -= sum_c h[c] V[c*ld + r] using the h the preceding mdot left on the device (red.result),
 // and returns sum_r w[r] x[r]^2 of the updated x (one pass, one sync)
-// Krylov vectors in float-float (hi + lo FP32 pairs, about 48 significant
-// bits, arithmetic on the FP32 pipes): y = split(a x); y = a x in the storage
-// type T.
-void ff_split(const Domain& d, double a, const double* x, float2* y, cudaStream_t s);
+// Ascending list of the indices r < n with x[r] > 0 (ordered compaction);
+// returns its length.
 template <typename T>
-void ff_convert(const Domain& d, double a, const float2* x, T* y, cudaStream_t s);
+int list_flagged(long long n, const T* x, DBuf<int>& out, cudaStream_t s);
+// Compact float-float vectors over an index list: y[i] = split(a x[list[i]]);
+// y[list[i]] = a x[i] in storage type T (other entries of y untouched).
+void ff_gather(long long n, const int* list, double a, const double* x, float2* y, cudaStream_t s);
+template <typename T>
+void ff_scatter(long long n, const int* list, double a, const float2* x, T* y, cudaStream_t s);
 // Delayed classical Gram-Schmidt (DCGS2) on float-float vectors: Q = the j
 // finished basis vectors, v = the pending vector, w = the new one.
 //   dcgs_dots: out = [Q^T v (j), Q^T w (j), v.v, v.w] (one pass, one sync)

@@ -21,21 +21,30 @@ namespace {
 constexpr int BX = 32, BY = 4, BZ = 2;
 const dim3 kBlock(BX, BY, BZ);
 
-// weight of coarse index J for fine index jf along an in-plane axis with nc coarse cells
-__device__ __forceinline__ float w_inplane(int jf, int J, int nc) {
-    const int c = jf >> 1;
-    const int nb = (jf & 1) ? c + 1 : c - 1;
-    const bool inside = nb >= 0 && nb < nc;
-    float w = 0.f;
-    if (c == J) w += inside ? 0.75f : 1.0f;
-    if (inside && nb == J) w += 0.25f;
-    return w;
-}
-// weight of coarse plane I for fine plane if_ along the face normal
-__device__ __forceinline__ float w_normal(int fi, int I) {
-    if ((fi & 1) == 0) return (fi >> 1) == I ? 1.0f : 0.0f;
-    const int lo = fi >> 1;
-    return (lo == I || lo + 1 == I) ? 0.5f : 0.0f;
+// Fine faces that a coarse face (coarse index c along an axis) gathers, with
+// the weights of P^T along that axis: along the face normal the fine planes
+// 2c-1, 2c, 2c+1 (weights 1/2, 1, 1/2); within the plane the fine cells
+// 2c-1 .. 2c+2 (weights 1/4, 3/4, 3/4, 1/4, the wall rule moving a missing
+// neighbour's 1/4 onto the nearer face).  Slots outside the grid get weight 0
+// and point at ghost positions (zero in every vector).
+__device__ __forceinline__ void restrict_axis(bool normal, int c, int nc, int nf, int idx[4], float w[4]) {
+    idx[0] = 2 * c - 1;
+    idx[1] = 2 * c;
+    idx[2] = 2 * c + 1;
+    idx[3] = 2 * c + 2;
+    if (normal) {
+        w[0] = c >= 1 ? 0.5f : 0.f;
+        w[1] = 1.f;
+        w[2] = 2 * c + 1 <= nf ? 0.5f : 0.f;
+        w[3] = 0.f;
+        idx[3] = 2 * c;
+    } else {
+        const bool lo = c >= 1, hi = c + 1 < nc;
+        w[0] = lo ? 0.25f : 0.f;
+        w[1] = lo ? 0.75f : 1.f;
+        w[2] = hi ? 0.75f : 1.f;
+        w[3] = hi ? 0.25f : 0.f;
+    }
 }
 
 template <typename T, typename TC>
@@ -46,31 +55,29 @@ __global__ void k_face_restrict(Grid3 gf, Grid3 gc, const TC* __restrict__ Ac, c
     block_node(gc, tiles, I, J, K);
     if (I > gc.nx || J > gc.ny || K > gc.nz) return;
     const int q = gc.idx(I, J, K);
-    const int nc[3] = {gc.nx, gc.ny, gc.nz};
-    const int nf[3] = {gf.nx, gf.ny, gf.nz};
-    const int cc[3] = {I, J, K};
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
         const int oq = comp * gc.np + q;
         C acc = C(0);
         if ((C)Ac[oq] > C(0)) {
-            // fine candidates per axis: normal axis 2c-1..2c+1, in-plane 2c-1..2c+2
-            int lo[3], hi[3];
+            int ix[4], iy[4], iz[4];
+            float wx[4], wy[4], wz[4];
+            restrict_axis(comp == 0, I, gc.nx, gf.nx, ix, wx);
+            restrict_axis(comp == 1, J, gc.ny, gf.ny, iy, wy);
+            restrict_axis(comp == 2, K, gc.nz, gf.nz, iz, wz);
+            const T* rc = r + comp * gf.np;
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                if (ax == comp) { lo[ax] = max(2 * cc[ax] - 1, 0); hi[ax] = min(2 * cc[ax] + 1, nf[ax]); }
-                else { lo[ax] = max(2 * cc[ax] - 1, 0); hi[ax] = min(2 * cc[ax] + 2, nf[ax] - 1); }
-            }
-            for (int fk = lo[2]; fk <= hi[2]; ++fk) {
-                const float wk = comp == 2 ? w_normal(fk, K) : w_inplane(fk, K, nc[2]);
-                if (wk == 0.f) continue;
-                for (int fj = lo[1]; fj <= hi[1]; ++fj) {
-                    const float wj = comp == 1 ? w_normal(fj, J) : w_inplane(fj, J, nc[1]);
-                    if (wj == 0.f) continue;
-                    for (int fi = lo[0]; fi <= hi[0]; ++fi) {
-                        const float wi = comp == 0 ? w_normal(fi, I) : w_inplane(fi, I, nc[0]);
-                        if (wi == 0.f) continue;
-                        acc += C(wk * wj * wi) * (C)to_c(r[comp * gf.np + gf.idx(fi, fj, fk)]);
+            for (int a = 0; a < 4; ++a) {
+                if (comp == 2 && a == 3) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if (comp == 1 && b == 3) continue;
+                    const float wab = wz[a] * wy[b];
+                    const T* row = rc + gf.idx(0, iy[b], iz[a]);
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        if (comp == 0 && d == 3) continue;
+                        acc += C(wab * wx[d]) * (C)to_c(row[ix[d]]);
                     }
                 }
             }
