@@ -92,6 +92,11 @@ def config_of(args, w, extra=None):
 # distributed helpers (replicas; host-side logic shared with the CPU tests)
 # ---------------------------------------------------------------------------
 
+def progress(msg):
+    """One line of progress on stderr (the JSON result stays alone on stdout)."""
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -443,7 +448,9 @@ def run_batch(args):
         return sum(rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0 for _, rep, st in out), out
 
     for _ in range(args.warmup):
+        tw = time.perf_counter()
         step()
+        progress(f"batch warm-up step {time.perf_counter() - tw:.1f} s")
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
@@ -494,8 +501,9 @@ def run_batch(args):
 
 def run_ninecell(args):
     """The learned-smoother configuration: the synthetic 9-cell cavity on a
-    96 x 96 x 1152 grid, 20 modes nearest sigma (below the accelerating
-    passband), FP32 V-cycle.  The network is trained on the GPU first (timed
+    96 x 96 x 1152 grid (``--grid`` scales it), the 20 lowest modes (the
+    accelerating passband and the next one) from a shift of the order of the
+    smallest nonzero eigenvalue, FP32 V-cycle.  The network is trained on the GPU first (timed
     separately); each step then solves with the learned correction, and one
     step without it is timed for comparison."""
     import numpy as np
@@ -523,6 +531,7 @@ def run_ninecell(args):
     hist = net.train(op, runs=2, epochs=6, lr=2e-3, seed=7)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    progress(f"ninecell training {train_s:.1f} s, loss {hist[0]:.4g} -> {hist[-1]:.4g}")
 
     def solve(learned):
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -534,6 +543,8 @@ def run_ninecell(args):
         torch.cuda.synchronize()
         secs = ev0.elapsed_time(ev1) * 1e-3
         ok = rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0
+        progress(f"ninecell solve (learned={learned}) {secs:.1f} s, status {st}, {ok} converged, "
+                 f"{rep['outer_iters']} outer / {rep['inner_iters']} inner iterations")
         return ok, secs, rep, k2
 
     for _ in range(args.warmup):

@@ -34,6 +34,9 @@ __all__ = [
 ]
 
 SEED_BASE = 1301
+# (kR)^2 of the lowest (TM_1) mode of a unit PEC sphere, kR = 2.743707: only
+# used to place the batch recipe's shifts below each cavity's lowest mode
+TM1_SPHERE_K2 = 2.743707 ** 2
 
 
 @dataclasses.dataclass(frozen=True)
@@ -238,8 +241,13 @@ def nine_cell_workload(nxy=96, nz=1152, seed=None, sigma=None, nev=20,
         scale = 1.0 + 0.01 * np.random.default_rng(seed).standard_normal(9)
     phi = nine_cell_phi(g, cell_length, r_equator, r_iris, equator_scale=scale)
     if sigma is None:
-        # below the accelerating passband: (2 pi f / c)^2 with f ~ 1.2 GHz
-        sigma = (2.0 * math.pi * 1.2e9 / 299792458.0) ** 2
+        # A shift of the order of the operator's smallest nonzero eigenvalue
+        # (Sec. 4.1), kept below it: a quarter of (pi / L)^2, L the length of
+        # the structure, the estimate of its lowest longitudinal grad-div mode.
+        # K - sigma A is then positive definite.  A shift just below the
+        # accelerating passband lies deep inside the spectrum, where the
+        # multigrid-preconditioned inner solve stalls.
+        sigma = 0.25 * (math.pi / (z1 - z0)) ** 2
     return Workload(f"ninecell{nxy}x{nxy}x{nz}", g, phi, sigma, nev, -1 if seed is None else seed,
                     {"cell_length": cell_length, "r_equator": r_equator, "r_iris": r_iris,
                      "equator_scale": None if scale is None else tuple(scale)})
@@ -247,7 +255,14 @@ def nine_cell_workload(nxy=96, nz=1152, seed=None, sigma=None, nev=20,
 
 def batch_workloads(count=48, seed=SEED_BASE + 4, sizes=(32, 48, 64, 80, 96)):
     """Uneven batch of cavities: spheres and ellipsoids with p = 1/2, grid size
-    drawn from ``sizes``, 1-4 sorted shifts U[5, 30] and 4-8 modes each.
+    drawn from ``sizes``, 1-4 sorted shifts and 4-8 modes each.
+
+    The shifts sit in the low end of each cavity's spectrum, as the paper's
+    shift-and-invert discussion (Sec. 4.1) asks: sigma = u * 7.5279 / r^2 with
+    u ~ U[0.3, 0.9] and r the largest semi-axis (the radius of a sphere), i.e.
+    below the estimated lowest electromagnetic mode (7.5279 = (kR)^2 of the
+    TM_1 sphere mode).  Shifts deep inside the spectrum make K - sigma A too
+    indefinite for a multigrid-preconditioned inner solve.
     Returns a list of (Workload, shifts, nev)."""
     rng = np.random.default_rng(seed)
     out = []
@@ -255,13 +270,16 @@ def batch_workloads(count=48, seed=SEED_BASE + 4, sizes=(32, 48, 64, 80, 96)):
         n = int(rng.choice(sizes))
         kind = "sphere" if rng.random() < 0.5 else "ellipsoid"
         nshift = int(rng.integers(1, 5))
-        shifts = np.sort(rng.uniform(5.0, 30.0, size=nshift))
+        u = np.sort(rng.uniform(0.3, 0.9, size=nshift))
         nev = int(rng.integers(4, 9))
         sub = int(rng.integers(0, 2 ** 31 - 1))
         if kind == "sphere":
+            shifts = u * TM1_SPHERE_K2
             w = sphere_workload(n=n, sigma=float(shifts[0]), nev=nev, offset_seed=sub)
         else:
-            w = ellipsoid_workload(n=n, seed=sub, sigma=float(shifts[0]), nev=nev)
+            w = ellipsoid_workload(n=n, seed=sub, sigma=5.0, nev=nev)
+            shifts = u * TM1_SPHERE_K2 / max(w.meta["semi_axes"]) ** 2
+            w.sigma = float(shifts[0])
         w.name = f"{kind}{n}_{c}"
         out.append((w, [float(s) for s in shifts], nev))
     return out
