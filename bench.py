@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--nev", type=int, default=None)
     ap.add_argument("--sigma", type=float, default=5.0)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--count", type=int, default=0, help="batch: solve only the first COUNT cavities")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
@@ -243,6 +244,15 @@ APPLY_FLOPS_PER_FACE = 22.0
 FP64_PEAK_TFLOPS = 1.204      # FMA probe on this machine's GB300
 
 
+# DRAM bytes (read + write) per launch of the fine-level stencil, from an ncu
+# capture of that kernel on the same cavity: (trace name, level-0 tile shape,
+# workload, grid) -> bytes.  profiles/stencil_jacobi_sphere128.md has the
+# capture and its command; a shape without a capture reports null.
+PROFILED_TRAFFIC = {
+    ("vec_stencil_f32_jacobi_L0", 0, "sphere", 128): 90_759_424 + 5_890_304,
+}
+
+
 def roofline(stats, open_faces, hbm_peak, peak_kind, precision="f32", traffic=None):
     """Fine-level V-cycle smoothing stencil (the metric's V-cycle kernel):
     algorithmic bytes per launch (open faces only) over its event-timed mean
@@ -359,8 +369,14 @@ def run_native(args):
     open_faces = geom_open = None
     g0info = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi_dev, g.origin)
     open_faces = g0info.level_info(0)["open"]
+    # tile shapes the autotuner chose for this cavity's levels (cached in the context, so no re-timing)
+    op_info = dm.Operator(ctx, g0info, args.sigma, precision=args.precision)
+    shapes = [op_info.stencil_shape(l) for l in range(op_info.num_levels - 1)]
+    op_info.close()
     g0info.close()
-    roof = roofline(stats, open_faces, hbm, kind, args.precision)
+    traffic = PROFILED_TRAFFIC.get((f"vec_stencil_{args.precision}_jacobi_L0", shapes[0] if shapes else -1,
+                                    args.workload, args.grid))
+    roof = roofline(stats, open_faces, hbm, kind, args.precision, traffic=traffic)
     roof64 = roofline_fp64_apply(stats, open_faces)
     # ---- plain FP64 multigrid on the same cavity ----
     plain = None
@@ -394,7 +410,7 @@ def run_native(args):
                    "mg_levels": reps[-1]["mg_levels"], "mg_complexity": round(reps[-1]["mg_complexity"], 3),
                    "rho_max": reps[-1]["rho_max"], "delta_max": reps[-1]["delta_max"],
                    "k2": [round(float(v), 10) for v in k2],
-                   "inner_rate": None},
+                   "inner_rate": None, "stencil_shapes": shapes},
         "plain_f64": plain,
         "kernels_top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
@@ -424,7 +440,7 @@ def run_batch(args):
     __graft_entry__.build()
     import paper_1301_3794_gb300 as dm
 
-    items = W.batch_workloads(48)
+    items = W.batch_workloads(48)[:args.count] if args.count else W.batch_workloads(48)
     stream = torch.cuda.Stream()
     ctx = dm.Context(local, stream=stream.cuda_stream)
     phis_host = [np.ascontiguousarray(w.phi.ravel()) for w, _, _ in items]
@@ -449,8 +465,12 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         tw = time.perf_counter()
-        step()
+        _, out_w = step()
         progress(f"batch warm-up step {time.perf_counter() - tw:.1f} s")
+        for (w, _, _), (_, rep, st) in zip([(w, sg, nv) for w, sh, nv in items for sg in sh], out_w):
+            progress(f"  {w.name}: status {st}, {rep['n_converged']} converged, setup {rep['setup_seconds']:.2f} s, "
+                     f"solve {rep['solve_seconds']:.2f} s, {rep['outer_iters']} outer / {rep['inner_iters']} inner / "
+                     f"{rep['proj_iters']} projection iterations")
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()

@@ -73,6 +73,8 @@ typedef struct dm_mg_params {
     int precision;         /* dm_precision of the V-cycle (DM_PREC_F64) */
     int autotune;          /* 1: time the stencil tile shapes per level at setup and keep the fastest;
                               results are cached in the context by level size and precision (1) */
+    int stencil_shape;     /* -1: the autotuner's choice (shape 0 when autotune = 0); 0..5: use this
+                              tile shape (see dm_operator_stencil_shape) on every level (-1) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
@@ -162,7 +164,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
                              const dm_mg_params* mg, dm_operator** out);
 void dm_operator_destroy(dm_operator* op);
 int dm_operator_num_levels(const dm_operator* op);
-/* Tile shape the vector stencil of `level` uses: 0 = 32x4x2, 1 = 32x2x4, 2 = 32x8x1 nodes
+/* Tile shape the vector stencil of `level` uses: 0 = 32x4x2, 1 = 32x2x4, 2 = 32x8x1 nodes, one
+ * node per thread; 3 = 32x8x8, 4 = 32x4x8, 5 = 32x8x4 nodes, a 32 x SY block marching along z
  * (chosen by the autotuner), -1 on a bad argument.  No counterpart in the paper. */
 int dm_operator_stencil_shape(const dm_operator* op, int level);
 /* Jacobi weight of `level` for the vector (scalar = 0) or the scalar (scalar = 1) cycle. */

@@ -196,7 +196,7 @@ class Geometry:
 
 
 def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
-              autotune=1):
+              autotune=1, force_shape=-1):
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -206,6 +206,7 @@ def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power
     p.power_iters = power_iters
     p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     p.autotune = int(autotune)
+    p.stencil_shape = int(force_shape)
     return p
 
 

@@ -941,6 +941,23 @@ void autotune_level(dm_operator* op, int l) {
     zero(op->wk[l].r.get(), op->wk[l].r.n, s);
 }
 
+// Use tile shape `sh` for the vector stencil of level l.
+void set_level_shape(dm_operator* op, int l, int sh) {
+    GeoLevel& g = *const_cast<dm_geometry*>(op->geom)->lv[l];
+    OpLevel& o = op->ol[l];
+    o.shape = sh;
+    o.nstiles = 0;
+    o.stiles = DBuf<int>();
+    if (sh == 0) return;
+    int sy, sz;
+    stencil_shape_dims(sh, sy, sz);
+    const int nt = ((g.g.nx + TX) / TX) * ((g.g.ny + sy) / sy) * ((g.g.nz + sz) / sz);
+    DBuf<int> flags(nt), cnt(1);
+    o.stiles.alloc(nt);
+    o.nstiles = geom_tiles_shape(g.g, sy, sz, g.A.get(), g.active.get(), o.stiles.get(), flags.get(), cnt.get(),
+                                 op->ctx->stream);
+}
+
 void setup_operator(dm_operator* op) {
     cudaStream_t s = op->ctx->stream;
     dm_geometry* geom = const_cast<dm_geometry*>(op->geom);
@@ -1035,7 +1052,9 @@ void setup_operator(dm_operator* op) {
             g0.nclist = list_flagged<unsigned char>((long long)g0.g.np, g0.active.get(), g0.clist, s);
         }
     }
-    if (op->mg.autotune) {
+    if (op->mg.stencil_shape >= 0) {
+        for (int l = 0; l + 1 < nl; ++l) set_level_shape(op, l, op->mg.stencil_shape);
+    } else if (op->mg.autotune) {
         for (int l = 0; l + 1 < nl; ++l) {
             switch (op->mg.precision) {
                 case DM_PREC_F64: autotune_level<double, double>(op, l); break;
@@ -1401,6 +1420,7 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->power_iters = 30;
     p->precision = DM_PREC_F64;
     p->autotune = 1;
+    p->stencil_shape = -1;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1420,6 +1440,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         DM_REQUIRE(op->mg.band_brick >= 1, DM_ERR_INVALID_ARG, "band_brick must be >= 1");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
+        DM_REQUIRE(op->mg.stencil_shape >= -1 && op->mg.stencil_shape < kStencilShapes, DM_ERR_INVALID_ARG,
+                   "stencil_shape out of range");
         const char* ng = std::getenv("DMEIG_NO_GRAPHS");
         op->graphs = !(ng && ng[0] && ng[0] != '0');
         setup_operator(op.get());

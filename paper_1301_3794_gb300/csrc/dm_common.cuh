@@ -296,10 +296,11 @@ struct VecOp {
     int nstiles = 0;
     int shape = 0;
 };
-// tile shapes of the tiled vector stencil: TX x SY x SZ with (SY, SZ) = (4,2), (2,4), (8,1)
-constexpr int kStencilShapes = 3;
+// tile shapes of the vector stencil: TX x SY x SZ with (SY, SZ) = (4,2), (2,4), (8,1) (one node per
+// thread) and (8,8), (4,8), (8,4) (z-marching: a TX x SY block walks SZ planes)
+constexpr int kStencilShapes = 6;
 inline void stencil_shape_dims(int shape, int& sy, int& sz) {
-    static const int d[kStencilShapes][2] = {{4, 2}, {2, 4}, {8, 1}};
+    static const int d[kStencilShapes][2] = {{4, 2}, {2, 4}, {8, 1}, {8, 8}, {4, 8}, {8, 4}};
     sy = d[shape][0];
     sz = d[shape][1];
 }

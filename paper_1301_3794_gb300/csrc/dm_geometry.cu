@@ -480,11 +480,13 @@ __global__ void k_tile_flags_shape(Grid3 g, int sy, int sz, const double* __rest
     const int t = blockIdx.x;
     const int nti = (g.nx + TX) / TX, ntj = (g.ny + sy) / sy;
     const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * sy, k0 = (t / (nti * ntj)) * sz;
-    const int i = i0 + (threadIdx.x & (TX - 1)), j = j0 + (threadIdx.x / TX) % sy, k = k0 + threadIdx.x / (TX * sy);
     bool any = false;
-    if (i <= g.nx && j <= g.ny && k <= g.nz) {
-        const int p = g.idx(i, j, k);
-        any = A[p] > 0.0 || A[g.np + p] > 0.0 || A[2 * g.np + p] > 0.0 || active[p] != 0;
+    for (int e = threadIdx.x; e < TX * sy * sz; e += blockDim.x) {
+        const int i = i0 + (e & (TX - 1)), j = j0 + (e / TX) % sy, k = k0 + e / (TX * sy);
+        if (i <= g.nx && j <= g.ny && k <= g.nz) {
+            const int p = g.idx(i, j, k);
+            any |= A[p] > 0.0 || A[g.np + p] > 0.0 || A[2 * g.np + p] > 0.0 || active[p] != 0;
+        }
     }
     const int v = __syncthreads_or(any);
     if (threadIdx.x == 0) flags[t] = v ? 1 : 0;
@@ -493,7 +495,7 @@ __global__ void k_tile_flags_shape(Grid3 g, int sy, int sz, const double* __rest
 int geom_tiles_shape(const Grid3& g, int sy, int sz, const double* A, const unsigned char* active, int* tiles,
                      int* flags, int* d_count, cudaStream_t s) {
     const int nt = ((g.nx + TX) / TX) * ((g.ny + sy) / sy) * ((g.nz + sz) / sz);
-    launch("k_tile_flags", k_tile_flags_shape, nt, TX * sy * sz, 0, s, g, sy, sz, A, active, flags);
+    launch("k_tile_flags", k_tile_flags_shape, nt, 256, 0, s, g, sy, sz, A, active, flags);
     launch("k_compact", k_compact, 1, 1024, 0, s, flags, nt, tiles, d_count);
     return read_count(d_count, s);
 }

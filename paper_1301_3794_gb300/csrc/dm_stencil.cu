@@ -248,6 +248,222 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
     }
 }
 
+// z-marching form of the same operator: a block of TX x SY threads owns a
+// TX x SY column of nodes and walks up to KZ planes along z.  Two planes of the
+// inputs (b and A, each with a one-node ring around the column) are staged in
+// shared memory; for each plane the block forms the cell divergences and z-edge
+// curls of that plane and the x/y-edge curls of the plane above (kept for two
+// planes), then every thread forms its node's three face outputs.  Each thread
+// loads and computes the entries of its own node, and the ring and the one-node
+// borders of the divergence and curl tiles are spread one entry per thread over
+// the block, so index arithmetic is done once per block rather than per entry.
+// Every input value is read from global memory about once per block (the ring
+// and the one plane below and above the column are the only re-reads), and each
+// curl and divergence is computed once.  The global loads of the next plane are
+// issued into registers before the current plane's outputs are formed, so their
+// latency overlaps that work.  Entries outside [-1, n+1] along x or y are taken
+// as zero; inside that box the padded layout already holds zeros at every
+// position that is not an element of the grid.
+template <typename T, typename TC, int MODE, int SY, int KZ>
+__global__ void __launch_bounds__(TX * SY, (std::is_same<T, double>::value ? 512 : 768) / (TX * SY)) k_vec_stencil_march(
+    Grid3 g, const TC* __restrict__ A, const TC* __restrict__ L, const TC* __restrict__ invV,
+    const TC* __restrict__ invD, typename Compute<T>::type sigma, const T* __restrict__ x, const T* __restrict__ f,
+    T* __restrict__ y, typename Compute<T>::type omega, const int* __restrict__ tiles) {
+    using C = typename Compute<T>::type;
+    constexpr int RW = TX + 2, RH = SY + 2, RP = RW * RH;   // ring plane: i0-1 .. i0+TX, j0-1 .. j0+SY
+    constexpr int NT = TX * SY;
+    constexpr int W1 = TX + 1;
+    constexpr int NRH = 2 * TX + 2 * RH;   // ring border entries
+    constexpr int NPH = W1 + SY;           // psi border: row j0-1 (i0-1 .. i0+TX-1), column i0-1 (j0 .. j0+SY-1)
+    constexpr int NZH = W1 + SY;           // z-edge border: row j0+SY (i0 .. i0+TX), column i0+TX (j0 .. j0+SY-1)
+    constexpr int NXH = TX;                // x-edge border: row j0+SY (i0 .. i0+TX-1)
+    constexpr int NYH = SY;                // y-edge border: column i0+TX (j0 .. j0+SY-1)
+    static_assert(NRH <= NT && NPH + NZH + NXH + NYH <= NT, "one border entry per thread");
+    __shared__ C s_ring[2][6 * RP];        // b_x, b_y, b_z, A_x, A_y, A_z (blocks of RP) of two planes
+    __shared__ C s_ex[2][(SY + 1) * TX];   // x-edges i0 .. i0+TX-1, j0 .. j0+SY (two planes)
+    __shared__ C s_ey[2][SY * W1];         // y-edges i0 .. i0+TX,   j0 .. j0+SY-1 (two planes)
+    __shared__ C s_ez[(SY + 1) * W1];      // z-edges i0 .. i0+TX,   j0 .. j0+SY
+    __shared__ C s_psi[(SY + 1) * W1];     // cells   i0-1 .. i0+TX-1, j0-1 .. j0+SY-1
+    const int t = tiles[blockIdx.x];
+    const int nti = (g.nx + TX) / TX, ntj = (g.ny + SY) / SY;
+    const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * SY, k0 = (t / (nti * ntj)) * KZ;
+    const int kend = min(k0 + KZ - 1, g.nz);
+    const int N = g.np, Z = g.sxy;
+    const int ilim = g.nx + 1, jlim = g.ny + 1;
+    const C rdx = inv_h<C>(g, 0), rdy = inv_h<C>(g, 1), rdz = inv_h<C>(g, 2);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + TX * ty;
+    // this thread's node
+    const int i = i0 + tx, j = j0 + ty;
+    const bool inb = i <= ilim && j <= jlim;          // inside the padded box
+    const bool own = i <= g.nx && j <= g.ny;          // an output node
+    const int p0 = g.idx(i, j, 0);
+    const int rown = (ty + 1) * RW + tx + 1;          // ring position of the node
+    // ring border entry of this thread
+    int hli = 0, hlj = 0;
+    if (tid < TX) { hli = tid + 1; hlj = 0; }
+    else if (tid < 2 * TX) { hli = tid - TX + 1; hlj = RH - 1; }
+    else if (tid < 2 * TX + RH) { hli = 0; hlj = tid - 2 * TX; }
+    else { hli = RW - 1; hlj = tid - 2 * TX - RH; }
+    const bool hval = tid < NRH && i0 - 1 + hli <= ilim && j0 - 1 + hlj <= jlim;
+    const int hp0 = hval ? g.idx(i0 - 1 + hli, j0 - 1 + hlj, 0) : 0;
+    const int rh = hlj * RW + hli;
+    // border entry of the divergence / curl tiles: role 0 psi, 1 z-edge, 2 x-edge, 3 y-edge, -1 none
+    int role = -1, di = 0, dj = 0, dsm = 0;
+    if (tid < NPH) {
+        role = 0;
+        if (tid < W1) { di = i0 - 1 + tid; dj = j0 - 1; dsm = tid; }
+        else { di = i0 - 1; dj = j0 + (tid - W1); dsm = (tid - W1 + 1) * W1; }
+    } else if (tid < NPH + NZH) {
+        const int e = tid - NPH;
+        role = 1;
+        if (e < W1) { di = i0 + e; dj = j0 + SY; dsm = SY * W1 + e; }
+        else { di = i0 + TX; dj = j0 + (e - W1); dsm = (e - W1) * W1 + TX; }
+    } else if (tid < NPH + NZH + NXH) {
+        const int e = tid - NPH - NZH;
+        role = 2; di = i0 + e; dj = j0 + SY; dsm = SY * TX + e;
+    } else if (tid < NPH + NZH + NXH + NYH) {
+        const int e = tid - NPH - NZH - NXH;
+        role = 3; di = i0 + TX; dj = j0 + e; dsm = e * W1 + TX;
+    }
+    const bool dval = role >= 0 && di <= ilim && dj <= jlim;
+    const int dp0 = dval ? g.idx(di, dj, 0) : 0;
+    // ring entry of array a (0..2: b, 3..5: A) at node (ii, jj) of the plane in `slot`
+    auto R = [&](int slot, int a, int ii, int jj) -> C { return s_ring[slot][a * RP + (jj - j0 + 1) * RW + (ii - i0 + 1)]; };
+    // prefetch registers: ring entries of the node and of the border entry, coefficients, f and 1/D
+    C pn[6], ph[6], cv = C(0), cz = C(0), cx = C(0), cy = C(0), hc = C(0), he = C(0), pf[3], pd[3];
+    auto fetch_ring = [&](int k) {
+        const int pn_ = p0 + k * Z, ph_ = hp0 + k * Z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pn[c] = inb ? (C)to_c(x[c * N + pn_]) : C(0);
+            pn[3 + c] = inb ? (C)A[c * N + pn_] : C(0);
+            ph[c] = hval ? (C)to_c(x[c * N + ph_]) : C(0);
+            ph[3 + c] = hval ? (C)A[c * N + ph_] : C(0);
+        }
+    };
+    auto store_ring = [&](int slot) {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            s_ring[slot][a * RP + rown] = pn[a];
+            if (tid < NRH) s_ring[slot][a * RP + rh] = ph[a];
+        }
+    };
+    // 1/V and L_z at plane k: the node's, and the border entry's for roles 0 and 1
+    auto fetch_cells = [&](int k) {
+        cv = inb ? (C)invV[p0 + k * Z] : C(0);
+        cz = inb ? (C)L[2 * N + p0 + k * Z] : C(0);
+        hc = C(0);
+        if (dval && role == 0) hc = (C)invV[dp0 + k * Z];
+        if (dval && role == 1) hc = (C)L[2 * N + dp0 + k * Z];
+    };
+    // L_x and L_y at plane kp: the node's, and the border entry's for roles 2 and 3
+    auto fetch_edges = [&](int kp) {
+        cx = inb ? (C)L[p0 + kp * Z] : C(0);
+        cy = inb ? (C)L[N + p0 + kp * Z] : C(0);
+        he = C(0);
+        if (dval && role == 2) he = (C)L[dp0 + kp * Z];
+        if (dval && role == 3) he = (C)L[N + dp0 + kp * Z];
+    };
+    auto fetch_out = [&](int k) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pf[c] = C(0);
+            pd[c] = C(0);
+            if (MODE != ST_APPLY && own) {
+                pf[c] = (C)to_c(f[c * N + p0 + k * Z]);
+                if (MODE == ST_JACOBI) pd[c] = (C)invD[c * N + p0 + k * Z];
+            }
+        }
+    };
+    // L-weighted curls and the Dey--Mittra divergence at (ii, jj) from the ring
+    auto ex_at = [&](int ii, int jj, int sm, int sp, C lx) -> C {
+        return lx * ((R(sm, 1, ii, jj) - R(sp, 1, ii, jj)) * rdz + (R(sp, 2, ii, jj) - R(sp, 2, ii, jj - 1)) * rdy);
+    };
+    auto ey_at = [&](int ii, int jj, int sm, int sp, C ly) -> C {
+        return ly * ((R(sp, 0, ii, jj) - R(sm, 0, ii, jj)) * rdz + (R(sp, 2, ii - 1, jj) - R(sp, 2, ii, jj)) * rdx);
+    };
+    auto ez_at = [&](int ii, int jj, int s0, C lz) -> C {
+        return lz * ((R(s0, 0, ii, jj - 1) - R(s0, 0, ii, jj)) * rdy + (R(s0, 1, ii, jj) - R(s0, 1, ii - 1, jj)) * rdx);
+    };
+    auto psi_at = [&](int ii, int jj, int s0, int s1, C iv) -> C {
+        const C fx = R(s0, 3, ii + 1, jj) * R(s0, 0, ii + 1, jj) - R(s0, 3, ii, jj) * R(s0, 0, ii, jj);
+        const C fy = R(s0, 4, ii, jj + 1) * R(s0, 1, ii, jj + 1) - R(s0, 4, ii, jj) * R(s0, 1, ii, jj);
+        const C fz = R(s1, 5, ii, jj) * R(s1, 2, ii, jj) - R(s0, 5, ii, jj) * R(s0, 2, ii, jj);
+        return iv * (fx * rdx + fy * rdy + fz * rdz);
+    };
+    // x- and y-edge curls of plane kp (ring slots: sm = plane kp-1, sp = plane kp) into edge slot es
+    auto edges_xy = [&](int sm, int sp, int es) {
+        s_ex[es][ty * TX + tx] = inb ? ex_at(i, j, sm, sp, cx) : C(0);
+        s_ey[es][ty * W1 + tx] = inb ? ey_at(i, j, sm, sp, cy) : C(0);
+        if (role == 2) s_ex[es][dsm] = dval ? ex_at(di, dj, sm, sp, he) : C(0);
+        if (role == 3) s_ey[es][dsm] = dval ? ey_at(di, dj, sm, sp, he) : C(0);
+    };
+    // cell divergences and z-edge curls of plane k (ring slots: s0 = plane k, s1 = plane k+1)
+    auto psi_ez = [&](int s0, int s1) {
+        s_psi[(ty + 1) * W1 + tx + 1] = inb ? psi_at(i, j, s0, s1, cv) : C(0);
+        s_ez[ty * W1 + tx] = inb ? ez_at(i, j, s0, cz) : C(0);
+        if (role == 0) s_psi[dsm] = dval ? psi_at(di, dj, s0, s1, hc) : C(0);
+        if (role == 1) s_ez[dsm] = dval ? ez_at(di, dj, s0, hc) : C(0);
+    };
+    // prologue: planes k0-1 (ring slot 0) and k0 (slot 1); edges of plane k0 (edge slot 0);
+    // psi(k0-1) at this thread's node; then the loads of the first iteration
+    fetch_ring(k0 - 1);
+    store_ring(0);
+    fetch_ring(k0);
+    store_ring(1);
+    fetch_edges(k0);
+    __syncthreads();
+    edges_xy(0, 1, 0);
+    C psi_below = own ? psi_at(i, j, 0, 1, (C)invV[p0 + (k0 - 1) * Z]) : C(0);
+    fetch_ring(k0 + 1);
+    fetch_cells(k0);
+    fetch_edges(k0 + 1);
+    for (int k = k0; k <= kend; ++k) {
+        const int s0 = (k - k0 + 1) & 1, s1 = s0 ^ 1;   // ring slots of planes k and k+1
+        const int e0 = (k - k0) & 1, e1 = e0 ^ 1;        // edge slots of planes k and k+1
+        fetch_out(k);     // f and 1/D of this plane: in flight through the barriers below
+        __syncthreads();
+        store_ring(s1);
+        __syncthreads();
+        psi_ez(s0, s1);
+        edges_xy(s0, s1, e1);
+        if (k < kend) {   // loads of the next iteration, in flight while this plane's outputs are formed
+            fetch_ring(k + 2);
+            fetch_cells(k + 1);
+            fetch_edges(k + 2);
+        }
+        __syncthreads();
+        if (own) {
+            const C ps0 = s_psi[(ty + 1) * W1 + tx + 1];
+            const C ez0 = s_ez[ty * W1 + tx];
+            const C ax = s_ring[s0][3 * RP + rown], ay = s_ring[s0][4 * RP + rown], az = s_ring[s0][5 * RP + rown];
+            const C bx = s_ring[s0][rown], by = s_ring[s0][RP + rown], bz = s_ring[s0][2 * RP + rown];
+            C out[3];
+            out[0] = (s_ez[(ty + 1) * W1 + tx] - ez0) * rdy - (s_ey[e1][ty * W1 + tx] - s_ey[e0][ty * W1 + tx]) * rdz +
+                     ax * ((s_psi[(ty + 1) * W1 + tx] - ps0) * rdx - sigma * bx);
+            out[1] = (s_ex[e1][ty * TX + tx] - s_ex[e0][ty * TX + tx]) * rdz - (s_ez[ty * W1 + tx + 1] - ez0) * rdx +
+                     ay * ((s_psi[ty * W1 + tx + 1] - ps0) * rdy - sigma * by);
+            out[2] = (s_ey[e0][ty * W1 + tx + 1] - s_ey[e0][ty * W1 + tx]) * rdx -
+                     (s_ex[e0][(ty + 1) * TX + tx] - s_ex[e0][ty * TX + tx]) * rdy +
+                     az * ((psi_below - ps0) * rdz - sigma * bz);
+            const C av[3] = {ax, ay, az}, bv[3] = {bx, by, bz};
+            const int p = p0 + k * Z;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                C v = av[c] > C(0) ? out[c] : C(0);
+                if (MODE == ST_RESID) {
+                    v = pf[c] - v;
+                } else if (MODE == ST_JACOBI) {
+                    v = bv[c] + omega * pd[c] * (pf[c] - v);
+                }
+                y[c * N + p] = to_store<T>(v);
+            }
+            psi_below = ps0;
+        }
+    }
+}
+
 template <typename T, typename TC>
 __global__ void k_jacobi_zero(Domain d, const TC* __restrict__ invD, const T* __restrict__ f, T* __restrict__ y,
                               typename Compute<T>::type om) {
@@ -426,8 +642,8 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         const int nt = op.stiles ? op.nstiles : op.ntiles;
         if (nt <= 0) return;
         const char* nm = stencil_name("vec_stencil", prec_index<T>(), mode, op.level == 0);
-        // tile shape: 0 = 32x4x2 (the level's active tiles), 1 = 32x2x4, 2 = 32x8x1 (op.tiles is the
-        // active-tile list of that shape)
+        // tile shape: 0 = 32x4x2 (the level's active tiles), 1 = 32x2x4, 2 = 32x8x1; 3 = 32x8x8,
+        // 4 = 32x4x8, 5 = 32x8x4 by the z-marching kernel (op.stiles is the active-tile list of that shape)
         switch (op.shape * 3 + mode) {
 #define DM_TILED(SH, MD, SY, SZ)                                                                              \
     case SH * 3 + MD:                                                                                         \
@@ -438,6 +654,15 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
             DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4)
             DM_TILED(2, ST_APPLY, 8, 1) DM_TILED(2, ST_RESID, 8, 1) DM_TILED(2, ST_JACOBI, 8, 1)
 #undef DM_TILED
+#define DM_MARCH(SH, MD, SY, KZ)                                                                                \
+    case SH * 3 + MD:                                                                                         \
+        launch(nm, k_vec_stencil_march<T, TC, MD, SY, KZ>, nt, dim3(TX, SY, 1), 0, s, g, op.A, op.L, op.invV, \
+               op.invD, op.sigma, x, f, y, omega, tl);                                                        \
+        break;
+            DM_MARCH(3, ST_APPLY, 8, 8) DM_MARCH(3, ST_RESID, 8, 8) DM_MARCH(3, ST_JACOBI, 8, 8)
+            DM_MARCH(4, ST_APPLY, 4, 8) DM_MARCH(4, ST_RESID, 4, 8) DM_MARCH(4, ST_JACOBI, 4, 8)
+            DM_MARCH(5, ST_APPLY, 8, 4) DM_MARCH(5, ST_RESID, 8, 4) DM_MARCH(5, ST_JACOBI, 8, 4)
+#undef DM_MARCH
             default: throw Error(DM_ERR_INVALID_ARG, "unknown stencil tile shape");
         }
         return;

@@ -47,11 +47,31 @@ def test_autotuned_shape_does_not_change_results(dm, ctx):
     tuned = dm.Operator(ctx, g, w.sigma, precision="f32", autotune=1)
     plain = dm.Operator(ctx, g, w.sigma, precision="f32", autotune=0)
     for l in range(tuned.num_levels - 1):
-        assert tuned.stencil_shape(l) in (0, 1, 2)
+        assert tuned.stencil_shape(l) in range(6)
         assert plain.stencil_shape(l) == 0
     _, A, _ = g.fractions(0)
     x = np.random.default_rng(0).standard_normal(A.size) * (A > 0)
     for l in range(tuned.num_levels - 1):
         tuned.set_omega(l, plain.omega(l))
-    assert np.array_equal(tuned.apply(x), plain.apply(x))
-    assert np.array_equal(tuned.vcycle(x), plain.vcycle(x))
+    # the one-node-per-thread and the z-marching kernels evaluate the same
+    # expressions; only the compiler's FMA contraction may differ between them
+    ya, yb = tuned.apply(x), plain.apply(x)
+    assert np.max(np.abs(ya - yb)) <= 1e-13 * np.max(np.abs(yb))
+    va, vb = tuned.vcycle(x), plain.vcycle(x)
+    assert np.max(np.abs(va - vb)) <= 1e-5 * np.max(np.abs(vb))
+
+
+@pytest.mark.parametrize("shape", range(6))
+def test_every_stencil_shape_matches_oracle(dm, ctx, shape):
+    """Each tile shape of the vector stencil, forced on every level, applies
+    K - sigma A (Eq. discLaplDM) like the oracle's assembled matrix."""
+    from oracle import geometry, operators
+    w = W.ellipsoid_workload(40, seed=1307, sigma=5.0)
+    g = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, g, w.sigma, precision="f64", autotune=0, force_shape=shape)
+    assert op.stencil_shape(0) == shape
+    ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
+    x = np.random.default_rng(shape).standard_normal(ops.a.size) * (ops.a > 0)
+    y = op.apply(x)
+    yr = ops.apply_K(x, w.sigma)
+    assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
