@@ -241,7 +241,7 @@ def stencil_bytes_per_open_face(name):
 # Algorithmic FP64 operations of one K - sigma A evaluation per open face:
 # about 66 per cell of 3 faces (two curls, the grad-div and the shift).
 APPLY_FLOPS_PER_FACE = 22.0
-FP64_PEAK_TFLOPS = 1.204      # FMA probe on this machine's GB300
+FP64_PEAK_TFLOPS = 1.204      # FP64 FMA-loop probe on a GB300 (measured rate, TFLOP/s)
 
 
 # DRAM bytes (read + write) per launch of the fine-level stencil, from an ncu

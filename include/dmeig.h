@@ -243,7 +243,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
  * (h = smallest spacing).  Inside the preconditioner it corrects the V-cycle
  * result z: with r = f - (K - sigma A) z and c the network's correction for r,
  * z <- z + alpha c where alpha = <r, K c> / <K c, K c> minimises the residual
- * along c (no step when alpha <= 0); the FP64 FGMRES residual judges it and
+ * along c (no step when alpha <= 0); the FP64 FGMRES residual decides on it and
  * switches it off for the rest of a solve when an iteration contracts by less
  * than 0.8.
  * Weights: [W1 | W2 | W3], each W[a][b][c][cin][cout] (a along k, b along j,

@@ -25,7 +25,7 @@ Modules and the passages of Bauer, Werner & Cary (arXiv:1301.3794) they follow:
 * ``analytic``   closed-form discrete Yee eigenvalues of a PEC box and the
                  spherical-cavity wavenumbers from Bessel-function zeros (Sec.
                  6.2), used to pin the oracle itself.
-* ``multigrid``  the geometric V-cycle this build uses as the preconditioner of
+* ``multigrid``  the library's geometric V-cycle, the preconditioner of
                  the inner solve (the paper used algebraic multigrid, Sec. 6):
                  written out as plain sparse-matrix steps in the order the
                  V-cycle takes them.

@@ -1,6 +1,6 @@
 """Oracle: the learned smoother's 3-layer convolutional network (plain FP64 numpy).
 
-The network is this build's design for the learned smoother that sits inside
+The network is the library's own design for the learned smoother that sits inside
 flexible GMRES next to the V-cycle preconditioner of the inner solve (the paper
 itself has no learned part).  On the node grid of a level (shape (nz+1, ny+1,
 nx+1)), with channel-last arrays X[k, j, i, c]:

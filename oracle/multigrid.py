@@ -1,12 +1,12 @@
-"""Oracle: the geometric multigrid V-cycles this build uses inside the inner solves.
+"""Oracle: the geometric multigrid V-cycles the library uses inside the inner solves.
 
 The paper inverts K - sigma A (Eq. discLaplDM) and D A D^T (Eq. proj) with GMRES
 preconditioned by algebraic multigrid: a V-cycle with one order-1 polynomial
 smoother step per level on the way down and one on the way up (Sec. 6, opening
-paragraphs).  This build replaces the algebraic hierarchy by a geometric one.
+paragraphs).  The library replaces the algebraic hierarchy by a geometric one.
 The V-cycles are written out here as plain sparse-matrix steps, in the order the
 cycle takes them, so that each stage of the CUDA cycle can be compared element
-by element.  Everything below is a design of this build, not the paper's:
+by element.  Everything below is the library's design, not the paper's:
 
 Vector cycle (faces, operator K - sigma A):
 * coarse grid: every second node; cut fractions of the coarse grid are the

@@ -780,7 +780,7 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
     auto prec = [op, fl, nfl](const float2* in, double scale, double* out) {
         precond_vec(op, CompactIn{in, fl, nfl}, out, scale);
     };
-    // the learned correction is judged by the FP64 residual: an iteration that
+    // the FP64 residual decides on the learned correction: an iteration that
     // contracts by less than 0.8 switches it off for the rest of the solve
     op->learned_active = op->lnet != nullptr;
     bool fell_back = false;

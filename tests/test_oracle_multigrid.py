@@ -1,4 +1,4 @@
-"""Pins of the oracle V-cycles (this build's geometric multigrid)."""
+"""Pins of the oracle V-cycles (the library's geometric multigrid)."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
