@@ -410,7 +410,9 @@ def run_native(args):
                    "mg_levels": reps[-1]["mg_levels"], "mg_complexity": round(reps[-1]["mg_complexity"], 3),
                    "rho_max": reps[-1]["rho_max"], "delta_max": reps[-1]["delta_max"],
                    "k2": [round(float(v), 10) for v in k2],
-                   "inner_rate": None, "stencil_shapes": shapes},
+                   "inner_rate": None, "stencil_shapes": shapes,
+                   # one shifted FGMRES solve (K - sigma A) x = A v per Krylov-Schur step
+                   "solves_per_s": round(sum(r["outer_iters"] for r in reps) * world / max_s, 3)},
         "plain_f64": plain,
         "kernels_top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
