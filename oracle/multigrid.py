@@ -178,16 +178,18 @@ def _coarse_grids(grid, max_coarse):
     return out
 
 
-def level_fractions(grid, phi, max_coarse=4):
+def level_fractions(grid, phi, max_coarse=4, fine=None):
+    """Grids and fractions of every level; ``fine`` replaces the fine-level
+    fractions computed from phi (for perturbation studies)."""
     grids = _coarse_grids(grid, max_coarse)
-    frs = [geometry.fractions(phi)]
+    frs = [geometry.fractions(phi) if fine is None else fine]
     for _ in grids[1:]:
         frs.append(coarsen_fractions(frs[-1]))
     return grids, frs
 
 
-def build_vector_hierarchy(grid, phi, sigma, max_coarse=4):
-    grids, frs = level_fractions(grid, phi, max_coarse)
+def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None):
+    grids, frs = level_fractions(grid, phi, max_coarse, fine)
     levels = [VectorLevel(g, f, sigma) for g, f in zip(grids, frs)]
     for l in range(len(levels) - 1):
         c = levels[l + 1].grid
