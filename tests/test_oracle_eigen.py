@@ -45,15 +45,20 @@ def test_sphere_16_close_to_analytic():
 
 
 @pytest.mark.slow
-def test_sphere_second_order_frequency_convergence():
+def test_frequency_convergence_second_order_and_first_order_with_face_neglect():
     """Sec. 6.2, Fig. freqErr3d: the unaltered Dey--Mittra method converges at
-    second order in the frequency; the TM_1 error drops ~4x per refinement."""
-    ref = analytic.sphere_k2_list(1.0, 3)[0]
-    errs = []
-    for n in (16, 32):
-        w = W.sphere_workload(n, offset_seed=W.SEED_BASE + 2, sigma=7.0, nev=3)
-        ops = _ops(w)
-        k2, _, _ = eigen.shift_invert_modes(ops, 7.0, 3)
-        f = np.sqrt(k2.mean())
-        errs.append(abs(f - np.sqrt(ref)) / np.sqrt(ref))
-    assert errs[0] / errs[1] > 2.8
+    second order in the frequency (the TM_1 error drops ~4x per refinement);
+    dropping cut faces with a < a_min (Sec. 3; here a_min = 0.1 a_vac) leaves
+    first-order convergence and larger errors."""
+    ref = np.sqrt(analytic.sphere_k2_list(1.0, 3)[0])
+    errs = {}
+    for a_min in (0.0, 0.1):
+        for n in (16, 32):
+            w = W.sphere_workload(n, offset_seed=W.SEED_BASE + 2, sigma=7.0, nev=3)
+            ops = operators.DMOperators(w.grid, geometry.fractions(w.phi, a_min=a_min))
+            k2, _, _ = eigen.shift_invert_modes(ops, 7.0, 3)
+            errs[a_min, n] = abs(np.sqrt(k2.mean()) - ref) / ref
+    assert errs[0.0, 16] / errs[0.0, 32] > 2.8, errs
+    order = {a: np.log2(errs[a, 16] / errs[a, 32]) for a in (0.0, 0.1)}
+    assert order[0.1] < 1.5, (order, errs)
+    assert errs[0.1, 32] > 3.0 * errs[0.0, 32], errs
