@@ -68,3 +68,15 @@ def test_stencil_byte_model():
     assert 0 < r["frac"] < 1
     f = bench.roofline_fp64_apply({"vec_stencil_f64_apply_L0": (4, 2.0)}, 10 ** 6)
     assert f["bound"] == "alu" and f["achieved"] == pytest.approx(22e6 / 5e-4 / 1e12)
+
+
+def test_profiled_traffic_only_for_the_captured_shape():
+    import bench
+    key = ("vec_stencil_f32_jacobi_L0", 0, "sphere", 128)
+    assert bench.PROFILED_TRAFFIC[key] == 90_759_424 + 5_890_304
+    # another tile shape on level 0, or another cavity, has no capture: traffic stays null
+    assert bench.PROFILED_TRAFFIC.get(("vec_stencil_f32_jacobi_L0", 3, "sphere", 128)) is None
+    r = bench.roofline({"vec_stencil_f32_jacobi_L0": (10, 1.0)}, 10 ** 6, 6758.5, "measured", "f32",
+                       traffic=bench.PROFILED_TRAFFIC[key])
+    assert r["traffic"] == bench.PROFILED_TRAFFIC[key]
+    assert json.loads(json.dumps(r)) == r
