@@ -209,3 +209,26 @@ def test_band_schwarz_brute_force_loops():
                         out[q] += d[q]
     got = MG.band_schwarz(lev, f, x, om, sweeps, brick)
     assert np.max(np.abs(got - out)) < 1e-12 * np.max(np.abs(out))
+
+
+def test_sphere_needs_as_few_iterations_as_the_cube_at_every_size():
+    """Tab. invPerf: with the Dey--Mittra grad-div term the cut-cell sphere
+    (R = 0.49 L, centred) inverts in about as many multigrid-preconditioned
+    iterations as the vacuum cube, independently of the grid (tolerance 1e-6)."""
+    counts = {}
+    for n in (16, 32):
+        box = W.box_workload(n, n, n, 1.0, 1.0, 1.0, sigma=5.0)
+        g = W.Grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, (0.0, 0.0, 0.0))
+        sph = W.Workload(f"sphere{n}", g, W.sphere_phi(g, np.array([0.5, 0.5, 0.5]), 0.49), 5.0, 4, -1, {})
+        for name, w in (("cube", box), ("sphere", sph)):
+            levels = MG.build_vector_hierarchy(w.grid, w.phi, 5.0)
+            om = _omegas(levels)
+            lev = levels[0]
+            b = np.random.default_rng(0).standard_normal(lev.K.shape[0]) * lev.mask
+            _, hist = MG.fgmres(lambda v: lev.K @ v, b, lambda v: MG.vcycle(levels, v, om), tol=1e-6, maxiter=60)
+            assert hist[-1] <= 1e-6, (name, n, hist[-1])
+            counts[name, n] = len(hist)
+    for n in (16, 32):
+        assert abs(counts["sphere", n] - counts["cube", n]) <= 3, counts
+    assert abs(counts["sphere", 32] - counts["sphere", 16]) <= 2, counts
+    assert max(counts.values()) <= 14, counts
