@@ -230,7 +230,10 @@ void dm_eig_params_default(dm_eig_params* p);
  * b_out (nullable): nev x F, natural face layout, A-normalised (b^T A b = 1),
  * sign such that the entry of largest magnitude is positive; host or device
  * per b_on_device.  DM_ERR_NO_CONVERGENCE still fills the converged prefix
- * and report->n_converged. */
+ * and report->n_converged.  If the scalar solve inside P_DM reaches its
+ * iteration cap (400) in 3 projections in a row, the solve stops at the end of
+ * the current Krylov cycle with DM_ERR_NO_CONVERGENCE and n_converged = 0:
+ * without the projection the pairs cannot be trusted. */
 dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_params* p,
                         double* k2_out, double* b_out, int b_on_device, dm_eig_report* report);
 

@@ -796,6 +796,13 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
     return it;
 }
 
+// Iteration cap of the scalar solve inside P_DM, and how many projections in a
+// row may reach it before an eigensolve gives up: a healthy projection takes a
+// few tens of iterations, so a run of capped ones means P_DM is not being
+// applied and the eigenpairs cannot be trusted.
+constexpr int kProjMaxit = 400;
+constexpr int kProjStallLimit = 3;
+
 // y = P_DM x (Eq. proj); x, y padded FP64 fine-level face vectors (may alias)
 int project(dm_operator* op, const double* x, double* y, double tol) {
     cudaStream_t s = op->ctx->stream;
@@ -818,7 +825,7 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
         precond_scal(op, CompactIn{in, cl, ncl}, out, scale);
     };
     double rr = 0.0;
-    const int it = fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, 400, &rr, tol * xscale);
+    const int it = fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, kProjMaxit, &rr, tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
     return it;
 }
@@ -1752,6 +1759,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                         double* b_out, int b_on_device, dm_eig_report* report) {
     if (!ctx || !geom || !prm || !k2_out) return DM_ERR_INVALID_ARG;
     dm_status conv = DM_OK;
+    bool stalled = false;   // kProjStallLimit projections in a row reached the scalar solve's cap
     const dm_status st = guarded(ctx, [&] {
         DM_CUDA(cudaSetDevice(ctx->device));
         cudaStream_t s = ctx->stream;
@@ -1787,7 +1795,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         }
         std::vector<double> H((size_t)(m + 1) * m, 0.0);
         auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-        int k = 0, restarts = 0, outer = 0, inner_total = 0, proj_total = 0, nconv = 0;
+        int k = 0, restarts = 0, outer = 0, inner_total = 0, proj_total = 0, nconv = 0, proj_capped = 0;
         std::vector<double> theta, Y, est;
         std::vector<int> order;
         while (true) {
@@ -1797,7 +1805,9 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 double rr = 0.0;
                 inner_total += solve_vec(op, rhs.get(), x.get(), p.inner_tol, p.inner_restart, p.inner_maxit, &rr);
                 double* w = V + (size_t)(j + 1) * n;
-                proj_total += project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
+                const int pit = project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
+                proj_total += pit;
+                proj_capped = pit >= kProjMaxit ? proj_capped + 1 : 0;
                 ++outer;
                 // A-orthogonalise against the basis: classical Gram-Schmidt,
                 // repeated when the first pass cancelled most of w
@@ -1829,7 +1839,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             nconv = 0;
             for (int i = 0; i < m; ++i) est[i] = std::fabs(beta_m * Y[(size_t)(m - 1) * m + order[i]]);
             while (nconv < p.nev && est[nconv] <= p.tol * std::fabs(theta[order[nconv]])) ++nconv;
-            if (nconv >= p.nev || restarts >= p.max_restarts) break;
+            stalled = proj_capped >= kProjStallLimit;
+            if (nconv >= p.nev || restarts >= p.max_restarts || stalled) break;
             // thick restart: keep the pk wanted Ritz vectors
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
             std::vector<double> Yk((size_t)m * pk);
@@ -1895,6 +1906,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             Sync::stream(s);
         }
         Sync::stream(s);
+        if (stalled) nconv = 0;   // P_DM was not applied: no pair counts as converged
         if (nconv < nev) conv = DM_ERR_NO_CONVERGENCE;
         if (report) {
             report->n_converged = nconv;
@@ -1913,6 +1925,9 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             report->learned_fallbacks = op->learned_fallbacks;
         }
     });
+    if (st == DM_OK && stalled)
+        ctx->err = "projection: the scalar solve of P_DM reached its iteration cap in " +
+                   std::to_string(kProjStallLimit) + " projections in a row";
     return st != DM_OK ? st : conv;
 }
 
