@@ -95,3 +95,33 @@ def test_projection_properties():
     k2, B = eigen.dense_modes(ops)
     b = B[:, 0]
     assert np.linalg.norm(ops.project(b) - b) < 1e-9 * np.linalg.norm(b)
+
+
+def test_sphere_spurious_modes_are_the_neumann_scalar_modes():
+    """Sec. 5.1: the Dey--Mittra grad-div term adds the scalar Laplacian's
+    spectrum as curl-free, divergent modes and leaves the electromagnetic ones
+    alone.  On the cut-cell sphere the lowest eigenvalues of (K, A) are the
+    l = 1 Neumann triplet (kR = 2.0816, the first zero of j_1') with curl-free
+    eigenvectors, and the next is the divergence-free TM_1 mode (kR = 2.7437)."""
+    import scipy.sparse.linalg as spla
+    w = W.sphere_workload(16, sigma=5.0)
+    ops = _ops(w)
+    K = ops.restrict(ops.K(0.0)).tocsc()
+    M = ops.restrict(ops.A).tocsc()
+    lam, vec = spla.eigsh(K, k=4, M=M, sigma=-1.0, which="LM")
+    o = np.argsort(lam)
+    lam, vec = lam[o], vec[:, o]
+    neumann = analytic.sphere_neumann_modes()[0]
+    assert neumann[1] == 1 and neumann[2] == 3
+    tm1 = analytic.sphere_k2_list(1.0, 1)[0]
+    for c in range(4):
+        b = np.zeros(ops.a.size)
+        b[ops.open_idx] = vec[:, c]
+        curl = np.linalg.norm(ops.l * (ops.C.T @ b)) / np.linalg.norm(b)
+        div = eigen.divergence_ratio(ops, b)
+        if c < 3:
+            assert abs(lam[c] - neumann[0] ** 2) / neumann[0] ** 2 < 1e-2, lam
+            assert curl < 1e-10 and div > 1e-2, (c, curl, div)
+        else:
+            assert abs(lam[c] - tm1) / tm1 < 5e-3, lam
+            assert div < 1e-8, (c, div)
