@@ -68,8 +68,10 @@ typedef struct dm_mg_params {
                               other faces frozen, and the brick keeps the faces it owns */
     int band_brick;        /* brick edge in nodes (8); 0 < band_brick, and the largest subdomain must fit
                               the sweep buffers in shared memory (DM_ERR_INVALID_ARG otherwise) */
-    double omega_scale;    /* Jacobi weight = omega_scale / lambda_max(D^-1 (K - sigma A)) (1.7) */
-    int power_iters;       /* power iterations for lambda_max (30) */
+    double omega_scale;    /* Jacobi weight = omega_scale / lambda_max(D^-1 (K - sigma A)), and
+                              omega_scale / 2 in the scalar cycle of P_DM (1.7) */
+    int power_iters;       /* power iterations for lambda_max of the vector cycle (30); the scalar cycle
+                              uses the bound 2 of D^-1 D A D^T (its rows sum to zero) */
     int precision;         /* dm_precision of the V-cycle (DM_PREC_F64) */
     int autotune;          /* 1: time the stencil tile shapes per level at setup and keep the fastest;
                               results are cached in the context by level size and precision (1) */
@@ -90,6 +92,8 @@ typedef struct dm_eig_params {
     unsigned long long seed; /* start vector seed */
     dm_mg_params mg;
     const dm_learned* learned; /* nullable: learned correction after each V-cycle (see dm_learned_*) */
+    double max_seconds;    /* wall-clock limit of one eigensolve, setup included; 0 = none (0).  Checked
+                              before every shifted solve: a solve that runs out returns DM_ERR_TIMEOUT */
 } dm_eig_params;
 
 typedef struct dm_eig_report {
@@ -121,6 +125,12 @@ void dm_context_destroy(dm_context* ctx);
 const char* dm_last_error(const dm_context* ctx);
 /* Kernels launched on this context so far. */
 long long dm_context_launch_count(const dm_context* ctx);
+/* Device buffers, pinned host buffers, CUDA events, streams and graph
+ * instantiations the library has created in this process, on any context (a
+ * diagnostic with no counterpart in the paper: it lets a caller check that a
+ * call which promises not to allocate, such as dm_operator_apply_noalloc,
+ * created none).  Thread-safe. */
+long long dm_debug_allocation_count(void);
 
 /* ---- kernel timing (profiling aid; no counterpart in the paper) ---------- */
 /* on = 1 clears the statistics and brackets every later kernel launch with a
@@ -139,7 +149,8 @@ dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long 
  * 6-tetrahedron (Kuhn) split of every cell; the multigrid levels' fractions
  * are averages of the fine ones.  phi: host or device, (nx+1)(ny+1)(nz+1).
  * a_min > 0 neglects faces with A < a_min and their edges (Sec. 3); 0 keeps
- * all faces (the paper's method).  nx, ny, nz >= 2. */
+ * all faces (the paper's method).  nx, ny, nz >= 2.  A phi holding NaN or
+ * infinite values is rejected with DM_ERR_GEOMETRY. */
 dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz,
                              double dx, double dy, double dz, const double origin[3],
                              const double* phi, int phi_on_device, double a_min,
@@ -230,10 +241,14 @@ void dm_eig_params_default(dm_eig_params* p);
  * b_out (nullable): nev x F, natural face layout, A-normalised (b^T A b = 1),
  * sign such that the entry of largest magnitude is positive; host or device
  * per b_on_device.  DM_ERR_NO_CONVERGENCE still fills the converged prefix
- * and report->n_converged.  If the scalar solve inside P_DM reaches its
- * iteration cap (400) in 3 projections in a row, the solve stops at the end of
- * the current Krylov cycle with DM_ERR_NO_CONVERGENCE and n_converged = 0:
- * without the projection the pairs cannot be trusted. */
+ * and report->n_converged.  Two failures return no pair at all (k2_out set to
+ * NaN, b_out untouched, n_converged = 0, the report's iteration counts and
+ * timings filled):
+ *  - the scalar solve inside P_DM reached its iteration cap (400) in 3
+ *    projections of this eigensolve: DM_ERR_NO_CONVERGENCE, because without
+ *    the projection the pairs cannot be trusted; the solve stops right after
+ *    the third such projection;
+ *  - p->max_seconds > 0 ran out before a shifted solve: DM_ERR_TIMEOUT. */
 dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_params* p,
                         double* k2_out, double* b_out, int b_on_device, dm_eig_report* report);
 

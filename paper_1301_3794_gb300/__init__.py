@@ -254,8 +254,16 @@ class Operator:
         CUDA tensors; the call allocates nothing (see include/dmeig.h)."""
         import torch
         F = self._faces(level)
-        if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == F):
-            raise ValueError("apply_noalloc needs a contiguous float64 CUDA tensor of the level's face count")
+        dev = self.ctx.device
+
+        def ok(t):
+            return (_is_torch(t) and t.is_cuda and t.device.index == dev and t.dtype == torch.float64
+                    and t.is_contiguous() and t.numel() == F)
+
+        if not ok(x):
+            raise ValueError(f"apply_noalloc: x must be a contiguous float64 tensor of {F} values on cuda:{dev}")
+        if out is not None and not ok(out):
+            raise ValueError(f"apply_noalloc: out must be a contiguous float64 tensor of {F} values on cuda:{dev}")
         y = torch.empty_like(x) if out is None else out
         self.ctx.check(lib.dm_operator_apply_noalloc(self.h, level, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())),
                        "dm_operator_apply_noalloc")
@@ -392,7 +400,7 @@ class Learned:
 
 
 def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
-               inner_restart=40, inner_maxit=400, seed=1301, learned=None, **mg):
+               inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, **mg):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     p.sigma = float(sigma)
@@ -407,6 +415,7 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.seed = seed
     p.mg = mg_params(**mg)
     p.learned = learned.h if learned is not None else None
+    p.max_seconds = float(max_seconds)
     return p
 
 
@@ -432,8 +441,10 @@ def eigensolve(ctx, geom, sigma, nev, vectors="host", out=None, **kw):
     rep = EigReport()
     st = lib.dm_eigensolve(ctx.h, geom.h, C.byref(p), k2.ctypes.data_as(C.POINTER(C.c_double)), bptr, dev,
                            C.byref(rep))
-    if st != 0 and (st != 2 or rep.outer_iters == 0):
-        # DM_ERR_NO_CONVERGENCE with a filled report is a partial result; anything else is an error
+    if st != 0 and not (st == 3 or (st == 2 and rep.outer_iters > 0)):
+        # DM_ERR_NO_CONVERGENCE with a filled report is a partial result and
+        # DM_ERR_TIMEOUT a stopped one (both returned with their status);
+        # anything else is an error
         ctx.check(st, "dm_eigensolve")
     return k2, B, rep.as_dict(), st
 

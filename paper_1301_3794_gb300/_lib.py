@@ -23,7 +23,7 @@ class EigParams(C.Structure):
     _fields_ = [("sigma", C.c_double), ("nev", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("proj_tol", C.c_double), ("basis", C.c_int), ("max_restarts", C.c_int),
                 ("inner_restart", C.c_int), ("inner_maxit", C.c_int), ("seed", C.c_ulonglong),
-                ("mg", MGParams), ("learned", C.c_void_p)]
+                ("mg", MGParams), ("learned", C.c_void_p), ("max_seconds", C.c_double)]
 
 
 class EigReport(C.Structure):
@@ -49,6 +49,7 @@ SIGNATURES = {
     "dm_context_destroy": (None, [_P]),
     "dm_last_error": (C.c_char_p, [_P]),
     "dm_context_launch_count": (C.c_longlong, [_P]),
+    "dm_debug_allocation_count": (C.c_longlong, []),
     "dm_trace_enable": (C.c_int, [_P, C.c_int]),
     "dm_trace_count": (C.c_int, [_P]),
     "dm_trace_entry": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <atomic>
 #include <memory>
 #include <mutex>
@@ -24,10 +25,15 @@ namespace dm {
 thread_local long long* g_launch_counter = nullptr;
 thread_local cudaStream_t g_stream = nullptr;
 thread_local Tracer* g_tracer = nullptr;
+thread_local int g_untraced = 0;
+
+static std::atomic<long long> g_allocations{0};
+void note_allocation() { g_allocations.fetch_add(1, std::memory_order_relaxed); }
 
 cudaEvent_t Tracer::get_event() {
     if (free_events.empty()) {
         cudaEvent_t e;
+        note_allocation();
         DM_CUDA(cudaEventCreate(&e));
         all_events.push_back(e);
         return e;
@@ -456,6 +462,7 @@ bool capture_graph(dm_operator* op, F&& f, cudaGraphExec_t* out, long long* kern
         cudaGetLastError();
         return false;
     }
+    note_allocation();
     const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
@@ -796,9 +803,9 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
     return it;
 }
 
-// Iteration cap of the scalar solve inside P_DM, and how many projections in a
-// row may reach it before an eigensolve gives up: a healthy projection takes a
-// few tens of iterations, so a run of capped ones means P_DM is not being
+// Iteration cap of the scalar solve inside P_DM, and how many projections of
+// one eigensolve may reach it before the solve gives up: a healthy projection
+// takes a few tens of iterations, so capped ones mean P_DM is not being
 // applied and the eigenpairs cannot be trusted.
 constexpr int kProjMaxit = 400;
 constexpr int kProjStallLimit = 3;
@@ -830,32 +837,25 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     return it;
 }
 
-double power_lambda_max(dm_operator* op, int l, bool scalar) {
+// Largest eigenvalue of D^-1 (K - sigma A) on level l by power iteration from
+// a seeded random vector on the open faces.  The start is not scaled by D^-1:
+// a face or cell with a tiny diagonal would then dominate it, and the
+// iteration would report that entry's local eigenvalue (near 1) instead of
+// the largest one.
+double power_lambda_max(dm_operator* op, int l) {
     cudaStream_t s = op->ctx->stream;
     const GeoLevel& g = glv(op, l);
-    const Domain D = scalar ? g.sdom() : g.vdom();
+    const Domain D = g.vdom();
     const long long n = D.len();
     DBuf<double> x(n), y(n);
-    if (scalar) {
-        // random start on the active cells (scaling by D^-1 zeroes the inactive ones)
-        DBuf<double> tmp(n);
-        fill_random(D, 12345 + l, nullptr, tmp.get(), s);
-        hadamard(D, op->ol[l].invDs.get(), tmp.get(), x.get(), s);
-    } else {
-        fill_random(D, 12345 + l, g.A.get(), x.get(), s);
-    }
+    fill_random(D, 12345 + l, g.A.get(), x.get(), s);
     double lam = 0.0;
     double nx = norm2(op->ctx, D, x.get());
     if (nx == 0.0) return 1.0;
     scale_copy(D, 1.0 / nx, x.get(), x.get(), s);
     for (int it = 0; it < op->mg.power_iters; ++it) {
-        if (scalar) {
-            apply_scal64(op, l, x.get(), y.get());
-            hadamard(D, op->ol[l].invDs.get(), y.get(), y.get(), s);
-        } else {
-            apply_vec64(op, l, x.get(), y.get());
-            hadamard(D, op->ol[l].invD.get(), y.get(), y.get(), s);
-        }
+        apply_vec64(op, l, x.get(), y.get());
+        hadamard(D, op->ol[l].invD.get(), y.get(), y.get(), s);
         const double ny = norm2(op->ctx, D, y.get());
         if (ny == 0.0) break;
         lam = ny;
@@ -863,6 +863,16 @@ double power_lambda_max(dm_operator* op, int l, bool scalar) {
     }
     return lam > 0.0 ? lam : 1.0;
 }
+
+// Largest eigenvalue of D^-1 D A D^T used for the scalar Jacobi weight.  Every
+// row of D A D^T on the active cells sums to zero (a face between an active
+// and an inactive cell, or on an outer wall, is closed), so by Gershgorin the
+// spectrum of D^-1 D A D^T lies in [0, 2]; the grid's checkerboard mode comes
+// within O(h^2) of 2.  The bound is exact enough and, unlike a power estimate,
+// cannot be fooled by a nearly isolated cut cell whose diagonal is ten orders
+// of magnitude below the bulk (its local eigenvalue is 1, and an estimate near
+// 1 would over-relax the smoother until the scalar cycle diverges).
+constexpr double kScalarLambdaMax = 2.0;
 
 void ensure_f32(GeoLevel& g, cudaStream_t s) {
     if (g.A32.get()) return;
@@ -917,7 +927,9 @@ void autotune_level(dm_operator* op, int l) {
         const T* f = reinterpret_cast<const T*>(w.f.get());
         T* y = reinterpret_cast<T*>(w.r.get());
         cudaEvent_t e0, e1;
+        note_allocation();
         DM_CUDA(cudaEventCreate(&e0));
+        note_allocation();
         DM_CUDA(cudaEventCreate(&e1));
         float best = 1e30f;
         int best_shape = 0;
@@ -1082,10 +1094,11 @@ void setup_operator(dm_operator* op) {
         op->complexity = fine > 0 ? (double)tot / (double)fine : 1.0;
         op->nopen0 = fine;
     }
-    // Jacobi weights from the largest eigenvalue of D^-1 (K - sigma A)
+    // Jacobi weights from the largest eigenvalue of D^-1 (K - sigma A) and of
+    // D^-1 D A D^T
     for (int l = 0; l + 1 < nl; ++l) {
-        op->ol[l].omega = op->mg.omega_scale / power_lambda_max(op, l, false);
-        op->ol[l].omega_s = op->mg.omega_scale / power_lambda_max(op, l, true);
+        op->ol[l].omega = op->mg.omega_scale / power_lambda_max(op, l);
+        op->ol[l].omega_s = op->mg.omega_scale / kScalarLambdaMax;
     }
     // coarsest vector level: dense inverse over the open faces
     {
@@ -1255,6 +1268,7 @@ dm_status dm_context_create(int device, void* cuda_stream, dm_context** out) {
         } else {
             // a blocking stream: ordered after work the caller queued on the
             // legacy default stream (e.g. torch copies of input tensors)
+            note_allocation();
             DM_CUDA(cudaStreamCreate(&ctx->stream));
             ctx->own_stream = true;
         }
@@ -1310,6 +1324,8 @@ dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long 
 }
 long long dm_context_launch_count(const dm_context* ctx) { return ctx ? ctx->launches : 0; }
 
+long long dm_debug_allocation_count(void) { return g_allocations.load(std::memory_order_relaxed); }
+
 dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
                              const double origin[3], const double* phi, int phi_on_device, double a_min,
                              dm_geometry** out) {
@@ -1340,6 +1356,13 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
                 DBuf<double> tmp;
                 const double* dphi = nullptr;
                 stage_in(ctx, phi, phi_on_device, nn, tmp, &dphi);
+                {
+                    DBuf<int> bad(1);
+                    const int nbad = count_nonfinite((long long)nn, dphi, bad.get(), s);
+                    DM_REQUIRE(nbad == 0, DM_ERR_GEOMETRY,
+                               "level set: " + std::to_string(nbad) + " of " + std::to_string(nn) +
+                                   " node values are NaN or infinite");
+                }
                 pack_nodes(lv->g, dphi, phi_pad.get(), s);
                 geom_fractions(lv->g, phi_pad.get(), lv->L.get(), lv->A.get(), lv->V.get(), s);
                 if (a_min > 0.0) geom_neglect_faces(lv->g, a_min, lv->L.get(), lv->A.get(), s);
@@ -1668,6 +1691,7 @@ void dm_eig_params_default(dm_eig_params* p) {
     p->seed = 1301;
     dm_mg_params_default(&p->mg);
     p->learned = nullptr;
+    p->max_seconds = 0.0;
 }
 
 }  // extern "C"
@@ -1759,7 +1783,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                         double* b_out, int b_on_device, dm_eig_report* report) {
     if (!ctx || !geom || !prm || !k2_out) return DM_ERR_INVALID_ARG;
     dm_status conv = DM_OK;
-    bool stalled = false;   // kProjStallLimit projections in a row reached the scalar solve's cap
+    bool stalled = false;     // kProjStallLimit projections reached the scalar solve's cap
+    bool timed_out = false;   // the wall-clock limit p.max_seconds ran out
     const dm_status st = guarded(ctx, [&] {
         DM_CUDA(cudaSetDevice(ctx->device));
         cudaStream_t s = ctx->stream;
@@ -1768,7 +1793,9 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         DM_REQUIRE(p.nev >= 1 && p.nev <= 40, DM_ERR_INVALID_ARG, "nev must be in [1, 40]");
         int m = p.basis > 0 ? p.basis : std::min(64, std::max(2 * p.nev + 10, 24));
         DM_REQUIRE(m >= p.nev + 2 && m <= 64, DM_ERR_INVALID_ARG, "basis must be in [nev + 2, 64]");
+        DM_REQUIRE(p.max_seconds >= 0.0, DM_ERR_INVALID_ARG, "max_seconds must be >= 0");
         const double t_setup0 = now_s();
+        auto out_of_time = [&] { return p.max_seconds > 0.0 && now_s() - t_setup0 > p.max_seconds; };
         dm_operator* op = nullptr;
         const dm_status cs = dm_operator_create(ctx, geom, p.sigma, &p.mg, &op);
         if (cs != DM_OK) throw Error(cs, std::string("operator setup: ") + ctx->err);
@@ -1800,6 +1827,10 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         std::vector<int> order;
         while (true) {
             for (int j = k; j < m; ++j) {
+                if (out_of_time()) {
+                    timed_out = true;
+                    break;
+                }
                 double* vj = V + (size_t)j * n;
                 hadamard(D, a, vj, rhs.get(), s);           // A v_j
                 double rr = 0.0;
@@ -1807,8 +1838,11 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 double* w = V + (size_t)(j + 1) * n;
                 const int pit = project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
                 proj_total += pit;
-                proj_capped = pit >= kProjMaxit ? proj_capped + 1 : 0;
                 ++outer;
+                if (pit >= kProjMaxit && ++proj_capped >= kProjStallLimit) {
+                    stalled = true;
+                    break;
+                }
                 // A-orthogonalise against the basis: classical Gram-Schmidt,
                 // repeated when the first pass cancelled most of w
                 std::vector<double> h(j + 1);
@@ -1826,6 +1860,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 DM_REQUIRE(beta > 0.0, DM_ERR_NO_CONVERGENCE, "Krylov space exhausted");
                 scale_copy(D, 1.0 / beta, w, w, s);
             }
+            // an interrupted expansion leaves no basis to extract pairs from
+            if (stalled || timed_out) break;
             // Rayleigh-Ritz on the symmetrised projected matrix
             std::vector<double> Hs((size_t)m * m);
             for (int i = 0; i < m; ++i)
@@ -1839,8 +1875,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             nconv = 0;
             for (int i = 0; i < m; ++i) est[i] = std::fabs(beta_m * Y[(size_t)(m - 1) * m + order[i]]);
             while (nconv < p.nev && est[nconv] <= p.tol * std::fabs(theta[order[nconv]])) ++nconv;
-            stalled = proj_capped >= kProjStallLimit;
-            if (nconv >= p.nev || restarts >= p.max_restarts || stalled) break;
+            if (nconv >= p.nev || restarts >= p.max_restarts) break;
             // thick restart: keep the pk wanted Ritz vectors
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
             std::vector<double> Yk((size_t)m * pk);
@@ -1860,8 +1895,31 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             ++restarts;
             Sync::stream(s);
         }
-        // Ritz vectors of the wanted pairs, in the order of |theta|
         const int nev = p.nev;
+        if (stalled || timed_out) {
+            // no pair is returned: k^2 are NaN, b_out is left untouched
+            for (int c = 0; c < nev; ++c) k2_out[c] = std::numeric_limits<double>::quiet_NaN();
+            conv = timed_out ? DM_ERR_TIMEOUT : DM_ERR_NO_CONVERGENCE;
+            if (report) {
+                *report = dm_eig_report{};
+                report->outer_iters = outer;
+                report->restarts = restarts;
+                report->inner_iters = inner_total;
+                report->proj_iters = proj_total;
+                report->mg_levels = op->nlev;
+                report->mg_complexity = op->complexity;
+                report->rho_max = std::numeric_limits<double>::quiet_NaN();
+                report->delta_max = std::numeric_limits<double>::quiet_NaN();
+                report->setup_seconds = t_solve0 - t_setup0;
+                report->solve_seconds = now_s() - t_solve0;
+                report->kernel_launches = ctx->launches - launches0;
+                report->learned_applied = op->learned_applied;
+                report->learned_fallbacks = op->learned_fallbacks;
+            }
+            Sync::stream(s);
+            return;
+        }
+        // Ritz vectors of the wanted pairs, in the order of |theta|
         std::vector<double> Yw((size_t)m * nev);
         for (int c = 0; c < nev; ++c)
             for (int r = 0; r < m; ++r) Yw[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
@@ -1906,7 +1964,6 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             Sync::stream(s);
         }
         Sync::stream(s);
-        if (stalled) nconv = 0;   // P_DM was not applied: no pair counts as converged
         if (nconv < nev) conv = DM_ERR_NO_CONVERGENCE;
         if (report) {
             report->n_converged = nconv;
@@ -1926,8 +1983,11 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         }
     });
     if (st == DM_OK && stalled)
-        ctx->err = "projection: the scalar solve of P_DM reached its iteration cap in " +
-                   std::to_string(kProjStallLimit) + " projections in a row";
+        ctx->err = "projection: the scalar solve of P_DM reached its iteration cap (" + std::to_string(kProjMaxit) +
+                   ") in " + std::to_string(kProjStallLimit) + " projections; no eigenpair is returned";
+    if (st == DM_OK && timed_out)
+        ctx->err = "eigensolve: the wall-clock limit of " + std::to_string(prm->max_seconds) +
+                   " s ran out; no eigenpair is returned";
     return st != DM_OK ? st : conv;
 }
 
@@ -1970,12 +2030,9 @@ extern "C" {
 dm_status dm_operator_apply_noalloc(dm_operator* op, int level, const double* x, double* y) {
     if (!op || !x || !y || level < 0 || level >= op->nlev) return DM_ERR_INVALID_ARG;
     return guarded(op->ctx, [&] {
-        Tracer* const saved = g_tracer;
-        g_tracer = nullptr;   // event timing would create events; this call creates nothing
-        struct Restore {
-            Tracer* t;
-            ~Restore() { g_tracer = t; }
-        } restore{saved};
+        // event timing would create CUDA events, and this call creates nothing:
+        // its launches are never traced (the context's tracer is left as it is)
+        UntracedScope untraced;
         DM_CUDA(cudaSetDevice(op->ctx->device));
         const GeoLevel& g = glv(op, level);
         const long long n3 = 3ll * g.g.np;

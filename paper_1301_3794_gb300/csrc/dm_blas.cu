@@ -491,8 +491,11 @@ int blocks_for(const Domain& d, K kernel) {
 void reducer_init(Reducer& r, int max_cols) {
     r.cap_blocks = kMaxBlocks;
     r.max_cols = max_cols;
+    note_allocation();
     DM_CUDA(cudaMalloc(&r.partial, sizeof(double) * (size_t)r.cap_blocks * max_cols));
+    note_allocation();
     DM_CUDA(cudaMalloc(&r.result, sizeof(double) * (size_t)max_cols));
+    note_allocation();
     DM_CUDA(cudaMallocHost(&r.host, sizeof(double) * (size_t)max_cols));
 }
 void reducer_free(Reducer& r) {

@@ -176,12 +176,21 @@ struct Tracer {
     ~Tracer();
 };
 extern thread_local Tracer* g_tracer;
+// Nonzero while the calling thread issues launches that must not be timed
+// (timing creates CUDA events): see UntracedScope.
+extern thread_local int g_untraced;
+struct UntracedScope {
+    UntracedScope() { ++g_untraced; }
+    ~UntracedScope() { --g_untraced; }
+    UntracedScope(const UntracedScope&) = delete;
+    UntracedScope& operator=(const UntracedScope&) = delete;
+};
 
 // Launch a kernel on stream s, counting it and (with tracing on) timing it.
 template <typename... KArgs, typename... Args>
 inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                    Args&&... args) {
-    Tracer* t = (g_tracer && g_tracer->on) ? g_tracer : nullptr;
+    Tracer* t = (g_tracer && g_tracer->on && !g_untraced) ? g_tracer : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (t) t->begin(s, &e0, &e1);
     kern<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
@@ -189,6 +198,11 @@ inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 blo
     count_launch();
     check_launch(name);
 }
+
+// Count of the device memory, pinned host memory, CUDA events and streams the
+// library has created in this process (a diagnostic for the calls that
+// promise to create none).
+void note_allocation();
 
 // Owning device buffer.
 template <typename T>
@@ -209,6 +223,7 @@ struct DBuf {
         release();
         n = count;
         if (count) {
+            note_allocation();
             DM_CUDA(cudaMalloc(&p, count * sizeof(T)));
             if (zero) DM_CUDA(cudaMemsetAsync(p, 0, count * sizeof(T), g_stream));
         }
@@ -259,6 +274,8 @@ int geom_band(const Grid3& g, const double* A, const double* V, int* cell_flag, 
 int geom_open_faces(const Grid3& g, const double* A, int* list, int* d_count, cudaStream_t s);
 // number of entries > 0
 int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
+// number of entries that are NaN or infinite
+int count_nonfinite(long long n, const double* a, int* d_count, cudaStream_t s);
 // active tiles of a level in ascending order (tiles: capacity of all tiles); returns the count
 int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
                cudaStream_t s);

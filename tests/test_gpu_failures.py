@@ -1,0 +1,126 @@
+"""Failure handling of the eigensolver (status codes on the host, no GPU fault)
+and the nearly isolated cut cells that once stalled the projection.
+
+Two cavities of the 48-cavity batch recipe, ``ellipsoid64_34`` and
+``sphere96_36``, each hold a cut cell whose six faces are open by only 2e-11 to
+5e-11 of their area: its diagonal in D A D^T (Eq. proj) is 1.7e-7 against about
+5e3 in the bulk.  The scalar Jacobi weight used to come from a power iteration
+whose start vector was scaled by 1/diag, so that cell dominated the start and
+the estimate of lambda_max(D^-1 D A D^T) came out near 1 instead of 2; the
+over-relaxed smoother made the scalar cycle diverge and every projection ran
+to its iteration cap.  The weight now uses the Gershgorin bound 2."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multigrid as MG
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_item(name):
+    for w, shifts, nev in W.batch_workloads():
+        if w.name == name:
+            return w, shifts, nev
+    raise KeyError(name)
+
+
+@pytest.fixture(scope="module")
+def ellipsoid64_34(dm, ctx):
+    w, shifts, nev = _batch_item("ellipsoid64_34")
+    return w, shifts, nev, dm.Geometry.from_workload(ctx, w)
+
+
+def test_scalar_weight_is_the_gershgorin_bound(dm, ctx, ellipsoid64_34):
+    w, shifts, nev, geom = ellipsoid64_34
+    op = dm.Operator(ctx, geom, shifts[0])
+    for l in range(op.num_levels - 1):
+        assert op.omega(l, scalar=True) == pytest.approx(1.7 / 2.0, rel=0, abs=1e-15)
+
+
+def test_isolated_cell_scalar_vcycle_matches_oracle(dm, ctx, ellipsoid64_34):
+    w, shifts, nev, geom = ellipsoid64_34
+    op = dm.Operator(ctx, geom, shifts[0])
+    sl = MG.build_scalar_hierarchy(w.grid, w.phi)
+    om = [op.omega(l, scalar=True) for l in range(len(sl))]
+    f = np.random.default_rng(11).standard_normal(sl[0].mask.size) * sl[0].mask
+    got = op.scalar_vcycle(f)
+    ref = MG.scalar_vcycle(sl, f, om)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_isolated_cell_projection_converges(dm, ctx, ellipsoid64_34, prec):
+    """Every projection converges in a few tens of scalar iterations and
+    matches the oracle's direct projection (Eq. proj)."""
+    from oracle import geometry, operators
+    w, shifts, nev, geom = ellipsoid64_34
+    op = dm.Operator(ctx, geom, shifts[0], precision=prec)
+    ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
+    x = np.random.default_rng(12).standard_normal(ops.a.size) * ops.open
+    y, it = op.project(x, tol=1e-12)
+    assert it <= 60, it
+    ref = ops.project(x)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["ellipsoid64_34", "sphere96_36"])
+def test_stalled_batch_cavities_now_converge(dm, ctx, name):
+    """The two batch cavities whose eigensolves never reached rho <= 1e-8 now
+    converge at their first shift with the batch's FP32 V-cycle, and no
+    projection comes near its cap (400)."""
+    w, shifts, nev = _batch_item(name)
+    geom = dm.Geometry.from_workload(ctx, w)
+    k2, _, rep, st = dm.eigensolve(ctx, geom, shifts[0], nev, vectors=None, precision="f32")
+    assert st == 0 and rep["n_converged"] == nev, rep
+    assert rep["rho_max"] <= 1e-8, rep
+    assert rep["proj_iters"] <= 60 * (rep["outer_iters"] + 1), rep
+
+
+def test_stall_guard_returns_no_pair(dm, ctx):
+    """An unreachable projection tolerance forces every scalar solve to its
+    cap; the eigensolve stops after the third and returns no pair."""
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, proj_tol=1e-30)
+    assert st == 2 and rep["n_converged"] == 0, rep
+    assert rep["outer_iters"] == 3, rep
+    # the start vector's projection plus the three capped ones
+    assert rep["proj_iters"] <= 4 * 400, rep
+    assert np.all(np.isnan(k2))
+    assert "iteration cap" in dm.lib.dm_last_error(ctx.h).decode()
+
+
+def test_time_limit_returns_timeout(dm, ctx):
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, max_seconds=1e-9)
+    assert st == 3 and rep["n_converged"] == 0, rep
+    assert np.all(np.isnan(k2))
+    assert "wall-clock" in dm.lib.dm_last_error(ctx.h).decode()
+    # a generous limit changes nothing
+    k2b, _, repb, stb = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, max_seconds=600.0)
+    assert stb == 0 and repb["n_converged"] == w.nev
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_level_set_is_a_geometry_error(dm, ctx, bad):
+    w = W.sphere_workload(12, sigma=7.0)
+    phi = np.array(w.phi, dtype=np.float64, copy=True)
+    phi.flat[phi.size // 3] = bad
+    g = w.grid
+    with pytest.raises(dm.DMError) as err:
+        dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi, g.origin)
+    assert err.value.status == 6 and "NaN or infinite" in str(err.value)
+
+
+@pytest.mark.parametrize("opts", [dict(tol=1e-30, max_restarts=1), dict(inner_maxit=1, max_restarts=1)])
+def test_unreachable_targets_return_a_partial_result(dm, ctx, opts):
+    """An impossible Ritz tolerance, or shifted solves cut to one FGMRES
+    iteration, end in DM_ERR_NO_CONVERGENCE with the converged prefix counted
+    and the Ritz values returned."""
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    k2, B, rep, st = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors="host", **opts)
+    assert st == 2 and 0 <= rep["n_converged"] < w.nev, rep
+    assert rep["restarts"] == 1 and np.all(np.isfinite(k2)) and np.all(np.isfinite(B))

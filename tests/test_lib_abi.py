@@ -61,3 +61,42 @@ def test_no_cpu_fallback_in_package():
             src = open(os.path.join(pkg, f)).read()
             assert "oracle" not in src.replace("oracle.", ""), f
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_eig_params_tail_fields_keep_their_c_offsets(lib):
+    """max_seconds, the last field, sits where the C struct has it: the C
+    default routine overwrites a value planted there through ctypes."""
+    from paper_1301_3794_gb300._lib import EigParams
+    p = EigParams()
+    p.max_seconds = 5.0
+    p.learned = 1234
+    lib.dm_eig_params_default(C.byref(p))
+    assert p.max_seconds == 0.0 and not p.learned
+
+
+def test_allocation_counter_needs_no_gpu(lib):
+    assert lib.dm_debug_allocation_count() >= 0
+
+
+def test_apply_noalloc_checks_both_tensors_before_any_library_call():
+    """x and out must be contiguous float64 tensors of the level's face count on
+    the operator's device; anything else is refused on the host, before the
+    library (and the GPU) sees a pointer."""
+    import types
+
+    import numpy as np
+    import torch
+
+    import paper_1301_3794_gb300 as dm
+    calls = []
+    op = dm.Operator.__new__(dm.Operator)
+    op.ctx = types.SimpleNamespace(device=0, check=lambda *a: calls.append(a))
+    op.h = None
+    op._faces = lambda level: 10
+    good = torch.zeros(10, dtype=torch.float64)   # a CPU tensor: refused as not on cuda:0
+    for bad_x in (np.zeros(10), good, torch.zeros(10, dtype=torch.float32), torch.zeros(12, dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            op.apply_noalloc(bad_x)
+    with pytest.raises(ValueError):
+        op.apply_noalloc(good, out=torch.zeros(10, dtype=torch.float32))
+    assert calls == []

@@ -46,3 +46,30 @@ def test_noalloc_rejects_levels_beyond_the_scratch(dm, ctx):
     F1 = geom.level_info(1)["faces"]
     x1 = torch.from_numpy(np.random.default_rng(1).standard_normal(F1)).cuda()
     assert _rel(op.apply_noalloc(x1, level=1).cpu().numpy(), op.apply(x1, level=1).cpu().numpy()) < 1e-13
+
+
+def test_noalloc_creates_no_buffer_event_or_stream(dm, ctx):
+    """The property the entry point exists for: after its first call on the
+    device (which only looks up the scratch's address), further calls leave the
+    library's count of created device buffers, pinned buffers, events, streams
+    and graphs unchanged, even while kernel tracing is on."""
+    import torch
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=5.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma)
+    F = geom.level_info(0)["faces"]
+    x = torch.from_numpy(np.random.default_rng(3).standard_normal(F)).cuda()
+    y = torch.empty_like(x)
+    op.apply_noalloc(x, out=y)
+    ctx.trace(True)
+    try:
+        before = dm.lib.dm_debug_allocation_count()
+        for _ in range(3):
+            op.apply_noalloc(x, out=y)
+        after = dm.lib.dm_debug_allocation_count()
+    finally:
+        ctx.trace(False)
+    assert after == before, (before, after)
+    # the calls were not traced (tracing would have created events)
+    assert ctx.trace_stats() == {}
+    assert _rel(y.cpu().numpy(), op.apply(x).cpu().numpy()) < 1e-13
