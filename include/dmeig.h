@@ -94,10 +94,15 @@ typedef struct dm_eig_params {
     const dm_learned* learned; /* nullable: learned correction after each V-cycle (see dm_learned_*) */
     double max_seconds;    /* wall-clock limit of one eigensolve, setup included; 0 = none (0).  Checked
                               before every shifted solve: a solve that runs out returns DM_ERR_TIMEOUT */
+    double rho_tol;        /* certificate every returned pair must meet, rho = ||K b - k^2 A b|| /
+                              (k^2 ||A b||) in FP64 (1e-8; 0 = Ritz estimates only).  When the Ritz
+                              estimates call the nev pairs converged but a certificate misses rho_tol,
+                              tol and inner_tol are divided by 10 (down to 1e-15 and 1e-13) and the
+                              Krylov-Schur iteration continues */
 } dm_eig_params;
 
 typedef struct dm_eig_report {
-    int n_converged;       /* leading eigenpairs that met tol */
+    int n_converged;       /* leading eigenpairs (nearest sigma first) that met tol and rho_tol */
     int outer_iters;       /* Krylov-Schur expansion steps (= shifted solves) */
     int restarts;
     int inner_iters;       /* FGMRES iterations summed over all shifted solves */
@@ -159,7 +164,8 @@ void dm_geometry_destroy(dm_geometry* geom);
 
 /* Multigrid levels available below (and including) the fine grid. */
 int dm_geometry_num_levels(const dm_geometry* geom);
-/* dims[3] = cells of `level`; counts[4] = natural faces F, edges E, cells, open faces. */
+/* dims[3] = cells of `level`; counts[4] = natural faces F, edges E, cells, open faces.
+ * Counts are kept from the geometry's creation: the call launches nothing. */
 dm_status dm_geometry_level_info(const dm_geometry* geom, int level, int dims[3], long long counts[4]);
 /* Copy the fractions of `level` out in natural layouts: L (E), A (F), V (cells).
  * Any pointer may be NULL.  Host or device per on_device. */

@@ -167,10 +167,15 @@ class Geometry:
         return lib.dm_geometry_num_levels(self.h)
 
     def level_info(self, level=0):
-        dims = (C.c_int * 3)()
-        counts = (C.c_longlong * 4)()
-        self.ctx.check(lib.dm_geometry_level_info(self.h, level, dims, counts), "dm_geometry_level_info")
-        return {"dims": tuple(dims), "faces": counts[0], "edges": counts[1], "cells": counts[2], "open": counts[3]}
+        """Dims and counts of a level (cached: a level never changes)."""
+        cache = self.__dict__.setdefault("_info", {})
+        if level not in cache:
+            dims = (C.c_int * 3)()
+            counts = (C.c_longlong * 4)()
+            self.ctx.check(lib.dm_geometry_level_info(self.h, level, dims, counts), "dm_geometry_level_info")
+            cache[level] = {"dims": tuple(dims), "faces": counts[0], "edges": counts[1], "cells": counts[2],
+                            "open": counts[3]}
+        return dict(cache[level])
 
     def fractions(self, level=0):
         """(L, A, V) in natural layouts as numpy arrays."""
@@ -400,7 +405,8 @@ class Learned:
 
 
 def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
-               inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, **mg):
+               inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, rho_tol=1e-8,
+               **mg):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     p.sigma = float(sigma)
@@ -416,6 +422,7 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.mg = mg_params(**mg)
     p.learned = learned.h if learned is not None else None
     p.max_seconds = float(max_seconds)
+    p.rho_tol = float(rho_tol)
     return p
 
 

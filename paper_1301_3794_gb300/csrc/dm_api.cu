@@ -119,7 +119,7 @@ struct GeoLevel {
     DBuf<int> band;
     int nband = 0;
     DBuf<unsigned char> active;
-    int nopen = 0;
+    int nopen = 0;       // open faces (counted once at creation)
     DBuf<int> tiles;     // active tiles (ascending)
     int ntiles = 0;
     Domain vdom() const { return Domain{g, tiles.get(), ntiles, 3}; }   // face vectors
@@ -1384,6 +1384,7 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
                 lv->tiles.alloc(nt);
                 lv->ntiles = geom_tiles(lv->g, lv->A.get(), lv->active.get(), lv->tiles.get(), tflags.get(), cnt.get(), s);
             }
+            lv->nopen = count_positive(n3, lv->A.get(), cnt.get(), s);
             geom->lv.push_back(std::move(lv));
             if (!can_coarsen(cx, cy, cz, 4)) break;
             cx /= 2; cy /= 2; cz /= 2;
@@ -1413,8 +1414,7 @@ dm_status dm_geometry_level_info(const dm_geometry* geom, int level, int dims[3]
             counts[0] = natural_faces(g.g);
             counts[1] = natural_edges(g.g);
             counts[2] = natural_cells(g.g);
-            DBuf<int> cnt(1);
-            counts[3] = count_positive(3ll * g.g.np, g.A.get(), cnt.get(), geom->ctx->stream);
+            counts[3] = g.nopen;
         }
     });
 }
@@ -1692,6 +1692,7 @@ void dm_eig_params_default(dm_eig_params* p) {
     dm_mg_params_default(&p->mg);
     p->learned = nullptr;
     p->max_seconds = 0.0;
+    p->rho_tol = 1e-8;
 }
 
 }  // extern "C"
@@ -1794,6 +1795,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         int m = p.basis > 0 ? p.basis : std::min(64, std::max(2 * p.nev + 10, 24));
         DM_REQUIRE(m >= p.nev + 2 && m <= 64, DM_ERR_INVALID_ARG, "basis must be in [nev + 2, 64]");
         DM_REQUIRE(p.max_seconds >= 0.0, DM_ERR_INVALID_ARG, "max_seconds must be >= 0");
+        DM_REQUIRE(p.rho_tol >= 0.0, DM_ERR_INVALID_ARG, "rho_tol must be >= 0");
+        DM_REQUIRE(p.tol > 0.0 && p.inner_tol > 0.0, DM_ERR_INVALID_ARG, "tol and inner_tol must be > 0");
         const double t_setup0 = now_s();
         auto out_of_time = [&] { return p.max_seconds > 0.0 && now_s() - t_setup0 > p.max_seconds; };
         dm_operator* op = nullptr;
@@ -1825,6 +1828,22 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         int k = 0, restarts = 0, outer = 0, inner_total = 0, proj_total = 0, nconv = 0, proj_capped = 0;
         std::vector<double> theta, Y, est;
         std::vector<int> order;
+        // Ritz and inner tolerances in force: both tighten by 10 whenever the
+        // Ritz estimates call the wanted pairs converged but their FP64
+        // certificate rho (the residual of K b = k^2 A b itself) misses rho_tol
+        double tol_eff = p.tol, inner_eff = p.inner_tol;
+        int cert_retries = 0;
+        // rho of the wanted Ritz pairs (|theta| order) from the current basis
+        auto certify_wanted = [&](std::vector<double>& rho_out) {
+            std::vector<double> Yw((size_t)m * p.nev), kk(p.nev);
+            for (int c = 0; c < p.nev; ++c)
+                for (int r = 0; r < m; ++r) Yw[(size_t)c * m + r] = Y[(size_t)r * m + order[c]];
+            DBuf<double> Yd((size_t)m * p.nev);
+            DM_CUDA(cudaMemcpyAsync(Yd.get(), Yw.data(), sizeof(double) * m * p.nev, cudaMemcpyHostToDevice, s));
+            vgemm(D, m, p.nev, V, n, Yd.get(), m, tmp.get(), n, s);
+            rho_out.assign(p.nev, 0.0);
+            certify_padded(ctx, g0, p.nev, tmp.get(), kk.data(), true, rho_out.data(), nullptr, nullptr);
+        };
         while (true) {
             for (int j = k; j < m; ++j) {
                 if (out_of_time()) {
@@ -1834,7 +1853,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 double* vj = V + (size_t)j * n;
                 hadamard(D, a, vj, rhs.get(), s);           // A v_j
                 double rr = 0.0;
-                inner_total += solve_vec(op, rhs.get(), x.get(), p.inner_tol, p.inner_restart, p.inner_maxit, &rr);
+                inner_total += solve_vec(op, rhs.get(), x.get(), inner_eff, p.inner_restart, p.inner_maxit, &rr);
                 double* w = V + (size_t)(j + 1) * n;
                 const int pit = project(op, x.get(), w, p.proj_tol);   // w = P_DM (K - sigma A)^-1 A v_j
                 proj_total += pit;
@@ -1874,7 +1893,20 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             est.assign(m, 0.0);
             nconv = 0;
             for (int i = 0; i < m; ++i) est[i] = std::fabs(beta_m * Y[(size_t)(m - 1) * m + order[i]]);
-            while (nconv < p.nev && est[nconv] <= p.tol * std::fabs(theta[order[nconv]])) ++nconv;
+            while (nconv < p.nev && est[nconv] <= tol_eff * std::fabs(theta[order[nconv]])) ++nconv;
+            if (nconv >= p.nev && p.rho_tol > 0.0) {
+                std::vector<double> rho_w;
+                certify_wanted(rho_w);
+                bool all_ok = true;
+                for (double r : rho_w) all_ok = all_ok && r <= p.rho_tol;
+                if (!all_ok && restarts < p.max_restarts && tol_eff > 1e-15) {
+                    tol_eff *= 0.1;
+                    inner_eff = std::max(inner_eff * 0.1, 1e-13);
+                    ++cert_retries;
+                    nconv = 0;
+                    while (nconv < p.nev && est[nconv] <= tol_eff * std::fabs(theta[order[nconv]])) ++nconv;
+                }
+            }
             if (nconv >= p.nev || restarts >= p.max_restarts) break;
             // thick restart: keep the pk wanted Ritz vectors
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
@@ -1939,6 +1971,12 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             launch("k_sign_fix", k_sign_fix, (int)std::min<long long>((n + 255) / 256, 1216), 256, 0, s, n, b, sign.get());
         }
         certify_padded(ctx, g0, nev, tmp.get(), k2.data(), true, rho.data(), delta.data(), rq.data());
+        if (p.rho_tol > 0.0) {
+            // the converged prefix (|theta| order) also needs its certificate
+            int nc = 0;
+            while (nc < nconv && rho[nc] <= p.rho_tol) ++nc;
+            nconv = nc;
+        }
         // ascending k^2
         std::vector<int> asc(nev);
         std::iota(asc.begin(), asc.end(), 0);

@@ -124,3 +124,17 @@ def test_unreachable_targets_return_a_partial_result(dm, ctx, opts):
     k2, B, rep, st = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors="host", **opts)
     assert st == 2 and 0 <= rep["n_converged"] < w.nev, rep
     assert rep["restarts"] == 1 and np.all(np.isfinite(k2)) and np.all(np.isfinite(B))
+
+
+def test_certificate_tolerance_is_enforced(dm, ctx):
+    """With rho_tol below what the default tolerances deliver, the solver
+    tightens them and keeps iterating until every returned pair's FP64
+    certificate meets rho_tol; rho_tol = 0 returns on the Ritz estimates."""
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0)
+    geom = dm.Geometry.from_workload(ctx, w)
+    k2a, _, repa, sta = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, rho_tol=0.0)
+    k2b, _, repb, stb = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, rho_tol=1e-12)
+    assert sta == 0 and stb == 0, (repa, repb)
+    assert repb["rho_max"] <= 1e-12 and repb["n_converged"] == w.nev, repb
+    assert repb["inner_iters"] >= repa["inner_iters"]
+    assert np.max(np.abs(k2a - k2b) / k2b) < 1e-10

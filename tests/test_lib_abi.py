@@ -69,9 +69,10 @@ def test_eig_params_tail_fields_keep_their_c_offsets(lib):
     from paper_1301_3794_gb300._lib import EigParams
     p = EigParams()
     p.max_seconds = 5.0
+    p.rho_tol = 5.0
     p.learned = 1234
     lib.dm_eig_params_default(C.byref(p))
-    assert p.max_seconds == 0.0 and not p.learned
+    assert p.max_seconds == 0.0 and not p.learned and p.rho_tol == 1e-8
 
 
 def test_allocation_counter_needs_no_gpu(lib):
