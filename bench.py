@@ -1,13 +1,14 @@
 """Throughput benchmark: converged Dey--Mittra eigenpairs per second on one GB300.
 
-Workload (the paper's spherical-cavity test, Sec. 6.2, at the larger grid of the
-plain-method configuration): a PEC sphere of radius 1 in [-1.1, 1.1]^3 on a
-128^3 Yee grid, centre moved by a seeded sub-cell offset, the 10 electromagnetic
-modes nearest sigma = 5 (the 10 lowest), residual <= 1e-8.  One step = geometry
-+ multigrid setup + Krylov--Schur eigensolve + FP64 certification of every
-returned eigenpair.  The headline uses the mixed-precision form (FP32 V-cycle
-inside FP64 FGMRES / FP64 Krylov--Schur); the plain FP64 multigrid is timed in
-the same run for comparison.
+Headline workload (the mixed-precision configuration): a seeded PEC ellipsoid
+(semi-axes U[0.6, 1.0]) on a 192^3 Yee grid with a seeded sub-cell offset, the
+16 electromagnetic modes nearest sigma = 5, every returned pair certified at
+rho = ||K b - k^2 A b|| / (k^2 ||A b||) <= 1e-8.  One step = geometry +
+multigrid setup + Krylov--Schur eigensolve + FP64 certification.  The headline
+runs the V-cycle in FP32 inside FP64 FGMRES / FP64 Krylov--Schur; the plain FP64
+multigrid is timed over the same steps and warm-up in the same run, and a BF16
+V-cycle beside it, with every eigenvalue's error against the FP64 result.
+``--workload sphere|batch|ninecell`` runs the other configurations.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -41,17 +42,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "ellipsoid", "batch", "ninecell"],
-                    help="sphere: 128^3 PEC sphere, 10 modes (the headline); ellipsoid: seeded ellipsoid on 192^3, "
-                         "16 modes; batch: 48 seeded cavities of 32^3-96^3 with 1-4 shifts each, batched solve; "
-                         "ninecell: synthetic 9-cell cavity on 96x96x1152, 20 modes, with and without the learned "
-                         "smoother")
+    ap.add_argument("--workload", default="ellipsoid", choices=["sphere", "ellipsoid", "batch", "ninecell"],
+                    help="ellipsoid: seeded ellipsoid on 192^3, 16 modes, FP32 and BF16 V-cycles against the plain "
+                         "FP64 multigrid (the headline); sphere: 128^3 PEC sphere, 10 modes; batch: 48 seeded "
+                         "cavities of 32^3-96^3 with 1-4 shifts each, batched solve; ninecell: synthetic 9-cell "
+                         "cavity on 96x96x1152, 20 modes, with and without the learned smoother")
     ap.add_argument("--grid", type=int, default=None)
     ap.add_argument("--nev", type=int, default=None)
     ap.add_argument("--sigma", type=float, default=5.0)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--count", type=int, default=0, help="batch: solve only the first COUNT cavities")
-    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arm")
+    ap.add_argument("--bf16-steps", type=int, default=3, help="timed steps of the BF16 V-cycle arm (0: skip)")
+    ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
     if a.grid is None:
@@ -81,7 +84,7 @@ def describe(args, w):
 
 def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
-         "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma,
+         "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:
@@ -212,78 +215,40 @@ def nvtx_mark(start):
         pass
 
 
-def stencil_bytes_per_cell(name):
-    """Bytes per grid cell of one vector-stencil launch that streams every cell
-    once: x (3 values) read, y (3) written, f (3) read for resid and jacobi;
-    coefficients A (3), L (3), 1/V (1) and 1/D (3, jacobi only)."""
-    parts = name.split("_")
-    prec, mode = parts[2], parts[3]
-    tv = {"f64": 8, "f32": 4, "bf16": 2}[prec]
-    tc = 8 if prec == "f64" else 4
-    vec = 3 * tv * (2 + (1 if mode in ("resid", "jacobi") else 0))
-    coef = tc * (7 + (3 if mode == "jacobi" else 0))
-    return vec + coef
-
-
-def stencil_bytes_per_open_face(name):
-    """Algorithmic bytes per OPEN face of one vector-stencil launch (conductor
-    regions excluded): the face's x, y and (resid / jacobi) f, its A and 1/D
-    (jacobi), about one edge fraction L and a third of a 1/V per face."""
-    parts = name.split("_")
-    prec, mode = parts[2], parts[3]
-    tv = {"f64": 8, "f32": 4, "bf16": 2}[prec]
-    tc = 8 if prec == "f64" else 4
-    vec = tv * (2 + (1 if mode in ("resid", "jacobi") else 0))
-    coef = tc * (2 + (1 if mode == "jacobi" else 0)) + tc / 3.0
-    return vec + coef
-
+# DRAM bytes (read + write) per launch from ncu captures of the same kernel:
+# (trace name, workload, grid, level-0 stencil shape) -> bytes.  The profiles/
+# summaries hold the captures and their commands; a kernel or shape without a
+# capture reports null.
+PROFILED_TRAFFIC = {}
 
 # Algorithmic FP64 operations of one K - sigma A evaluation per open face:
 # about 66 per cell of 3 faces (two curls, the grad-div and the shift).
 APPLY_FLOPS_PER_FACE = 22.0
-FP64_PEAK_TFLOPS = 1.204      # FP64 FMA-loop probe on a GB300 (measured rate, TFLOP/s)
 
 
-# DRAM bytes (read + write) per launch of the fine-level stencil, from an ncu
-# capture of that kernel on the same cavity: (trace name, level-0 tile shape,
-# workload, grid) -> bytes.  profiles/stencil_jacobi_sphere128.md has the
-# capture and its command; a shape without a capture reports null.
-PROFILED_TRAFFIC = {
-    ("vec_stencil_f32_jacobi_L0", 0, "sphere", 128): 90_759_424 + 5_890_304,
-}
-
-
-def roofline(stats, open_faces, hbm_peak, peak_kind, precision="f32", traffic=None):
-    """Fine-level V-cycle smoothing stencil (the metric's V-cycle kernel):
-    algorithmic bytes per launch (open faces only) over its event-timed mean
-    duration."""
-    name = f"vec_stencil_{precision}_jacobi_L0"
-    if name not in stats:
-        cands = {k: v for k, v in stats.items() if k.startswith("vec_stencil") and k.endswith("_L0")}
-        if not cands:
-            return None
-        name = max(cands.items(), key=lambda kv: kv[1][1])[0]
-    launches, ms = stats[name]
-    avg_s = ms / launches * 1e-3
-    bytes_per_launch = stencil_bytes_per_open_face(name) * open_faces
-    achieved = bytes_per_launch / avg_s / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-            "bytes_per_launch": int(bytes_per_launch), "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches,
-            "peak_kind": f"{peak_kind} (copy)", "unit_of_work": "open face"}
-
-
-def roofline_fp64_apply(stats, open_faces):
-    """The FP64 outer K - sigma A apply: bounded by GB300's FP64 pipes."""
-    name = "vec_stencil_f64_apply_L0"
-    if name not in stats:
-        return None
-    launches, ms = stats[name]
-    avg_s = ms / launches * 1e-3
-    tf = APPLY_FLOPS_PER_FACE * open_faces / avg_s / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "avg_launch_us": round(avg_s * 1e6, 2), "launches": launches,
-            "peak_kind": "measured FP64 FMA probe"}
+def rooflines(stats, hbm_peak, peak_kind, fp64_tflops, open_faces, top=8, key=None):
+    """Per-kernel roofline of the top kernels by time in the traced step:
+    achieved = the library's algorithmic bytes of the kernel's launches over
+    their summed CUDA-event duration (on the library's stream).  The FP64
+    operator apply is also given against the measured FP64 FMA rate."""
+    total_ms = sum(v[1] for v in stats.values())
+    out = []
+    for name, (launches, ms, by) in sorted(stats.items(), key=lambda kv: -kv[1][1])[:top]:
+        ent = {"kernel": name, "share": round(ms / total_ms, 4), "launches": launches,
+               "avg_launch_us": round(ms / launches * 1e3, 2)}
+        if by > 0:
+            gbs = by / (ms * 1e-3) / 1e9
+            ent.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                        "frac": round(gbs / hbm_peak, 4), "bytes_per_launch": int(by / launches),
+                        "peak_kind": f"{peak_kind} (copy)",
+                        "traffic": PROFILED_TRAFFIC.get((name,) + (key or ()))})
+        if name == "vec_stencil_f64_apply_L0" and fp64_tflops:
+            tf = APPLY_FLOPS_PER_FACE * open_faces * launches / (ms * 1e-3) / 1e12
+            ent["alu"] = {"bound": "alu", "achieved": round(tf, 4), "peak": round(fp64_tflops, 4),
+                          "unit": "TFLOP/s", "frac": round(tf / fp64_tflops, 4),
+                          "peak_kind": "measured FP64 FMA rate (dm_measure_fma_rates)"}
+        out.append(ent)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -317,40 +282,57 @@ def run_native(args):
         geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi, g.origin)
         vec = "host" if host_io else "device"
         k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
-                                       out=None if host_io else B_dev, precision=precision)
+                                       out=None if host_io else B_dev, precision=precision,
+                                       inner_tol=args.inner_tol)
         geom.close()
         return k2, rep, st
 
     def converged(rep, st):
         return rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0
 
-    for _ in range(args.warmup):
-        step(args.precision)
-    # ---- timed region: inputs resident in HBM ----
+    def timed(precision, steps, warmup, label):
+        """warmup untimed steps, then `steps` steps between CUDA events on the
+        library's stream (barrier + synchronize on both sides)."""
+        for i in range(warmup):
+            t = time.perf_counter()
+            step(precision)
+            progress(f"{label} warm-up {i + 1}/{warmup}: {time.perf_counter() - t:.2f} s")
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = ctx.launches
+        e0.record(stream)
+        units, reps, per = 0, [], []
+        for _ in range(steps):
+            t = time.perf_counter()
+            k2, rep, st = step(precision)
+            units += converged(rep, st)
+            reps.append(rep)
+            per.append(time.perf_counter() - t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        secs = e0.elapsed_time(e1) * 1e-3
+        progress(f"{label}: {steps} steps in {secs:.2f} s, {units} pairs converged")
+        return {"units": units, "secs": secs, "reps": reps, "k2": k2, "launches": ctx.launches - l0,
+                "per_step_s": per}
+
+    # ---- timed region of the headline: inputs resident in HBM ----
     clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
+    for i in range(args.warmup):
+        t = time.perf_counter()
+        step(args.precision)
+        progress(f"warm-up {i + 1}/{args.warmup}: {time.perf_counter() - t:.2f} s")
     clocks.start()
-    l0 = ctx.launches
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    units = 0
-    reps = []
     nvtx_mark(True)      # an NVTX range "timed", for profilers that filter on it
-    for _ in range(args.steps):
-        k2, rep, st = step(args.precision)
-        units += converged(rep, st)
-        reps.append(rep)
+    main = timed(args.precision, args.steps, 0, f"mixed ({args.precision} V-cycle)")
     nvtx_mark(False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
     clk = clocks.stop()
-    launches = ctx.launches - l0
-    local_s = e0.elapsed_time(e1) * 1e-3
-    tot_units, max_s = aggregate(units, local_s, device=f"cuda:{local}")
+    tot_units, max_s = aggregate(main["units"], main["secs"], device=f"cuda:{local}")
     value = tot_units / max_s
+    reps = main["reps"]
+    k2 = main["k2"]
     # ---- end-to-end through the public API with host buffers ----
     t0 = time.perf_counter()
     units_e2e = 0
@@ -360,13 +342,14 @@ def run_native(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     tot_e2e, max_e2e = aggregate(units_e2e, e2e_s, device=f"cuda:{local}")
-    # ---- one traced step: per-kernel event timings on the launching stream ----
+    progress(f"e2e: {args.steps} steps in {e2e_s:.2f} s")
+    # ---- one traced step: per-kernel event timings and algorithmic bytes ----
     ctx.trace(True)
-    k2t, rept, stt = step(args.precision)
+    step(args.precision)
     ctx.trace(False)
-    stats = ctx.trace_stats()
+    stats = ctx.trace_stats(with_bytes=True)
     hbm, kind = peaks()
-    open_faces = geom_open = None
+    fp64_tf, fp32_tf = ctx.fma_rates()
     g0info = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi_dev, g.origin)
     open_faces = g0info.level_info(0)["open"]
     # tile shapes the autotuner chose for this cavity's levels (cached in the context, so no re-timing)
@@ -374,25 +357,33 @@ def run_native(args):
     shapes = [op_info.stencil_shape(l) for l in range(op_info.num_levels - 1)]
     op_info.close()
     g0info.close()
-    traffic = PROFILED_TRAFFIC.get((f"vec_stencil_{args.precision}_jacobi_L0", shapes[0] if shapes else -1,
-                                    args.workload, args.grid))
-    roof = roofline(stats, open_faces, hbm, kind, args.precision, traffic=traffic)
-    roof64 = roofline_fp64_apply(stats, open_faces)
-    # ---- plain FP64 multigrid on the same cavity ----
-    plain = None
+    roofs = rooflines(stats, hbm, kind, fp64_tf, open_faces, key=(args.workload, args.grid, shapes[0] if shapes else -1))
+    # ---- plain FP64 multigrid on the same cavity, same steps and warm-up ----
+    plain, errs = None, {}
     if not args.no_compare and args.precision != "f64":
-        torch.cuda.synchronize()
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        k2p, repp, stp = step("f64")
-        p1.record(stream)
-        torch.cuda.synchronize()
-        ps = p0.elapsed_time(p1) * 1e-3
-        plain = {"value": round(converged(repp, stp) / ps, 4), "unit": UNIT, "ms_per_step": round(ps * 1e3, 1),
-                 "steps": 1, "inner_iters": repp["inner_iters"], "outer_iters": repp["outer_iters"],
-                 "rho_max": repp["rho_max"],
-                 "max_rel_k2_diff_vs_mixed": float(np.max(np.abs(k2p - k2) / np.abs(k2p)))}
+        p64 = timed("f64", args.steps, args.warmup, "plain FP64 multigrid")
+        k2p = p64["k2"]
+        plain = {"value": round(p64["units"] / p64["secs"], 4), "unit": UNIT,
+                 "ms_per_step": round(p64["secs"] / args.steps * 1e3, 1), "steps": args.steps,
+                 "warmup": args.warmup, "per_step_s": [round(v, 3) for v in p64["per_step_s"]],
+                 "inner_iters": p64["reps"][-1]["inner_iters"], "outer_iters": p64["reps"][-1]["outer_iters"],
+                 "rho_max": p64["reps"][-1]["rho_max"]}
+        errs[args.precision] = [float(v) for v in np.abs(k2 - k2p) / np.abs(k2p)]
+        # the BF16 V-cycle beside it (a shorter run: its errors and its rate)
+        if args.precision != "bf16" and args.bf16_steps > 0:
+            b16 = timed("bf16", args.bf16_steps, 1, "bf16 V-cycle")
+            errs["bf16"] = [float(v) for v in np.abs(b16["k2"] - k2p) / np.abs(k2p)]
+            plain["bf16"] = {"value": round(b16["units"] / b16["secs"], 4), "unit": UNIT,
+                             "ms_per_step": round(b16["secs"] / args.bf16_steps * 1e3, 1),
+                             "steps": args.bf16_steps, "warmup": 1,
+                             "inner_iters": b16["reps"][-1]["inner_iters"],
+                             "rho_max": b16["reps"][-1]["rho_max"]}
+    dominant = next((r for r in roofs if r.get("bound") == "hbm"), None)
+    roof = None
+    if dominant:
+        roof = {k: dominant[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic",
+                                         "bytes_per_launch", "avg_launch_us", "launches", "share", "peak_kind")}
+        roof["unit_of_work"] = "the library's per-kernel byte model (open faces, band rows, compact vectors)"
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(max_s / args.steps * 1e3, 2), "higher_is_better": True,
@@ -401,20 +392,24 @@ def run_native(args):
         "config": config_of(args, w, {"parallelism": f"replicas x{world}"}),
         "e2e": {"value": round(tot_e2e / max_e2e, 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(phi_host.nbytes), "d2h_bytes_per_step": int(args.nev * nf * 8)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(main["launches"]),
         "roofline": roof,
-        "roofline_fp64_apply": roof64,
+        "rooflines_top": roofs,
+        "peaks_measured": {"fp64_tflops": round(fp64_tf, 4), "fp32_tflops": round(fp32_tf, 2),
+                           "how": "dm_measure_fma_rates: FMA-chain loop, CUDA events, this run"},
         "clocks": clk,
         "solver": {"inner_iters_per_step": reps[-1]["inner_iters"], "outer_iters": reps[-1]["outer_iters"],
                    "restarts": reps[-1]["restarts"], "proj_iters": reps[-1]["proj_iters"],
                    "mg_levels": reps[-1]["mg_levels"], "mg_complexity": round(reps[-1]["mg_complexity"], 3),
                    "rho_max": reps[-1]["rho_max"], "delta_max": reps[-1]["delta_max"],
                    "k2": [round(float(v), 10) for v in k2],
-                   "inner_rate": None, "stencil_shapes": shapes,
+                   "inner_rate": None, "stencil_shapes": shapes, "open_faces": int(open_faces),
+                   "per_step_s": [round(v, 3) for v in main["per_step_s"]],
                    # one shifted FGMRES solve (K - sigma A) x = A v per Krylov-Schur step
                    "solves_per_s": round(sum(r["outer_iters"] for r in reps) * world / max_s, 3)},
         "plain_f64": plain,
-        "kernels_top": {k: {"launches": c, "ms": round(ms, 3)} for k, (c, ms) in
+        "rel_k2_error_vs_f64": errs,
+        "kernels_top": {k: {"launches": c, "ms": round(ms, 3), "bytes": int(by)} for k, (c, ms, by) in
                         sorted(stats.items(), key=lambda kv: -kv[1][1])[:16]},
     }
     if reps[-1]["inner_iters"] and reps[-1]["outer_iters"]:
@@ -613,14 +608,21 @@ def run_ninecell(args):
 CPU_SAMPLE_GRID = 24
 
 
+def sample_workload(args):
+    """The bounded host sample of the workload: the same cavity family (same
+    seeds, shape recipe, sigma and mode count) at CPU_SAMPLE_GRID^3 cells."""
+    import workloads as W
+    if args.workload == "ellipsoid":
+        return W.ellipsoid_workload(CPU_SAMPLE_GRID, seed=W.SEED_BASE + 3, sigma=args.sigma, nev=args.nev)
+    return W.sphere_workload(CPU_SAMPLE_GRID, radius=1.0, half_width=1.1, sigma=args.sigma, nev=args.nev,
+                             offset_seed=W.SEED_BASE + 2)
+
+
 def oracle_step(args):
     """One bounded sample of the workload on the host: the oracle's sparse
-    shift-invert eigensolve of the same cavity family (same radius, domain,
-    offset seed, sigma and mode count) at 32^3 cells."""
-    import workloads as W
+    shift-invert eigensolve of the sample cavity, every pair certified."""
     from oracle import eigen, geometry, operators
-    w = W.sphere_workload(CPU_SAMPLE_GRID, radius=1.0, half_width=1.1, sigma=args.sigma, nev=args.nev,
-                          offset_seed=W.SEED_BASE + 2)
+    w = sample_workload(args)
     t0 = time.perf_counter()
     ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
     k2, B, _ = eigen.shift_invert_modes(ops, w.sigma, w.nev)
@@ -644,8 +646,8 @@ def cpu_baseline(args, reps=1):
         units += u
         secs += s
     return {"value": round(units / secs, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (scipy SuperLU + ARPACK shift-invert, single-threaded) on the same sphere family at "
-                       f"{CPU_SAMPLE_GRID}^3 cells, {args.nev} modes, sigma={args.sigma}; {reps} solve(s), "
+            "sample": (f"oracle (scipy SuperLU + ARPACK shift-invert, single-threaded) on the same {args.workload} "
+                       f"family at {CPU_SAMPLE_GRID}^3 cells, {args.nev} modes, sigma={args.sigma}; {reps} solve(s), "
                        f"{secs:.1f} s; host has {cpu_info()} cores available")}
 
 
@@ -670,8 +672,8 @@ def run_reference(args):
            "data": "synthetic (seeded level set)",
            "config": config_of(args, w, {"parallelism": "host oracle", "sample_grid": [CPU_SAMPLE_GRID] * 3}),
            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": (f"each step: the oracle's sparse shift-invert eigensolve of the same sphere "
-                                       f"family at {CPU_SAMPLE_GRID}^3 cells ({args.nev} modes); "
+                            "sample": (f"each step: the oracle's sparse shift-invert eigensolve of the same "
+                                       f"{args.workload} family at {CPU_SAMPLE_GRID}^3 cells ({args.nev} modes); "
                                        f"{cpu_info()} host cores available, SuperLU/ARPACK single-threaded")},
            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -145,6 +145,17 @@ dm_status dm_trace_enable(dm_context* ctx, int on);
 int dm_trace_count(dm_context* ctx);
 /* Entry i: kernel name (copied into name[name_cap]), launches, summed device ms. */
 dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long long* launches, double* total_ms);
+/* Entry i: algorithmic DRAM bytes of its launches, summed, by the library's
+ * per-kernel model (the bytes a launch must read and write at least, counted
+ * on the elements that can be nonzero: open faces, band rows, active cells,
+ * compact Krylov vectors); 0 for kernels without a model. */
+dm_status dm_trace_entry_bytes(dm_context* ctx, int i, double* bytes);
+/* FMA issue rates of the context's device, in TFLOP/s (2 flops per FMA), from
+ * a register-resident loop of independent FMA chains timed with CUDA events
+ * (best of 3 after a warm-up launch; about 0.1 s).  They are the peaks the
+ * ALU-bound kernels (the FP64 operator apply) are measured against.  Either
+ * pointer may be NULL. */
+dm_status dm_measure_fma_rates(dm_context* ctx, double* fp64_tflops, double* fp32_tflops);
 
 /* ---- geometry (Sec. 2, Eq. farInt / Fig. dmFace; Sec. 5.1, Eq. divBInt /
  *      Fig. dmVol; Sec. 6.1 tetrahedral cut volumes) ------------------------ */

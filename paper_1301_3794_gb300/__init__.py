@@ -105,8 +105,9 @@ class Context:
         """Start (clearing earlier statistics) or stop per-kernel event timing."""
         self.check(lib.dm_trace_enable(self.h, int(bool(on))), "dm_trace_enable")
 
-    def trace_stats(self):
-        """{kernel name: (launches, total device ms)} recorded while tracing."""
+    def trace_stats(self, with_bytes=False):
+        """{kernel name: (launches, total device ms)} recorded while tracing;
+        with_bytes adds the summed algorithmic bytes of the launches."""
         out = {}
         buf = C.create_string_buffer(128)
         n = lib.dm_trace_count(self.h)
@@ -114,8 +115,19 @@ class Context:
             cnt = C.c_longlong()
             ms = C.c_double()
             self.check(lib.dm_trace_entry(self.h, i, buf, 128, C.byref(cnt), C.byref(ms)), "dm_trace_entry")
-            out[buf.value.decode()] = (cnt.value, ms.value)
+            if with_bytes:
+                by = C.c_double()
+                self.check(lib.dm_trace_entry_bytes(self.h, i, C.byref(by)), "dm_trace_entry_bytes")
+                out[buf.value.decode()] = (cnt.value, ms.value, by.value)
+            else:
+                out[buf.value.decode()] = (cnt.value, ms.value)
         return out
+
+    def fma_rates(self):
+        """(FP64, FP32) FMA issue rates of the device in TFLOP/s (measured)."""
+        r64, r32 = C.c_double(), C.c_double()
+        self.check(lib.dm_measure_fma_rates(self.h, C.byref(r64), C.byref(r32)), "dm_measure_fma_rates")
+        return r64.value, r32.value
 
     def _adopt(self, obj):
         """Record a geometry, operator or network made on this context: the C

@@ -54,6 +54,8 @@ SIGNATURES = {
     "dm_trace_enable": (C.c_int, [_P, C.c_int]),
     "dm_trace_count": (C.c_int, [_P]),
     "dm_trace_entry": (C.c_int, [_P, C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
+    "dm_trace_entry_bytes": (C.c_int, [_P, C.c_int, C.POINTER(C.c_double)]),
+    "dm_measure_fma_rates": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dm_geometry_create": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      _D, _P, C.c_int, C.c_double, C.POINTER(_P)]),
     "dm_geometry_destroy": (None, [_P]),

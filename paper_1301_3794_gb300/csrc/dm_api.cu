@@ -45,7 +45,7 @@ cudaEvent_t Tracer::get_event() {
 int Tracer::stat_index(const char* name) {
     for (size_t i = 0; i < stats.size(); ++i)
         if (stats[i].name == name) return (int)i;
-    stats.push_back(Stat{name, 0, 0.0});
+    stats.push_back(Stat{name, 0, 0.0, 0.0});
     return (int)stats.size() - 1;
 }
 void Tracer::begin(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
@@ -54,9 +54,11 @@ void Tracer::begin(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1) {
     *e1 = get_event();
     DM_CUDA(cudaEventRecord(*e0, s));
 }
-void Tracer::end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+void Tracer::end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, double bytes) {
     DM_CUDA(cudaEventRecord(e1, s));
-    pending.push_back({stat_index(name), {e0, e1}});
+    const int i = stat_index(name);
+    stats[i].bytes += bytes;
+    pending.push_back({i, {e0, e1}});
 }
 void Tracer::resolve() {
     for (auto& p : pending) {
@@ -254,6 +256,7 @@ struct OpLevel {
     DBuf<float> sd_v32;
     int sd_nsub = 0, sd_ncopies = 0, sd_maxrows = 0, sd_maxbox = 0;
     int sd_cls_first[kSchwarzClasses] = {}, sd_cls_count[kSchwarzClasses] = {};
+    long long sd_cls_copies[kSchwarzClasses] = {}, sd_cls_owned[kSchwarzClasses] = {};
     bool sd_fixed = false;
 };
 
@@ -343,6 +346,8 @@ BandSchwarz<TC> schwarz_view(const OpLevel& o, const TC* vals) {
     for (int k = 0; k < kSchwarzClasses; ++k) {
         b.cls_first[k] = o.sd_cls_first[k];
         b.cls_count[k] = o.sd_cls_count[k];
+        b.cls_copies[k] = o.sd_cls_copies[k];
+        b.cls_owned[k] = o.sd_cls_owned[k];
     }
     return b;
 }
@@ -1027,6 +1032,8 @@ void setup_operator(dm_operator* op) {
             for (int k = 0; k < kSchwarzClasses; ++k) {
                 o.sd_cls_first[k] = sl.cls_first[k];
                 o.sd_cls_count[k] = sl.cls_count[k];
+                o.sd_cls_copies[k] = sl.cls_copies[k];
+                o.sd_cls_owned[k] = sl.cls_owned[k];
             }
             switch (op->mg.precision) {
                 case DM_PREC_F64: band_schwarz_prepare<double, double>(sl); break;
@@ -1324,6 +1331,26 @@ dm_status dm_trace_entry(dm_context* ctx, int i, char* name, int name_cap, long 
 }
 long long dm_context_launch_count(const dm_context* ctx) { return ctx ? ctx->launches : 0; }
 
+dm_status dm_measure_fma_rates(dm_context* ctx, double* fp64_tflops, double* fp32_tflops) {
+    if (!ctx) return DM_ERR_INVALID_ARG;
+    return guarded(ctx, [&] {
+        DM_CUDA(cudaSetDevice(ctx->device));
+        double r64 = 0.0, r32 = 0.0;
+        probe_fma_rates(ctx->stream, &r64, &r32);
+        if (fp64_tflops) *fp64_tflops = r64 * 1e-12;
+        if (fp32_tflops) *fp32_tflops = r32 * 1e-12;
+    });
+}
+
+dm_status dm_trace_entry_bytes(dm_context* ctx, int i, double* bytes) {
+    if (!ctx || i < 0 || !bytes) return DM_ERR_INVALID_ARG;
+    return guarded(ctx, [&] {
+        ctx->tracer.resolve();
+        DM_REQUIRE(i < (int)ctx->tracer.stats.size(), DM_ERR_INVALID_ARG, "trace entry out of range");
+        *bytes = ctx->tracer.stats[i].bytes;
+    });
+}
+
 long long dm_debug_allocation_count(void) { return g_allocations.load(std::memory_order_relaxed); }
 
 dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
@@ -1385,6 +1412,8 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
                 lv->ntiles = geom_tiles(lv->g, lv->A.get(), lv->active.get(), lv->tiles.get(), tflags.get(), cnt.get(), s);
             }
             lv->nopen = count_positive(n3, lv->A.get(), cnt.get(), s);
+            lv->g.nopen = lv->nopen;
+            lv->g.nact = count_flags(n1, lv->active.get(), cnt.get(), s);
             geom->lv.push_back(std::move(lv));
             if (!can_coarsen(cx, cy, cz, 4)) break;
             cx /= 2; cy /= 2; cz /= 2;

@@ -286,7 +286,10 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
     std::stable_sort(runs.begin(), runs.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
         return schwarz_class(a.second - a.first) < schwarz_class(b.second - b.first);
     });
-    for (int k = 0; k < kSchwarzClasses; ++k) out.cls_first[k] = out.cls_count[k] = 0;
+    for (int k = 0; k < kSchwarzClasses; ++k) {
+        out.cls_first[k] = out.cls_count[k] = 0;
+        out.cls_copies[k] = out.cls_owned[k] = 0;
+    }
     out.copy.reserve(nc);
     out.pos.reserve(nc);
     for (size_t rI = 0; rI < runs.size(); ++rI) {
@@ -314,9 +317,11 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         out.dims.push_back(l[0] | (l[1] << 10) | (l[2] << 20));
         out.maxrows = std::max(out.maxrows, c1 - c0);
         out.maxbox = std::max(out.maxbox, 3 * l[0] * l[1] * l[2]);
+        out.cls_copies[cl] += c1 - c0;
         for (int c = c0; c < c1; ++c) {
             const int t = cp[c].t;
             const int comp = cp[c].q / g.np;
+            if (cp[c].owned) ++out.cls_owned[cl];
             const int li = node[3 * t] - lo[0], lj = node[3 * t + 1] - lo[1], lk = node[3 * t + 2] - lo[2];
             out.copy.push_back(cp[c].owned ? t : -1 - t);
             out.pos.push_back(((comp * l[2] + lk) * l[1] + lj) * l[0] + li);
@@ -364,15 +369,25 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
         const int first = single ? 0 : bs.cls_first[cl];
         const int count = single ? bs.nsub : bs.cls_count[cl];
         const size_t smem = schwarz_smem<T>(bs.maxbox, bs.maxrows, R);
+        // bytes: per row copy its 15 coefficients, copy and pos words, and the
+        // row's x, f and 1/D (the slot gathers of x hit the row's neighbours,
+        // which are other copies' rows); per owned copy the correction u
+        long long copies = 0, owned = 0;
+        for (int k = 0; k < kSchwarzClasses; ++k)
+            if (single || k == cl) {
+                copies += bs.cls_copies[k];
+                owned += bs.cls_owned[k];
+            }
+        const double bytes = (double)copies * (16.0 * sizeof(TC) + 8.0 + 2.0 * sizeof(T)) + 8.0 * (double)owned;
 #define DM_SCHWARZ(RV, NV)                                                                                         \
     if (bs.fixed)                                                                                                  \
-        launch(name, k_band_schwarz<T, TC, RV, NV, true>, count, NV, smem, s, first, bs.off, bs.copy, bs.pos,      \
-               bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,      \
-               bs.maxbox, bs.maxrows);                                                                           \
+        launch_b(name, bytes, k_band_schwarz<T, TC, RV, NV, true>, count, NV, smem, s, first, bs.off, bs.copy,     \
+                 bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx,   \
+                 g.sxy, bs.maxbox, bs.maxrows);                                                                  \
     else                                                                                                           \
-    launch(name, k_band_schwarz<T, TC, RV, NV, false>, count, NV, smem, s, first, bs.off, bs.copy,               \
-           bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx, g.sxy,  \
-           bs.maxbox, bs.maxrows)
+    launch_b(name, bytes, k_band_schwarz<T, TC, RV, NV, false>, count, NV, smem, s, first, bs.off, bs.copy,      \
+             bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx,      \
+             g.sxy, bs.maxbox, bs.maxrows)
         if (nt == 256) DM_SCHWARZ(1, 256);
         else if (R == 1) DM_SCHWARZ(1, 512);
         else if (R == 2) DM_SCHWARZ(2, 512);
@@ -380,8 +395,8 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
         else DM_SCHWARZ(0, 512);
 #undef DM_SCHWARZ
     }
-    launch(stencil_name("band_add", prec_index<T>(), ST_JACOBI, fine), k_band_add<T>, (nband + 255) / 256, 256, 0, s,
-           band, nband, (const double*)u, x);
+    launch_b(stencil_name("band_add", prec_index<T>(), ST_JACOBI, fine), (double)nband * (12.0 + 2.0 * sizeof(T)),
+             k_band_add<T>, (nband + 255) / 256, 256, 0, s, band, nband, (const double*)u, x);
 }
 
 // Allow each variant the device's opt-in shared memory less its static share;

@@ -509,7 +509,8 @@ void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, c
           double* host_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
     const int nb = blocks_for(d, k_mdot_partial);
-    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 0);
+    launch_b("k_mdot_partial", 8.0 * d.live() * (m + 1 + (w ? 1 : 0)), k_mdot_partial, nb, kThreads, 0, s, d, m, V,
+             ld, x, w, red.partial, red.max_cols, 0);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -520,7 +521,8 @@ void mdot_self(Reducer& red, const Domain& d, int m, const double* V, long long 
                double* host_out, double* self_out, cudaStream_t s) {
     DM_REQUIRE(m >= 1 && m + 1 <= red.max_cols, DM_ERR_INVALID_ARG, "mdot: too many columns");
     const int nb = blocks_for(d, k_mdot_partial);
-    launch("k_mdot_partial", k_mdot_partial, nb, kThreads, 0, s, d, m, V, ld, x, w, red.partial, red.max_cols, 1);
+    launch_b("k_mdot_partial", 8.0 * d.live() * (m + 1 + (w ? 1 : 0)), k_mdot_partial, nb, kThreads, 0, s, d, m, V,
+             ld, x, w, red.partial, red.max_cols, 1);
     launch("k_mdot_final", k_mdot_final, (m + 1 + 7) / 8, 256, 0, s, nb, m + 1, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * (m + 1), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -534,7 +536,8 @@ double maxpy_norm(Reducer& red, const Domain& d, int m, const double* V, long lo
     const int nb = blocks_for(d, k_maxpy_norm);
     // h = red.result (written by the preceding mdot on this stream); partials in a separate stripe
     double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
-    launch("k_maxpy_norm", k_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld, red.result, x, w, part);
+    launch_b("k_maxpy_norm", 8.0 * d.live() * (m + 2 + (w ? 1 : 0)), k_maxpy_norm, nb, kThreads, 0, s, d, m, V, ld,
+             red.result, x, w, part);
     launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -548,7 +551,8 @@ void maxpy(Reducer& red, const Domain& d, int m, const double* V, long long ld, 
     DM_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < m; ++c) red.host[c] = h_host[c];
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * m, cudaMemcpyHostToDevice, s));
-    launch("k_maxpy", k_maxpy, blocks_for(d, k_maxpy), kThreads, 0, s, d, m, V, ld, red.result, x);
+    launch_b("k_maxpy", 8.0 * d.live() * (m + 2), k_maxpy, blocks_for(d, k_maxpy), kThreads, 0, s, d, m, V, ld,
+             red.result, x);
 }
 
 template <typename T>
@@ -577,12 +581,13 @@ template int list_flagged<unsigned char>(long long, const unsigned char*, DBuf<i
 
 void ff_gather(long long n, const int* list, double a, const double* x, float2* y, cudaStream_t s) {
     const int nb = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
-    launch("k_ff_gather", k_ff_gather, nb, kThreads, 0, s, n, list, a, x, y);
+    launch_b("k_ff_gather", 20.0 * n, k_ff_gather, nb, kThreads, 0, s, n, list, a, x, y);
 }
 template <typename T>
 void ff_scatter(long long n, const int* list, double a, const float2* x, T* y, cudaStream_t s) {
     const int nb = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
-    launch("k_ff_scatter", k_ff_scatter<T>, nb, kThreads, 0, s, n, list, (typename Compute<T>::type)a, x, y);
+    launch_b("k_ff_scatter", (12.0 + sizeof(T)) * n, k_ff_scatter<T>, nb, kThreads, 0, s, n, list,
+             (typename Compute<T>::type)a, x, y);
 }
 template void ff_scatter<double>(long long, const int*, double, const float2*, double*, cudaStream_t);
 template void ff_scatter<float>(long long, const int*, double, const float2*, float*, cudaStream_t);
@@ -593,7 +598,9 @@ void dcgs_dots(Reducer& red, const Domain& d, int j, const float2* Q, long long 
     const int m = 2 * j + 2;
     DM_REQUIRE(j >= 0 && j <= 120 && m < red.max_cols, DM_ERR_INVALID_ARG, "dcgs: too many columns");
     const int nb = blocks_for(d, k_ff_dcgs_dots);
-    launch("k_ff_dcgs_dots", k_ff_dcgs_dots, nb, kThreads, 0, s, d, j, Q, ld, v, w, red.partial, red.max_cols);
+    // j finished basis vectors, v and w: float-float, 8 bytes an entry
+    launch_b("k_ff_dcgs_dots", 8.0 * d.live() * (j + 2), k_ff_dcgs_dots, nb, kThreads, 0, s, d, j, Q, ld, v, w,
+             red.partial, red.max_cols);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -608,8 +615,9 @@ double dcgs_update(Reducer& red, const Domain& d, int j, const float2* Q, long l
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * (2 * j + 2), cudaMemcpyHostToDevice, s));
     const int nb = blocks_for(d, k_ff_dcgs_update);
     double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
-    launch("k_ff_dcgs_update", k_ff_dcgs_update, nb, kThreads, 0, s, d, j, Q, ld, (const double*)red.result, v, w,
-           out, part);
+    // reads Q (j vectors), v and w; writes v and out
+    launch_b("k_ff_dcgs_update", 8.0 * d.live() * (j + 4), k_ff_dcgs_update, nb, kThreads, 0, s, d, j, Q, ld,
+             (const double*)red.result, v, w, out, part);
     launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -619,22 +627,28 @@ void vgemm(const Domain& d, int m, int p, const double* V, long long ld, const d
            long long ldo, cudaStream_t s) {
     const size_t sm = sizeof(double) * (size_t)m * p;
     DM_REQUIRE(sm <= 48 * 1024, DM_ERR_INVALID_ARG, "vgemm: basis too large");
-    launch("k_vgemm", k_vgemm, blocks_for(d, k_vgemm), kThreads, sm, s, d, m, p, V, ld, Y_dev, ldy, out, ldo);
+    launch_b("k_vgemm", 8.0 * d.live() * (m + p), k_vgemm, blocks_for(d, k_vgemm), kThreads, sm, s, d, m, p, V, ld,
+             Y_dev, ldy, out, ldo);
 }
 
 void axpby(const Domain& d, double a, const double* x, double b, double* y, cudaStream_t s) {
-    launch("k_axpby", k_axpby, blocks_for(d, k_axpby), kThreads, 0, s, d, a, x, b, y);
+    launch_b("k_axpby", 24.0 * d.live(), k_axpby, blocks_for(d, k_axpby), kThreads, 0, s, d, a, x, b, y);
 }
 void scale_copy(const Domain& d, double a, const double* x, double* y, cudaStream_t s) {
-    if (x == y) launch("k_scale_inplace", k_scale_inplace, blocks_for(d, k_scale_inplace), kThreads, 0, s, d, a, y);
-    else launch("k_scale_copy", k_scale_copy, blocks_for(d, k_scale_copy), kThreads, 0, s, d, a, x, y);
+    if (x == y)
+        launch_b("k_scale_inplace", 16.0 * d.live(), k_scale_inplace, blocks_for(d, k_scale_inplace), kThreads, 0, s,
+                 d, a, y);
+    else
+        launch_b("k_scale_copy", 16.0 * d.live(), k_scale_copy, blocks_for(d, k_scale_copy), kThreads, 0, s, d, a, x,
+                 y);
 }
 void hadamard(const Domain& d, const double* a, const double* x, double* y, cudaStream_t s) {
-    launch("k_hadamard", k_hadamard, blocks_for(d, k_hadamard), kThreads, 0, s, d, a, x, y);
+    launch_b("k_hadamard", 24.0 * d.live(), k_hadamard, blocks_for(d, k_hadamard), kThreads, 0, s, d, a, x, y);
 }
 template <typename TD, typename TS>
 void convert(const Domain& d, const TS* x, TD* y, cudaStream_t s) {
-    launch("k_convert", k_convert<TD, TS>, blocks_for(d, k_convert<TD, TS>), kThreads, 0, s, d, x, y);
+    launch_b("k_convert", (double)(sizeof(TD) + sizeof(TS)) * d.live(), k_convert<TD, TS>, blocks_for(d, k_convert<TD, TS>),
+             kThreads, 0, s, d, x, y);
 }
 template <typename TD>
 void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s) {

@@ -56,6 +56,7 @@ struct Grid3 {
     double hx, hy, hz;     // spacing
     double rhx, rhy, rhz;  // 1 / spacing (computed once on the host, so kernels divide nothing)
     float rhxf, rhyf, rhzf;
+    int nopen = 0, nact = 0;   // open faces and active cells of the level (set once counted; byte models)
 
     __host__ __device__ int idx(int i, int j, int k) const { return off0 + i + sx * (j + sy * k); }
 };
@@ -99,6 +100,9 @@ struct Domain {
     int ntiles = 0;
     int ncomp = 3;    // 3: face vector, 1: cell vector
     __host__ __device__ long long len() const { return (long long)ncomp * g.np; }
+    // entries that can be nonzero: open faces or active cells of a tiled
+    // domain, every entry of a flat one (the unit of the byte models)
+    double live() const { return tiles ? (double)(ncomp == 3 ? g.nopen : g.nact) : (double)len(); }
 };
 
 // Iterate the entries of a domain owned by this thread: calls f(r) for every
@@ -162,6 +166,7 @@ struct Tracer {
         std::string name;
         long long launches = 0;
         double ms = 0.0;
+        double bytes = 0.0;   // algorithmic bytes of the launches (the launch sites' models; 0 = none)
     };
     std::vector<Stat> stats;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -170,7 +175,7 @@ struct Tracer {
     cudaEvent_t get_event();
     int stat_index(const char* name);
     void begin(cudaStream_t s, cudaEvent_t* e0, cudaEvent_t* e1);
-    void end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1);
+    void end(const char* name, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, double bytes);
     void resolve();
     void reset();
     ~Tracer();
@@ -186,17 +191,25 @@ struct UntracedScope {
     UntracedScope& operator=(const UntracedScope&) = delete;
 };
 
-// Launch a kernel on stream s, counting it and (with tracing on) timing it.
+// Launch a kernel on stream s, counting it and (with tracing on) timing it;
+// `bytes` is the launch's algorithmic DRAM traffic by the launch site's model
+// (what the kernel must read and write at least, counted on the elements that
+// can be nonzero), accumulated per kernel name for roofline reports.
 template <typename... KArgs, typename... Args>
-inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                   Args&&... args) {
+inline void launch_b(const char* name, double bytes, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args&&... args) {
     Tracer* t = (g_tracer && g_tracer->on && !g_untraced) ? g_tracer : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (t) t->begin(s, &e0, &e1);
     kern<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
-    if (t) t->end(name, s, e0, e1);
+    if (t) t->end(name, s, e0, e1, bytes);
     count_launch();
     check_launch(name);
+}
+template <typename... KArgs, typename... Args>
+inline void launch(const char* name, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args&&... args) {
+    launch_b(name, 0.0, kern, grid, block, smem, s, std::forward<Args>(args)...);
 }
 
 // Count of the device memory, pinned host memory, CUDA events and streams the
@@ -276,6 +289,8 @@ int geom_open_faces(const Grid3& g, const double* A, int* list, int* d_count, cu
 int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
 // number of entries that are NaN or infinite
 int count_nonfinite(long long n, const double* a, int* d_count, cudaStream_t s);
+// number of nonzero flags
+int count_flags(long long n, const unsigned char* a, int* d_count, cudaStream_t s);
 // active tiles of a level in ascending order (tiles: capacity of all tiles); returns the count
 int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
                cudaStream_t s);
@@ -374,6 +389,7 @@ struct SchwarzLayout {
     int maxrows = 0, maxbox = 0;
     bool fixed = false;           // every subdomain uses the fixed box of the default brick
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
+    long long cls_copies[kSchwarzClasses] = {}, cls_owned[kSchwarzClasses] = {};   // row copies, owned ones
 };
 template <typename TC>
 struct BandSchwarz {
@@ -384,6 +400,7 @@ struct BandSchwarz {
     const TC* vals = nullptr;     // [15][ncopies] slot coefficients of each copy's row
     int nsub = 0, ncopies = 0, maxrows = 0, maxbox = 0;
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
+    long long cls_copies[kSchwarzClasses] = {}, cls_owned[kSchwarzClasses] = {};
     bool fixed = false;
 };
 void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int brick, SchwarzLayout& out,
@@ -507,5 +524,8 @@ template <typename TD>
 void convert_coeff(long long n, const double* x, TD* y, cudaStream_t s);
 void fill_random(const Domain& d, unsigned long long seed, const double* mask, double* x, cudaStream_t s);
 void zero(void* p, size_t bytes, cudaStream_t s);
+
+// FMA issue rates of the current device in FP64 and FP32, flop/s (dm_probe.cu)
+void probe_fma_rates(cudaStream_t s, double* fp64_flops, double* fp32_flops);
 
 }  // namespace dm

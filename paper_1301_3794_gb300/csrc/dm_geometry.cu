@@ -453,6 +453,22 @@ int count_nonfinite(long long n, const double* a, int* d_count, cudaStream_t s) 
     return read_count(d_count, s);
 }
 
+__global__ void k_count_flags(long long n, const unsigned char* __restrict__ a, int* __restrict__ count) {
+    int c = 0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        c += a[r] ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+int count_flags(long long n, const unsigned char* a, int* d_count, cudaStream_t s) {
+    DM_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+    launch("k_count_flags", k_count_flags, blocks, 256, 0, s, n, a, d_count);
+    return read_count(d_count, s);
+}
+
 // flags[t] = 1 if tile t holds an open face or an active cell
 __global__ void k_tile_flags(Grid3 g, const double* __restrict__ A, const unsigned char* __restrict__ active,
                              int* __restrict__ flags) {

@@ -634,9 +634,26 @@ const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
     return names->insert(n).first->c_str();
 }
 
+// Algorithmic bytes of one vector-stencil launch: per open face its x and y
+// (and f for resid / jacobi), its A (and 1/D for jacobi), about one edge
+// fraction L and a third of a cell's 1/V.
+template <typename T, typename TC>
+double vec_stencil_bytes(const Grid3& g, int mode) {
+    const double tv = sizeof(T), tc = sizeof(TC);
+    return (double)g.nopen * (tv * (2 + (mode != ST_APPLY)) + tc * (2.0 + 1.0 / 3.0 + (mode == ST_JACOBI)));
+}
+// per active cell: x, y (and f), three face fractions (six faces, each shared
+// by two cells), 1/D for jacobi, and the activity flag
+template <typename T, typename TC>
+double scal_stencil_bytes(const Grid3& g, int mode) {
+    const double tv = sizeof(T), tc = sizeof(TC);
+    return (double)g.nact * (tv * (2 + (mode != ST_APPLY)) + tc * (3 + (mode == ST_JACOBI)) + 1.0);
+}
+
 template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
+    const double bytes = vec_stencil_bytes<T, TC>(g, mode);
     if (op.tiles) {
         const int* tl = op.stiles ? op.stiles : op.tiles;
         const int nt = op.stiles ? op.nstiles : op.ntiles;
@@ -647,8 +664,8 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         switch (op.shape * 3 + mode) {
 #define DM_TILED(SH, MD, SY, SZ)                                                                              \
     case SH * 3 + MD:                                                                                         \
-        launch(nm, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, nt, dim3(TX, SY, SZ), 0, s, g, op.A, op.L, op.invV, \
-               op.invD, op.sigma, x, f, y, omega, tl);                                                        \
+        launch_b(nm, bytes, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, nt, dim3(TX, SY, SZ), 0, s, g, op.A, op.L,  \
+                 op.invV, op.invD, op.sigma, x, f, y, omega, tl);                                             \
         break;
             DM_TILED(0, ST_APPLY, 4, 2) DM_TILED(0, ST_RESID, 4, 2) DM_TILED(0, ST_JACOBI, 4, 2)
             DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4)
@@ -656,8 +673,8 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
 #undef DM_TILED
 #define DM_MARCH(SH, MD, SY, KZ)                                                                                \
     case SH * 3 + MD:                                                                                         \
-        launch(nm, k_vec_stencil_march<T, TC, MD, SY, KZ>, nt, dim3(TX, SY, 1), 0, s, g, op.A, op.L, op.invV, \
-               op.invD, op.sigma, x, f, y, omega, tl);                                                        \
+        launch_b(nm, bytes, k_vec_stencil_march<T, TC, MD, SY, KZ>, nt, dim3(TX, SY, 1), 0, s, g, op.A, op.L,  \
+                 op.invV, op.invD, op.sigma, x, f, y, omega, tl);                                             \
         break;
             DM_MARCH(3, ST_APPLY, 8, 8) DM_MARCH(3, ST_RESID, 8, 8) DM_MARCH(3, ST_JACOBI, 8, 8)
             DM_MARCH(4, ST_APPLY, 4, 8) DM_MARCH(4, ST_RESID, 4, 8) DM_MARCH(4, ST_JACOBI, 4, 8)
@@ -668,11 +685,11 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         return;
     }
     if (mode == ST_APPLY)
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_vec_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), bytes, k_vec_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_vec_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), bytes, k_vec_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else
-        launch(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), bytes, k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
 }
 
 // y = (K - sigma A) x in FP64 over every node of the level (dense grid of
@@ -693,8 +710,9 @@ template <typename T, typename TC>
 void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
     const Domain d{op.g, op.tiles, op.ntiles, 3};
     const int blocks = op.tiles ? std::max(op.ntiles, 1) : (int)std::min<long long>((d.len() + 255) / 256, 152 * 16);
-    launch(stencil_name("jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0), k_jacobi_zero<T, TC>, blocks, 256,
-           0, s, d, op.invD, f, y, omega);
+    launch_b(stencil_name("jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0),
+             (double)op.g.nopen * (2.0 * sizeof(T) + sizeof(TC)), k_jacobi_zero<T, TC>, blocks, 256, 0, s, d, op.invD,
+             f, y, omega);
 }
 
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
@@ -712,19 +730,20 @@ template <typename T, typename TC>
 void scal_stencil(const ScalOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s) {
     const Grid3& g = op.g;
     if (mode == ST_APPLY)
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_APPLY, op.level == 0), k_scal_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("scal_stencil", prec_index<T>(), ST_APPLY, op.level == 0), scal_stencil_bytes<T, TC>(g, ST_APPLY), k_scal_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_RESID, op.level == 0), k_scal_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("scal_stencil", prec_index<T>(), ST_RESID, op.level == 0), scal_stencil_bytes<T, TC>(g, ST_RESID), k_scal_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
     else
-        launch(stencil_name("scal_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), k_scal_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
+        launch_b(stencil_name("scal_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), scal_stencil_bytes<T, TC>(g, ST_JACOBI), k_scal_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 0), kBlock, 0, s, g, op.A, op.active, op.invD, x, f, y, omega, op.tiles);
 }
 
 template <typename T, typename TC>
 void scal_jacobi_zero(const ScalOp<T, TC>& op, const T* f, T* y, double omega, cudaStream_t s) {
     const Domain d{op.g, op.tiles, op.ntiles, 1};
     const int blocks = op.tiles ? std::max(op.ntiles, 1) : (int)std::min<long long>((d.len() + 255) / 256, 152 * 16);
-    launch(stencil_name("scal_jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0), k_jacobi_zero<T, TC>, blocks,
-           256, 0, s, d, op.invD, f, y, omega);
+    launch_b(stencil_name("scal_jacobi_zero", prec_index<T>(), ST_JACOBI, op.level == 0),
+             (double)op.g.nact * (2.0 * sizeof(T) + sizeof(TC)), k_jacobi_zero<T, TC>, blocks, 256, 0, s, d, op.invD,
+             f, y, omega);
 }
 
 void scal_diagonal(const Grid3& g, const double* A, const unsigned char* active, double* d, cudaStream_t s) {
@@ -739,12 +758,14 @@ void scal_dense_assemble(const Grid3& g, const double* A, const int* list, const
 
 void dm_div_a(const Grid3& g, const double* A, const double* x, double* s_out, const int* tiles, int ntiles,
               cudaStream_t s) {
-    launch("k_div_a", k_div_a, tile_grid(g, tiles, ntiles, 0), kBlock, 0, s, g, A, x, s_out, tiles);
+    launch_b("k_div_a", 16.0 * g.nopen + 8.0 * g.nact, k_div_a, tile_grid(g, tiles, ntiles, 0), kBlock, 0, s, g, A, x,
+             s_out, tiles);
 }
 
 void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double* phi, double* y, const int* tiles,
                  int ntiles, cudaStream_t s) {
-    launch("k_sub_grad", k_sub_grad, tile_grid(g, tiles, ntiles, 1), kBlock, 0, s, g, A, x, phi, y, tiles);
+    launch_b("k_sub_grad", 24.0 * g.nopen + 8.0 * g.nact, k_sub_grad, tile_grid(g, tiles, ntiles, 1), kBlock, 0, s, g,
+             A, x, phi, y, tiles);
 }
 
 // explicit instantiations: FP64 storage / FP64 coefficients, FP32 / FP32, BF16 / FP32

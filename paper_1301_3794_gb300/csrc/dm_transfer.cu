@@ -171,26 +171,30 @@ inline dim3 grid_for(const Grid3& g, int extra) {
 template <typename T, typename TC>
 void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, const int* tiles_c,
                    int ntiles_c, cudaStream_t s) {
-    launch("k_face_restrict", k_face_restrict<T, TC>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock, 0, s, gf, gc, Ac, r,
-           fc, tiles_c);
+    // every open fine face's r once; per open coarse face its A and f_c
+    const double bytes = (double)gf.nopen * sizeof(T) + (double)gc.nopen * (sizeof(T) + sizeof(TC));
+    launch_b("k_face_restrict", bytes, k_face_restrict<T, TC>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock, 0, s, gf,
+             gc, Ac, r, fc, tiles_c);
 }
 template <typename T, typename TC>
 void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, const int* tiles_f,
                       int ntiles_f, cudaStream_t s) {
-    launch("k_face_prolong", k_face_prolong<T, TC>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0, s, gf, gc, Af, ec,
-           x, tiles_f);
+    // every open coarse face's e_c once; per open fine face its A and x read and written
+    const double bytes = (double)gc.nopen * sizeof(T) + (double)gf.nopen * (2.0 * sizeof(T) + sizeof(TC));
+    launch_b("k_face_prolong", bytes, k_face_prolong<T, TC>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0, s, gf, gc,
+             Af, ec, x, tiles_f);
 }
 template <typename T>
 void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
                    const int* tiles_c, int ntiles_c, cudaStream_t s) {
-    launch("k_cell_restrict", k_cell_restrict<T>, tile_grid(gc, tiles_c, ntiles_c, 0), kBlock, 0, s, gf, gc,
-           active_c, r, fc, tiles_c);
+    launch_b("k_cell_restrict", (double)gf.nact * sizeof(T) + (double)gc.nact * (sizeof(T) + 1.0), k_cell_restrict<T>,
+             tile_grid(gc, tiles_c, ntiles_c, 0), kBlock, 0, s, gf, gc, active_c, r, fc, tiles_c);
 }
 template <typename T>
 void cell_prolong_add(const Grid3& gf, const Grid3& gc, const unsigned char* active_f, const T* ec, T* x,
                       const int* tiles_f, int ntiles_f, cudaStream_t s) {
-    launch("k_cell_prolong", k_cell_prolong<T>, tile_grid(gf, tiles_f, ntiles_f, 0), kBlock, 0, s, gf, gc, active_f,
-           ec, x, tiles_f);
+    launch_b("k_cell_prolong", (double)gc.nact * sizeof(T) + (double)gf.nact * (2.0 * sizeof(T) + 1.0),
+             k_cell_prolong<T>, tile_grid(gf, tiles_f, ntiles_f, 0), kBlock, 0, s, gf, gc, active_f, ec, x, tiles_f);
 }
 
 #define DM_INST(T, TC)                                                                                   \

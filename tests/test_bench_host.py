@@ -53,30 +53,45 @@ def test_aggregate_single_process_is_identity():
     assert bench.aggregate(7, 0.5) == (7.0, 0.5)
 
 
-def test_stencil_byte_model():
+def test_rooflines_from_the_library_byte_models():
     import bench
-    # FP64 apply: x, y (3 x 8 B each) + A, L, 1/V (7 x 8 B) = 104 B per cell
-    assert bench.stencil_bytes_per_cell("vec_stencil_f64_apply_L0") == 104
-    # FP32 Jacobi: x, f, y (3 x 4 B each) + A, L, 1/V, 1/D (10 x 4 B)
-    assert bench.stencil_bytes_per_cell("vec_stencil_f32_jacobi_L0") == 36 + 40
-    # per open face, FP32 Jacobi: x, f, y (4 B each) + A, 1/D (4 B each) + L (4 B) + 1/V / 3
-    assert bench.stencil_bytes_per_open_face("vec_stencil_f32_jacobi_L0") == pytest.approx(12 + 12 + 4 / 3)
-    r = bench.roofline({"vec_stencil_f32_jacobi_L0": (10, 1.0), "k_mdot_partial": (5, 100.0)}, 10 ** 6, 6758.5,
-                       "measured", "f32")
-    assert r["kernel"] == "vec_stencil_f32_jacobi_L0"
-    assert r["achieved"] == pytest.approx((24 + 4 / 3) * 10 ** 6 / 1e-4 / 1e9, rel=1e-3)
-    assert 0 < r["frac"] < 1
-    f = bench.roofline_fp64_apply({"vec_stencil_f64_apply_L0": (4, 2.0)}, 10 ** 6)
-    assert f["bound"] == "alu" and f["achieved"] == pytest.approx(22e6 / 5e-4 / 1e12)
-
-
-def test_profiled_traffic_only_for_the_captured_shape():
-    import bench
-    key = ("vec_stencil_f32_jacobi_L0", 0, "sphere", 128)
-    assert bench.PROFILED_TRAFFIC[key] == 90_759_424 + 5_890_304
-    # another tile shape on level 0, or another cavity, has no capture: traffic stays null
-    assert bench.PROFILED_TRAFFIC.get(("vec_stencil_f32_jacobi_L0", 3, "sphere", 128)) is None
-    r = bench.roofline({"vec_stencil_f32_jacobi_L0": (10, 1.0)}, 10 ** 6, 6758.5, "measured", "f32",
-                       traffic=bench.PROFILED_TRAFFIC[key])
-    assert r["traffic"] == bench.PROFILED_TRAFFIC[key]
+    stats = {"band_schwarz_f32_jacobi_L0": (8, 4.0, 8 * 2.0e7),
+             "vec_stencil_f64_apply_L0": (2, 1.0, 2 * 1.0e8),
+             "k_gj_pivot": (1, 0.5, 0.0)}
+    r = bench.rooflines(stats, 6794.8, "measured", 1.2, 10 ** 6)
+    assert [e["kernel"] for e in r] == ["band_schwarz_f32_jacobi_L0", "vec_stencil_f64_apply_L0", "k_gj_pivot"]
+    assert r[0]["share"] == pytest.approx(4.0 / 5.5, abs=1e-4)
+    assert r[0]["achieved"] == pytest.approx(1.6e8 / 4e-3 / 1e9, rel=1e-3)
+    assert r[0]["frac"] == pytest.approx(r[0]["achieved"] / 6794.8, abs=1e-4)
+    assert r[0]["bytes_per_launch"] == 2 * 10 ** 7
+    # a kernel without a byte model carries no HBM roofline
+    assert "frac" not in r[2]
+    # the FP64 apply is also measured against the FP64 FMA rate: 22 flops per open face
+    alu = r[1]["alu"]
+    assert alu["achieved"] == pytest.approx(22e6 * 2 / 1e-3 / 1e12, rel=1e-3) and alu["peak"] == 1.2
     assert json.loads(json.dumps(r)) == r
+
+
+def test_profiled_traffic_reaches_only_the_captured_case():
+    import bench
+    saved = dict(bench.PROFILED_TRAFFIC)
+    try:
+        bench.PROFILED_TRAFFIC[("band_schwarz_f32_jacobi_L0", "ellipsoid", 192, 0)] = 12345
+        stats = {"band_schwarz_f32_jacobi_L0": (8, 4.0, 8 * 2.0e7)}
+        hit = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 192, 0))
+        miss = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 192, 3))
+        assert hit[0]["traffic"] == 12345 and miss[0]["traffic"] is None
+    finally:
+        bench.PROFILED_TRAFFIC.clear()
+        bench.PROFILED_TRAFFIC.update(saved)
+
+
+def test_host_sample_is_the_same_cavity_family():
+    import argparse
+
+    import bench
+    a = argparse.Namespace(workload="ellipsoid", sigma=5.0, nev=16)
+    w = bench.sample_workload(a)
+    assert w.grid.nx == bench.CPU_SAMPLE_GRID and w.nev == 16 and "semi_axes" in w.meta
+    a.workload = "sphere"
+    assert "radius" in bench.sample_workload(a).meta
