@@ -97,8 +97,9 @@ typedef struct dm_eig_params {
     double rho_tol;        /* certificate every returned pair must meet, rho = ||K b - k^2 A b|| /
                               (k^2 ||A b||) in FP64 (1e-8; 0 = Ritz estimates only).  When the Ritz
                               estimates call the nev pairs converged but a certificate misses rho_tol,
-                              tol and inner_tol are divided by 10 (down to 1e-15 and 1e-13) and the
-                              Krylov-Schur iteration continues */
+                              the Ritz tolerance drops to a tenth of the worst current estimate, inner_tol
+                              to a tenth (down to 1e-15 and 1e-13), and the Krylov-Schur iteration
+                              continues */
 } dm_eig_params;
 
 typedef struct dm_eig_report {
@@ -304,6 +305,15 @@ dm_status dm_learned_loss_grad(dm_learned* net, const dm_geometry* geom, const f
  * host, epochs floats) receives the mean loss of every epoch. */
 dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epochs, float lr, unsigned long long seed,
                            float* loss_history);
+/* One Adam step of the training above on a given residual r (natural face
+ * layout, host or device per on_device; zero on closed faces): features from
+ * r / RMS(r), the residual objective with op's operator in FP32, its gradient
+ * by the backward pass, then the Adam update with step size lr (Adam's moment
+ * state and step count carry over between calls; dm_learned_set_weights
+ * resets them).  loss (nullable, host): the objective before the update;
+ * grad (nullable, host, dm_learned_num_params() floats): its gradient. */
+dm_status dm_learned_train_step(dm_learned* net, dm_operator* op, const double* r, int on_device, float lr,
+                                float* loss, float* grad);
 /* Use (net) or stop using (NULL) the learned correction in op's preconditioner. */
 dm_status dm_operator_set_learned(dm_operator* op, const dm_learned* net);
 

@@ -11,18 +11,30 @@ conv is a 3x3x3 cross-correlation with zero padding and no bias:
 
     conv(X, W)[k, j, i, o] = sum_{a, b, c in {0,1,2}} sum_q W[a, b, c, q, o] X[k+a-1, j+b-1, i+c-1, q]
 
-Input channels (7): the residual on the x, y, z faces of each node (the faces
+Input channels (8): the residual on the x, y, z faces of each node (the faces
 whose lower corner is the node), divided by its RMS over the open faces, then
-the face fractions A_x, A_y, A_z and the cell fraction V of the node's cell.
-Output channels (3): the predicted error on those faces, in units of
-(RMS of r) * h^2.  The training loss is the mean squared error over the open
-faces.  Without biases, relu networks are positively homogeneous, and the
-scaling above makes the prediction independent of the residual's magnitude.
+the face fractions A_x, A_y, A_z, the cell fraction V of the node's cell, and a
+zero channel.  Output channels (3): the predicted error on those faces, in
+units of (RMS of r) * h^2.  Without biases, relu networks are positively
+homogeneous, and the scaling above makes the prediction independent of the
+residual's magnitude.
+
+Two training objectives:
+* ``loss_and_grads``: the masked mean squared error against a target error E;
+* ``residual_loss_and_grads``: the residual the correction leaves, the one the
+  library trains on:  0.5 |m (s - K (h^2 y))|^2 / n_open, where s = r / RMS(r)
+  on the open faces, y = the network output placed on the faces, K the shifted
+  operator K - sigma A (symmetric), m the open-face mask.  Its gradient with
+  respect to y is -h^2 K m (s - K h^2 y) / n_open (K = K^T), which enters the
+  same backward pass as the MSE gradient.
+The optimiser is Adam (Kingma & Ba 2015), ``adam_step``.
 
 Pins (tests/test_oracle_learned.py): single-channel conv equals
 scipy.ndimage.correlate with zero padding (a library routine); a delta kernel
 shifts; the analytic gradients of every weight and of the input match central
-finite differences.
+finite differences, for both objectives; with K = h^-2 I the residual objective
+is the MSE objective with target s; Adam's first step moves every weight by lr
+against its gradient's sign, and a constant gradient keeps moving it by lr.
 """
 from __future__ import annotations
 
@@ -76,11 +88,18 @@ def forward(X, Ws):
 
 def loss_and_grads(X, E, M, Ws):
     """Masked MSE 0.5 * sum(M (Y - E)^2) / sum(M) and its gradients."""
-    Y, (X0, Z1, H1, Z2, H2) = forward(X, Ws)
+    Y, cache = forward(X, Ws)
     msum = max(float(M.sum()), 1.0)
     R = M * (Y - E)
     loss = 0.5 * float((R * (Y - E)).sum()) / msum
     dY = R / msum
+    grads, dX = _backward(cache, dY, Ws)
+    return loss, grads, dX
+
+
+def _backward(cache, dY, Ws):
+    """Weight gradients (and the input's) of a forward pass given dloss/dY."""
+    X0, Z1, H1, Z2, H2 = cache
     W1, W2, W3 = Ws
     dW3 = conv_grad_weight(H2, dY)
     dH2 = conv_grad_input(dY, W3) * (Z2 > 0)
@@ -88,10 +107,29 @@ def loss_and_grads(X, E, M, Ws):
     dH1 = conv_grad_input(dH2, W2) * (Z1 > 0)
     dW1 = conv_grad_weight(X0, dH1)
     dX = conv_grad_input(dH1, W1)
-    return loss, (dW1, dW2, dW3), dX
+    return (dW1, dW2, dW3), dX
 
 
-def init_weights(rng, cin=7, hidden=16, cout=3):
+def residual_loss_and_grads(X, s_faces, Ws, K, h2, faces_of, nodes_of, open_mask):
+    """The residual objective 0.5 |m (s - K h2 y)|^2 / n_open and its gradients.
+
+    X: network input (nodes, 8 channels); s_faces: r / RMS(r) on the faces
+    (natural face vector, zero on closed faces); K: the shifted operator as a
+    (faces x faces) matrix; faces_of(Y) maps the network output (nodes, 3) to
+    a face vector, nodes_of(v) the reverse (the adjoint placement);
+    open_mask: 1 on open faces.  Returns (loss, (dW1, dW2, dW3), dX)."""
+    Y, cache = forward(X, Ws)
+    y = open_mask * faces_of(Y)
+    res = open_mask * (s_faces - K @ (h2 * y))
+    n = max(float(open_mask.sum()), 1.0)
+    loss = 0.5 * float(res @ res) / n
+    gy = -h2 * open_mask * (K.T @ res) / n          # dloss/dy on the faces
+    dY = nodes_of(gy)
+    grads, dX = _backward(cache, dY, Ws)
+    return loss, grads, dX
+
+
+def init_weights(rng, cin=8, hidden=16, cout=3):
     """He-normal initialisation (fan-in 27 * Cin)."""
     def he(ci, co):
         return rng.standard_normal((3, 3, 3, ci, co)) * np.sqrt(2.0 / (27 * ci))

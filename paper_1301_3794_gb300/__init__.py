@@ -404,6 +404,15 @@ class Learned:
                                             hist.ctypes.data_as(C.POINTER(C.c_float))), "dm_learned_train")
         return hist
 
+    def train_step(self, op, r, lr=1e-3):
+        """One Adam step on the residual r: returns (loss, gradient) before the update."""
+        a = _Arg(r, op._faces(0))
+        loss = C.c_float()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        self.ctx.check(lib.dm_learned_train_step(self.h, op.h, a.ptr, a.device, float(lr), C.byref(loss),
+                                                 g.ctypes.data_as(C.POINTER(C.c_float))), "dm_learned_train_step")
+        return loss.value, g
+
     def close(self):
         if getattr(self, "h", None):
             lib.dm_learned_destroy(self.h)

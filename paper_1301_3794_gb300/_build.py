@@ -24,7 +24,8 @@ COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # per-file extra flags: the geometry is compiled without FMA contraction so that
 # fraction sums (and the 0 < V < 1 band tests) round identically on every build
 EXTRA = {"dm_geometry.cu": ["-fmad=false"]}
-SOURCES = ["dm_geometry.cu", "dm_stencil.cu", "dm_band.cu", "dm_transfer.cu", "dm_blas.cu", "dm_dense.cu", "dm_learned.cu", "dm_probe.cu", "dm_api.cu"]
+SOURCES = ["dm_geometry.cu", "dm_stencil.cu", "dm_band.cu", "dm_transfer.cu", "dm_blas.cu", "dm_dense.cu", "dm_learned.cu", "dm_conv_tc.cu", "dm_probe.cu",
+           "dm_api.cu"]
 
 
 def nvcc():

@@ -93,6 +93,8 @@ SIGNATURES = {
     "dm_learned_loss_grad": (C.c_int, [_P, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float),
                                        C.POINTER(C.c_float)]),
     "dm_learned_train": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_float, C.c_ulonglong, C.POINTER(C.c_float)]),
+    "dm_learned_train_step": (C.c_int, [_P, _P, _P, C.c_int, C.c_float, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_float)]),
     "dm_operator_set_learned": (C.c_int, [_P, _P]),
 }
 

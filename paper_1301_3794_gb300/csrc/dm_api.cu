@@ -521,6 +521,7 @@ void learned_correct(dm_operator* op, const T* f, T* z, T* scratch) {
     net.alloc(g0.g);
     net.features(g0.A.get(), g0.V.get(), 1.0 / scale, scratch, prec_index<T>(), s);
     net.forward(s);
+    net.check(s);
     zero(c, sizeof(T) * (size_t)n, s);
     net.add_correction<T>(g0.A.get(), scale * h * h, c, s);
     vec_stencil(o, ST_APPLY, c, (const T*)nullptr, kc, 0.0, s);
@@ -1929,7 +1930,12 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 bool all_ok = true;
                 for (double r : rho_w) all_ok = all_ok && r <= p.rho_tol;
                 if (!all_ok && restarts < p.max_restarts && tol_eff > 1e-15) {
-                    tol_eff *= 0.1;
+                    // below the worst current estimate, so that at least one more
+                    // cycle runs with the tighter inner tolerance
+                    double worst = 0.0;
+                    for (int c = 0; c < p.nev; ++c)
+                        worst = std::max(worst, est[c] / std::max(std::fabs(theta[order[c]]), 1e-300));
+                    tol_eff = 0.1 * std::min(tol_eff, worst);
                     inner_eff = std::max(inner_eff * 0.1, 1e-13);
                     ++cert_retries;
                     nconv = 0;
@@ -2204,6 +2210,7 @@ dm_status dm_learned_apply(dm_learned* net, const dm_geometry* geom, const doubl
             net->net.alloc(g0.g);
             net->net.features(g0.A.get(), g0.V.get(), 1.0 / scale, rp.get(), 0, s);
             net->net.forward(s);
+            net->net.check(s);
             net->net.add_correction<double>(g0.A.get(), scale * h * h, yp.get(), s);
         }
         if (on_device) {
@@ -2237,6 +2244,7 @@ dm_status dm_learned_loss_grad(dm_learned* net, const dm_geometry* geom, const f
         const long long nopen = count_positive(3ll * g0.g.np, g0.A.get(), cnt.get(), s);
         const float l = L.loss(g0.A.get(), (double)nopen, s);
         L.backward(s);
+        L.check(s);
         if (loss) *loss = l;
         if (grad) {
             DM_CUDA(cudaMemcpyAsync(grad, L.G.get(), sizeof(float) * LearnedNet::n_params(), cudaMemcpyDeviceToHost, s));
@@ -2316,7 +2324,48 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
                 L.adam(lr, s);
             }
             if (loss_history) loss_history[ep] = (float)(tot / (double)order.size());
+            L.check(s);
         }
+        Sync::stream(s);
+    });
+}
+
+dm_status dm_learned_train_step(dm_learned* net, dm_operator* op, const double* r, int on_device, float lr,
+                                float* loss, float* grad) {
+    if (!net || !op || !r || !(lr >= 0.f)) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        dm_context* ctx = op->ctx;
+        cudaStream_t s = ctx->stream;
+        GeoLevel& g0 = *const_cast<dm_geometry*>(op->geom)->lv[0];
+        const long long n3 = 3ll * g0.g.np;
+        const double h = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
+        DBuf<double> rp(n3);
+        faces_in(op, 0, r, on_device, rp.get());
+        const double ss = sumsq<double>(n3, rp.get(), s);
+        DM_REQUIRE(ss > 0.0 && op->nopen0 > 0, DM_ERR_INVALID_ARG, "learned train step: zero residual");
+        const double rms = std::sqrt(ss / (double)op->nopen0);
+        {
+            std::lock_guard<std::mutex> lock(const_cast<dm_geometry*>(op->geom)->mu);
+            ensure_f32(g0, s);
+        }
+        DBuf<float> r32(n3), ybuf(n3), kbuf(n3);
+        convert<float, double>(g0.vdom(), rp.get(), r32.get(), s);
+        const VecOp<float, float> o32{g0.g, g0.A32.get(), g0.L32.get(), g0.invV32.get(), nullptr, op->sigma, 0,
+                                      g0.tiles.get(), g0.ntiles, nullptr, 0, 0};
+        LearnedNet& L = net->net;
+        L.alloc(g0.g);
+        L.features(g0.A.get(), g0.V.get(), 1.0 / rms, r32.get(), 1, s);
+        L.forward(s);
+        const float l = L.residual_loss(o32, g0.A.get(), r32.get(), 1.0 / rms, h * h, ybuf.get(), kbuf.get(),
+                                        (double)op->nopen0, s);
+        L.backward(s);
+        L.check(s);
+        if (loss) *loss = l;
+        if (grad) {
+            DM_CUDA(cudaMemcpyAsync(grad, L.G.get(), sizeof(float) * LearnedNet::n_params(), cudaMemcpyDeviceToHost, s));
+            Sync::stream(s);
+        }
+        L.adam(lr, s);
         Sync::stream(s);
     });
 }

@@ -10,10 +10,13 @@
 // the cell fraction V, and a zero channel.  Y has 3 channels: the predicted
 // error on the node's faces in units of RMS(r) * h^2.
 //
-// Activations are BF16, channel-last ([np][C]) on the padded node grid (the
-// ghost layer gives the zero padding); weights, accumulation, losses and the
-// optimiser state are FP32.  The weight gradient is reduced in a fixed order
-// (per-block partials, then a column sum), so training is deterministic.
+// Activations are BF16 in the channel-blocked layout of ActLayout on the
+// padded node grid (the ghost layer and the margins give the zero padding);
+// weights, accumulation, losses and the optimiser state are FP32, and the
+// tensor cores multiply BF16 copies of the weights.  The convolutions, their
+// adjoints and the weight gradients are implicit GEMMs on the tensor cores
+// (dm_conv_tc.cu); the weight gradient is reduced in a fixed order (per-CTA
+// partials, then a sum in CTA order), so training is deterministic.
 #include "dm_common.cuh"
 
 #include "dm_learned.cuh"
@@ -25,127 +28,7 @@ namespace dm {
 
 namespace {
 
-constexpr int LX = TX, LY = TY, LZ = TZ;                 // output tile (one block)
-constexpr int HX = LX + 2, HY = LY + 2, HZ = LZ + 2;     // input tile with halo
-constexpr int NHALO = HX * HY * HZ;
-
-template <typename T> __device__ __forceinline__ float ldf(const T* p) { return to_c(*p); }
-__device__ __forceinline__ float ldf(const float* p) { return *p; }
-
-// Generic conv over the node grid, one 32 x 4 x 2 output tile per block.
-// in: [np][CIN] (TIN), W: [27][CIN][COUT] fp32 (flip = 1 uses W[26 - o][co][ci]
-// transposed, the adjoint of the forward conv), out: [np][COUT] (TOUT).
-// relu_mask (nullable, [np][COUT] bf16): zero the output where mask <= 0
-// (backward through a relu); relu_out: apply relu to the output.
-template <int CIN, int COUT, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(LX * LY * LZ) k_conv(Grid3 g, const TIN* __restrict__ in, const float* __restrict__ W,
-                                                       int flip, int relu_out, const __nv_bfloat16* __restrict__ relu_mask,
-                                                       TOUT* __restrict__ out) {
-    extern __shared__ float smem[];
-    float* w_s = smem;                                     // 27 * CIN * COUT
-    float* in_s = smem + 27 * CIN * COUT;                  // NHALO * CIN
-    const int tid = threadIdx.x + LX * (threadIdx.y + LY * threadIdx.z);
-    for (int e = tid; e < 27 * CIN * COUT; e += LX * LY * LZ) {
-        const int o = e / (CIN * COUT), rem = e % (CIN * COUT), ci = rem / COUT, co = rem % COUT;
-        // forward: W[o][ci][co]; adjoint: the input of this conv is dY (COUT = original CIN ...):
-        // out[q][ci'] = sum_o sum_co' W[o][ci'][co'] dY[q - off(o)][co'] = sum_o' W[26 - o'][ci'][co'] dY[q + off(o')][co']
-        w_s[e] = flip ? W[(size_t)(26 - o) * CIN * COUT + (size_t)co * CIN + ci] : W[e];
-    }
-    int i0, j0, k0;
-    i0 = blockIdx.x * LX;
-    j0 = blockIdx.y * LY;
-    k0 = blockIdx.z * LZ;
-    for (int e = tid; e < NHALO; e += LX * LY * LZ) {
-        const int li = e % HX, lj = (e / HX) % HY, lk = e / (HX * HY);
-        const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
-        const bool inside = i >= -1 && j >= -1 && k >= -1 && i <= g.nx + 1 && j <= g.ny + 1 && k <= g.nz + 1;
-        const int p = inside ? g.idx(i, j, k) : 0;
-#pragma unroll
-        for (int c = 0; c < CIN; ++c) in_s[e * CIN + c] = inside ? ldf(in + (size_t)p * CIN + c) : 0.f;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
-    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
-    if (i > g.nx || j > g.ny || k > g.nz) return;
-    float acc[COUT];
-#pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[co] = 0.f;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float* xin = in_s + ((tz + a) * HY * HX + (ty + b) * HX + (tx + c)) * CIN;
-                const float* wo = w_s + (a * 9 + b * 3 + c) * CIN * COUT;
-#pragma unroll
-                for (int ci = 0; ci < CIN; ++ci) {
-                    const float v = xin[ci];
-#pragma unroll
-                    for (int co = 0; co < COUT; ++co) acc[co] += v * wo[ci * COUT + co];
-                }
-            }
-    const int p = g.idx(i, j, k);
-#pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-        float v = acc[co];
-        if (relu_out) v = fmaxf(v, 0.f);
-        if (relu_mask && !(to_c(relu_mask[(size_t)p * COUT + co]) > 0.f)) v = 0.f;
-        out[(size_t)p * COUT + co] = to_store<TOUT>(v);
-    }
-}
-
-// Weight gradient partials: part[b][o][ci][co] = sum over the tiles of block b
-// of X[p + off(o)][ci] * dY[p][co].  Blocks take tiles (dense tile index)
-// b, b + G, ... so the reduction order is fixed.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) k_conv_dw(Grid3 g, const __nv_bfloat16* __restrict__ X,
-                                                 const __nv_bfloat16* __restrict__ dY, float* __restrict__ part) {
-    extern __shared__ float smem[];
-    constexpr int NW = 27 * CIN * COUT;
-    float* x_s = smem;                          // NHALO * CIN
-    float* dy_s = smem + NHALO * CIN;           // LX*LY*LZ * COUT
-    float* acc_s = dy_s + LX * LY * LZ * COUT;  // NW: this block's partial (entry w owned by thread w % 256)
-    const int tid = threadIdx.x;
-    for (int w = tid; w < NW; w += 256) acc_s[w] = 0.f;
-    const int ntx = (g.nx + LX) / LX, nty = (g.ny + LY) / LY, ntz = (g.nz + LZ) / LZ;
-    const int ntot = ntx * nty * ntz;
-    for (int t = blockIdx.x; t < ntot; t += gridDim.x) {
-        const int i0 = (t % ntx) * LX, j0 = ((t / ntx) % nty) * LY, k0 = (t / (ntx * nty)) * LZ;
-        __syncthreads();
-        for (int e = tid; e < NHALO; e += 256) {
-            const int li = e % HX, lj = (e / HX) % HY, lk = e / (HX * HY);
-            const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
-            const bool inside = i >= -1 && j >= -1 && k >= -1 && i <= g.nx + 1 && j <= g.ny + 1 && k <= g.nz + 1;
-            const int p = inside ? g.idx(i, j, k) : 0;
-#pragma unroll
-            for (int c = 0; c < CIN; ++c) x_s[e * CIN + c] = inside ? to_c(X[(size_t)p * CIN + c]) : 0.f;
-        }
-        for (int e = tid; e < LX * LY * LZ; e += 256) {
-            const int li = e % LX, lj = (e / LX) % LY, lk = e / (LX * LY);
-            const int i = i0 + li, j = j0 + lj, k = k0 + lk;
-            const bool valid = i <= g.nx && j <= g.ny && k <= g.nz;
-            const int p = valid ? g.idx(i, j, k) : 0;
-#pragma unroll
-            for (int c = 0; c < COUT; ++c) dy_s[e * COUT + c] = valid ? to_c(dY[(size_t)p * COUT + c]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int w = tid; w < NW; w += 256) {
-            const int o = w / (CIN * COUT), rem = w % (CIN * COUT), ci = rem / COUT, co = rem % COUT;
-            const int a = o / 9, b = (o / 3) % 3, c = o % 3;
-            float s = 0.f;
-            for (int lk = 0; lk < LZ; ++lk)
-                for (int lj = 0; lj < LY; ++lj) {
-                    const float* xr = x_s + ((lk + a) * HY * HX + (lj + b) * HX + c) * CIN + ci;
-                    const float* dr = dy_s + ((lk * LY + lj) * LX) * COUT + co;
-#pragma unroll 8
-                    for (int li = 0; li < LX; ++li) s += xr[li * CIN] * dr[li * COUT];
-                }
-            acc_s[w] += s;
-        }
-    }
-    __syncthreads();
-    for (int w = tid; w < NW; w += 256) part[(size_t)blockIdx.x * NW + w] = acc_s[w];
-}
+constexpr int LX = TX, LY = TY, LZ = TZ;                 // node tile of the elementwise kernels
 
 // column sums of part[nb][n] in block order
 __global__ void k_colsum(const float* __restrict__ part, int nb, int n, float* __restrict__ out) {
@@ -158,12 +41,12 @@ __global__ void k_colsum(const float* __restrict__ part, int nb, int n, float* _
 
 // input features of every node: residual / scale on the three faces, A_x, A_y, A_z, V, 0
 template <typename T>
-__global__ void k_features(Grid3 g, const T* __restrict__ r, const double* __restrict__ A, const double* __restrict__ V,
-                           double inv_scale, __nv_bfloat16* __restrict__ X) {
+__global__ void k_features(Grid3 g, ActLayout L, const T* __restrict__ r, const double* __restrict__ A,
+                           const double* __restrict__ V, double inv_scale, __nv_bfloat16* __restrict__ X) {
     const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int p = g.idx(i, j, k);
-    __nv_bfloat16* x = X + (size_t)p * 8;
+    __align__(16) __nv_bfloat16 x[8];
     for (int c = 0; c < 3; ++c) {
         const double a = A[c * g.np + p];
         x[c] = __float2bfloat16(a > 0.0 ? (float)(to_c(r[c * g.np + p]) * inv_scale) : 0.f);
@@ -171,6 +54,7 @@ __global__ void k_features(Grid3 g, const T* __restrict__ r, const double* __res
     }
     x[6] = __float2bfloat16((float)V[p]);
     x[7] = __float2bfloat16(0.f);
+    *reinterpret_cast<uint4*>(X + L.at(0, p)) = *reinterpret_cast<const uint4*>(x);
 }
 
 // z += scale * Y on the open faces (Y: [np][3] fp32)
@@ -187,8 +71,9 @@ __global__ void k_add_correction(Grid3 g, const float* __restrict__ Y, const dou
 }
 
 // loss = 0.5 sum M (Y - E)^2 / sum M (block partials) and dY = M (Y - E) / sum M (bf16)
-__global__ void k_mse(Grid3 g, const float* __restrict__ Y, const float* __restrict__ E, const double* __restrict__ A,
-                      float inv_msum, __nv_bfloat16* __restrict__ dY, float* __restrict__ part) {
+__global__ void k_mse(Grid3 g, ActLayout L, const float* __restrict__ Y, const float* __restrict__ E,
+                      const double* __restrict__ A, float inv_msum, __nv_bfloat16* __restrict__ dY,
+                      float* __restrict__ part) {
     __shared__ float red[256];
     const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
     const int tid = threadIdx.x + LX * (threadIdx.y + LY * threadIdx.z);
@@ -199,7 +84,7 @@ __global__ void k_mse(Grid3 g, const float* __restrict__ Y, const float* __restr
             const float m = A[c * g.np + p] > 0.0 ? 1.f : 0.f;
             const float d = m * (Y[(size_t)p * 3 + c] - E[(size_t)p * 3 + c]);
             l += 0.5f * d * d;
-            dY[(size_t)p * 3 + c] = __float2bfloat16(d * inv_msum);
+            dY[L.at(0, p) + c] = __float2bfloat16(d * inv_msum);
         }
     }
     red[tid] = l;
@@ -230,14 +115,14 @@ __global__ void k_res_loss(long long n, const float* __restrict__ r, float inv, 
     if (threadIdx.x == 0) part[blockIdx.x] = red[0] * inv_msum;
 }
 // dY = a g on the open faces of each node (gathered to node-channel order)
-__global__ void k_grad_gather(Grid3 g, const float* __restrict__ gv, const double* __restrict__ A, float a,
-                              __nv_bfloat16* __restrict__ dY) {
+__global__ void k_grad_gather(Grid3 g, ActLayout L, const float* __restrict__ gv, const double* __restrict__ A,
+                              float a, __nv_bfloat16* __restrict__ dY) {
     const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int p = g.idx(i, j, k);
     for (int c = 0; c < 3; ++c) {
         const int q = c * g.np + p;
-        dY[(size_t)p * 3 + c] = __float2bfloat16(A[q] > 0.0 ? a * gv[q] : 0.f);
+        dY[L.at(0, p) + c] = __float2bfloat16(A[q] > 0.0 ? a * gv[q] : 0.f);
     }
 }
 
@@ -253,14 +138,21 @@ __global__ void k_adam(int n, float* __restrict__ w, const float* __restrict__ g
     w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
 }
 
-// channel-last natural node array (i fastest) -> padded node grid
-template <typename TOUT>
-__global__ void k_pack_nodes_ch(Grid3 g, int C, const float* __restrict__ nat, TOUT* __restrict__ pad) {
+// natural node array (i fastest, channel last) -> X in the blocked layout (8 channels)
+__global__ void k_pack_X(Grid3 g, ActLayout L, const float* __restrict__ nat, __nv_bfloat16* __restrict__ X) {
     const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const long long n = i + (long long)(g.nx + 1) * (j + (long long)(g.ny + 1) * k);
     const int p = g.idx(i, j, k);
-    for (int c = 0; c < C; ++c) pad[(size_t)p * C + c] = to_store<TOUT>(nat[n * C + c]);
+    for (int c = 0; c < 8; ++c) X[L.at(0, p) + c] = __float2bfloat16(nat[n * 8 + c]);
+}
+// natural node array -> [np][C] FP32 on the padded grid
+__global__ void k_pack_nodes_f32(Grid3 g, int C, const float* __restrict__ nat, float* __restrict__ pad) {
+    const int i = blockIdx.x * LX + threadIdx.x, j = blockIdx.y * LY + threadIdx.y, k = blockIdx.z * LZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const long long n = i + (long long)(g.nx + 1) * (j + (long long)(g.ny + 1) * k);
+    const int p = g.idx(i, j, k);
+    for (int c = 0; c < C; ++c) pad[(size_t)p * C + c] = nat[n * C + c];
 }
 
 // training target: E[p][c] = e_c[p] * inv on open faces (e: padded fp32 face vector)
@@ -304,33 +196,6 @@ inline dim3 node_blocks(const Grid3& g) {
     return dim3((g.nx + LX) / LX, (g.ny + LY) / LY, (g.nz + LZ) / LZ);
 }
 
-template <int CIN, int COUT, typename TIN, typename TOUT>
-void conv_launch(const Grid3& g, const TIN* in, const float* W, int flip, int relu_out, const __nv_bfloat16* mask,
-                 TOUT* out, cudaStream_t s) {
-    const size_t sm = sizeof(float) * (27 * CIN * COUT + NHALO * CIN);
-    static std::atomic<bool> attr_set{false};
-    if (!attr_set.load()) {
-        DM_CUDA(cudaFuncSetAttribute(k_conv<CIN, COUT, TIN, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set.store(true);
-    }
-    launch("conv_fwd", k_conv<CIN, COUT, TIN, TOUT>, node_blocks(g), dim3(LX, LY, LZ), sm, s, g, in, W, flip, relu_out,
-           mask, out);
-}
-
-template <int CIN, int COUT>
-void conv_dw_launch(const Grid3& g, const __nv_bfloat16* X, const __nv_bfloat16* dY, float* part, float* dW, int nb,
-                    cudaStream_t s) {
-    const size_t sm = sizeof(float) * (NHALO * CIN + LX * LY * LZ * COUT + 27 * CIN * COUT);
-    static std::atomic<bool> attr_set{false};
-    if (!attr_set.load()) {
-        DM_CUDA(cudaFuncSetAttribute(k_conv_dw<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set.store(true);
-    }
-    launch("conv_dw", k_conv_dw<CIN, COUT>, nb, 256, sm, s, g, X, dY, part);
-    const int n = 27 * CIN * COUT;
-    launch("conv_dw_sum", k_colsum, (n + 255) / 256, 256, 0, s, part, nb, n, dW);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -338,18 +203,25 @@ void conv_dw_launch(const Grid3& g, const __nv_bfloat16* X, const __nv_bfloat16*
 void LearnedNet::alloc(const Grid3& grid) {
     if (g.np == grid.np && g.nx == grid.nx && g.ny == grid.ny && g.nz == grid.nz && X.get()) return;
     g = grid;
+    L = act_layout(g);
     const size_t np = (size_t)g.np;
-    X.alloc(np * CIN_);
-    H1.alloc(np * HID);
-    H2.alloc(np * HID);
+    X.alloc(L.elems(1));
+    H1.alloc(L.elems(2));
+    H2.alloc(L.elems(2));
+    dY.alloc(L.elems(1));
+    dH1.alloc(L.elems(2));
+    dH2.alloc(L.elems(2));
     Y.alloc(np * COUT_);
-    dY.alloc(np * COUT_);
-    dH1.alloc(np * HID);
-    dH2.alloc(np * HID);
     E.alloc(np * COUT_);
+    wt1.alloc((size_t)conv_wtile_steps(1) * 256);
+    wt2.alloc((size_t)conv_wtile_steps(2) * 256);
+    wt3.alloc((size_t)conv_wtile_steps(2) * 256);
+    wt3a.alloc((size_t)conv_wtile_steps(1) * 256);
+    wt2a.alloc((size_t)conv_wtile_steps(2) * 256);
+    err.alloc(1);
     const dim3 nb = node_blocks(g);
     loss_part.alloc((size_t)nb.x * nb.y * nb.z);
-    dw_part.alloc((size_t)kDwBlocks * 27 * HID * HID);
+    dw_part.alloc((size_t)conv_dw_tc_parts() * 27 * 256);
 }
 
 void LearnedNet::init_params() {
@@ -362,35 +234,55 @@ void LearnedNet::init_params() {
 void LearnedNet::features(const double* A, const double* V, double inv_scale, const void* r, int r_prec,
                           cudaStream_t s) {
     const dim3 nb = node_blocks(g);
+    const dim3 bl(LX, LY, LZ);
     if (r_prec == 0)
-        launch("learned_features", k_features<double>, nb, dim3(LX, LY, LZ), 0, s, g, (const double*)r, A, V, inv_scale, X.get());
+        launch("learned_features", k_features<double>, nb, bl, 0, s, g, L, (const double*)r, A, V, inv_scale, X.get());
     else if (r_prec == 1)
-        launch("learned_features", k_features<float>, nb, dim3(LX, LY, LZ), 0, s, g, (const float*)r, A, V, inv_scale, X.get());
+        launch("learned_features", k_features<float>, nb, bl, 0, s, g, L, (const float*)r, A, V, inv_scale, X.get());
     else
-        launch("learned_features", k_features<__nv_bfloat16>, nb, dim3(LX, LY, LZ), 0, s, g, (const __nv_bfloat16*)r, A,
-               V, inv_scale, X.get());
+        launch("learned_features", k_features<__nv_bfloat16>, nb, bl, 0, s, g, L, (const __nv_bfloat16*)r, A, V,
+               inv_scale, X.get());
 }
 
+// conv_tc epilogues
+constexpr int kEpiRelu = 0, kEpiMask = 1, kEpiOut = 2;
+
 void LearnedNet::forward(cudaStream_t s) {
-    conv_launch<CIN_, HID, __nv_bfloat16, __nv_bfloat16>(g, X.get(), w1(), 0, 1, nullptr, H1.get(), s);
-    conv_launch<HID, HID, __nv_bfloat16, __nv_bfloat16>(g, H1.get(), w2(), 0, 1, nullptr, H2.get(), s);
-    conv_launch<HID, COUT_, __nv_bfloat16, float>(g, H2.get(), w3(), 0, 0, nullptr, Y.get(), s);
+    conv_pack_weights(w1(), CIN_, HID, CIN_, HID, 1, 0, wt1.get(), s);
+    conv_pack_weights(w2(), HID, HID, HID, HID, 2, 0, wt2.get(), s);
+    conv_pack_weights(w3(), HID, COUT_, HID, COUT_, 2, 0, wt3.get(), s);
+    conv_tc(g, L, 1, kEpiRelu, X.get(), wt1.get(), nullptr, H1.get(), nullptr, err.get(), s);
+    conv_tc(g, L, 2, kEpiRelu, H1.get(), wt2.get(), nullptr, H2.get(), nullptr, err.get(), s);
+    conv_tc(g, L, 2, kEpiOut, H2.get(), wt3.get(), nullptr, nullptr, Y.get(), err.get(), s);
 }
 
 void LearnedNet::backward(cudaStream_t s) {
     // dW3 = dW(H2, dY); dH2 = conv^T(dY, W3) * (H2 > 0); dW2 = dW(H1, dH2); dH1 = conv^T(dH2, W2) * (H1 > 0);
     // dW1 = dW(X, dH1)
-    conv_dw_launch<HID, COUT_>(g, H2.get(), dY.get(), dw_part.get(), G.get() + off3(), kDwBlocks, s);
-    conv_launch<COUT_, HID, __nv_bfloat16, __nv_bfloat16>(g, dY.get(), w3(), 1, 0, H2.get(), dH2.get(), s);
-    conv_dw_launch<HID, HID>(g, H1.get(), dH2.get(), dw_part.get(), G.get() + off2(), kDwBlocks, s);
-    conv_launch<HID, HID, __nv_bfloat16, __nv_bfloat16>(g, dH2.get(), w2(), 1, 0, H1.get(), dH1.get(), s);
-    conv_dw_launch<CIN_, HID>(g, X.get(), dH1.get(), dw_part.get(), G.get(), kDwBlocks, s);
+    conv_pack_weights(w3(), HID, COUT_, COUT_, HID, 1, 1, wt3a.get(), s);
+    conv_pack_weights(w2(), HID, HID, HID, HID, 2, 1, wt2a.get(), s);
+    conv_dw_tc(g, L, 2, HID, H2.get(), 1, COUT_, dY.get(), dw_part.get(), G.get() + off3(), err.get(), s);
+    conv_tc(g, L, 1, kEpiMask, dY.get(), wt3a.get(), H2.get(), dH2.get(), nullptr, err.get(), s);
+    conv_dw_tc(g, L, 2, HID, H1.get(), 2, HID, dH2.get(), dw_part.get(), G.get() + off2(), err.get(), s);
+    conv_tc(g, L, 2, kEpiMask, dH2.get(), wt2a.get(), H1.get(), dH1.get(), nullptr, err.get(), s);
+    conv_dw_tc(g, L, 1, CIN_, X.get(), 2, HID, dH1.get(), dw_part.get(), G.get(), err.get(), s);
+}
+
+void LearnedNet::check(cudaStream_t s) {
+    int h = 0;
+    DM_CUDA(cudaMemcpyAsync(&h, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    DM_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        DM_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+        throw Error(DM_ERR_TIMEOUT, "learned network: a tensor-core conv kernel timed out waiting (code " +
+                                        std::to_string(h) + ")");
+    }
 }
 
 float LearnedNet::loss(const double* A, double msum, cudaStream_t s) {
     const dim3 nb = node_blocks(g);
-    launch("learned_mse", k_mse, nb, dim3(LX, LY, LZ), 0, s, g, Y.get(), E.get(), A, (float)(1.0 / std::max(msum, 1.0)),
-           dY.get(), loss_part.get());
+    launch("learned_mse", k_mse, nb, dim3(LX, LY, LZ), 0, s, g, L, Y.get(), E.get(), A,
+           (float)(1.0 / std::max(msum, 1.0)), dY.get(), loss_part.get());
     const int n = nb.x * nb.y * nb.z;
     DBuf<float> tot(1);
     launch("learned_mse_sum", k_colsum, 1, 256, 0, s, loss_part.get(), n, 1, tot.get());
@@ -416,7 +308,7 @@ float LearnedNet::residual_loss(const VecOp<float, float>& o, const double* A, c
     launch("learned_mse_sum", k_colsum, 1, 256, 0, s, loss_part.get(), nb, 1, tot.get());
     // dloss/dy = -K res / msum (K symmetric), dloss/dY = h^2 dloss/dy
     vec_stencil<float, float>(o, ST_APPLY, kbuf, nullptr, ybuf, 0.0, s);
-    launch("learned_grad_gather", k_grad_gather, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, ybuf, A,
+    launch("learned_grad_gather", k_grad_gather, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, L, ybuf, A,
            (float)(-h2 * inv_m), dY.get());
     float h = 0.f;
     DM_CUDA(cudaMemcpyAsync(&h, tot.get(), sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -434,11 +326,10 @@ void LearnedNet::adam(float lr, cudaStream_t s) {
 }
 
 void LearnedNet::set_X(const float* nat_dev, cudaStream_t s) {
-    launch("learned_pack", k_pack_nodes_ch<__nv_bfloat16>, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, CIN_, nat_dev,
-           X.get());
+    launch("learned_pack", k_pack_X, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, L, nat_dev, X.get());
 }
 void LearnedNet::set_E(const float* nat_dev, cudaStream_t s) {
-    launch("learned_pack", k_pack_nodes_ch<float>, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, COUT_, nat_dev, E.get());
+    launch("learned_pack", k_pack_nodes_f32, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, COUT_, nat_dev, E.get());
 }
 void LearnedNet::target_from(const float* e_pad, const double* A, double inv, cudaStream_t s) {
     launch("learned_target", k_target, node_blocks(g), dim3(LX, LY, LZ), 0, s, g, e_pad, A, inv, E.get());

@@ -94,7 +94,48 @@ def test_loss_and_gradient_match_oracle(dm, ctx):
     assert cos > 0.995, cos
     for a, b in ((0, 27 * 8 * 16), (27 * 8 * 16, 27 * 8 * 16 + 27 * 16 * 16), (27 * 8 * 16 + 27 * 16 * 16, g.size)):
         rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
-        assert rel < 6e-2, (a, rel)
+        print(f"layer gradient [{a}:{b}] relative error {rel:.2e}")
+        assert rel < 2e-2, (a, rel)      # BF16 activations and weights on the tensor cores
+
+
+def test_train_step_matches_oracle_residual_objective_and_adam(dm, ctx):
+    """One training step of the library (features, forward, the residual
+    objective with the FP32 operator, backward on the tensor cores, Adam)
+    against the oracle's residual objective in FP64 and its Adam update."""
+    w = W.sphere_workload(10, offset_seed=6, sigma=5.0)
+    g = w.grid
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma, precision="f32")
+    net = dm.Learned(ctx, seed=5)
+    wts = net.get_weights()
+    wts[27 * 8 * 16 + 27 * 16 * 16:] *= 10.0
+    net.set_weights(wts)
+    Ws = _weights(wts)
+    fr = geometry.fractions(w.phi)
+    ops = operators.DMOperators(g, fr)
+    A = operators.face_vector(fr)
+    m = (A > 0).astype(float)
+    r = np.random.default_rng(2).standard_normal(A.size) * m
+    lr = 1e-3
+    loss, grad = net.train_step(op, r, lr=lr)
+    X, _, scale, _ = _features(w, r)
+    h = min(g.dx, g.dy, g.dz)
+    K = ops.K(w.sigma)
+    lref, Gref, _ = OL.residual_loss_and_grads(_bf16(X), m * r / scale, Ws, K, h * h,
+                                               lambda Y: _faces_from_nodes(Y, g), lambda v: _node_faces(v, g), m)
+    print(f"\nresidual objective: GPU {loss:.6g}, oracle {lref:.6g}")
+    assert abs(loss - lref) / lref < 1e-2, (loss, lref)
+    gref = np.concatenate([G.ravel() for G in Gref])
+    for a, b in ((0, 27 * 8 * 16), (27 * 8 * 16, 27 * 8 * 16 + 27 * 16 * 16), (27 * 8 * 16 + 27 * 16 * 16, grad.size)):
+        rel = np.linalg.norm(grad[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
+        print(f"train-step gradient [{a}:{b}] relative error {rel:.2e}")
+        assert rel < 2e-2, (a, rel)
+    # Adam: the GPU's update from its own gradient equals the oracle's update from that gradient
+    state = {"t": 0, "m": [np.zeros_like(x) for x in Ws], "v": [np.zeros_like(x) for x in Ws]}
+    Wn = OL.adam_step(Ws, _weights(grad.astype(np.float64)), state, lr=lr)
+    wref = np.concatenate([x.ravel() for x in Wn])
+    wgpu = net.get_weights().astype(np.float64)
+    assert np.max(np.abs(wgpu - wref)) <= 1e-6 * lr + 1e-6 * np.max(np.abs(wref)), np.max(np.abs(wgpu - wref))
 
 
 def test_training_lowers_loss_and_solver_uses_network(dm, ctx):
