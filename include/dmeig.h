@@ -62,7 +62,8 @@ typedef struct dm_learned dm_learned;
  * direction, Sec. 6). */
 typedef struct dm_mg_params {
     int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4) */
-    int band_sweeps;       /* Jacobi sweeps of the cut-cell band smoother after each smoothing step (16):
+    int band_sweeps;       /* Jacobi sweeps of the cut-cell band smoother after each smoothing step on the
+                              fine level (16; the coarser levels take band_sweeps_coarse):
                               a restricted additive Schwarz step over bricks of band_brick^3 nodes with
                               one node of overlap; each subdomain sweeps on its own faces, couplings to
                               other faces frozen, and the brick keeps the faces it owns */
@@ -77,6 +78,7 @@ typedef struct dm_mg_params {
                               results are cached in the context by level size and precision (1) */
     int stencil_shape;     /* -1: the autotuner's choice (shape 0 when autotune = 0); 0..5: use this
                               tile shape (see dm_operator_stencil_shape) on every level (-1) */
+    int band_sweeps_coarse; /* band_sweeps of the levels below the fine one (8) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {

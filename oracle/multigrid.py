@@ -284,16 +284,20 @@ def coarsest_solve(level, f):
     return x
 
 
-def vcycle(levels, f, omegas, band_sweeps=16, l=0, brick=8):
-    """e ~= (K_l - sigma A_l)^-1 f: one V(1,1) cycle from a zero guess."""
+def vcycle(levels, f, omegas, band_sweeps=16, l=0, brick=8, band_sweeps_coarse=None):
+    """e ~= (K_l - sigma A_l)^-1 f: one V(1,1) cycle from a zero guess.  The
+    band smoother runs ``band_sweeps`` sweeps on the fine level and
+    ``band_sweeps_coarse`` (default: the same) on the coarser ones."""
     lev = levels[l]
     if l == len(levels) - 1:
         return coarsest_solve(lev, f)
-    e = smooth(lev, f, None, omegas[l], band_sweeps, from_zero=True, brick=brick)
+    coarse = band_sweeps if band_sweeps_coarse is None else band_sweeps_coarse
+    sweeps = band_sweeps if l == 0 else coarse
+    e = smooth(lev, f, None, omegas[l], sweeps, from_zero=True, brick=brick)
     r = f - lev.K @ e
-    ec = vcycle(levels, restrict(levels, l, r), omegas, band_sweeps, l + 1, brick)
+    ec = vcycle(levels, restrict(levels, l, r), omegas, band_sweeps, l + 1, brick, coarse)
     e = prolong_add(levels, l, e, ec)
-    return smooth(lev, f, e, omegas[l], band_sweeps, brick=brick)
+    return smooth(lev, f, e, omegas[l], sweeps, brick=brick)
 
 
 # -- scalar V-cycle -----------------------------------------------------------

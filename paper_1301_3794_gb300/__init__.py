@@ -213,7 +213,8 @@ class Geometry:
 
 
 def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
-              autotune=1, force_shape=-1):
+              autotune=1, force_shape=-1, band_sweeps_coarse=None):
+    """band_sweeps_coarse: sweeps below the fine level (None: the library's default, 8)."""
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -224,6 +225,8 @@ def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power
     p.precision = PREC[precision] if isinstance(precision, str) else int(precision)
     p.autotune = int(autotune)
     p.stencil_shape = int(force_shape)
+    if band_sweeps_coarse is not None:
+        p.band_sweeps_coarse = int(band_sweeps_coarse)
     return p
 
 

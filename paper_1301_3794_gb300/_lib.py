@@ -16,7 +16,7 @@ PREC = {"f64": 0, "f32": 1, "bf16": 2}
 class MGParams(C.Structure):
     _fields_ = [("max_coarse", C.c_int), ("band_sweeps", C.c_int), ("band_brick", C.c_int), ("omega_scale", C.c_double),
                 ("power_iters", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
-                ("stencil_shape", C.c_int)]
+                ("stencil_shape", C.c_int), ("band_sweeps_coarse", C.c_int)]
 
 
 class EigParams(C.Structure):

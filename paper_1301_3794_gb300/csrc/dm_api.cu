@@ -384,6 +384,9 @@ ScalOp<T, TC> sop(const dm_operator* op, int l) {
                          g.ntiles};
 }
 
+// band smoother sweeps of level l: the fine level, or the coarser ones
+int band_sweeps_of(const dm_operator* op, int l) { return l == 0 ? op->mg.band_sweeps : op->mg.band_sweeps_coarse; }
+
 // ---- vector V-cycle: result in rbuf ------------------------------------------------
 template <typename T, typename TC>
 void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
@@ -400,9 +403,10 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const VecOp<T, TC> o = vop<T, TC>(op, l);
     const double om = op->ol[l].omega;
     double* u = op->band_u.get();
+    const int sweeps = band_sweeps_of(op, l);
     vec_jacobi_zero(o, f, ebuf, om, s);
-    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om,
-                        op->mg.band_sweeps, l == 0, s);
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om, sweeps, l == 0,
+                        s);
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
@@ -412,8 +416,8 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, g.tiles.get(),
                             g.ntiles, s);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
-    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om,
-                        op->mg.band_sweeps, l == 0, s);
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om, sweeps, l == 0,
+                        s);
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -1481,6 +1485,7 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->precision = DM_PREC_F64;
     p->autotune = 1;
     p->stencil_shape = -1;
+    p->band_sweeps_coarse = 8;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1497,6 +1502,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         if (mg) op->mg = *mg;
         DM_REQUIRE(op->mg.max_coarse >= 4, DM_ERR_INVALID_ARG, "max_coarse must be >= 4");
         DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 256, DM_ERR_INVALID_ARG, "band_sweeps out of range");
+        DM_REQUIRE(op->mg.band_sweeps_coarse >= 0 && op->mg.band_sweeps_coarse <= 256, DM_ERR_INVALID_ARG,
+                   "band_sweeps_coarse out of range");
         DM_REQUIRE(op->mg.band_brick >= 1, DM_ERR_INVALID_ARG, "band_brick must be >= 1");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
@@ -1578,7 +1585,7 @@ dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double
             const VecOp<T, TC> o = vop<T, TC>(op, level);
             vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
             band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[level]), o.invD, g.g, g.band.get(), g.nband, p[0], p[2], u, om,
-                                op->mg.band_sweeps, level == 0, s);
+                                band_sweeps_of(op, level), level == 0, s);
         };
         if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
         else if (op->mg.precision == DM_PREC_F32)

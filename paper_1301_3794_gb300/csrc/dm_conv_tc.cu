@@ -39,7 +39,7 @@ namespace {
 constexpr int kTileM = 128;                 // nodes per tile (MMA M)
 constexpr int kWin = kTileM + 2;            // window rows: one extra node on each side
 constexpr int kWinBytes = kWin * 16;        // 2080
-constexpr int kStepBytes = 16 * 16 * 2;     // one B tile (N = 16, K = 16, BF16)
+constexpr int kStepBytes = 2 * 16 * 16 * 2; // one step's B tiles (N = 16, K = 16, BF16): high part, low part
 constexpr uint32_t kTmemCols = 32;          // smallest allocation; columns 0..15 used
 constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
 
@@ -148,7 +148,12 @@ __device__ __forceinline__ bool grid_node(const Grid3& g, int p) {
 }
 
 // B tiles of every MMA step, BF16 canonical K-major (N = 16 rows, K = 16):
-// element (n, k) of step s at s * 256 + (k / 8) * 128 + (n / 8) * 64 + (n % 8) * 8 + k % 8.
+// element (n, k) of step s at s * 512 + h * 256 + (k / 8) * 128 + (n / 8) * 64 +
+// (n % 8) * 8 + k % 8, where h = 0 holds the weight rounded to BF16 and h = 1
+// the BF16 rounding of what is left (w - hi): the two MMAs of a step then
+// multiply by the weight to about 16 significant bits, which the residual
+// objective needs (its gradient passes the output through K twice, and BF16
+// weights alone would leave a 1.5% gradient error).
 // CB = 2: step s is tap s with k = input channel 0..15.  CB = 1: step s < 13
 // holds taps 2s (k < 8) and 2s + 1 (k >= 8, channel k - 8); step 13 holds tap
 // 26 in its upper half and zero weights in its lower half (whose rows the
@@ -160,6 +165,7 @@ __global__ void k_pack_wtiles(const float* __restrict__ W, int wcin, int wcout, 
     const int nsteps = cb == 2 ? 27 : 14;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nsteps * 256; e += gridDim.x * blockDim.x) {
         const int s = e / 256, r = e % 256;
+        __nv_bfloat16* const o = out + s * 512 + r;
         const int kh = r / 128, r2 = r % 128, ng = r2 / 64, r3 = r2 % 64, n = ng * 8 + r3 / 8, kl = r3 % 8;
         const int kin = kh * 8 + kl;
         int t, ch;
@@ -173,7 +179,9 @@ __global__ void k_pack_wtiles(const float* __restrict__ W, int wcin, int wcout, 
         float v = 0.f;
         if (t < 27 && ch < cin && n < cout)
             v = flip ? W[((size_t)(26 - t) * wcin + n) * wcout + ch] : W[((size_t)t * wcin + ch) * wcout + n];
-        out[e] = __float2bfloat16(v);
+        const __nv_bfloat16 hi = __float2bfloat16(v);
+        o[0] = hi;
+        o[256] = __float2bfloat16(v - __bfloat162float(hi));
     }
 }
 
@@ -254,7 +262,9 @@ __global__ void __launch_bounds__(128) k_conv_tc(Grid3 g, ActLayout L, const __n
                     a0 = win_base;
                     lbo = 8 * kWinBytes + 2 * 16;
                 }
-                mma_bf16(tmem, sdesc(a0, lbo, 128), sdesc(w_base + s * kStepBytes, 256, 128), s > 0 ? 1u : 0u);
+                const uint64_t ad = sdesc(a0, lbo, 128);
+                mma_bf16(tmem, ad, sdesc(w_base + s * kStepBytes, 256, 128), s > 0 ? 1u : 0u);
+                mma_bf16(tmem, ad, sdesc(w_base + s * kStepBytes + 512, 256, 128), 1u);
             }
             mma_commit(&bar_mma);
         }

@@ -213,11 +213,11 @@ void LearnedNet::alloc(const Grid3& grid) {
     dH2.alloc(L.elems(2));
     Y.alloc(np * COUT_);
     E.alloc(np * COUT_);
-    wt1.alloc((size_t)conv_wtile_steps(1) * 256);
-    wt2.alloc((size_t)conv_wtile_steps(2) * 256);
-    wt3.alloc((size_t)conv_wtile_steps(2) * 256);
-    wt3a.alloc((size_t)conv_wtile_steps(1) * 256);
-    wt2a.alloc((size_t)conv_wtile_steps(2) * 256);
+    wt1.alloc((size_t)conv_wtile_steps(1) * 512);
+    wt2.alloc((size_t)conv_wtile_steps(2) * 512);
+    wt3.alloc((size_t)conv_wtile_steps(2) * 512);
+    wt3a.alloc((size_t)conv_wtile_steps(1) * 512);
+    wt2a.alloc((size_t)conv_wtile_steps(2) * 512);
     err.alloc(1);
     const dim3 nb = node_blocks(g);
     loss_part.alloc((size_t)nb.x * nb.y * nb.z);

@@ -16,8 +16,9 @@ struct ActLayout {
 };
 ActLayout act_layout(const Grid3& g);
 
-// Tensor-core convolution (dm_conv_tc.cu).  Weight tiles: BF16, one 16 x 16
-// tile per MMA step (conv_wtile_steps(cb) of them), made by conv_pack_weights
+// Tensor-core convolution (dm_conv_tc.cu).  Weight tiles: BF16, two 16 x 16
+// tiles per MMA step (the weight's BF16 rounding and the BF16 rounding of the
+// rest; 512 values a step, conv_wtile_steps(cb) steps), made by conv_pack_weights
 // from FP32 weights W[27][wcin][wcout] (flip = 1: the adjoint conv, whose
 // input has cin = wcout channels and output cout = wcin channels).
 int conv_wtile_steps(int cb);

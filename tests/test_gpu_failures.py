@@ -127,14 +127,18 @@ def test_unreachable_targets_return_a_partial_result(dm, ctx, opts):
 
 
 def test_certificate_tolerance_is_enforced(dm, ctx):
-    """With rho_tol below what the default tolerances deliver, the solver
-    tightens them and keeps iterating until every returned pair's FP64
-    certificate meets rho_tol; rho_tol = 0 returns on the Ritz estimates."""
+    """Shifted solves to only 1e-6 leave residuals of the pencil above 1e-8
+    although the Ritz estimates converge; with rho_tol = 1e-8 the solver then
+    tightens its tolerances and keeps iterating until every returned pair's
+    FP64 certificate meets 1e-8.  rho_tol = 0 returns on the Ritz estimates."""
     w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=7.0)
     geom = dm.Geometry.from_workload(ctx, w)
-    k2a, _, repa, sta = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, rho_tol=0.0)
-    k2b, _, repb, stb = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, rho_tol=1e-12)
-    assert sta == 0 and stb == 0, (repa, repb)
-    assert repb["rho_max"] <= 1e-12 and repb["n_converged"] == w.nev, repb
-    assert repb["inner_iters"] >= repa["inner_iters"]
-    assert np.max(np.abs(k2a - k2b) / k2b) < 1e-10
+    k2a, _, repa, sta = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, inner_tol=1e-6, rho_tol=0.0)
+    k2b, _, repb, stb = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, inner_tol=1e-6, rho_tol=1e-8)
+    print(f"\ninner 1e-6: rho_max {repa['rho_max']:.2e} on the Ritz estimates, {repb['rho_max']:.2e} certified; "
+          f"inner iterations {repa['inner_iters']} -> {repb['inner_iters']}")
+    assert sta == 0 and repa["rho_max"] > 1e-8, repa
+    assert stb == 0 and repb["rho_max"] <= 1e-8 and repb["n_converged"] == w.nev, repb
+    assert repb["inner_iters"] > repa["inner_iters"]
+    k2c, _, repc, stc = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None)
+    assert np.max(np.abs(k2b - k2c) / k2c) < 1e-9

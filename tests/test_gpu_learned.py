@@ -70,7 +70,8 @@ def test_forward_matches_oracle(dm, ctx):
     h = min(w.grid.dx, w.grid.dy, w.grid.dz)
     yref = _faces_from_nodes(Y, w.grid) * scale * h * h * (A > 0)
     rel = np.linalg.norm(y - yref) / np.linalg.norm(yref)
-    assert rel < 3e-2, rel          # BF16 activations
+    print(f"forward relative error {rel:.2e}")
+    assert rel < 1e-2, rel          # BF16 activations
 
 
 def test_loss_and_gradient_match_oracle(dm, ctx):
@@ -95,7 +96,7 @@ def test_loss_and_gradient_match_oracle(dm, ctx):
     for a, b in ((0, 27 * 8 * 16), (27 * 8 * 16, 27 * 8 * 16 + 27 * 16 * 16), (27 * 8 * 16 + 27 * 16 * 16, g.size)):
         rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
         print(f"layer gradient [{a}:{b}] relative error {rel:.2e}")
-        assert rel < 2e-2, (a, rel)      # BF16 activations and weights on the tensor cores
+        assert rel < 1e-2, (a, rel)      # BF16 activations on the tensor cores
 
 
 def test_train_step_matches_oracle_residual_objective_and_adam(dm, ctx):
@@ -129,7 +130,7 @@ def test_train_step_matches_oracle_residual_objective_and_adam(dm, ctx):
     for a, b in ((0, 27 * 8 * 16), (27 * 8 * 16, 27 * 8 * 16 + 27 * 16 * 16), (27 * 8 * 16 + 27 * 16 * 16, grad.size)):
         rel = np.linalg.norm(grad[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
         print(f"train-step gradient [{a}:{b}] relative error {rel:.2e}")
-        assert rel < 2e-2, (a, rel)
+        assert rel < 1e-2, (a, rel)
     # Adam: the GPU's update from its own gradient equals the oracle's update from that gradient
     state = {"t": 0, "m": [np.zeros_like(x) for x in Ws], "v": [np.zeros_like(x) for x in Ws]}
     Wn = OL.adam_step(Ws, _weights(grad.astype(np.float64)), state, lr=lr)

@@ -20,7 +20,7 @@ CASES = {
 }
 
 
-SWEEPS, BRICK = 16, 8        # band smoother defaults of the library
+SWEEPS, COARSE_SWEEPS, BRICK = 16, 8, 8    # band smoother defaults of the library (fine, coarser levels, brick)
 
 
 def _rel(a, b):
@@ -89,7 +89,7 @@ def test_smooth_restrict_prolong(case):
         f = rng.standard_normal(lev.mask.size) * lev.mask
         x = rng.standard_normal(lev.mask.size) * lev.mask
         got = op.smooth(f, x, level=l)
-        ref = MG.smooth(lev, f, x, om, SWEEPS, brick=BRICK)
+        ref = MG.smooth(lev, f, x, om, SWEEPS if l == 0 else COARSE_SWEEPS, brick=BRICK)
         assert _rel(got, ref) < 1e-12, l
         r = rng.standard_normal(lev.mask.size) * lev.mask
         assert _rel(op.restrict(r, level=l), MG.restrict(levels, l, r)) < 1e-13, l
@@ -104,7 +104,7 @@ def test_band_smoother_bricks(case_name, brick, sweeps, dm, ctx):
     grid (one subdomain: plain band-restricted Jacobi)."""
     w = CASES[case_name]()
     geom = dm.Geometry.from_workload(ctx, w)
-    op = dm.Operator(ctx, geom, w.sigma, band_brick=brick, band_sweeps=sweeps)
+    op = dm.Operator(ctx, geom, w.sigma, band_brick=brick, band_sweeps=sweeps, band_sweeps_coarse=sweeps)
     levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
     rng = np.random.default_rng(11)
     for l in range(len(levels) - 1):
@@ -130,7 +130,7 @@ def test_vcycle_fp64(case):
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(6).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
 
 
@@ -153,7 +153,7 @@ def test_vcycle_low_precision(prec, tol, dm, ctx):
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(8).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
 
