@@ -174,6 +174,16 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz,
                              double dx, double dy, double dz, const double origin[3],
                              const double* phi, int phi_on_device, double a_min,
                              dm_geometry** out);
+/* A geometry from cut fractions the caller supplies instead of a level set:
+ * L (edges, natural edge layout), A (faces) and V (cells), host or device per
+ * on_device; the coarser multigrid levels average them as in
+ * dm_geometry_create.  L and A must lie in [0, 1]; V must be finite and
+ * non-negative and may exceed 1 (perturbed volumes, as in Sec. 6.1's study of
+ * Eq. volPert1).  Entries on the outer walls are ignored: the walls are perfect
+ * conductors.  Out-of-range values give DM_ERR_GEOMETRY. */
+dm_status dm_geometry_create_from_fractions(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                                            const double* L, const double* A, const double* V, int on_device,
+                                            dm_geometry** out);
 void dm_geometry_destroy(dm_geometry* geom);
 
 /* Multigrid levels available below (and including) the fine grid. */

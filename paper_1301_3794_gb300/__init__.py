@@ -170,6 +170,26 @@ class Geometry:
         ctx._adopt(self)
 
     @classmethod
+    def from_fractions(cls, ctx, nx, ny, nz, dx, dy, dz, L, A, V):
+        """A geometry from given edge, face and cell fractions (natural layouts)."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.dims = (int(nx), int(ny), int(nz))
+        self.spacing = (float(dx), float(dy), float(dz))
+        la = _Arg(L, edge_count(nx, ny, nz))
+        aa = _Arg(A, face_count(nx, ny, nz))
+        va = _Arg(V, cell_count(nx, ny, nz))
+        if not (la.device == aa.device == va.device):
+            raise ValueError("L, A and V must all be host arrays or all device tensors")
+        h = C.c_void_p()
+        st = lib.dm_geometry_create_from_fractions(ctx.h, nx, ny, nz, dx, dy, dz, la.ptr, aa.ptr, va.ptr, la.device,
+                                                   C.byref(h))
+        ctx.check(st, "dm_geometry_create_from_fractions")
+        self.h = h
+        ctx._adopt(self)
+        return self
+
+    @classmethod
     def from_workload(cls, ctx, w, a_min=0.0, phi=None):
         g = w.grid
         return cls(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, w.phi.ravel() if phi is None else phi, g.origin, a_min)

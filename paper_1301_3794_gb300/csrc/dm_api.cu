@@ -1358,17 +1358,20 @@ dm_status dm_trace_entry_bytes(dm_context* ctx, int i, double* bytes) {
 
 long long dm_debug_allocation_count(void) { return g_allocations.load(std::memory_order_relaxed); }
 
-dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
-                             const double origin[3], const double* phi, int phi_on_device, double a_min,
-                             dm_geometry** out) {
-    if (!ctx || !out || !phi) return DM_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// The multigrid levels of a geometry: `fine` fills level 0's L, A and V
+// (padded layouts); every coarser level averages the level above.
+template <class Fine>
+dm_status build_geometry(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz, Fine&& fine,
+                         dm_geometry** out) {
     *out = nullptr;
-    (void)origin;
     auto geom = std::make_unique<dm_geometry>();
     const dm_status st = guarded(ctx, [&] {
         DM_REQUIRE(nx >= 2 && ny >= 2 && nz >= 2, DM_ERR_INVALID_ARG, "grid needs at least 2 cells per dimension");
         DM_REQUIRE(dx > 0 && dy > 0 && dz > 0, DM_ERR_INVALID_ARG, "cell sizes must be positive");
-        DM_REQUIRE(a_min >= 0.0 && a_min < 1.0, DM_ERR_INVALID_ARG, "a_min must be in [0, 1)");
         DM_CUDA(cudaSetDevice(ctx->device));
         cudaStream_t s = ctx->stream;
         geom->ctx = ctx;
@@ -1383,21 +1386,7 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
             lv->V.alloc(n1);
             lv->invV.alloc(n1);
             if (l == 0) {
-                DBuf<double> phi_pad(n1);
-                const size_t nn = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
-                DBuf<double> tmp;
-                const double* dphi = nullptr;
-                stage_in(ctx, phi, phi_on_device, nn, tmp, &dphi);
-                {
-                    DBuf<int> bad(1);
-                    const int nbad = count_nonfinite((long long)nn, dphi, bad.get(), s);
-                    DM_REQUIRE(nbad == 0, DM_ERR_GEOMETRY,
-                               "level set: " + std::to_string(nbad) + " of " + std::to_string(nn) +
-                                   " node values are NaN or infinite");
-                }
-                pack_nodes(lv->g, dphi, phi_pad.get(), s);
-                geom_fractions(lv->g, phi_pad.get(), lv->L.get(), lv->A.get(), lv->V.get(), s);
-                if (a_min > 0.0) geom_neglect_faces(lv->g, a_min, lv->L.get(), lv->A.get(), s);
+                fine(*lv, s);
                 Sync::stream(s);
             } else {
                 const GeoLevel& f = *geom->lv[l - 1];
@@ -1429,6 +1418,68 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
     if (st != DM_OK) return st;
     *out = geom.release();
     return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                             const double origin[3], const double* phi, int phi_on_device, double a_min,
+                             dm_geometry** out) {
+    if (!ctx || !out || !phi) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    (void)origin;
+    if (!(a_min >= 0.0 && a_min < 1.0)) {
+        ctx->err = "a_min must be in [0, 1)";
+        return DM_ERR_INVALID_ARG;
+    }
+    return build_geometry(ctx, nx, ny, nz, dx, dy, dz, [&](GeoLevel& lv, cudaStream_t s) {
+        DBuf<double> phi_pad(lv.g.np);
+        const size_t nn = (size_t)(nx + 1) * (ny + 1) * (nz + 1);
+        DBuf<double> tmp;
+        const double* dphi = nullptr;
+        stage_in(ctx, phi, phi_on_device, nn, tmp, &dphi);
+        {
+            DBuf<int> bad(1);
+            const int nbad = count_nonfinite((long long)nn, dphi, bad.get(), s);
+            DM_REQUIRE(nbad == 0, DM_ERR_GEOMETRY,
+                       "level set: " + std::to_string(nbad) + " of " + std::to_string(nn) +
+                           " node values are NaN or infinite");
+        }
+        pack_nodes(lv.g, dphi, phi_pad.get(), s);
+        geom_fractions(lv.g, phi_pad.get(), lv.L.get(), lv.A.get(), lv.V.get(), s);
+        if (a_min > 0.0) geom_neglect_faces(lv.g, a_min, lv.L.get(), lv.A.get(), s);
+        Sync::stream(s);
+    }, out);
+}
+
+dm_status dm_geometry_create_from_fractions(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                                            const double* L, const double* A, const double* V, int on_device,
+                                            dm_geometry** out) {
+    if (!ctx || !out || !L || !A || !V) return DM_ERR_INVALID_ARG;
+    *out = nullptr;
+    return build_geometry(ctx, nx, ny, nz, dx, dy, dz, [&](GeoLevel& lv, cudaStream_t s) {
+        const Grid3& g = lv.g;
+        const size_t ne = (size_t)natural_edges(g), nf = (size_t)natural_faces(g), nc = (size_t)natural_cells(g);
+        DBuf<double> tl, ta, tv;
+        const double *dl = nullptr, *da = nullptr, *dv = nullptr;
+        stage_in(ctx, L, on_device, ne, tl, &dl);
+        stage_in(ctx, A, on_device, nf, ta, &da);
+        stage_in(ctx, V, on_device, nc, tv, &dv);
+        DBuf<int> bad(1);
+        const int bl = count_outside((long long)ne, dl, 0.0, 1.0, bad.get(), s);
+        const int ba = count_outside((long long)nf, da, 0.0, 1.0, bad.get(), s);
+        const int bv = count_outside((long long)nc, dv, 0.0, std::numeric_limits<double>::max(), bad.get(), s);
+        DM_REQUIRE(bl == 0 && ba == 0 && bv == 0, DM_ERR_GEOMETRY,
+                   "fractions: " + std::to_string(bl) + " edge and " + std::to_string(ba) +
+                       " face values outside [0, 1], " + std::to_string(bv) + " cell values negative or not finite");
+        pack_edges(g, dl, lv.L.get(), s);
+        pack_faces(g, da, lv.A.get(), s);
+        pack_cells(g, dv, lv.V.get(), s);
+        geom_close_walls(g, lv.L.get(), lv.A.get(), s);
+        Sync::stream(s);
+    }, out);
 }
 
 void dm_geometry_destroy(dm_geometry* geom) {

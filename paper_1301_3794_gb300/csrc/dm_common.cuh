@@ -291,6 +291,10 @@ int count_positive(long long n, const double* a, int* d_count, cudaStream_t s);
 int count_nonfinite(long long n, const double* a, int* d_count, cudaStream_t s);
 // number of nonzero flags
 int count_flags(long long n, const unsigned char* a, int* d_count, cudaStream_t s);
+// number of entries outside [lo, hi] (NaN included)
+int count_outside(long long n, const double* a, double lo, double hi, int* d_count, cudaStream_t s);
+// zero the normal faces and tangential edges on the outer walls
+void geom_close_walls(const Grid3& g, double* L, double* A, cudaStream_t s);
 // active tiles of a level in ascending order (tiles: capacity of all tiles); returns the count
 int geom_tiles(const Grid3& g, const double* A, const unsigned char* active, int* tiles, int* flags, int* d_count,
                cudaStream_t s);
@@ -302,6 +306,7 @@ int geom_active_cells(const Grid3& g, const double* A, int* list, unsigned char*
 // natural <-> padded layouts
 void pack_nodes(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
 void pack_faces(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
+void pack_edges(const Grid3& g, const double* nat, double* pad, cudaStream_t s);
 void unpack_faces(const Grid3& g, const double* pad, double* nat, cudaStream_t s);
 void unpack_edges(const Grid3& g, const double* pad, double* nat, cudaStream_t s);
 void pack_cells(const Grid3& g, const double* nat, double* pad, cudaStream_t s);

@@ -122,6 +122,22 @@ __global__ void k_fractions(Grid3 g, const double* __restrict__ phi, double* __r
     }
 }
 
+// The outer walls are perfect conductors: normal faces and tangential edges on
+// them are closed whatever fractions a caller supplied.
+__global__ void k_close_walls(Grid3 g, double* __restrict__ L, double* __restrict__ A) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z * BZ + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k), N = g.np;
+    if (i < g.nx && (j == 0 || j == g.ny || k == 0 || k == g.nz)) L[p] = 0.0;
+    if (j < g.ny && (i == 0 || i == g.nx || k == 0 || k == g.nz)) L[N + p] = 0.0;
+    if (k < g.nz && (i == 0 || i == g.nx || j == 0 || j == g.ny)) L[2 * N + p] = 0.0;
+    if (j < g.ny && k < g.nz && (i == 0 || i == g.nx)) A[p] = 0.0;
+    if (i < g.nx && k < g.nz && (j == 0 || j == g.ny)) A[N + p] = 0.0;
+    if (i < g.nx && j < g.ny && (k == 0 || k == g.nz)) A[2 * N + p] = 0.0;
+}
+
 // Sec. 3: faces with 0 < A < a_min are neglected together with their edges.
 __global__ void k_neglect(Grid3 g, double a_min, double* __restrict__ L, double* __restrict__ A) {
     const int i = blockIdx.x * BX + threadIdx.x;
@@ -453,6 +469,23 @@ int count_nonfinite(long long n, const double* a, int* d_count, cudaStream_t s) 
     return read_count(d_count, s);
 }
 
+__global__ void k_count_outside(long long n, const double* __restrict__ a, double lo, double hi,
+                                int* __restrict__ count) {
+    int c = 0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        c += (a[r] >= lo && a[r] <= hi) ? 0 : 1;   // NaN counts as outside
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+int count_outside(long long n, const double* a, double lo, double hi, int* d_count, cudaStream_t s) {
+    DM_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int), s));
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+    launch("k_count_outside", k_count_outside, blocks, 256, 0, s, n, a, lo, hi, d_count);
+    return read_count(d_count, s);
+}
+
 __global__ void k_count_flags(long long n, const unsigned char* __restrict__ a, int* __restrict__ count) {
     int c = 0;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
@@ -561,6 +594,12 @@ void pack_faces(const Grid3& g, const double* nat, double* pad, cudaStream_t s) 
 }
 void unpack_faces(const Grid3& g, const double* pad, double* nat, cudaStream_t s) {
     launch("k_pack3", k_pack3, node_grid(g), kBlock, 0, s, g, 0, nat, const_cast<double*>(pad), 1);
+}
+void pack_edges(const Grid3& g, const double* nat, double* pad, cudaStream_t s) {
+    launch("k_pack3", k_pack3, node_grid(g), kBlock, 0, s, g, 1, const_cast<double*>(nat), pad, 0);
+}
+void geom_close_walls(const Grid3& g, double* L, double* A, cudaStream_t s) {
+    launch("k_close_walls", k_close_walls, node_grid(g), kBlock, 0, s, g, L, A);
 }
 void unpack_edges(const Grid3& g, const double* pad, double* nat, cudaStream_t s) {
     launch("k_pack3", k_pack3, node_grid(g), kBlock, 0, s, g, 1, nat, const_cast<double*>(pad), 1);

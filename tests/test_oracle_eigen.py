@@ -62,3 +62,23 @@ def test_frequency_convergence_second_order_and_first_order_with_face_neglect():
     order = {a: np.log2(errs[a, 16] / errs[a, 32]) for a in (0.0, 0.1)}
     assert order[0.1] < 1.5, (order, errs)
     assert errs[0.1, 32] > 3.0 * errs[0.0, 32], errs
+
+
+def test_octant_lowest_mode_is_the_l3_tm_mode_at_second_order():
+    """Sec. 6.2: with perfectly conducting planes at x, y, z = 0 (here the
+    grid's own walls) the lowest mode of the sphere octant is the TM mode of
+    l = 3 whose angular part is x y z / r^3 (kR = 4.973420, the only l = 3
+    combination that vanishes tangentially on all three planes); the TM_1,
+    TM_2 and TE_1 modes do not fit the planes.  It is not degenerate, and its
+    eigenvalue converges at second order."""
+    k3 = [r for r, kind, l, _ in analytic.sphere_modes(xmax=6.0) if kind == "TM" and l == 3][0]
+    errs = {}
+    for n in (12, 24):
+        w = W.octant_sphere_workload(n)
+        ops = operators.DMOperators(w.grid, geometry.fractions(w.phi))
+        k2, _, _ = eigen.shift_invert_modes(ops, 20.0, 2)
+        k2 = np.sort(k2)
+        assert k2[1] > 1.3 * k2[0], k2                     # the next mode (TE_2) is far above
+        errs[n] = abs(k2[0] - k3 ** 2) / k3 ** 2
+    assert errs[24] < 3e-3, errs
+    assert np.log2(errs[12] / errs[24]) > 1.8, errs

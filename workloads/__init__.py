@@ -29,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "Grid", "Workload", "node_coords", "sphere_phi", "box_phi", "ellipsoid_phi",
-    "nine_cell_profile", "nine_cell_phi", "sphere_workload", "box_workload",
+    "nine_cell_profile", "nine_cell_phi", "sphere_workload", "octant_sphere_workload", "box_workload",
     "ellipsoid_workload", "nine_cell_workload", "batch_workloads", "SEED_BASE",
 ]
 
@@ -199,6 +199,16 @@ def sphere_workload(n=16, radius=1.0, half_width=1.1, sigma=7.0, nev=4, offset_s
         center = np.random.default_rng(seed).uniform(0.0, h, size=3)
     return Workload(f"sphere{n}", g, sphere_phi(g, center, radius), sigma, nev, seed,
                     {"center": tuple(center), "radius": radius})
+
+
+def octant_sphere_workload(n=16, radius=1.0, extent=1.1, sigma=20.0, nev=1):
+    """The positive octant of a sphere centred at the origin on [0, extent]^3
+    (Sec. 6.2's convergence study): the grid's walls at x, y, z = 0 are the
+    perfectly conducting symmetry planes."""
+    h = extent / n
+    g = Grid(n, n, n, h, h, h, (0.0, 0.0, 0.0))
+    return Workload(f"octant{n}", g, sphere_phi(g, (0.0, 0.0, 0.0), radius), sigma, nev, -1,
+                    {"center": (0.0, 0.0, 0.0), "radius": radius})
 
 
 def box_workload(nx=12, ny=10, nz=8, lx=1.0, ly=0.8, lz=0.6, sigma=7.0, nev=4):
