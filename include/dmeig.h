@@ -61,7 +61,8 @@ typedef struct dm_learned dm_learned;
  * an algebraic V-cycle with one order-1 polynomial smoother step per level and
  * direction, Sec. 6). */
 typedef struct dm_mg_params {
-    int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4) */
+    int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4),
+                              and while the level has more than dense_coarse open faces */
     int band_sweeps;       /* Jacobi sweeps of the cut-cell band smoother after each smoothing step on the
                               fine level (16; the coarser levels take band_sweeps_coarse):
                               a restricted additive Schwarz step over bricks of band_brick^3 nodes with
@@ -79,6 +80,12 @@ typedef struct dm_mg_params {
     int stencil_shape;     /* -1: the autotuner's choice (shape 0 when autotune = 0); 0..5: use this
                               tile shape (see dm_operator_stencil_shape) on every level (-1) */
     int band_sweeps_coarse; /* band_sweeps of the levels below the fine one (8) */
+    int symmetric_transform; /* 1: the V-cycle of Eq. fullMat2's symmetric form (Sec. 5.3): every level
+                              congruence-scaled by A^-1/2, which for this cycle amounts to the transfers
+                              A_c^1/2 R A^-1/2 and A^-1/2 P A_c^1/2 (smoothing and the coarsest solve
+                              are invariant under the scaling); the outer solves still use K (0) */
+    int dense_coarse;      /* a level with at most this many open faces is the coarsest and is solved
+                              densely (2048; 0 = coarsen by max_coarse alone; at most 6000) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
@@ -102,6 +109,11 @@ typedef struct dm_eig_params {
                               the Ritz tolerance drops to a tenth of the worst current estimate, inner_tol
                               to a tenth (down to 1e-15 and 1e-13), and the Krylov-Schur iteration
                               continues */
+    int inner_relax;       /* 1: after each restart, solve the new shifted systems only to
+                              inner_tol / r (at most 1e-6), r the largest relative Ritz residual of the
+                              wanted pairs not yet converged -- a direction added then enters their
+                              vectors with a weight of order r (inexact shift-and-invert, after
+                              Simoncini 2005); rho_tol still certifies every returned pair (1) */
 } dm_eig_params;
 
 typedef struct dm_eig_report {

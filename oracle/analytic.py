@@ -148,3 +148,45 @@ def sphere_neumann_modes(xmax=5.0, lmax=4):
 
 def sphere_volume(radius=1.0):
     return 4.0 / 3.0 * math.pi * radius ** 3
+
+
+# ---------------------------------------------------------------------------
+# the octant's lowest mode: TM, l = 3, angular part x y z / r^3
+# ---------------------------------------------------------------------------
+
+def _xyz_harmonic_curl(pts):
+    """(x cross grad) u for u = x y z / r^3 (a real l = 3 harmonic), at pts (N x 3)."""
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    r2 = x * x + y * y + z * z
+    r3 = r2 * np.sqrt(r2)
+    r5 = r3 * r2
+    p = x * y * z
+    g = np.stack([y * z / r3 - 3.0 * x * p / r5, x * z / r3 - 3.0 * y * p / r5, x * y / r3 - 3.0 * z * p / r5], axis=1)
+    return np.cross(pts, g)
+
+
+def tm_xyz_b(k, pts):
+    """Magnetic field of the spherical cavity's TM mode of l = 3 with angular
+    part x y z / r^3 (Jackson's TM modes: B = j_l(k r) (r cross grad) Y, E
+    from Ampere's law), up to a constant factor: B = j_3(k r) (x cross grad) u."""
+    pts = np.asarray(pts, dtype=float)
+    r = np.linalg.norm(pts, axis=1)
+    j3 = np.array([sph_jn(3, k * v) for v in r])
+    return j3[:, None] * _xyz_harmonic_curl(pts)
+
+
+def curl_numeric(f, pts, h=1e-4):
+    """curl f at pts by fourth-order central differences of the vector field f."""
+    pts = np.asarray(pts, dtype=float)
+    J = np.zeros((pts.shape[0], 3, 3))   # J[:, i, j] = d f_i / d x_j
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        J[:, :, j] = (-f(pts + 2 * e) + 8 * f(pts + e) - 8 * f(pts - e) + f(pts - 2 * e)) / (12 * h)
+    return np.stack([J[:, 2, 1] - J[:, 1, 2], J[:, 0, 2] - J[:, 2, 0], J[:, 1, 0] - J[:, 0, 1]], axis=1)
+
+
+def tm_xyz_e(k, pts):
+    """Electric field of the same mode, up to the same constant (and a factor
+    i c): E = curl B / k."""
+    return curl_numeric(lambda p: tm_xyz_b(k, p), pts) / k

@@ -168,28 +168,32 @@ class ScalarLevel:
         self.inv_d = np.where(self.active, 1.0 / np.where(self.active, d, 1.0), 0.0)
 
 
-def _coarse_grids(grid, max_coarse):
-    from workloads import Grid
-    out = [grid]
-    g = grid
-    while can_coarsen(g.nx, g.ny, g.nz, max_coarse):
-        g = Grid(g.nx // 2, g.ny // 2, g.nz // 2, 2 * g.dx, 2 * g.dy, 2 * g.dz, g.origin)
-        out.append(g)
-    return out
+def open_face_count(fr):
+    return int((fr["Ax"] > 0).sum() + (fr["Ay"] > 0).sum() + (fr["Az"] > 0).sum())
 
 
-def level_fractions(grid, phi, max_coarse=4, fine=None):
+# a level with at most this many open faces is the coarsest (solved exactly)
+DENSE_COARSE = 2048
+
+
+def level_fractions(grid, phi, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE):
     """Grids and fractions of every level; ``fine`` replaces the fine-level
-    fractions computed from phi (for perturbation studies)."""
-    grids = _coarse_grids(grid, max_coarse)
+    fractions computed from phi (for perturbation studies).  Coarsening stops
+    when the grid cannot be halved (``can_coarsen``) or when the current level
+    has at most ``dense_coarse`` open faces (0: no such limit)."""
+    from workloads import Grid
+    grids = [grid]
     frs = [geometry.fractions(phi) if fine is None else fine]
-    for _ in grids[1:]:
+    g = grid
+    while can_coarsen(g.nx, g.ny, g.nz, max_coarse) and (dense_coarse <= 0 or open_face_count(frs[-1]) > dense_coarse):
+        g = Grid(g.nx // 2, g.ny // 2, g.nz // 2, 2 * g.dx, 2 * g.dy, 2 * g.dz, g.origin)
+        grids.append(g)
         frs.append(coarsen_fractions(frs[-1]))
     return grids, frs
 
 
-def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None):
-    grids, frs = level_fractions(grid, phi, max_coarse, fine)
+def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE):
+    grids, frs = level_fractions(grid, phi, max_coarse, fine, dense_coarse)
     levels = [VectorLevel(g, f, sigma) for g, f in zip(grids, frs)]
     for l in range(len(levels) - 1):
         c = levels[l + 1].grid
@@ -197,8 +201,8 @@ def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None):
     return levels
 
 
-def build_scalar_hierarchy(grid, phi, max_coarse=4):
-    grids, frs = level_fractions(grid, phi, max_coarse)
+def build_scalar_hierarchy(grid, phi, max_coarse=4, dense_coarse=DENSE_COARSE):
+    grids, frs = level_fractions(grid, phi, max_coarse, dense_coarse=dense_coarse)
     levels = [ScalarLevel(g, f) for g, f in zip(grids, frs)]
     for l in range(len(levels) - 1):
         c = levels[l + 1].grid

@@ -233,8 +233,9 @@ class Geometry:
 
 
 def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
-              autotune=1, force_shape=-1, band_sweeps_coarse=None):
-    """band_sweeps_coarse: sweeps below the fine level (None: the library's default, 8)."""
+              autotune=1, force_shape=-1, band_sweeps_coarse=None, symmetric_transform=0, dense_coarse=None):
+    """band_sweeps_coarse: sweeps below the fine level (None: the library's default, 8);
+    symmetric_transform: 1 for the V-cycle of Eq. fullMat2's symmetric form."""
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -247,6 +248,9 @@ def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power
     p.stencil_shape = int(force_shape)
     if band_sweeps_coarse is not None:
         p.band_sweeps_coarse = int(band_sweeps_coarse)
+    p.symmetric_transform = int(symmetric_transform)
+    if dense_coarse is not None:
+        p.dense_coarse = int(dense_coarse)
     return p
 
 
@@ -450,7 +454,7 @@ class Learned:
 
 def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
                inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, rho_tol=1e-8,
-               **mg):
+               inner_relax=1, **mg):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     p.sigma = float(sigma)
@@ -467,6 +471,7 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.learned = learned.h if learned is not None else None
     p.max_seconds = float(max_seconds)
     p.rho_tol = float(rho_tol)
+    p.inner_relax = int(inner_relax)
     return p
 
 

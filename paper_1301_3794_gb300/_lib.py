@@ -16,7 +16,8 @@ PREC = {"f64": 0, "f32": 1, "bf16": 2}
 class MGParams(C.Structure):
     _fields_ = [("max_coarse", C.c_int), ("band_sweeps", C.c_int), ("band_brick", C.c_int), ("omega_scale", C.c_double),
                 ("power_iters", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
-                ("stencil_shape", C.c_int), ("band_sweeps_coarse", C.c_int)]
+                ("stencil_shape", C.c_int), ("band_sweeps_coarse", C.c_int), ("symmetric_transform", C.c_int),
+                ("dense_coarse", C.c_int)]
 
 
 class EigParams(C.Structure):
@@ -24,7 +25,7 @@ class EigParams(C.Structure):
                 ("proj_tol", C.c_double), ("basis", C.c_int), ("max_restarts", C.c_int),
                 ("inner_restart", C.c_int), ("inner_maxit", C.c_int), ("seed", C.c_ulonglong),
                 ("mg", MGParams), ("learned", C.c_void_p), ("max_seconds", C.c_double),
-                ("rho_tol", C.c_double)]
+                ("rho_tol", C.c_double), ("inner_relax", C.c_int)]
 
 
 class EigReport(C.Structure):

@@ -411,10 +411,13 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
     T* fc = reinterpret_cast<T*>(wc.f.get());
-    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, gc.tiles.get(), gc.ntiles, s);
-    vcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.e.get()), reinterpret_cast<T*>(wc.r.get()));
-    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), reinterpret_cast<const T*>(wc.r.get()), ebuf, g.tiles.get(),
-                            g.ntiles, s);
+    const bool sym = op->mg.symmetric_transform != 0;
+    if (sym) scale_sqrt_a<T, TC>(g.vdom(), Pick<T, TC>::A(g), true, rbuf, s);
+    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, gc.tiles.get(), gc.ntiles, s, sym);
+    T* ec = reinterpret_cast<T*>(wc.r.get());
+    vcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.e.get()), ec);
+    if (sym) scale_sqrt_a<T, TC>(gc.vdom(), Pick<T, TC>::A(gc), false, ec, s);
+    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), ec, ebuf, g.tiles.get(), g.ntiles, s, sym);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
     band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om, sweeps, l == 0,
                         s);
@@ -819,6 +822,8 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
 // applied and the eigenpairs cannot be trusted.
 constexpr int kProjMaxit = 400;
 constexpr int kProjStallLimit = 3;
+// loosest inner tolerance the relaxation of the shifted solves may reach
+constexpr double kRelaxMax = 1e-6;
 
 // y = P_DM x (Eq. proj); x, y padded FP64 fine-level face vectors (may alias)
 int project(dm_operator* op, const double* x, double* y, double tol) {
@@ -995,6 +1000,9 @@ void setup_operator(dm_operator* op) {
     while (nl < (int)geom->lv.size()) {
         const Grid3& g = geom->lv[nl - 1]->g;
         if (!can_coarsen(g.nx, g.ny, g.nz, op->mg.max_coarse)) break;
+        // a level this small is solved densely instead: its coarse-level
+        // launches would be latency-bound for no gain
+        if (op->mg.dense_coarse > 0 && geom->lv[nl - 1]->nopen <= op->mg.dense_coarse) break;
         ++nl;
     }
     op->nlev = nl;
@@ -1537,6 +1545,8 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->autotune = 1;
     p->stencil_shape = -1;
     p->band_sweeps_coarse = 8;
+    p->symmetric_transform = 0;
+    p->dense_coarse = 2048;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1552,6 +1562,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         dm_mg_params_default(&op->mg);
         if (mg) op->mg = *mg;
         DM_REQUIRE(op->mg.max_coarse >= 4, DM_ERR_INVALID_ARG, "max_coarse must be >= 4");
+        DM_REQUIRE(op->mg.dense_coarse >= 0 && op->mg.dense_coarse <= 6000, DM_ERR_INVALID_ARG,
+                   "dense_coarse must be in [0, 6000]");
         DM_REQUIRE(op->mg.band_sweeps >= 0 && op->mg.band_sweeps <= 256, DM_ERR_INVALID_ARG, "band_sweeps out of range");
         DM_REQUIRE(op->mg.band_sweeps_coarse >= 0 && op->mg.band_sweeps_coarse <= 256, DM_ERR_INVALID_ARG,
                    "band_sweeps_coarse out of range");
@@ -1781,6 +1793,7 @@ void dm_eig_params_default(dm_eig_params* p) {
     p->learned = nullptr;
     p->max_seconds = 0.0;
     p->rho_tol = 1e-8;
+    p->inner_relax = 1;
 }
 
 }  // extern "C"
@@ -1919,7 +1932,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         // Ritz and inner tolerances in force: both tighten by 10 whenever the
         // Ritz estimates call the wanted pairs converged but their FP64
         // certificate rho (the residual of K b = k^2 A b itself) misses rho_tol
-        double tol_eff = p.tol, inner_eff = p.inner_tol;
+        double tol_eff = p.tol, inner_base = p.inner_tol, inner_eff = p.inner_tol;
         int cert_retries = 0;
         // rho of the wanted Ritz pairs (|theta| order) from the current basis
         auto certify_wanted = [&](std::vector<double>& rho_out) {
@@ -1994,7 +2007,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                     for (int c = 0; c < p.nev; ++c)
                         worst = std::max(worst, est[c] / std::max(std::fabs(theta[order[c]]), 1e-300));
                     tol_eff = 0.1 * std::min(tol_eff, worst);
-                    inner_eff = std::max(inner_eff * 0.1, 1e-13);
+                    inner_base = std::max(inner_base * 0.1, 1e-13);
+                    inner_eff = inner_base;
                     ++cert_retries;
                     nconv = 0;
                     while (nconv < p.nev && est[nconv] <= tol_eff * std::fabs(theta[order[nconv]])) ++nconv;
@@ -2002,6 +2016,17 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             }
             if (nconv >= p.nev || restarts >= p.max_restarts) break;
             // thick restart: keep the pk wanted Ritz vectors
+            // Inexact shift-and-invert (after Simoncini 2005): a direction added
+            // once the wanted Ritz pairs have relative residual r enters their
+            // vectors with a weight of order r, so its shifted solve may be
+            // solved to inner_base / r (at most kRelaxMax).  The certificate
+            // above still decides which pairs count.
+            if (p.inner_relax) {
+                double r_w = 0.0;
+                for (int c = nconv; c < p.nev; ++c)
+                    r_w = std::max(r_w, est[c] / std::max(std::fabs(theta[order[c]]), 1e-300));
+                inner_eff = r_w > 0.0 ? std::min(kRelaxMax, std::max(inner_base, inner_base / r_w)) : inner_base;
+            }
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
             std::vector<double> Yk((size_t)m * pk);
             for (int c = 0; c < pk; ++c)

@@ -452,12 +452,20 @@ void dm_sub_grad(const Grid3& g, const double* A, const double* x, const double*
 
 // transfers (dm_transfer.cu)
 // tiles_c / tiles_f: active tiles of the level written (nullptr: whole grid)
+// sym: the transfers of Eq. fullMat2's congruence form (b~ = A^1/2 b on every
+// level): restriction A_c^1/2 R A^-1/2 (the fine input must come pre-scaled by
+// A^-1/2, see scale_sqrt_a; the kernel applies A_c^1/2), prolongation
+// A^-1/2 P A_c^1/2 (the coarse input must come pre-scaled by A_c^1/2; the
+// kernel applies A^-1/2)
 template <typename T, typename TC>
 void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, const int* tiles_c,
-                   int ntiles_c, cudaStream_t s);
+                   int ntiles_c, cudaStream_t s, bool sym = false);
 template <typename T, typename TC>
 void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, const int* tiles_f,
-                      int ntiles_f, cudaStream_t s);
+                      int ntiles_f, cudaStream_t s, bool sym = false);
+// x <- A^-1/2 x (inverse) or A^1/2 x on the open faces of the domain
+template <typename T, typename TC>
+void scale_sqrt_a(const Domain& d, const TC* A, bool inverse, T* x, cudaStream_t s);
 template <typename T>
 void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
                    const int* tiles_c, int ntiles_c, cudaStream_t s);

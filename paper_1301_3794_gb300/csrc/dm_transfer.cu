@@ -47,7 +47,7 @@ __device__ __forceinline__ void restrict_axis(bool normal, int c, int nc, int nf
     }
 }
 
-template <typename T, typename TC>
+template <typename T, typename TC, bool SYM>
 __global__ void k_face_restrict(Grid3 gf, Grid3 gc, const TC* __restrict__ Ac, const T* __restrict__ r,
                                 T* __restrict__ fc, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
@@ -82,12 +82,13 @@ __global__ void k_face_restrict(Grid3 gf, Grid3 gc, const TC* __restrict__ Ac, c
                 }
             }
             acc *= C(0.125);
+            if (SYM) acc *= sqrt((C)Ac[oq]);
         }
         fc[oq] = to_store<T>(acc);
     }
 }
 
-template <typename T, typename TC>
+template <typename T, typename TC, bool SYM>
 __global__ void k_face_prolong(Grid3 gf, Grid3 gc, const TC* __restrict__ Af, const T* __restrict__ ec,
                                T* __restrict__ x, const int* __restrict__ tiles) {
     using C = typename Compute<T>::type;
@@ -127,8 +128,20 @@ __global__ void k_face_prolong(Grid3 gf, Grid3 gc, const TC* __restrict__ Af, co
                     const float w = wi[2][a] * wi[1][b] * wi[0][d];
                     if (w != 0.f) acc += C(w) * (C)to_c(ec[comp * gc.np + gc.idx(ci[0][d], ci[1][b], ci[2][a])]);
                 }
+        if (SYM) acc /= sqrt((C)Af[op]);
         x[op] = to_store<T>((C)to_c(x[op]) + acc);
     }
+}
+
+// x <- A^(-1/2) x (inverse) or A^(1/2) x on the open faces (closed: 0)
+template <typename T, typename TC>
+__global__ void k_scale_sqrt_a(Domain d, const TC* __restrict__ A, int inverse, T* __restrict__ x) {
+    using C = typename Compute<T>::type;
+    for_each_entry(d, [&](long long r) {
+        const C a = (C)A[r];
+        const C f = a > C(0) ? (inverse ? C(1) / sqrt(a) : sqrt(a)) : C(0);
+        x[r] = to_store<T>((C)to_c(x[r]) * f);
+    });
 }
 
 template <typename T>
@@ -170,19 +183,32 @@ inline dim3 grid_for(const Grid3& g, int extra) {
 
 template <typename T, typename TC>
 void face_restrict(const Grid3& gf, const Grid3& gc, const TC* Ac, const T* r, T* fc, const int* tiles_c,
-                   int ntiles_c, cudaStream_t s) {
+                   int ntiles_c, cudaStream_t s, bool sym) {
     // every open fine face's r once; per open coarse face its A and f_c
     const double bytes = (double)gf.nopen * sizeof(T) + (double)gc.nopen * (sizeof(T) + sizeof(TC));
-    launch_b("k_face_restrict", bytes, k_face_restrict<T, TC>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock, 0, s, gf,
-             gc, Ac, r, fc, tiles_c);
+    if (sym)
+        launch_b("k_face_restrict", bytes, k_face_restrict<T, TC, true>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock, 0,
+                 s, gf, gc, Ac, r, fc, tiles_c);
+    else
+        launch_b("k_face_restrict", bytes, k_face_restrict<T, TC, false>, tile_grid(gc, tiles_c, ntiles_c, 1), kBlock,
+                 0, s, gf, gc, Ac, r, fc, tiles_c);
 }
 template <typename T, typename TC>
 void face_prolong_add(const Grid3& gf, const Grid3& gc, const TC* Af, const T* ec, T* x, const int* tiles_f,
-                      int ntiles_f, cudaStream_t s) {
+                      int ntiles_f, cudaStream_t s, bool sym) {
     // every open coarse face's e_c once; per open fine face its A and x read and written
     const double bytes = (double)gc.nopen * sizeof(T) + (double)gf.nopen * (2.0 * sizeof(T) + sizeof(TC));
-    launch_b("k_face_prolong", bytes, k_face_prolong<T, TC>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0, s, gf, gc,
-             Af, ec, x, tiles_f);
+    if (sym)
+        launch_b("k_face_prolong", bytes, k_face_prolong<T, TC, true>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0,
+                 s, gf, gc, Af, ec, x, tiles_f);
+    else
+        launch_b("k_face_prolong", bytes, k_face_prolong<T, TC, false>, tile_grid(gf, tiles_f, ntiles_f, 1), kBlock, 0,
+                 s, gf, gc, Af, ec, x, tiles_f);
+}
+template <typename T, typename TC>
+void scale_sqrt_a(const Domain& d, const TC* A, bool inverse, T* x, cudaStream_t s) {
+    launch_b("k_scale_sqrt_a", d.live() * (2.0 * sizeof(T) + sizeof(TC)), k_scale_sqrt_a<T, TC>,
+             d.tiles ? std::max(d.ntiles, 1) : 1216, 256, 0, s, d, A, inverse ? 1 : 0, x);
 }
 template <typename T>
 void cell_restrict(const Grid3& gf, const Grid3& gc, const unsigned char* active_c, const T* r, T* fc,
@@ -199,9 +225,10 @@ void cell_prolong_add(const Grid3& gf, const Grid3& gc, const unsigned char* act
 
 #define DM_INST(T, TC)                                                                                   \
     template void face_restrict<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, const int*, int,  \
-                                       cudaStream_t);                                                      \
+                                       cudaStream_t, bool);                                                \
     template void face_prolong_add<T, TC>(const Grid3&, const Grid3&, const TC*, const T*, T*, const int*, int, \
-                                          cudaStream_t);
+                                          cudaStream_t, bool);                                               \
+    template void scale_sqrt_a<T, TC>(const Domain&, const TC*, bool, T*, cudaStream_t);
 DM_INST(double, double)
 DM_INST(float, float)
 DM_INST(__nv_bfloat16, float)

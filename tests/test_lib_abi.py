@@ -39,7 +39,8 @@ def test_struct_layouts_match_defaults(lib):
     m = MGParams()
     lib.dm_mg_params_default(C.byref(m))
     assert m.power_iters == 30 and m.precision == 0
-    assert m.autotune == 1 and m.stencil_shape == -1 and m.band_sweeps_coarse == 8
+    assert m.autotune == 1 and m.stencil_shape == -1 and m.band_sweeps_coarse == 8 and m.symmetric_transform == 0
+    assert m.dense_coarse == 2048
     # the field after the embedded multigrid settings lands where the C struct has it
     assert p.mg.autotune == 1 and p.mg.stencil_shape == -1 and not p.learned
 
@@ -72,7 +73,7 @@ def test_eig_params_tail_fields_keep_their_c_offsets(lib):
     p.rho_tol = 5.0
     p.learned = 1234
     lib.dm_eig_params_default(C.byref(p))
-    assert p.max_seconds == 0.0 and not p.learned and p.rho_tol == 1e-8
+    assert p.max_seconds == 0.0 and not p.learned and p.rho_tol == 1e-8 and p.inner_relax == 1
 
 
 def test_allocation_counter_needs_no_gpu(lib):

@@ -82,3 +82,22 @@ def test_octant_lowest_mode_is_the_l3_tm_mode_at_second_order():
         errs[n] = abs(k2[0] - k3 ** 2) / k3 ** 2
     assert errs[24] < 3e-3, errs
     assert np.log2(errs[12] / errs[24]) > 1.8, errs
+
+
+@pytest.mark.slow
+def test_octant_surface_fields_converge_only_without_face_neglect():
+    """Sec. 6.2, Eq. errorNorm / Fig. fieldErr3d on the oracle: the electric
+    field of the octant's lowest mode on a shell 3 dx inside the surface
+    converges (at about second order) when every cut face is kept, and does
+    not converge when faces below a_min = 0.1 a_vac are neglected."""
+    from field_sampling import surface_field_error
+    err = {}
+    for a_min in (0.0, 0.1):
+        for n in (16, 24):
+            w = W.octant_sphere_workload(n)
+            ops = operators.DMOperators(w.grid, geometry.fractions(w.phi, a_min=a_min))
+            _, B, _ = eigen.shift_invert_modes(ops, w.sigma, 1)
+            err[a_min, n] = surface_field_error(w, a_min, B[:, 0])
+    assert err[0.0, 16] / err[0.0, 24] > (24 / 16) ** 1.5, err     # ~ second order
+    assert err[0.1, 16] / err[0.1, 24] < 1.2, err                   # no convergence
+    assert err[0.1, 24] > 3.0 * err[0.0, 24], err
