@@ -319,9 +319,15 @@ struct dm_operator {
     bool learned_active = false;
     int learned_applied = 0, learned_fallbacks = 0;
     long long nopen0 = 0;
+    Fork fork;                 // side streams of the band smoother's class launches
     ~dm_operator() {
         if (vexec) cudaGraphExecDestroy(vexec);
         if (sexec) cudaGraphExecDestroy(sexec);
+        for (int a = 0; a < fork.naux; ++a) {
+            cudaStreamDestroy(fork.aux[a]);
+            cudaEventDestroy(fork.join[a]);
+        }
+        if (fork.fork) cudaEventDestroy(fork.fork);
     }
 };
 
@@ -406,7 +412,7 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const int sweeps = band_sweeps_of(op, l);
     vec_jacobi_zero(o, f, ebuf, om, s);
     band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om, sweeps, l == 0,
-                        s);
+                        s, &op->fork);
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
@@ -420,7 +426,7 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), ec, ebuf, g.tiles.get(), g.ntiles, s, sym);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
     band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om, sweeps, l == 0,
-                        s);
+                        s, &op->fork);
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -697,10 +703,13 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
     const long long n = D.len();
     DM_REQUIRE(m >= 1 && 2 * m + 2 < ctx->red.max_cols, DM_ERR_INVALID_ARG, "FGMRES restart length too large");
     DM_REQUIRE(nl >= 1 && nl < (1ll << 31), DM_ERR_INVALID_ARG, "FGMRES: empty basis index space");
-    ws.ensure(n, nl, m);
+    // the compact vectors' length and stride, even for the two-entry passes
+    // (the pad entry stays zero: nothing writes it but the update, from zeros)
+    const long long nlp = (nl + 1) & ~1ll;
+    ws.ensure(n, nlp, m);
     // flat domain of the compact vectors
     Grid3 gc = D.g;
-    gc.np = (int)nl;
+    gc.np = (int)nlp;
     const Domain Dc{gc, nullptr, 0, 1};
     float2* V = ws.V.get();
     float2* wf = ws.wf.get();
@@ -733,12 +742,12 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
         double prev = beta;
         int k = 0;                // columns of H built in this cycle
         for (int j = 0; j < m && total < maxit; ++j) {
-            float2* Vj = V + (size_t)j * nl;
+            float2* Vj = V + (size_t)j * nlp;
             prec(Vj, 1.0 / nu, Z + (size_t)j * n);
             apply(Z + (size_t)j * n, w);
             ff_gather(nl, list, 1.0, w, wf, s);
             // one sweep: Q^T v, Q^T w, v.v, v.w with Q = V_0 .. V_{j-1} finished
-            dcgs_dots(ctx->red, Dc, j, V, nl, Vj, wf, dots.data(), s);
+            dcgs_dots(ctx->red, Dc, j, V, nlp, Vj, wf, dots.data(), s);
             double ss = 0.0, sc = 0.0;
             for (int i = 0; i < j; ++i) {
                 ss += dots[i] * dots[i];
@@ -761,7 +770,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
             H[(size_t)j * m + j] = hj;
             coef[2 * j] = 1.0 / bj;
             coef[2 * j + 1] = hj / bj;
-            const double nn2 = dcgs_update(ctx->red, Dc, j, V, nl, coef.data(), Vj, wf, V + (size_t)(j + 1) * nl, s);
+            const double nn2 = dcgs_update(ctx->red, Dc, j, V, nlp, coef.data(), Vj, wf, V + (size_t)(j + 1) * nlp, s);
             nu = std::sqrt(std::max(nn2, 0.0));
             H[(size_t)(j + 1) * m + j] = nu;   // provisional until the next iteration
             k = j + 1;
@@ -1082,6 +1091,17 @@ void setup_operator(dm_operator* op) {
         max_band = std::max(max_band, g.nband);
     }
     op->band_u.alloc((size_t)max_band);
+    {
+        note_allocation();
+        DM_CUDA(cudaEventCreateWithFlags(&op->fork.fork, cudaEventDisableTiming));
+        for (int a = 0; a < kForkStreams; ++a) {
+            note_allocation();
+            DM_CUDA(cudaStreamCreateWithFlags(&op->fork.aux[a], cudaStreamNonBlocking));
+            note_allocation();
+            DM_CUDA(cudaEventCreateWithFlags(&op->fork.join[a], cudaEventDisableTiming));
+            op->fork.naux = a + 1;
+        }
+    }
     {
         // compact index spaces of the fine level's Krylov bases
         GeoLevel& g0 = *const_cast<dm_geometry*>(geom)->lv[0];
@@ -1934,6 +1954,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         // certificate rho (the residual of K b = k^2 A b itself) misses rho_tol
         double tol_eff = p.tol, inner_base = p.inner_tol, inner_eff = p.inner_tol;
         int cert_retries = 0;
+        bool relax = p.inner_relax != 0;
         // rho of the wanted Ritz pairs (|theta| order) from the current basis
         auto certify_wanted = [&](std::vector<double>& rho_out) {
             std::vector<double> Yw((size_t)m * p.nev), kk(p.nev);
@@ -2009,6 +2030,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                     tol_eff = 0.1 * std::min(tol_eff, worst);
                     inner_base = std::max(inner_base * 0.1, 1e-13);
                     inner_eff = inner_base;
+                    relax = false;   // a certificate missed: no more relaxed solves in this eigensolve
                     ++cert_retries;
                     nconv = 0;
                     while (nconv < p.nev && est[nconv] <= tol_eff * std::fabs(theta[order[nconv]])) ++nconv;
@@ -2017,15 +2039,22 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             if (nconv >= p.nev || restarts >= p.max_restarts) break;
             // thick restart: keep the pk wanted Ritz vectors
             // Inexact shift-and-invert (after Simoncini 2005): a direction added
-            // once the wanted Ritz pairs have relative residual r enters their
-            // vectors with a weight of order r, so its shifted solve may be
-            // solved to inner_base / r (at most kRelaxMax).  The certificate
-            // above still decides which pairs count.
-            if (p.inner_relax) {
-                double r_w = 0.0;
-                for (int c = nconv; c < p.nev; ++c)
-                    r_w = std::max(r_w, est[c] / std::max(std::fabs(theta[order[c]]), 1e-300));
-                inner_eff = r_w > 0.0 ? std::min(kRelaxMax, std::max(inner_base, inner_base / r_w)) : inner_base;
+            // once a wanted Ritz pair has relative residual r and relative gap g
+            // to the other Ritz values enters its vector with a weight of order
+            // r / g, so the new shifted systems may be solved to inner_base g / r
+            // (at most kRelaxMax) over the pairs not yet converged.  Clustered
+            // pairs (small g) keep the solves tight.  The certificate above still
+            // decides which pairs count.
+            if (relax) {
+                double worst = 0.0;
+                for (int c = nconv; c < p.nev; ++c) {
+                    const double th = theta[order[c]];
+                    double gap = 1.0;
+                    for (int o = 0; o < m; ++o)
+                        if (o != order[c]) gap = std::min(gap, std::fabs(theta[o] - th) / std::max(std::fabs(th), 1e-300));
+                    worst = std::max(worst, est[c] / std::max(std::fabs(th), 1e-300) / std::max(gap, 1e-300));
+                }
+                inner_eff = worst > 0.0 ? std::min(kRelaxMax, std::max(inner_base, inner_base / worst)) : inner_base;
             }
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
             std::vector<double> Yk((size_t)m * pk);

@@ -353,7 +353,7 @@ void class_shape(int cl, int& R, int& nt) {
 
 template <typename T, typename TC>
 void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, const int* band, int nband, const T* f,
-                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s) {
+                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s0, const Fork* fk) {
     if (nband <= 0 || bs.nsub <= 0 || sweeps <= 0) return;
     const char* name = stencil_name("band_schwarz", prec_index<T>(), ST_JACOBI, fine);
     // a level whose subdomains fit in one wave goes in a single launch shaped for
@@ -362,8 +362,20 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
     for (int cl = 0; cl < kSchwarzClasses; ++cl)
         if (bs.cls_count[cl] > 0) top = cl;
     const bool single = bs.nsub <= kSingleLaunchSubdomains;
+    // classes launched here, and the stream each takes
+    int nl = 0;
+    for (int cl = 0; cl < kSchwarzClasses; ++cl)
+        if (bs.cls_count[cl] > 0 && !(single && cl != top)) ++nl;
+    const bool forked = fk && fk->naux > 0 && nl > 1;
+    if (forked) {
+        DM_CUDA(cudaEventRecord(fk->fork, s0));
+        for (int a = 0; a < std::min(nl - 1, fk->naux); ++a) DM_CUDA(cudaStreamWaitEvent(fk->aux[a], fk->fork, 0));
+    }
+    int li = 0;
     for (int cl = 0; cl < kSchwarzClasses; ++cl) {
         if (bs.cls_count[cl] == 0 || (single && cl != top)) continue;
+        const int ai = li++;   // the first class stays on s0
+        cudaStream_t s = (forked && ai > 0 && ai - 1 < fk->naux) ? fk->aux[ai - 1] : s0;
         int R, nt;
         class_shape<T>(single ? top : cl, R, nt);
         const int first = single ? 0 : bs.cls_first[cl];
@@ -395,8 +407,13 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
         else DM_SCHWARZ(0, 512);
 #undef DM_SCHWARZ
     }
+    if (forked)
+        for (int a = 0; a < std::min(nl - 1, fk->naux); ++a) {
+            DM_CUDA(cudaEventRecord(fk->join[a], fk->aux[a]));
+            DM_CUDA(cudaStreamWaitEvent(s0, fk->join[a], 0));
+        }
     launch_b(stencil_name("band_add", prec_index<T>(), ST_JACOBI, fine), (double)nband * (12.0 + 2.0 * sizeof(T)),
-             k_band_add<T>, (nband + 255) / 256, 256, 0, s, band, nband, (const double*)u, x);
+             k_band_add<T>, (nband + 255) / 256, 256, 0, s0, band, nband, (const double*)u, x);
 }
 
 // Allow each variant the device's opt-in shared memory less its static share;
@@ -437,7 +454,7 @@ void band_schwarz_prepare(const SchwarzLayout& sl) {
 
 #define DM_INST(T, TC)                                                                                           \
     template void band_schwarz<T, TC>(const BandSchwarz<TC>&, const TC*, const Grid3&, const int*, int, const T*, \
-                                      T*, double*, double, int, bool, cudaStream_t);                             \
+                                      T*, double*, double, int, bool, cudaStream_t, const Fork*);                \
     template void band_schwarz_prepare<T, TC>(const SchwarzLayout&);
 DM_INST(double, double)
 DM_INST(float, float)

@@ -258,9 +258,12 @@ __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + 
 //   partial[b][c] = Q_c . v, [j + c] = Q_c . w (c < j), [2j] = v . v, [2j + 1] = v . w
 // Columns go in chunks of up to 8 whose size is a compile-time constant, so the
 // accumulators stay in registers and no predicated-off column is issued.
+// The compact vectors have an even length and stride (a zero pad entry when
+// needed), and every thread takes two entries per step with one 16-byte load
+// per vector, so twice the bytes are in flight per load instruction.
 template <int NC>
-__device__ __forceinline__ void dcgs_chunk(const Domain& d, int j, int c0, const float2* __restrict__ Q, long long ld,
-                                           const float2* __restrict__ v, const float2* __restrict__ w, bool first,
+__device__ __forceinline__ void dcgs_chunk(long long n2, int j, int c0, const float4* __restrict__ Q, long long ld2,
+                                           const float4* __restrict__ v, const float4* __restrict__ w, bool first,
                                            float& as, float& ae, float& ds, float& de, double* __restrict__ partial,
                                            int ldp) {
     __shared__ double red[kThreads / 32][16];
@@ -268,19 +271,25 @@ __device__ __forceinline__ void dcgs_chunk(const Domain& d, int j, int c0, const
     float ss[N1], se[N1], cs[N1], ce[N1];
 #pragma unroll
     for (int c = 0; c < N1; ++c) ss[c] = se[c] = cs[c] = ce[c] = 0.f;
-    for_each_entry(d, [&](long long r) {
-        const float2 vv = v[r], ww = w[r];
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n2; r += (long long)gridDim.x * blockDim.x) {
+        const float4 vv = v[r], ww = w[r];
         if (first) {
             ff_madd(vv.x, vv.y, vv.x, vv.y, as, ae);
+            ff_madd(vv.z, vv.w, vv.z, vv.w, as, ae);
             ff_madd(vv.x, vv.y, ww.x, ww.y, ds, de);
+            ff_madd(vv.z, vv.w, ww.z, ww.w, ds, de);
         }
+        float4 q[N1];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) q[c] = Q[(c0 + c) * ld2 + r];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const float2 q = Q[(c0 + c) * ld + r];
-            ff_madd(q.x, q.y, vv.x, vv.y, ss[c], se[c]);
-            ff_madd(q.x, q.y, ww.x, ww.y, cs[c], ce[c]);
+            ff_madd(q[c].x, q[c].y, vv.x, vv.y, ss[c], se[c]);
+            ff_madd(q[c].z, q[c].w, vv.z, vv.w, ss[c], se[c]);
+            ff_madd(q[c].x, q[c].y, ww.x, ww.y, cs[c], ce[c]);
+            ff_madd(q[c].z, q[c].w, ww.z, ww.w, cs[c], ce[c]);
         }
-    });
+    }
     if constexpr (NC > 0) {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -304,9 +313,10 @@ __device__ __forceinline__ void dcgs_chunk(const Domain& d, int j, int c0, const
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(Domain d, int j, const float2* __restrict__ Q, long long ld,
-                               const float2* __restrict__ v, const float2* __restrict__ w, double* __restrict__ partial,
-                               int ldp) {
+__global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(long long n2, int j, const float4* __restrict__ Q,
+                                                              long long ld2, const float4* __restrict__ v,
+                                                              const float4* __restrict__ w, double* __restrict__ partial,
+                                                              int ldp) {
     __shared__ double red2[kThreads / 32][2];
     float as = 0.f, ae = 0.f, ds = 0.f, de = 0.f;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -314,15 +324,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(Domain d, int j, c
         const int nc = j > 0 ? min(8, j - c0) : 0;
         const bool first = c0 == 0;
         switch (nc) {
-            case 0: dcgs_chunk<0>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 1: dcgs_chunk<1>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 2: dcgs_chunk<2>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 3: dcgs_chunk<3>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 4: dcgs_chunk<4>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 5: dcgs_chunk<5>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 6: dcgs_chunk<6>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            case 7: dcgs_chunk<7>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp); break;
-            default: dcgs_chunk<8>(d, j, c0, Q, ld, v, w, first, as, ae, ds, de, partial, ldp);
+            case 0: dcgs_chunk<0>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 1: dcgs_chunk<1>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 2: dcgs_chunk<2>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 3: dcgs_chunk<3>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 4: dcgs_chunk<4>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 5: dcgs_chunk<5>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 6: dcgs_chunk<6>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            case 7: dcgs_chunk<7>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp); break;
+            default: dcgs_chunk<8>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp);
         }
     }
     const double ta = warp_sum((double)as + (double)ae);
@@ -342,9 +352,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(Domain d, int j, c
 // The update pass of DCGS2, with coef = [s (j), gamma (j), 1/beta, delta]:
 //   v <- (v - Q s) / beta   (the pending vector, now finished)
 //   out <- w - Q gamma - delta v_old   and the block partial of |out|^2
-__global__ void k_ff_dcgs_update(Domain d, int j, const float2* __restrict__ Q, long long ld,
-                                 const double* __restrict__ coef, float2* __restrict__ v, const float2* __restrict__ w,
-                                 float2* __restrict__ out, double* __restrict__ partial) {
+// Two entries per thread and step, as in the dots pass.
+__global__ void k_ff_dcgs_update(long long n2, int j, const float4* __restrict__ Q, long long ld2,
+                                 const double* __restrict__ coef, float4* __restrict__ v, const float4* __restrict__ w,
+                                 float4* __restrict__ out, double* __restrict__ partial) {
     __shared__ float2 cs[128], cg[128];
     __shared__ float2 rb, dl;
     __shared__ double red[kThreads / 32];
@@ -358,24 +369,31 @@ __global__ void k_ff_dcgs_update(Domain d, int j, const float2* __restrict__ Q, 
     }
     __syncthreads();
     float ns = 0.f, ne = 0.f;
-    for_each_entry(d, [&](long long r) {
-        const float2 vv = v[r], ww = w[r];
-        float ts = vv.x, te = vv.y, us = ww.x, ue = ww.y;
-        ff_madd(dl.x, dl.y, vv.x, vv.y, us, ue);
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n2; r += (long long)gridDim.x * blockDim.x) {
+        const float4 vv = v[r], ww = w[r];
+        float ts0 = vv.x, te0 = vv.y, ts1 = vv.z, te1 = vv.w;
+        float us0 = ww.x, ue0 = ww.y, us1 = ww.z, ue1 = ww.w;
+        ff_madd(dl.x, dl.y, vv.x, vv.y, us0, ue0);
+        ff_madd(dl.x, dl.y, vv.z, vv.w, us1, ue1);
 #pragma unroll 4
         for (int c = 0; c < j; ++c) {
-            const float2 q = Q[c * ld + r];
-            ff_madd(cs[c].x, cs[c].y, q.x, q.y, ts, te);
-            ff_madd(cg[c].x, cg[c].y, q.x, q.y, us, ue);
+            const float4 q = Q[c * ld2 + r];
+            ff_madd(cs[c].x, cs[c].y, q.x, q.y, ts0, te0);
+            ff_madd(cs[c].x, cs[c].y, q.z, q.w, ts1, te1);
+            ff_madd(cg[c].x, cg[c].y, q.x, q.y, us0, ue0);
+            ff_madd(cg[c].x, cg[c].y, q.z, q.w, us1, ue1);
         }
-        const float2 t = ff_norm(ts, te);
-        float qs = 0.f, qe = 0.f;
-        ff_madd(rb.x, rb.y, t.x, t.y, qs, qe);
-        v[r] = ff_norm(qs, qe);
-        const float2 o = ff_norm(us, ue);
-        out[r] = o;
-        ff_madd(o.x, o.y, o.x, o.y, ns, ne);
-    });
+        const float2 t0 = ff_norm(ts0, te0), t1 = ff_norm(ts1, te1);
+        float qs0 = 0.f, qe0 = 0.f, qs1 = 0.f, qe1 = 0.f;
+        ff_madd(rb.x, rb.y, t0.x, t0.y, qs0, qe0);
+        ff_madd(rb.x, rb.y, t1.x, t1.y, qs1, qe1);
+        const float2 n0 = ff_norm(qs0, qe0), n1 = ff_norm(qs1, qe1);
+        v[r] = make_float4(n0.x, n0.y, n1.x, n1.y);
+        const float2 o0 = ff_norm(us0, ue0), o1 = ff_norm(us1, ue1);
+        out[r] = make_float4(o0.x, o0.y, o1.x, o1.y);
+        ff_madd(o0.x, o0.y, o0.x, o0.y, ns, ne);
+        ff_madd(o1.x, o1.y, o1.x, o1.y, ns, ne);
+    }
     const double t = warp_sum((double)ns + (double)ne);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
@@ -593,14 +611,27 @@ template void ff_scatter<double>(long long, const int*, double, const float2*, d
 template void ff_scatter<float>(long long, const int*, double, const float2*, float*, cudaStream_t);
 template void ff_scatter<__nv_bfloat16>(long long, const int*, double, const float2*, __nv_bfloat16*, cudaStream_t);
 
+// blocks of the two-entry DCGS passes: enough for one wave of pairs
+template <typename K>
+int pair_blocks(long long n2, K kernel) {
+    int per_sm = 0;
+    DM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    const long long need = (n2 + kThreads - 1) / kThreads;
+    return (int)std::max<long long>(1, std::min<long long>(need, 152ll * std::max(per_sm, 1)));
+}
+
 void dcgs_dots(Reducer& red, const Domain& d, int j, const float2* Q, long long ld, const float2* v, const float2* w,
                double* host_out, cudaStream_t s) {
     const int m = 2 * j + 2;
     DM_REQUIRE(j >= 0 && j <= 120 && m < red.max_cols, DM_ERR_INVALID_ARG, "dcgs: too many columns");
-    const int nb = blocks_for(d, k_ff_dcgs_dots);
+    DM_REQUIRE(d.tiles == nullptr && d.len() % 2 == 0 && ld % 2 == 0, DM_ERR_INVALID_ARG,
+               "dcgs: compact vectors need an even length and stride");
+    const long long n2 = d.len() / 2;
+    const int nb = std::min(pair_blocks(n2, k_ff_dcgs_dots), red.cap_blocks);
     // j finished basis vectors, v and w: float-float, 8 bytes an entry
-    launch_b("k_ff_dcgs_dots", 8.0 * d.live() * (j + 2), k_ff_dcgs_dots, nb, kThreads, 0, s, d, j, Q, ld, v, w,
-             red.partial, red.max_cols);
+    launch_b("k_ff_dcgs_dots", 8.0 * d.live() * (j + 2), k_ff_dcgs_dots, nb, kThreads, 0, s, n2, j,
+             reinterpret_cast<const float4*>(Q), ld / 2, reinterpret_cast<const float4*>(v),
+             reinterpret_cast<const float4*>(w), red.partial, red.max_cols);
     launch("k_mdot_final", k_mdot_final, (m + 7) / 8, 256, 0, s, nb, m, red.partial, red.max_cols, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));
@@ -613,11 +644,15 @@ double dcgs_update(Reducer& red, const Domain& d, int j, const float2* Q, long l
     // coefficients through the pinned host buffer (the preceding dots have synchronised the stream)
     for (int c = 0; c < 2 * j + 2; ++c) red.host[c] = coef_host[c];
     DM_CUDA(cudaMemcpyAsync(red.result, red.host, sizeof(double) * (2 * j + 2), cudaMemcpyHostToDevice, s));
-    const int nb = blocks_for(d, k_ff_dcgs_update);
+    DM_REQUIRE(d.tiles == nullptr && d.len() % 2 == 0 && ld % 2 == 0, DM_ERR_INVALID_ARG,
+               "dcgs: compact vectors need an even length and stride");
+    const long long n2 = d.len() / 2;
+    const int nb = std::min(pair_blocks(n2, k_ff_dcgs_update), red.cap_blocks);
     double* part = red.partial + (size_t)red.cap_blocks * (red.max_cols - 1);
     // reads Q (j vectors), v and w; writes v and out
-    launch_b("k_ff_dcgs_update", 8.0 * d.live() * (j + 4), k_ff_dcgs_update, nb, kThreads, 0, s, d, j, Q, ld,
-             (const double*)red.result, v, w, out, part);
+    launch_b("k_ff_dcgs_update", 8.0 * d.live() * (j + 4), k_ff_dcgs_update, nb, kThreads, 0, s, n2, j,
+             reinterpret_cast<const float4*>(Q), ld / 2, (const double*)red.result, reinterpret_cast<float4*>(v),
+             reinterpret_cast<const float4*>(w), reinterpret_cast<float4*>(out), part);
     launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, part, 1, red.result + red.max_cols - 1);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result + red.max_cols - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));

@@ -416,9 +416,20 @@ void band_copy_vals(const int* copy, int ncopies, const double* band_vals, int n
 template <typename T, typename TC>
 void band_schwarz_prepare(const SchwarzLayout& sl);
 // x <- x + (restricted additive Schwarz correction on the band); u: nband doubles of scratch
+// Streams and events that let the band smoother's class launches run side by
+// side (they read the same x and f and write disjoint parts of u): the classes
+// after the first go on aux[0 .. naux-1], forked from and joined back into the
+// calling stream with the events (in a stream capture these become parallel
+// branches of the graph).  naux = 0 launches every class on the calling stream.
+constexpr int kForkStreams = kSchwarzClasses - 1;
+struct Fork {
+    int naux = 0;
+    cudaStream_t aux[kForkStreams] = {};
+    cudaEvent_t fork = nullptr, join[kForkStreams] = {};
+};
 template <typename T, typename TC>
 void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, const int* band, int nband, const T* f,
-                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s);
+                  T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s, const Fork* fk = nullptr);
 void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
                          const double* x, double* y, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
