@@ -52,11 +52,11 @@ def parse():
     ap.add_argument("--sigma", type=float, default=5.0)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16"])
     ap.add_argument("--count", type=int, default=0, help="batch: solve only the first COUNT cavities")
+    ap.add_argument("--streams", type=int, default=8, help="batch: worker streams of dm_eigensolve_batched")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arm")
     ap.add_argument("--bf16-steps", type=int, default=3, help="timed steps of the BF16 V-cycle arm (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
     ap.add_argument("--inner-restart", type=int, default=40, help="FGMRES restart length of the shifted solves")
-    ap.add_argument("--no-relax", action="store_true", help="every shifted solve to --inner-tol (no relaxation)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
     if a.grid is None:
@@ -87,7 +87,7 @@ def describe(args, w):
 def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
-         "inner_restart": args.inner_restart, "inner_relax": 0 if args.no_relax else 1,
+         "inner_restart": args.inner_restart,
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:
@@ -286,8 +286,7 @@ def run_native(args):
         vec = "host" if host_io else "device"
         k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
                                        out=None if host_io else B_dev, precision=precision,
-                                       inner_tol=args.inner_tol, inner_restart=args.inner_restart,
-                                       inner_relax=0 if args.no_relax else 1)
+                                       inner_tol=args.inner_tol, inner_restart=args.inner_restart)
         geom.close()
         return k2, rep, st
 
@@ -459,7 +458,7 @@ def run_batch(args):
             geoms.append(geom)
             for sg in shifts:
                 jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision})
-        out = dm.eigensolve_batched(ctx, jobs, streams=8)
+        out = dm.eigensolve_batched(ctx, jobs, streams=args.streams)
         for geom in geoms:
             geom.close()
         return sum(rep["n_converged"] if (st == 0 and rep["rho_max"] <= RHO_TOL) else 0 for _, rep, st in out), out
@@ -505,7 +504,7 @@ def run_batch(args):
         "config": {"workload": (f"batch of {len(items)} seeded cavities (spheres and ellipsoids, grids {sizes}), "
                                 f"{sum(len(sh) for _, sh, _ in items)} (cavity, shift) solves, {npairs} eigenpairs "
                                 f"requested per step, residual<={RHO_TOL}"),
-                   "mg_precision": args.precision, "outer_precision": "f64", "streams": 8,
+                   "mg_precision": args.precision, "outer_precision": "f64", "streams": args.streams,
                    "l2": "inputs larger than L2 (48 cavities' solver state)", "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(tot_e2e / max_e2e, 4), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(p.nbytes for p in phis_host)),

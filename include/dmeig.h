@@ -109,13 +109,6 @@ typedef struct dm_eig_params {
                               the Ritz tolerance drops to a tenth of the worst current estimate, inner_tol
                               to a tenth (down to 1e-15 and 1e-13), and the Krylov-Schur iteration
                               continues */
-    int inner_relax;       /* 1: after each restart, solve the new shifted systems only to
-                              inner_tol / r (at most 1e-6), r the largest ratio of relative Ritz residual
-                              to relative gap among the wanted pairs not yet converged -- a direction
-                              added then enters their vectors with a weight of order r (inexact
-                              shift-and-invert, after Simoncini 2005).  rho_tol still certifies every
-                              returned pair; the first certificate that misses it ends the relaxation
-                              for the rest of the eigensolve (1) */
 } dm_eig_params;
 
 typedef struct dm_eig_report {

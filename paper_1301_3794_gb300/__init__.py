@@ -454,7 +454,7 @@ class Learned:
 
 def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
                inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, rho_tol=1e-8,
-               inner_relax=1, **mg):
+               **mg):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     p.sigma = float(sigma)
@@ -471,7 +471,6 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.learned = learned.h if learned is not None else None
     p.max_seconds = float(max_seconds)
     p.rho_tol = float(rho_tol)
-    p.inner_relax = int(inner_relax)
     return p
 
 

@@ -25,7 +25,7 @@ class EigParams(C.Structure):
                 ("proj_tol", C.c_double), ("basis", C.c_int), ("max_restarts", C.c_int),
                 ("inner_restart", C.c_int), ("inner_maxit", C.c_int), ("seed", C.c_ulonglong),
                 ("mg", MGParams), ("learned", C.c_void_p), ("max_seconds", C.c_double),
-                ("rho_tol", C.c_double), ("inner_relax", C.c_int)]
+                ("rho_tol", C.c_double)]
 
 
 class EigReport(C.Structure):

@@ -831,8 +831,6 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
 // applied and the eigenpairs cannot be trusted.
 constexpr int kProjMaxit = 400;
 constexpr int kProjStallLimit = 3;
-// loosest inner tolerance the relaxation of the shifted solves may reach
-constexpr double kRelaxMax = 1e-6;
 
 // y = P_DM x (Eq. proj); x, y padded FP64 fine-level face vectors (may alias)
 int project(dm_operator* op, const double* x, double* y, double tol) {
@@ -1813,7 +1811,6 @@ void dm_eig_params_default(dm_eig_params* p) {
     p->learned = nullptr;
     p->max_seconds = 0.0;
     p->rho_tol = 1e-8;
-    p->inner_relax = 1;
 }
 
 }  // extern "C"
@@ -1952,9 +1949,8 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         // Ritz and inner tolerances in force: both tighten by 10 whenever the
         // Ritz estimates call the wanted pairs converged but their FP64
         // certificate rho (the residual of K b = k^2 A b itself) misses rho_tol
-        double tol_eff = p.tol, inner_base = p.inner_tol, inner_eff = p.inner_tol;
+        double tol_eff = p.tol, inner_eff = p.inner_tol;
         int cert_retries = 0;
-        bool relax = p.inner_relax != 0;
         // rho of the wanted Ritz pairs (|theta| order) from the current basis
         auto certify_wanted = [&](std::vector<double>& rho_out) {
             std::vector<double> Yw((size_t)m * p.nev), kk(p.nev);
@@ -2028,9 +2024,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                     for (int c = 0; c < p.nev; ++c)
                         worst = std::max(worst, est[c] / std::max(std::fabs(theta[order[c]]), 1e-300));
                     tol_eff = 0.1 * std::min(tol_eff, worst);
-                    inner_base = std::max(inner_base * 0.1, 1e-13);
-                    inner_eff = inner_base;
-                    relax = false;   // a certificate missed: no more relaxed solves in this eigensolve
+                    inner_eff = std::max(inner_eff * 0.1, 1e-13);
                     ++cert_retries;
                     nconv = 0;
                     while (nconv < p.nev && est[nconv] <= tol_eff * std::fabs(theta[order[nconv]])) ++nconv;
@@ -2038,24 +2032,6 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             }
             if (nconv >= p.nev || restarts >= p.max_restarts) break;
             // thick restart: keep the pk wanted Ritz vectors
-            // Inexact shift-and-invert (after Simoncini 2005): a direction added
-            // once a wanted Ritz pair has relative residual r and relative gap g
-            // to the other Ritz values enters its vector with a weight of order
-            // r / g, so the new shifted systems may be solved to inner_base g / r
-            // (at most kRelaxMax) over the pairs not yet converged.  Clustered
-            // pairs (small g) keep the solves tight.  The certificate above still
-            // decides which pairs count.
-            if (relax) {
-                double worst = 0.0;
-                for (int c = nconv; c < p.nev; ++c) {
-                    const double th = theta[order[c]];
-                    double gap = 1.0;
-                    for (int o = 0; o < m; ++o)
-                        if (o != order[c]) gap = std::min(gap, std::fabs(theta[o] - th) / std::max(std::fabs(th), 1e-300));
-                    worst = std::max(worst, est[c] / std::max(std::fabs(th), 1e-300) / std::max(gap, 1e-300));
-                }
-                inner_eff = worst > 0.0 ? std::min(kRelaxMax, std::max(inner_base, inner_base / worst)) : inner_base;
-            }
             const int pk = std::min(m - 1, p.nev + (m - p.nev) / 2);
             std::vector<double> Yk((size_t)m * pk);
             for (int c = 0; c < pk; ++c)

@@ -73,7 +73,7 @@ def test_eig_params_tail_fields_keep_their_c_offsets(lib):
     p.rho_tol = 5.0
     p.learned = 1234
     lib.dm_eig_params_default(C.byref(p))
-    assert p.max_seconds == 0.0 and not p.learned and p.rho_tol == 1e-8 and p.inner_relax == 1
+    assert p.max_seconds == 0.0 and not p.learned and p.rho_tol == 1e-8
 
 
 def test_allocation_counter_needs_no_gpu(lib):
