@@ -107,8 +107,8 @@ typedef struct dm_eig_params {
                               (k^2 ||A b||) in FP64 (1e-8; 0 = Ritz estimates only).  When the Ritz
                               estimates call the nev pairs converged but a certificate misses rho_tol,
                               the Ritz tolerance drops to a tenth of the worst current estimate, inner_tol
-                              to a tenth (down to 1e-15 and 1e-13), and the Krylov-Schur iteration
-                              continues */
+                              to a tenth (down to 1e-15 and 1e-13), and the Krylov-Schur basis is rebuilt
+                              from the sum of the wanted Ritz vectors (a counted restart) */
 } dm_eig_params;
 
 typedef struct dm_eig_report {
