@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--bf16-steps", type=int, default=3, help="timed steps of the BF16 V-cycle arm (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
     ap.add_argument("--inner-restart", type=int, default=40, help="FGMRES restart length of the shifted solves")
+    ap.add_argument("--no-krylov-ff", action="store_true",
+                    help="FP64 operator applies inside the shifted solves' FGMRES iterations (instead of float-float)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
     if a.grid is None:
@@ -87,7 +89,7 @@ def describe(args, w):
 def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
-         "inner_restart": args.inner_restart,
+         "inner_restart": args.inner_restart, "krylov_apply": "f64" if args.no_krylov_ff else "float-float",
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:
@@ -286,7 +288,8 @@ def run_native(args):
         vec = "host" if host_io else "device"
         k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
                                        out=None if host_io else B_dev, precision=precision,
-                                       inner_tol=args.inner_tol, inner_restart=args.inner_restart)
+                                       inner_tol=args.inner_tol, inner_restart=args.inner_restart,
+                                       krylov_ff=0 if (args.no_krylov_ff or precision == "f64") else 1)
         geom.close()
         return k2, rep, st
 

@@ -86,6 +86,12 @@ typedef struct dm_mg_params {
                               are invariant under the scaling); the outer solves still use K (0) */
     int dense_coarse;      /* a level with at most this many open faces is the coarsest and is solved
                               densely (2048; 0 = coarsen by max_coarse alone; at most 6000) */
+    int krylov_ff;         /* 1: inside the shifted solves' FGMRES iterations, (K - sigma A) z is formed in
+                              float-float arithmetic (two FP32 numbers per value, about 48 significant
+                              bits) on the FP32 pipes, straight into the float-float Krylov basis; the
+                              restart residuals, the final residual check and every certificate stay in
+                              FP64.  0: the FP64 apply plus a gather.  Allocates about 68 bytes per
+                              fine-level node on the geometry (1) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
@@ -223,6 +229,12 @@ dm_status dm_operator_set_omega(dm_operator* op, int level, int scalar, double o
 /* y = (K - sigma A) x on `level` in FP64 (Eq. discLaplDM; K = C L C^T +
  * A D^T V^-1 D A with V^-1 = 0 where V = 0).  x, y: natural face layout. */
 dm_status dm_operator_apply(dm_operator* op, int level, const double* x, double* y, int on_device);
+/* The same product on the fine level as the shifted solves' FGMRES iterations
+ * form it with krylov_ff = 1: float-float arithmetic (about 48 significant
+ * bits), each open face's value hi + lo returned as an FP64 number (closed
+ * faces 0).  DM_ERR_INVALID_ARG when the operator was created with
+ * krylov_ff = 0.  x, y: natural face layout, caller-owned. */
+dm_status dm_operator_apply_ff(dm_operator* op, const double* x, double* y, int on_device);
 /* The same y = (K - sigma A) x as dm_operator_apply, for callers that must not
  * allocate memory once they are running: a loop that may not pay the device-
  * wide synchronisation cudaMalloc / cudaFree can cause, or an application

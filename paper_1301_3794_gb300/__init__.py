@@ -233,9 +233,11 @@ class Geometry:
 
 
 def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
-              autotune=1, force_shape=-1, band_sweeps_coarse=None, symmetric_transform=0, dense_coarse=None):
+              autotune=1, force_shape=-1, band_sweeps_coarse=None, symmetric_transform=0, dense_coarse=None,
+              krylov_ff=1):
     """band_sweeps_coarse: sweeps below the fine level (None: the library's default, 8);
-    symmetric_transform: 1 for the V-cycle of Eq. fullMat2's symmetric form."""
+    symmetric_transform: 1 for the V-cycle of Eq. fullMat2's symmetric form;
+    krylov_ff: 1 to form the shifted solves' FGMRES operator applies in float-float."""
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -251,6 +253,7 @@ def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power
     p.symmetric_transform = int(symmetric_transform)
     if dense_coarse is not None:
         p.dense_coarse = int(dense_coarse)
+    p.krylov_ff = int(krylov_ff)
     return p
 
 
@@ -291,6 +294,13 @@ class Operator:
         a = _Arg(x, self._faces(level))
         y, yp = _out_like(a, self._faces(level))
         self.ctx.check(lib.dm_operator_apply(self.h, level, a.ptr, yp, a.device), "dm_operator_apply")
+        return y
+
+    def apply_ff(self, x):
+        """(K - sigma A) x on the fine level in float-float (dm_operator_apply_ff)."""
+        a = _Arg(x, self._faces(0))
+        y, yp = _out_like(a, self._faces(0))
+        self.ctx.check(lib.dm_operator_apply_ff(self.h, a.ptr, yp, a.device), "dm_operator_apply_ff")
         return y
 
     def apply_noalloc(self, x, level=0, out=None):

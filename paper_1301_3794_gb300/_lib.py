@@ -17,7 +17,7 @@ class MGParams(C.Structure):
     _fields_ = [("max_coarse", C.c_int), ("band_sweeps", C.c_int), ("band_brick", C.c_int), ("omega_scale", C.c_double),
                 ("power_iters", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
                 ("stencil_shape", C.c_int), ("band_sweeps_coarse", C.c_int), ("symmetric_transform", C.c_int),
-                ("dense_coarse", C.c_int)]
+                ("dense_coarse", C.c_int), ("krylov_ff", C.c_int)]
 
 
 class EigParams(C.Structure):
@@ -73,6 +73,7 @@ SIGNATURES = {
     "dm_operator_get_omega": (C.c_double, [_P, C.c_int, C.c_int]),
     "dm_operator_set_omega": (C.c_int, [_P, C.c_int, C.c_int, C.c_double]),
     "dm_operator_apply": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    "dm_operator_apply_ff": (C.c_int, [_P, _P, _P, C.c_int]),
     "dm_operator_diagonal": (C.c_int, [_P, C.c_int, _P, C.c_int]),
     "dm_operator_apply_noalloc": (C.c_int, [_P, C.c_int, _P, _P]),
     "dm_operator_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),

@@ -130,6 +130,12 @@ struct GeoLevel {
     // spaces of the Krylov bases); built with the first operator on the level
     DBuf<int> flist, clist;
     int nflist = -1, nclist = -1;
+    // float-float copies of A, L, 1/V and the padded-to-compact face map, for
+    // the float-float operator apply of the shifted solves (fine level only,
+    // built with the first operator that asks for them)
+    DBuf<float2> ffA, ffL, ffV;
+    DBuf<int> fmap;
+    bool ff = false;
 };
 
 struct Sync {
@@ -691,14 +697,22 @@ double hessenberg_lsq(const std::vector<double>& H, int ld, int k, double beta, 
 struct NoMonitor {
     void operator()(double) const {}
 };
+// no float-float apply: the iterations apply the FP64 operator and gather
+struct NoApplyFF {
+    static constexpr bool on = false;
+    void operator()(const double*, float2*) const {}
+};
 
 // monitor(ratio) is told the residual contraction of every iteration
 // The basis lives in the compact index space of `list` (the nl entries of the
 // padded domain D that can be nonzero); b, x and the operator work on D.
-template <class Apply, class Prec, class Monitor = NoMonitor>
+// apply_ff(z, wf), when ApplyFF::on, forms the operator of an iteration
+// straight into the compact float-float vector wf; restart residuals and the
+// final check use the FP64 apply.
+template <class Apply, class Prec, class Monitor = NoMonitor, class ApplyFF = NoApplyFF>
 int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long long nl, int m, Apply apply, Prec prec,
            const double* b, double* x, double tol, int maxit, double* relres, double abs_tol = 0.0,
-           Monitor monitor = Monitor()) {
+           Monitor monitor = Monitor(), ApplyFF apply_ff = ApplyFF()) {
     cudaStream_t s = ctx->stream;
     const long long n = D.len();
     DM_REQUIRE(m >= 1 && 2 * m + 2 < ctx->red.max_cols, DM_ERR_INVALID_ARG, "FGMRES restart length too large");
@@ -744,8 +758,12 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
         for (int j = 0; j < m && total < maxit; ++j) {
             float2* Vj = V + (size_t)j * nlp;
             prec(Vj, 1.0 / nu, Z + (size_t)j * n);
-            apply(Z + (size_t)j * n, w);
-            ff_gather(nl, list, 1.0, w, wf, s);
+            if constexpr (ApplyFF::on) {
+                apply_ff(Z + (size_t)j * n, wf);
+            } else {
+                apply(Z + (size_t)j * n, w);
+                ff_gather(nl, list, 1.0, w, wf, s);
+            }
             // one sweep: Q^T v, Q^T w, v.v, v.w with Q = V_0 .. V_{j-1} finished
             dcgs_dots(ctx->red, Dc, j, V, nlp, Vj, wf, dots.data(), s);
             double ss = 0.0, sc = 0.0;
@@ -800,6 +818,17 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
     return total;
 }
 
+// the float-float apply of the shifted solves' iterations (fine level)
+struct FFApply {
+    static constexpr bool on = true;
+    dm_operator* op;
+    void operator()(const double* z, float2* wf) const {
+        const GeoLevel& l0 = glv(op, 0);
+        vec_apply_ff(l0.g, l0.tiles.get(), l0.ntiles, l0.ffA.get(), l0.ffL.get(), l0.ffV.get(), op->sigma, z,
+                     l0.fmap.get(), wf, op->ctx->stream);
+    }
+};
+
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
@@ -819,7 +848,12 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
             fell_back = true;
         }
     };
-    const int it = fgmres(op->ctx, op->vg, n, fl, nfl, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
+    int it;
+    if (op->mg.krylov_ff && g0.ff) {
+        it = fgmres(op->ctx, op->vg, n, fl, nfl, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor, FFApply{op});
+    } else {
+        it = fgmres(op->ctx, op->vg, n, fl, nfl, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
+    }
     if (fell_back) ++op->learned_fallbacks;
     op->learned_active = false;
     return it;
@@ -1107,6 +1141,20 @@ void setup_operator(dm_operator* op) {
         if (g0.nflist < 0) {
             g0.nflist = list_flagged<double>(3ll * g0.g.np, g0.A.get(), g0.flist, s);
             g0.nclist = list_flagged<unsigned char>((long long)g0.g.np, g0.active.get(), g0.clist, s);
+        }
+        if (op->mg.krylov_ff && !g0.ff) {
+            const long long n3 = 3ll * g0.g.np;
+            g0.ffA = DBuf<float2>(n3);
+            g0.ffL = DBuf<float2>(n3);
+            g0.ffV = DBuf<float2>(g0.g.np);
+            g0.fmap = DBuf<int>(n3);
+            note_allocation();
+            to_ff(n3, g0.A.get(), g0.ffA.get(), s);
+            to_ff(n3, g0.L.get(), g0.ffL.get(), s);
+            to_ff(g0.g.np, g0.invV.get(), g0.ffV.get(), s);
+            compact_map(n3, g0.flist.get(), g0.nflist, g0.fmap.get(), s);
+            Sync::stream(s);
+            g0.ff = true;
         }
     }
     if (op->mg.stencil_shape >= 0) {
@@ -1565,6 +1613,7 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->band_sweeps_coarse = 8;
     p->symmetric_transform = 0;
     p->dense_coarse = 2048;
+    p->krylov_ff = 1;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1586,6 +1635,7 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
         DM_REQUIRE(op->mg.band_sweeps_coarse >= 0 && op->mg.band_sweeps_coarse <= 256, DM_ERR_INVALID_ARG,
                    "band_sweeps_coarse out of range");
         DM_REQUIRE(op->mg.band_brick >= 1, DM_ERR_INVALID_ARG, "band_brick must be >= 1");
+        DM_REQUIRE(op->mg.krylov_ff == 0 || op->mg.krylov_ff == 1, DM_ERR_INVALID_ARG, "krylov_ff must be 0 or 1");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
         DM_REQUIRE(op->mg.stencil_shape >= -1 && op->mg.stencil_shape < kStencilShapes, DM_ERR_INVALID_ARG,
@@ -1635,6 +1685,24 @@ dm_status dm_operator_apply(dm_operator* op, int level, const double* x, double*
         faces_in(op, level, x, on_device, xp.get());
         apply_vec64(op, level, xp.get(), yp.get());
         faces_out(op, level, yp.get(), y, on_device);
+    });
+}
+
+dm_status dm_operator_apply_ff(dm_operator* op, const double* x, double* y, int on_device) {
+    if (!op || !x || !y) return DM_ERR_INVALID_ARG;
+    return guarded(op->ctx, [&] {
+        const GeoLevel& g0 = glv(op, 0);
+        DM_REQUIRE(op->mg.krylov_ff && g0.ff, DM_ERR_INVALID_ARG, "operator created with krylov_ff = 0");
+        cudaStream_t s = op->ctx->stream;
+        const long long n3 = 3ll * g0.g.np;
+        DBuf<double> xp(n3), yp(n3);
+        DBuf<float2> wf(std::max(g0.nflist, 1));
+        faces_in(op, 0, x, on_device, xp.get());
+        vec_apply_ff(g0.g, g0.tiles.get(), g0.ntiles, g0.ffA.get(), g0.ffL.get(), g0.ffV.get(), op->sigma, xp.get(),
+                     g0.fmap.get(), wf.get(), s);
+        zero(yp.get(), sizeof(double) * n3, s);
+        ff_scatter<double>(g0.nflist, g0.flist.get(), 1.0, wf.get(), yp.get(), s);
+        faces_out(op, 0, yp.get(), y, on_device);
     });
 }
 

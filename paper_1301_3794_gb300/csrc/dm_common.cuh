@@ -432,6 +432,14 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
                   T* x, double* u, double omega, int sweeps, bool fine, cudaStream_t s, const Fork* fk = nullptr);
 void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,
                          const double* x, double* y, cudaStream_t s);
+// (K - sigma A) x in float-float into the compact vector out (out[cmap[q]] for
+// the open faces q), over the level's 32 x 4 x 2 active tiles; A, L, invV:
+// float-float copies of the level's coefficients (to_ff)
+void vec_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A, const float2* L, const float2* invV,
+                  double sigma, const double* x, const int* cmap, float2* out, cudaStream_t s);
+void to_ff(long long n, const double* a, float2* out, cudaStream_t s);
+// cmap[q] = position of q in the ascending list (nl entries), -1 elsewhere (n3 entries)
+void compact_map(long long n3, const int* list, int nl, int* cmap, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,
                   cudaStream_t s);
 void vec_dense_assemble(const Grid3& g, const double* A, const double* L, const double* invV, double sigma,

@@ -16,6 +16,7 @@
 //
 // Scalar operator inside the projection (Eq. proj): S = D A D^T on cells.
 #include "dm_common.cuh"
+#include "dm_ff.cuh"
 
 #include <atomic>
 #include <mutex>
@@ -620,7 +621,178 @@ __global__ void k_sub_grad(Grid3 g, const double* __restrict__ A, const double* 
     y[2 * N + p] = A[2 * N + p] > 0.0 ? x[2 * N + p] - (phi[p - Z] - ph) * g.rhz : 0.0;
 }
 
+// (K - sigma A) x in float-float on the FP32 pipes, for the shifted solves'
+// Krylov vectors: x is FP64, the coefficients are float-float copies of the
+// level's FP64 A, L, 1/V, and every product and sum is a float-float operation
+// (about 48 significant bits).  The result goes straight into the compact
+// float-float vector of the FGMRES basis: out[cmap[q]] for every open face q.
+// Same tiles and the same sharing of edge curls and cell divergences through
+// shared memory as k_vec_stencil_tiled (32 x 4 x 2 tiles); in addition the
+// block splits the x it needs (the tile with a one-node ring) into float-float
+// once, into shared memory, so that each value is converted once per block.
+__global__ void __launch_bounds__(TX * TY * TZ) k_vec_apply_ff(Grid3 g, const float2* __restrict__ A,
+                                                               const float2* __restrict__ L,
+                                                               const float2* __restrict__ invV, ffv rdx, ffv rdy,
+                                                               ffv rdz, ffv sigma, const double* __restrict__ x,
+                                                               const int* __restrict__ cmap, float2* __restrict__ out,
+                                                               const int* __restrict__ tiles) {
+    constexpr int SY = TY, SZ = TZ;
+    constexpr int BXW = TX + 2, BYW = SY + 2, BZW = SZ + 2, NB = BXW * BYW * BZW;   // x: i0-1 .. i0+TX (j, k alike)
+    constexpr int PSI_X = TX + 1, PSI_Y = SY + 1, PSI_Z = SZ + 1;
+    constexpr int EX_X = TX, EX_Y = SY + 1, EX_Z = SZ + 1;
+    constexpr int EY_X = TX + 1, EY_Y = SY, EY_Z = SZ + 1;
+    constexpr int EZ_X = TX + 1, EZ_Y = SY + 1, EZ_Z = SZ;
+    constexpr int N_PSI = PSI_X * PSI_Y * PSI_Z, N_EX = EX_X * EX_Y * EX_Z, N_EY = EY_X * EY_Y * EY_Z,
+                  N_EZ = EZ_X * EZ_Y * EZ_Z;
+    constexpr int NT = TX * SY * SZ;
+    __shared__ ffv s_b[3][NB];
+    __shared__ ffv s_psi[N_PSI], s_ex[N_EX], s_ey[N_EY], s_ez[N_EZ];
+    const int t = tiles[blockIdx.x];
+    const int nti = (g.nx + TX) / TX, ntj = (g.ny + SY) / SY;
+    const int i0 = (t % nti) * TX, j0 = ((t / nti) % ntj) * SY, k0 = (t / (nti * ntj)) * SZ;
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    const int tid = threadIdx.x + TX * (threadIdx.y + SY * threadIdx.z);
+    // x over the box; the padded layout holds nodes -1 .. n+1 along each axis
+    // (zero where no face exists), and nodes past n+1 are taken as zero
+    for (int e = tid; e < NB; e += NT) {
+        const int li = e % BXW, lj = (e / BXW) % BYW, lk = e / (BXW * BYW);
+        const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
+        const bool in = i <= g.nx + 1 && j <= g.ny + 1 && k <= g.nz + 1;
+        const int p = in ? g.idx(i, j, k) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s_b[c][e] = in ? ff_from_double(x[c * N + p]) : ff_zero();
+    }
+    __syncthreads();
+    // b(c, li, lj, lk): box coordinates (node i0-1+li ...)
+    auto b = [&](int c, int li, int lj, int lk) { return s_b[c][(lk * BYW + lj) * BXW + li]; };
+    auto a = [&](int c, int p) { return ff_load(A + c * N + p); };
+    auto l = [&](int c, int p) { return ff_load(L + c * N + p); };
+    for (int e = tid; e < N_PSI; e += NT) {
+        const int li = e % PSI_X, lj = (e / PSI_X) % PSI_Y, lk = e / (PSI_X * PSI_Y);   // box coords of the cell
+        const int i = i0 - 1 + li, j = j0 - 1 + lj, k = k0 - 1 + lk;
+        ffv v = ff_zero();
+        if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz) {
+            const int p = g.idx(i, j, k);
+            const ffv iv = ff_load(invV + p);
+            if (iv.hi != 0.f) {
+                const ffv fx = a(0, p + X) * b(0, li + 1, lj, lk) - a(0, p) * b(0, li, lj, lk);
+                const ffv fy = a(1, p + Y) * b(1, li, lj + 1, lk) - a(1, p) * b(1, li, lj, lk);
+                const ffv fz = a(2, p + Z) * b(2, li, lj, lk + 1) - a(2, p) * b(2, li, lj, lk);
+                v = iv * (fx * rdx + fy * rdy + fz * rdz);
+            }
+        }
+        s_psi[e] = v;
+    }
+    for (int e = tid; e < N_EX; e += NT) {
+        const int li = e % EX_X, lj = (e / EX_X) % EX_Y, lk = e / (EX_X * EX_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        ffv v = ff_zero();
+        if (i < g.nx && j <= g.ny && k <= g.nz) {
+            const ffv lv = l(0, g.idx(i, j, k));
+            const int bi = li + 1, bj = lj + 1, bk = lk + 1;
+            if (lv.hi != 0.f)
+                v = lv * ((b(1, bi, bj, bk - 1) - b(1, bi, bj, bk)) * rdz + (b(2, bi, bj, bk) - b(2, bi, bj - 1, bk)) * rdy);
+        }
+        s_ex[e] = v;
+    }
+    for (int e = tid; e < N_EY; e += NT) {
+        const int li = e % EY_X, lj = (e / EY_X) % EY_Y, lk = e / (EY_X * EY_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        ffv v = ff_zero();
+        if (i <= g.nx && j < g.ny && k <= g.nz) {
+            const ffv lv = l(1, g.idx(i, j, k));
+            const int bi = li + 1, bj = lj + 1, bk = lk + 1;
+            if (lv.hi != 0.f)
+                v = lv * ((b(0, bi, bj, bk) - b(0, bi, bj, bk - 1)) * rdz + (b(2, bi - 1, bj, bk) - b(2, bi, bj, bk)) * rdx);
+        }
+        s_ey[e] = v;
+    }
+    for (int e = tid; e < N_EZ; e += NT) {
+        const int li = e % EZ_X, lj = (e / EZ_X) % EZ_Y, lk = e / (EZ_X * EZ_Y);
+        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+        ffv v = ff_zero();
+        if (i <= g.nx && j <= g.ny && k < g.nz) {
+            const ffv lv = l(2, g.idx(i, j, k));
+            const int bi = li + 1, bj = lj + 1, bk = lk + 1;
+            if (lv.hi != 0.f)
+                v = lv * ((b(0, bi, bj - 1, bk) - b(0, bi, bj, bk)) * rdy + (b(1, bi, bj, bk) - b(1, bi - 1, bj, bk)) * rdx);
+        }
+        s_ez[e] = v;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int i = i0 + tx, j = j0 + ty, k = k0 + tz;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int p = g.idx(i, j, k);
+    auto PSI = [&](int aa, int bb, int cc) { return s_psi[(cc * PSI_Y + bb) * PSI_X + aa]; };
+    auto EXS = [&](int aa, int bb, int cc) { return s_ex[(cc * EX_Y + bb) * EX_X + aa]; };
+    auto EYS = [&](int aa, int bb, int cc) { return s_ey[(cc * EY_Y + bb) * EY_X + aa]; };
+    auto EZS = [&](int aa, int bb, int cc) { return s_ez[(cc * EZ_Y + bb) * EZ_X + aa]; };
+    const ffv ps0 = PSI(tx + 1, ty + 1, tz + 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int ci = cmap[c * N + p];
+        if (ci < 0) continue;   // closed face
+        const ffv av = a(c, p);
+        const ffv bv = b(c, tx + 1, ty + 1, tz + 1);
+        ffv v;
+        if (c == 0)
+            v = (EZS(tx, ty + 1, tz) - EZS(tx, ty, tz)) * rdy - (EYS(tx, ty, tz + 1) - EYS(tx, ty, tz)) * rdz +
+                av * ((PSI(tx, ty + 1, tz + 1) - ps0) * rdx - sigma * bv);
+        else if (c == 1)
+            v = (EXS(tx, ty, tz + 1) - EXS(tx, ty, tz)) * rdz - (EZS(tx + 1, ty, tz) - EZS(tx, ty, tz)) * rdx +
+                av * ((PSI(tx + 1, ty, tz + 1) - ps0) * rdy - sigma * bv);
+        else
+            v = (EYS(tx + 1, ty, tz) - EYS(tx, ty, tz)) * rdx - (EXS(tx, ty + 1, tz) - EXS(tx, ty, tz)) * rdy +
+                av * ((PSI(tx + 1, ty + 1, tz) - ps0) * rdz - sigma * bv);
+        out[ci] = make_float2(v.hi, v.lo);
+    }
+}
+
+// float-float copy of an FP64 array: hi = the double rounded to FP32, lo =
+// the rest rounded (setup only, FP64 arithmetic)
+__global__ void k_to_ff(long long n, const double* __restrict__ a, float2* __restrict__ out) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const float hi = __double2float_rn(a[r]);
+        out[r] = make_float2(hi, __double2float_rn(a[r] - (double)hi));
+    }
+}
+
+// cmap[q] = the compact index of open face q (the position of q in the
+// ascending list of open faces), -1 elsewhere
+__global__ void k_compact_map(long long n3, const int* __restrict__ list, int nl, int* __restrict__ cmap) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nl; r += (long long)gridDim.x * blockDim.x)
+        cmap[list[r]] = (int)r;
+    (void)n3;
+}
+
+ffv host_ff(double v) {
+    ffv f;
+    f.hi = (float)v;
+    f.lo = (float)(v - (double)f.hi);
+    return f;
+}
+
 }  // namespace
+
+void to_ff(long long n, const double* a, float2* out, cudaStream_t s) {
+    launch("k_to_ff", k_to_ff, (int)std::min<long long>((n + 255) / 256, 152 * 8), 256, 0, s, n, a, out);
+}
+
+void compact_map(long long n3, const int* list, int nl, int* cmap, cudaStream_t s) {
+    DM_CUDA(cudaMemsetAsync(cmap, 0xff, sizeof(int) * (size_t)n3, s));
+    launch("k_compact_map", k_compact_map, (int)std::min<long long>(((long long)nl + 255) / 256, 152 * 8), 256, 0, s, n3,
+           list, nl, cmap);
+}
+
+void vec_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A, const float2* L, const float2* invV,
+                  double sigma, const double* x, const int* cmap, float2* out, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    // bytes: per open face its x (8), A and about one L (8 each), a third of a 1/V (8), the output (8) and cmap (4)
+    const double bytes = (double)g.nopen * (8.0 + 16.0 + 8.0 / 3.0 + 12.0);
+    launch_b("vec_apply_ff_L0", bytes, k_vec_apply_ff, ntiles, dim3(TX, TY, TZ), 0, s, g, A, L, invV, host_ff(g.rhx),
+             host_ff(g.rhy), host_ff(g.rhz), host_ff(sigma), x, cmap, out, tiles);
+}
 
 const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
     // interned names: a node-based set keeps every c_str() pointer stable;

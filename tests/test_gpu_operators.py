@@ -73,6 +73,43 @@ def test_apply_device_pointers(case):
     assert _rel(y.cpu().numpy(), lev.K @ x) < 1e-13
 
 
+def test_apply_float_float(case):
+    """The float-float product of the shifted solves' iterations against the
+    oracle's FP64 matrix: about 48 significant bits per operation, and the
+    result cancels against terms up to (k h)^-2 times its size on smooth
+    fields, so 1e-12 (random) and 1e-11 (smooth) of the largest entry."""
+    w, geom, levels, op = case
+    lev = levels[0]
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(lev.mask.size) * lev.mask
+    assert _rel(op.apply_ff(x), lev.K @ x) < 1e-12
+    xs = np.cos(np.arange(lev.mask.size) * 1e-3) * lev.mask
+    assert _rel(op.apply_ff(xs), lev.K @ xs) < 1e-11
+    y = op.apply_ff(x)
+    assert np.all(y[lev.mask == 0] == 0.0)
+
+
+def test_krylov_float_float_solve_matches_f64(dm, ctx, case):
+    """The shifted solve with float-float iterations reaches the same FP64
+    residual, and the same solution, as with FP64 iterations."""
+    w, geom, levels, op = case
+    lev = levels[0]
+    b = np.random.default_rng(8).standard_normal(lev.mask.size) * lev.mask
+    x1, it1, rr1 = op.solve(b, tol=1e-10)
+    op0 = dm.Operator(ctx, geom, w.sigma, krylov_ff=0)
+    x0, it0, rr0 = op0.solve(b, tol=1e-10)
+    op0.close()
+    assert rr1 < 1e-9 and rr0 < 1e-9
+    assert abs(it1 - it0) <= 1, (it0, it1)
+    assert np.linalg.norm(x1 - x0) / np.linalg.norm(x0) < 1e-8
+    with pytest.raises(Exception):
+        op_no = dm.Operator(ctx, geom, w.sigma, krylov_ff=0)
+        try:
+            op_no.apply_ff(b)
+        finally:
+            op_no.close()
+
+
 def test_diagonal(case):
     w, geom, levels, op = case
     for l, lev in enumerate(levels):
