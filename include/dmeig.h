@@ -187,6 +187,27 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz,
                              double dx, double dy, double dz, const double origin[3],
                              const double* phi, int phi_on_device, double a_min,
                              dm_geometry** out);
+/* Kinds of the six outer walls (Sec. 6.2-6.3: symmetry planes that reduce the
+ * domain).  DM_WALL_PEC: a perfect electric conductor on the wall's node plane
+ * (normal faces and tangential edges closed); an electric symmetry plane is
+ * this wall.  DM_WALL_PMC: a magnetic symmetry plane half a cell OUTSIDE the
+ * wall's node plane (through the centres of the cells the mirror would add),
+ * so the grid's first node plane lies h/2 from the plane; the wall's normal
+ * faces and tangential edges keep their fractions and the field beyond is
+ * zero.  With that placement the half-domain problem has exactly the modes of
+ * the mirrored full domain whose normal flux is even under the mirror. */
+typedef enum { DM_WALL_PEC = 0, DM_WALL_PMC = 1 } dm_wall;
+
+/* dm_geometry_create with chosen wall kinds: walls[6] in the order x-low,
+ * x-high, y-low, y-high, z-low, z-high (NULL = all DM_WALL_PEC).  The coarser
+ * levels average the fine fractions, walls included.  A vacuum region that
+ * reaches a magnetic wall carries no constant null vector of D A D^T (the
+ * potential is zero beyond the wall), so P_DM pins nothing there.  An entry
+ * that is neither kind gives DM_ERR_INVALID_ARG. */
+dm_status dm_geometry_create_walls(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                                   const double origin[3], const double* phi, int phi_on_device, double a_min,
+                                   const int walls[6], dm_geometry** out);
+
 /* A geometry from cut fractions the caller supplies instead of a level set:
  * L (edges, natural edge layout), A (faces) and V (cells), host or device per
  * on_device; the coarser multigrid levels average them as in

@@ -38,6 +38,28 @@ def box_eigenvalues(nx, ny, nz, dx, dy, dz):
     return np.sort(np.array(out))
 
 
+def box_eigenvalues_magnetic_x(m, ny, nz, dx, dy, dz):
+    """Sorted electromagnetic eigenvalues of the box of m cells along x whose
+    x-low wall is a magnetic symmetry plane half a cell outside it (and whose
+    other walls are conductors): the modes of the conductor box of 2m + 1
+    cells that are even under x -> -x about its middle.  There B_x ~ sin(p pi
+    x' / L) (x' from the conductor wall) is even exactly for odd p, so the
+    spectrum is the box rule above restricted to odd p (p never zero)."""
+    nx = 2 * m + 1
+    sx = (2.0 / dx * np.sin(np.pi * np.arange(nx) / (2 * nx))) ** 2
+    sy = (2.0 / dy * np.sin(np.pi * np.arange(ny) / (2 * ny))) ** 2
+    sz = (2.0 / dz * np.sin(np.pi * np.arange(nz) / (2 * nz))) ** 2
+    out = []
+    for p in range(1, nx, 2):
+        for q in range(ny):
+            for r in range(nz):
+                zeros = (q == 0) + (r == 0)
+                if zeros >= 2:
+                    continue
+                out += [sx[p] + sy[q] + sz[r]] * (2 if zeros == 0 else 1)
+    return np.sort(np.array(out))
+
+
 def box_scalar_eigenvalues(nx, ny, nz, dx, dy, dz):
     """Nonzero Neumann eigenvalues of the cell Laplacian D D^T on the box."""
     sx = (2.0 / dx * np.sin(np.pi * np.arange(nx) / (2 * nx))) ** 2

@@ -20,7 +20,14 @@ so the three measures are mutually consistent.  phi < 0 is vacuum, phi >= 0 is
 conductor (a node exactly on the surface counts as conductor).
 
 Domain walls are perfect conductors (Sec. 6): normal faces and tangential edges
-on the outer walls get fraction 0.
+on the outer walls get fraction 0.  A wall may instead be a symmetry plane of
+the perfect-magnetic-conductor kind (Sec. 6.3, the quarter TESLA cavity); the
+reading used here puts that plane half a cell outside the wall's node plane
+(through the centres of the mirrored cells), where the Yee unknowns of fields
+that are even under the mirror map pair up exactly with their images: the
+wall's normal faces and tangential edges then keep their fractions, and every
+entity beyond the wall is zero.  A perfect-electric symmetry plane (Sec. 6.2,
+the octant sphere) lies on the wall's node plane and is the ordinary wall.
 
 Pins (tests/test_oracle_geometry.py): simplex fractions against brute-force
 lattice sampling and the divided-difference closed form; half-space and corner
@@ -111,7 +118,10 @@ def _quad_fraction(c00, c10, c01, c11):
     return 0.5 * (triangle_fraction(c00, c10, c11) + triangle_fraction(c00, c01, c11))
 
 
-def fractions(phi, a_min=0.0):
+WALLS_PEC = ("pec",) * 6
+
+
+def fractions(phi, a_min=0.0, walls=WALLS_PEC):
     """Cut fractions of every edge, face and cell.
 
     ``phi`` has shape (nz+1, ny+1, nx+1).  Returns a dict of arrays in natural
@@ -120,6 +130,10 @@ def fractions(phi, a_min=0.0):
 
     ``a_min`` > 0 neglects faces with 0 < A < a_min (Sec. 3): the face and the
     edges bounding it get fraction 0.
+
+    ``walls``: the kind of each outer wall, in the order x-low, x-high, y-low,
+    y-high, z-low, z-high: "pec" (closed) or "pmc" (symmetry plane half a cell
+    outside, its faces and edges open).
     """
     p = np.asarray(phi, dtype=np.float64)
     nz, ny, nx = (s - 1 for s in p.shape)
@@ -145,13 +159,22 @@ def fractions(phi, a_min=0.0):
             path.append(tuple(cur))
         vol += tet_fraction(*(corner(v) for v in path))
     f["V"] = vol / 6.0
-    # outer walls are perfect conductors
-    f["Lx"][:, 0, :] = 0.0; f["Lx"][:, -1, :] = 0.0; f["Lx"][0, :, :] = 0.0; f["Lx"][-1, :, :] = 0.0
-    f["Ly"][:, :, 0] = 0.0; f["Ly"][:, :, -1] = 0.0; f["Ly"][0, :, :] = 0.0; f["Ly"][-1, :, :] = 0.0
-    f["Lz"][:, :, 0] = 0.0; f["Lz"][:, :, -1] = 0.0; f["Lz"][:, 0, :] = 0.0; f["Lz"][:, -1, :] = 0.0
-    f["Ax"][:, :, 0] = 0.0; f["Ax"][:, :, -1] = 0.0
-    f["Ay"][:, 0, :] = 0.0; f["Ay"][:, -1, :] = 0.0
-    f["Az"][0, :, :] = 0.0; f["Az"][-1, :, :] = 0.0
+    # perfect-conductor walls: their normal faces and tangential edges are closed
+    walls = tuple(walls)
+    if len(walls) != 6 or any(w not in ("pec", "pmc") for w in walls):
+        raise ValueError("walls: six entries, each 'pec' or 'pmc'")
+    for axis in range(3):                      # 0 = x, 1 = y, 2 = z
+        ax_arr = 2 - axis                      # array axis of that direction (arrays are (z, y, x))
+        for side, idx in ((0, 0), (1, -1)):
+            if walls[2 * axis + side] != "pec":
+                continue
+            sl = [slice(None)] * 3
+            sl[ax_arr] = idx
+            sl = tuple(sl)
+            f["A" + "xyz"[axis]][sl] = 0.0     # normal faces
+            for e in range(3):                 # tangential edges
+                if e != axis:
+                    f["L" + "xyz"[e]][sl] = 0.0
     if a_min > 0.0:
         _neglect_faces(f, a_min)
     return f

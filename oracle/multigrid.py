@@ -41,7 +41,8 @@ Scalar cycle (cells, operator S = D A D^T):
   (constant), masked by the active fine cells (cells with an open face);
   R = P^T / 8; damped Jacobi; coarsest: exact solve with, in each connected
   component of active cells, the lowest-index cell pinned to 0 (S is singular
-  with one constant null vector per component).
+  with one constant null vector per component), except in components that
+  reach an open outer-wall face (a magnetic symmetry plane), which are regular.
 
 Pins (tests/test_oracle_multigrid.py): P's partition of unity and exactness for
 affine fields away from walls; restriction as the explicit transpose; the
@@ -176,14 +177,16 @@ def open_face_count(fr):
 DENSE_COARSE = 2048
 
 
-def level_fractions(grid, phi, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE):
+def level_fractions(grid, phi, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE, walls=geometry.WALLS_PEC):
     """Grids and fractions of every level; ``fine`` replaces the fine-level
     fractions computed from phi (for perturbation studies).  Coarsening stops
     when the grid cannot be halved (``can_coarsen``) or when the current level
-    has at most ``dense_coarse`` open faces (0: no such limit)."""
+    has at most ``dense_coarse`` open faces (0: no such limit).  ``walls``: the
+    outer-wall kinds of oracle.geometry.fractions (the coarse levels average
+    the fine fractions, walls included)."""
     from workloads import Grid
     grids = [grid]
-    frs = [geometry.fractions(phi) if fine is None else fine]
+    frs = [geometry.fractions(phi, walls=walls) if fine is None else fine]
     g = grid
     while can_coarsen(g.nx, g.ny, g.nz, max_coarse) and (dense_coarse <= 0 or open_face_count(frs[-1]) > dense_coarse):
         g = Grid(g.nx // 2, g.ny // 2, g.nz // 2, 2 * g.dx, 2 * g.dy, 2 * g.dz, g.origin)
@@ -192,8 +195,9 @@ def level_fractions(grid, phi, max_coarse=4, fine=None, dense_coarse=DENSE_COARS
     return grids, frs
 
 
-def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE):
-    grids, frs = level_fractions(grid, phi, max_coarse, fine, dense_coarse)
+def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None, dense_coarse=DENSE_COARSE,
+                           walls=geometry.WALLS_PEC):
+    grids, frs = level_fractions(grid, phi, max_coarse, fine, dense_coarse, walls)
     levels = [VectorLevel(g, f, sigma) for g, f in zip(grids, frs)]
     for l in range(len(levels) - 1):
         c = levels[l + 1].grid
@@ -201,8 +205,8 @@ def build_vector_hierarchy(grid, phi, sigma, max_coarse=4, fine=None, dense_coar
     return levels
 
 
-def build_scalar_hierarchy(grid, phi, max_coarse=4, dense_coarse=DENSE_COARSE):
-    grids, frs = level_fractions(grid, phi, max_coarse, dense_coarse=dense_coarse)
+def build_scalar_hierarchy(grid, phi, max_coarse=4, dense_coarse=DENSE_COARSE, walls=geometry.WALLS_PEC):
+    grids, frs = level_fractions(grid, phi, max_coarse, dense_coarse=dense_coarse, walls=walls)
     levels = [ScalarLevel(g, f) for g, f in zip(grids, frs)]
     for l in range(len(levels) - 1):
         c = levels[l + 1].grid
@@ -308,13 +312,16 @@ def vcycle(levels, f, omegas, band_sweeps=16, l=0, brick=8, band_sweeps_coarse=N
 
 def scalar_coarsest_solve(level, f):
     """Exact solve with the lowest-index cell of every connected component of
-    active cells pinned to 0."""
+    active cells pinned to 0 (components with an open wall face: none)."""
     act = np.nonzero(level.active)[0]
     Sa = level.S[act][:, act].tocsr()
     ncomp, labels = csgraph.connected_components(Sa, directed=False)
+    grounded = level.ops.grounded_cells()[act]
     keep = np.ones(act.size, dtype=bool)
     for c in range(ncomp):
-        keep[np.nonzero(labels == c)[0][0]] = False
+        members = np.nonzero(labels == c)[0]
+        if not grounded[members].any():
+            keep[members[0]] = False
     kk = np.nonzero(keep)[0]
     x = np.zeros_like(f)
     if kk.size:

@@ -146,16 +146,22 @@ class DMOperators:
         """P_DM x = x - D^T (D A D^T)^-1 D A x (Eq. proj) on the full face space.
 
         D A D^T is singular with one constant null vector per connected vacuum
-        component; D A x has zero sum on each component, so pinning one cell of
-        each component gives an exact solution (the constant is irrelevant to
-        D^T restricted to open faces).  Closed faces of the result are 0."""
+        component enclosed by closed faces; D A x has zero sum on each such
+        component, so pinning one cell of each gives an exact solution (the
+        constant is irrelevant to D^T restricted to open faces).  A component
+        that reaches an open face on the outer wall (a magnetic symmetry
+        plane, see oracle.geometry) sees the zero potential beyond it and is
+        regular: it is not pinned.  Closed faces of the result are 0."""
         S = self.scalar_laplacian()
         active = np.nonzero(self.v > 0)[0]
         Sa = S[active][:, active].tocsr()
         ncomp, labels = csgraph.connected_components(Sa, directed=False)
+        grounded = self.grounded_cells()[active]
         keep = np.ones(active.size, dtype=bool)
         for c in range(ncomp):
-            keep[np.nonzero(labels == c)[0][0]] = False
+            members = np.nonzero(labels == c)[0]
+            if not grounded[members].any():
+                keep[members[0]] = False
         s = (self.D @ (self.a * x))[active]
         psi_a = np.zeros(active.size)
         kk = np.nonzero(keep)[0]
@@ -166,6 +172,12 @@ class DMOperators:
         y = x - self.D.T @ psi
         y[~self.open] = 0.0
         return y
+
+    def grounded_cells(self):
+        """Cells with an open face on the outer wall (a face of D with one cell)."""
+        cells_per_face = np.asarray((self.D != 0).sum(axis=0)).ravel()
+        wall_open = (cells_per_face == 1) & self.open
+        return np.asarray(abs(self.D) @ wall_open.astype(float)).ravel() > 0
 
     def vacuum_components(self):
         S = self.scalar_laplacian()

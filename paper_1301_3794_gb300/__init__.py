@@ -157,15 +157,29 @@ class Context:
 class Geometry:
     """Cut-cell fractions of a Yee grid and its multigrid levels."""
 
-    def __init__(self, ctx, nx, ny, nz, dx, dy, dz, phi, origin=(0.0, 0.0, 0.0), a_min=0.0):
+    WALL_KINDS = {"pec": 0, "pmc": 1}
+
+    def __init__(self, ctx, nx, ny, nz, dx, dy, dz, phi, origin=(0.0, 0.0, 0.0), a_min=0.0, walls=None):
+        """walls: None (every wall a conductor) or six of "pec" / "pmc" in the
+        order x-low, x-high, y-low, y-high, z-low, z-high (dm_geometry_create_walls)."""
         self.ctx = ctx
         self.dims = (int(nx), int(ny), int(nz))
         self.spacing = (float(dx), float(dy), float(dz))
         arg = _Arg(phi, (nx + 1) * (ny + 1) * (nz + 1))
         org = (C.c_double * 3)(*origin)
         h = C.c_void_p()
-        st = lib.dm_geometry_create(ctx.h, nx, ny, nz, dx, dy, dz, org, arg.ptr, arg.device, float(a_min), C.byref(h))
-        ctx.check(st, "dm_geometry_create")
+        if walls is None:
+            st = lib.dm_geometry_create(ctx.h, nx, ny, nz, dx, dy, dz, org, arg.ptr, arg.device, float(a_min),
+                                        C.byref(h))
+            ctx.check(st, "dm_geometry_create")
+        else:
+            walls = tuple(walls)
+            if len(walls) != 6 or any(w not in self.WALL_KINDS for w in walls):
+                raise ValueError("walls: six entries, each 'pec' or 'pmc'")
+            wk = (C.c_int * 6)(*(self.WALL_KINDS[w] for w in walls))
+            st = lib.dm_geometry_create_walls(ctx.h, nx, ny, nz, dx, dy, dz, org, arg.ptr, arg.device, float(a_min),
+                                              wk, C.byref(h))
+            ctx.check(st, "dm_geometry_create_walls")
         self.h = h
         ctx._adopt(self)
 
@@ -192,7 +206,11 @@ class Geometry:
     @classmethod
     def from_workload(cls, ctx, w, a_min=0.0, phi=None):
         g = w.grid
-        return cls(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, w.phi.ravel() if phi is None else phi, g.origin, a_min)
+        walls = getattr(w, "walls", None)
+        if walls is not None and all(x == "pec" for x in walls):
+            walls = None
+        return cls(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, w.phi.ravel() if phi is None else phi, g.origin, a_min,
+                   walls=walls)
 
     @property
     def num_levels(self):

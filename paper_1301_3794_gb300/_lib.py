@@ -59,6 +59,8 @@ SIGNATURES = {
     "dm_measure_fma_rates": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dm_geometry_create": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
                                      _D, _P, C.c_int, C.c_double, C.POINTER(_P)]),
+    "dm_geometry_create_walls": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                           _D, _P, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(_P)]),
     "dm_geometry_create_from_fractions": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                                     C.c_double, _P, _P, _P, C.c_int, C.POINTER(_P)]),
     "dm_geometry_destroy": (None, [_P]),

@@ -1501,12 +1501,26 @@ extern "C" {
 dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
                              const double origin[3], const double* phi, int phi_on_device, double a_min,
                              dm_geometry** out) {
+    return dm_geometry_create_walls(ctx, nx, ny, nz, dx, dy, dz, origin, phi, phi_on_device, a_min, nullptr, out);
+}
+
+dm_status dm_geometry_create_walls(dm_context* ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                                   const double origin[3], const double* phi, int phi_on_device, double a_min,
+                                   const int walls[6], dm_geometry** out) {
     if (!ctx || !out || !phi) return DM_ERR_INVALID_ARG;
     *out = nullptr;
     (void)origin;
     if (!(a_min >= 0.0 && a_min < 1.0)) {
         ctx->err = "a_min must be in [0, 1)";
         return DM_ERR_INVALID_ARG;
+    }
+    int pmc = 0;
+    for (int w = 0; walls && w < 6; ++w) {
+        if (walls[w] != DM_WALL_PEC && walls[w] != DM_WALL_PMC) {
+            ctx->err = "walls[" + std::to_string(w) + "] is neither DM_WALL_PEC nor DM_WALL_PMC";
+            return DM_ERR_INVALID_ARG;
+        }
+        if (walls[w] == DM_WALL_PMC) pmc |= 1 << w;
     }
     return build_geometry(ctx, nx, ny, nz, dx, dy, dz, [&](GeoLevel& lv, cudaStream_t s) {
         DBuf<double> phi_pad(lv.g.np);
@@ -1522,7 +1536,7 @@ dm_status dm_geometry_create(dm_context* ctx, int nx, int ny, int nz, double dx,
                            " node values are NaN or infinite");
         }
         pack_nodes(lv.g, dphi, phi_pad.get(), s);
-        geom_fractions(lv.g, phi_pad.get(), lv.L.get(), lv.A.get(), lv.V.get(), s);
+        geom_fractions(lv.g, phi_pad.get(), pmc, lv.L.get(), lv.A.get(), lv.V.get(), s);
         if (a_min > 0.0) geom_neglect_faces(lv.g, a_min, lv.L.get(), lv.A.get(), s);
         Sync::stream(s);
     }, out);

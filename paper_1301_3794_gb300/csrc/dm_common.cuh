@@ -276,7 +276,9 @@ template <typename T> __device__ __forceinline__ T to_store(float v) { return fr
 // ---------------------------------------------------------------------------
 
 // geometry (dm_geometry.cu)
-void geom_fractions(const Grid3& g, const double* phi_pad, double* L, double* A, double* V, cudaStream_t s);
+// pmc_walls: bit 2a + s set for a magnetic symmetry plane on the wall of axis a, side s
+void geom_fractions(const Grid3& g, const double* phi_pad, int pmc_walls, double* L, double* A, double* V,
+                    cudaStream_t s);
 void geom_neglect_faces(const Grid3& g, double a_min, double* L, double* A, cudaStream_t s);
 void geom_coarsen(const Grid3& gf, const Grid3& gc, const double* Lf, const double* Af, const double* Vf,
                   double* Lc, double* Ac, double* Vc, cudaStream_t s);

@@ -153,7 +153,24 @@ __global__ void k_components(Grid3 g, const double* __restrict__ A, const int* _
         if (!changed) break;
         __syncthreads();
     }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) pinned[r] = label[r] == r ? 1 : 0;
+    // components with an open face on the outer wall (a magnetic symmetry
+    // plane) are regular: the potential beyond the wall is zero.  pinned[]
+    // first marks their roots, then takes the final flags.
+    for (int r = threadIdx.x; r < n; r += blockDim.x) pinned[r] = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const int p = list[r];
+        const int i = (p - g.off0) % g.sx, j = ((p - g.off0) / g.sx) % g.sy, k = (p - g.off0) / g.sxy;
+        const bool wall = (i == 0 && A[p] > 0.0) || (i == g.nx - 1 && A[p + X] > 0.0) ||
+                          (j == 0 && A[N + p] > 0.0) || (j == g.ny - 1 && A[N + p + Y] > 0.0) ||
+                          (k == 0 && A[2 * N + p] > 0.0) || (k == g.nz - 1 && A[2 * N + p + Z] > 0.0);
+        if (wall) pinned[label[r]] = 2;   // benign race: every writer stores the same value
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const bool root = label[r] == r;
+        pinned[r] = (root && pinned[r] != 2) ? 1 : 0;
+    }
 }
 
 }  // namespace

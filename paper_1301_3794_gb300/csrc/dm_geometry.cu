@@ -70,7 +70,16 @@ __device__ __forceinline__ double quad_frac(double c00, double c10, double c01, 
     return 0.5 * (tri_frac(c00, c10, c11) + tri_frac(c00, c01, c11));
 }
 
-__global__ void k_fractions(Grid3 g, const double* __restrict__ phi, double* __restrict__ L,
+// Walls: bit 2a + s of `pmc` set when the wall of axis a (0 x, 1 y, 2 z) on
+// side s (0 low, 1 high) is a magnetic symmetry plane, which lies half a cell
+// outside the wall's node plane; its normal faces and tangential edges then
+// keep their fractions.  Every other wall is a perfect conductor on the node
+// plane and closes them.
+__device__ __forceinline__ bool closed_on(int pmc, int axis, int idx, int n) {
+    return (idx == 0 && !((pmc >> (2 * axis)) & 1)) || (idx == n && !((pmc >> (2 * axis + 1)) & 1));
+}
+
+__global__ void k_fractions(Grid3 g, const double* __restrict__ phi, int pmc, double* __restrict__ L,
                             double* __restrict__ A, double* __restrict__ V) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
@@ -79,32 +88,15 @@ __global__ void k_fractions(Grid3 g, const double* __restrict__ phi, double* __r
     const int p = g.idx(i, j, k);
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
     const double c000 = phi[p];
-    // edges
-    if (i < g.nx) {
-        const bool wall = (j == 0 || j == g.ny || k == 0 || k == g.nz);
-        L[p] = wall ? 0.0 : seg_frac(c000, phi[p + X]);
-    }
-    if (j < g.ny) {
-        const bool wall = (i == 0 || i == g.nx || k == 0 || k == g.nz);
-        L[N + p] = wall ? 0.0 : seg_frac(c000, phi[p + Y]);
-    }
-    if (k < g.nz) {
-        const bool wall = (i == 0 || i == g.nx || j == 0 || j == g.ny);
-        L[2 * N + p] = wall ? 0.0 : seg_frac(c000, phi[p + Z]);
-    }
-    // faces (corner order: first in-plane axis, then second)
-    if (j < g.ny && k < g.nz) {
-        const bool wall = (i == 0 || i == g.nx);
-        A[p] = wall ? 0.0 : quad_frac(c000, phi[p + Y], phi[p + Z], phi[p + Y + Z]);
-    }
-    if (i < g.nx && k < g.nz) {
-        const bool wall = (j == 0 || j == g.ny);
-        A[N + p] = wall ? 0.0 : quad_frac(c000, phi[p + X], phi[p + Z], phi[p + X + Z]);
-    }
-    if (i < g.nx && j < g.ny) {
-        const bool wall = (k == 0 || k == g.nz);
-        A[2 * N + p] = wall ? 0.0 : quad_frac(c000, phi[p + X], phi[p + Y], phi[p + X + Y]);
-    }
+    const bool wx = closed_on(pmc, 0, i, g.nx), wy = closed_on(pmc, 1, j, g.ny), wz = closed_on(pmc, 2, k, g.nz);
+    // edges (closed on conductor walls they are tangential to)
+    if (i < g.nx) L[p] = (wy || wz) ? 0.0 : seg_frac(c000, phi[p + X]);
+    if (j < g.ny) L[N + p] = (wx || wz) ? 0.0 : seg_frac(c000, phi[p + Y]);
+    if (k < g.nz) L[2 * N + p] = (wx || wy) ? 0.0 : seg_frac(c000, phi[p + Z]);
+    // faces (corner order: first in-plane axis, then second; closed on conductor walls they are normal to)
+    if (j < g.ny && k < g.nz) A[p] = wx ? 0.0 : quad_frac(c000, phi[p + Y], phi[p + Z], phi[p + Y + Z]);
+    if (i < g.nx && k < g.nz) A[N + p] = wy ? 0.0 : quad_frac(c000, phi[p + X], phi[p + Z], phi[p + X + Z]);
+    if (i < g.nx && j < g.ny) A[2 * N + p] = wz ? 0.0 : quad_frac(c000, phi[p + X], phi[p + Y], phi[p + X + Y]);
     // cell: the 6 Kuhn tetrahedra (0,0,0) -> e_a -> e_a + e_b -> (1,1,1), summed in
     // the order of the permutations (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x)
     if (i < g.nx && j < g.ny && k < g.nz) {
@@ -411,8 +403,9 @@ long long natural_edges(const Grid3& g) {
 }
 long long natural_cells(const Grid3& g) { return (long long)g.nx * g.ny * g.nz; }
 
-void geom_fractions(const Grid3& g, const double* phi_pad, double* L, double* A, double* V, cudaStream_t s) {
-    launch("k_fractions", k_fractions, node_grid(g), kBlock, 0, s, g, phi_pad, L, A, V);
+void geom_fractions(const Grid3& g, const double* phi_pad, int pmc_walls, double* L, double* A, double* V,
+                    cudaStream_t s) {
+    launch("k_fractions", k_fractions, node_grid(g), kBlock, 0, s, g, phi_pad, pmc_walls, L, A, V);
 }
 
 void geom_neglect_faces(const Grid3& g, double a_min, double* L, double* A, cudaStream_t s) {

@@ -78,6 +78,10 @@ class Workload:
     nev: int
     seed: int
     meta: dict = dataclasses.field(default_factory=dict)
+    # outer-wall kinds (x-low, x-high, y-low, y-high, z-low, z-high): "pec" is
+    # a perfect conductor on the wall's node plane, "pmc" a magnetic symmetry
+    # plane half a cell outside it
+    walls: tuple = ("pec",) * 6
 
 
 def node_coords(g: Grid):
@@ -209,6 +213,40 @@ def octant_sphere_workload(n=16, radius=1.0, extent=1.1, sigma=20.0, nev=1):
     g = Grid(n, n, n, h, h, h, (0.0, 0.0, 0.0))
     return Workload(f"octant{n}", g, sphere_phi(g, (0.0, 0.0, 0.0), radius), sigma, nev, -1,
                     {"center": (0.0, 0.0, 0.0), "radius": radius})
+
+
+def quarter_nine_cell_workload(nq=48, nz=1152, seed=None, sigma=None, nev=9, n_cavities=1, gap_cells=4,
+                               cell_length=0.1154, r_equator=0.1033, r_iris=0.035):
+    """The quarter x >= 0, y >= 0 of the synthetic 9-cell cavity with magnetic
+    symmetry planes x = 0 and y = 0 (Sec. 6.3: the TM010-like accelerating
+    modes are then the lowest ones).  The grid has nq cells of the full
+    cavity's 2 nq-cell spacing across x and y, its first node planes half a
+    cell from the symmetry planes (origin (h/2, h/2, z0)).  ``n_cavities`` > 1
+    strings that many cavities end to end along z, beam pipes of
+    ``gap_cells`` cell lengths between them (the cryomodule of Sec. 6.3);
+    nz is then the cell count of the whole string."""
+    hw = 1.065 * r_equator
+    h = 2 * hw / (2 * nq)
+    period = (9 + gap_cells) * cell_length
+    z0 = -2.0 * cell_length
+    z1 = (n_cavities - 1) * period + 11.0 * cell_length
+    g = Grid(nq, nq, nz, h, h, (z1 - z0) / nz, (0.5 * h, 0.5 * h, z0))
+    scale = None
+    if seed is not None:
+        scale = 1.0 + 0.01 * np.random.default_rng(seed).standard_normal(9)
+    X, Y, Z = node_coords(g)
+    r = np.full(Z.shape, float(r_iris))
+    for c in range(n_cavities):
+        rc = nine_cell_profile(Z - c * period, cell_length, r_equator, r_iris, equator_scale=scale)
+        r = np.maximum(r, rc)
+    phi = np.sqrt(X ** 2 + Y ** 2) - r
+    if sigma is None:
+        sigma = 0.25 * (math.pi / (z1 - z0)) ** 2
+    name = f"quarter_ninecell{nq}x{nq}x{nz}" + (f"_string{n_cavities}" if n_cavities > 1 else "")
+    return Workload(name, g, phi, sigma, nev, -1 if seed is None else seed,
+                    {"cell_length": cell_length, "r_equator": r_equator, "r_iris": r_iris,
+                     "n_cavities": n_cavities, "symmetry_planes": "x = 0 and y = 0, magnetic"},
+                    walls=("pmc", "pec", "pmc", "pec", "pec", "pec"))
 
 
 def box_workload(nx=12, ny=10, nz=8, lx=1.0, ly=0.8, lz=0.6, sigma=7.0, nev=4):
