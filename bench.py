@@ -411,6 +411,8 @@ def run_native(args):
                    "k2": [round(float(v), 10) for v in k2],
                    "inner_rate": None, "stencil_shapes": shapes, "open_faces": int(open_faces),
                    "per_step_s": [round(v, 3) for v in main["per_step_s"]],
+                   "setup_s": round(reps[-1].get("setup_seconds", 0.0), 3),
+                   "solve_s": round(reps[-1].get("solve_seconds", 0.0), 3),
                    # one shifted FGMRES solve (K - sigma A) x = A v per Krylov-Schur step
                    "solves_per_s": round(sum(r["outer_iters"] for r in reps) * world / max_s, 3)},
         "plain_f64": plain,

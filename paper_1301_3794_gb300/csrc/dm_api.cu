@@ -257,7 +257,7 @@ struct OpLevel {
     DBuf<int> stiles;         // active tiles of that shape (shape != 0)
     int nstiles = 0;
     // subdomains of the band smoother (see dm_band.cu) and their rows' slot coefficients
-    DBuf<int> sd_off, sd_copy, sd_pos, sd_dims;
+    DBuf<int> sd_off, sd_copy, sd_pos, sd_dims, sd_org;
     DBuf<double> sd_v64;
     DBuf<float> sd_v32;
     int sd_nsub = 0, sd_ncopies = 0, sd_maxrows = 0, sd_maxbox = 0;
@@ -348,6 +348,7 @@ BandSchwarz<TC> schwarz_view(const OpLevel& o, const TC* vals) {
     b.off = o.sd_off.get();
     b.copy = o.sd_copy.get();
     b.pos = o.sd_pos.get();
+    b.org = o.sd_org.get();
     b.dims = o.sd_dims.get();
     b.vals = vals;
     b.nsub = o.sd_nsub;
@@ -1101,6 +1102,7 @@ void setup_operator(dm_operator* op) {
             upload(o.sd_off, sl.off);
             upload(o.sd_copy, sl.copy);
             upload(o.sd_pos, sl.pos);
+            upload(o.sd_org, sl.org);
             upload(o.sd_dims, sl.dims);
             const size_t nb = (size_t)g.nband, nv = (size_t)kBandSlots * o.sd_ncopies;
             DBuf<double> rows(kBandSlots * nb, false);

@@ -92,10 +92,10 @@ __device__ __forceinline__ C row_dot_fixed(int c, const C* v, const C* d, int p)
 template <typename T, typename TC, int R, int NT, bool FIXED>
 __global__ void __launch_bounds__(NT)
     k_band_schwarz(int sub0, const int* __restrict__ off, const int* __restrict__ copy, const int* __restrict__ pos,
-                   const int* __restrict__ dims, const TC* __restrict__ vals, int ncopies,
+                   const int* __restrict__ dims, const int* __restrict__ org, const TC* __restrict__ vals, int ncopies,
                    const int* __restrict__ band, const TC* __restrict__ invD, const T* __restrict__ f,
-                   const T* __restrict__ x, double* __restrict__ u, typename Compute<T>::type om, int sweeps, int np,
-                   int sx, int sxy, int maxbox, int maxrows) {
+                   const T* __restrict__ x, double* __restrict__ u, typename Compute<T>::type om, int sweeps, Grid3 g,
+                   int maxbox, int maxrows) {
     using C = typename Compute<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* const buf0 = reinterpret_cast<C*>(smem_raw);
@@ -108,9 +108,21 @@ __global__ void __launch_bounds__(NT)
     const int dm = dims[sd];
     const int lx = FIXED ? kFX : dm & 1023, ly = FIXED ? kFY : (dm >> 10) & 1023, lz = FIXED ? kFZ : dm >> 20;
     const int lxy = lx * ly, l3 = lxy * lz;
-    for (int k = threadIdx.x; k < 3 * l3; k += blockDim.x) {
-        buf0[k] = C(0);
-        buf1[k] = C(0);
+    // x over the local box (nodes org + local coordinates; outside the padded
+    // grid's -1 .. n+1 it is zero), so that the start residuals read it from
+    // shared memory at the rows' slot offsets: one coalesced pass over the box
+    // instead of 15 scattered loads per row
+    {
+        const int ox = org[3 * sd], oy = org[3 * sd + 1], oz = org[3 * sd + 2];
+        for (int k = threadIdx.x; k < 3 * l3; k += blockDim.x) {
+            const int comp = k / l3, n = k - comp * l3;
+            const int lk = n / lxy, rem = n - lk * lxy;
+            const int lj = rem / lx, li = rem - lj * lx;
+            const int i = ox + li, j = oy + lj, kk = oz + lk;
+            const bool in = i >= -1 && j >= -1 && kk >= -1 && i <= g.nx + 1 && j <= g.ny + 1 && kk <= g.nz + 1;
+            buf0[k] = C(0);
+            buf1[k] = in ? (C)to_c(x[(size_t)comp * g.np + g.idx(i, j, kk)]) : C(0);
+        }
     }
     __syncthreads();
     constexpr int RR = R > 0 ? R : 1;
@@ -121,32 +133,43 @@ __global__ void __launch_bounds__(NT)
     // residual of the full row at the start values, and the first sweep from d = 0
     auto start_row = [&](int r, C* ve, C& rr, C& ww) {
         const int ct = copy[b0 + r];
+        if (ct == kDummyCopy) {   // an empty lane of a warp group: no row, no loads
+#pragma unroll
+            for (int e = 0; e < kBandSlots; ++e) ve[e] = C(0);
+            rr = C(0);
+            ww = C(0);
+            return;
+        }
         const int t = ct >= 0 ? ct : -1 - ct;
         const int q = band[t];
-        const int c = q / np;
-        C acc = C(0);
+        const int ps = pos[b0 + r];
 #pragma unroll
-        for (int e = 0; e < kBandSlots; ++e) {
-            ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
-            acc += ve[e] * (C)to_c(x[q + band_slot_offset(c, e, np, sx, sxy)]);
-        }
+        for (int e = 0; e < kBandSlots; ++e) ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
+        const C acc = FIXED ? row_dot_fixed(ps / l3, ve, buf1, ps) : row_dot(ve, buf1, row_addr(ps, l3, lx, lxy), lx, lxy);
         rr = (C)to_c(f[q]) - acc;
         ww = om * (C)invD[q];
-        buf0[pos[b0 + r]] = ww * rr;
+        buf0[ps] = ww * rr;
     };
     if constexpr (R > 0) {
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const int r = threadIdx.x + k * blockDim.x;
+            cm[k] = -1;
             if (r < nr) {
                 start_row(r, v[k], r0[k], w[k]);
-                ad[k] = row_addr(pos[b0 + r], l3, lx, lxy);
-                cm[k] = pos[b0 + r] / l3;
+                const int ps = pos[b0 + r];
+                if (ps >= 0) {
+                    ad[k] = row_addr(ps, l3, lx, lxy);
+                    cm[k] = ps / l3;
+                }
             }
         }
     } else {
         for (int r = threadIdx.x; r < nr; r += blockDim.x) start_row(r, v[0], s_r0[r], s_w[r]);
     }
+    __syncthreads();
+    // buf1 becomes the second correction buffer: zero outside the rows
+    for (int k = threadIdx.x; k < 3 * l3; k += blockDim.x) buf1[k] = C(0);
     __syncthreads();
     C* dc = buf0;
     C* dn = buf1;
@@ -155,14 +178,16 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int k = 0; k < RR; ++k) {
                 const int r = threadIdx.x + k * blockDim.x;
-                if (r < nr) {
+                if (r < nr && cm[k] >= 0) {
                     const C acc = FIXED ? row_dot_fixed(cm[k], v[k], dc, ad[k].b0) : row_dot(v[k], dc, ad[k], lx, lxy);
                     dn[ad[k].b0] = dc[ad[k].b0] + w[k] * (r0[k] - acc);
                 }
             }
         } else {
             for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-                const RowAddr a = row_addr(pos[b0 + r], l3, lx, lxy);
+                const int ps = pos[b0 + r];
+                if (ps < 0) continue;
+                const RowAddr a = row_addr(ps, l3, lx, lxy);
                 C ve[kBandSlots];
 #pragma unroll
                 for (int e = 0; e < kBandSlots; ++e) ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
@@ -195,6 +220,10 @@ __global__ void k_band_copy_vals(const int* __restrict__ copy, int ncopies, cons
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncopies) return;
     const int ct = copy[c];
+    if (ct == kDummyCopy) {
+        for (int e = 0; e < kBandSlots; ++e) out[(size_t)e * ncopies + c] = 0.0;
+        return;
+    }
     const int t = ct >= 0 ? ct : -1 - ct;
     for (int e = 0; e < kBandSlots; ++e) out[(size_t)e * ncopies + c] = band_vals[(size_t)e * nband + t];
 }
@@ -283,18 +312,39 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         runs.push_back({c0, c1});
         c0 = c1;
     }
-    std::stable_sort(runs.begin(), runs.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
-        return schwarz_class(a.second - a.first) < schwarz_class(b.second - b.first);
+    // slots of a run: its rows per component rounded up to whole warp groups
+    auto slots_of = [&](const std::pair<int, int>& r) {
+        int n[3] = {0, 0, 0};
+        for (int c = r.first; c < r.second; ++c) ++n[cp[c].q / g.np];
+        return 32 * ((n[0] + 31) / 32 + (n[1] + 31) / 32 + (n[2] + 31) / 32);
+    };
+    std::vector<int> run_slots;
+    run_slots.reserve(runs.size());
+    for (const auto& r : runs) run_slots.push_back(slots_of(r));
+    std::vector<int> order(runs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return schwarz_class(run_slots[a]) < schwarz_class(run_slots[b]);
     });
+    {
+        std::vector<std::pair<int, int>> sorted;
+        sorted.reserve(runs.size());
+        for (int i : order) sorted.push_back(runs[i]);
+        runs.swap(sorted);
+        std::vector<int> rs;
+        rs.reserve(order.size());
+        for (int i : order) rs.push_back(run_slots[i]);
+        run_slots.swap(rs);
+    }
     for (int k = 0; k < kSchwarzClasses; ++k) {
         out.cls_first[k] = out.cls_count[k] = 0;
         out.cls_copies[k] = out.cls_owned[k] = 0;
     }
-    out.copy.reserve(nc);
-    out.pos.reserve(nc);
+    out.copy.reserve((size_t)nc + 96 * runs.size());
+    out.pos.reserve((size_t)nc + 96 * runs.size());
     for (size_t rI = 0; rI < runs.size(); ++rI) {
         const int c0 = runs[rI].first, c1 = runs[rI].second;
-        const int cl = schwarz_class(c1 - c0);
+        const int cl = schwarz_class(run_slots[rI]);
         if (out.cls_count[cl] == 0) out.cls_first[cl] = (int)rI;
         ++out.cls_count[cl];
         const long long kb = cp[c0].brick;
@@ -315,19 +365,43 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         DM_REQUIRE(l[0] < 1024 && l[1] < 1024 && l[2] < 1024, DM_ERR_INVALID_ARG, "band brick too large");
         out.off.push_back((int)out.copy.size());
         out.dims.push_back(l[0] | (l[1] << 10) | (l[2] << 20));
-        out.maxrows = std::max(out.maxrows, c1 - c0);
+        out.org.insert(out.org.end(), {lo[0], lo[1], lo[2]});
         out.maxbox = std::max(out.maxbox, 3 * l[0] * l[1] * l[2]);
         out.cls_copies[cl] += c1 - c0;
+        // Rows are laid out in warp groups of 32 slots.  Per component, the rows
+        // are sorted by their shared-memory bank (box position mod 32) and dealt
+        // round-robin over the component's ceil(n / 32) groups, so the lanes of
+        // a warp mostly sit in distinct banks; every slot offset is the same for
+        // the rows of one component, so each of the 15 loads of a sweep is then
+        // (nearly) free of bank conflicts.  Unfilled slots are empty lanes.
+        std::vector<std::pair<int, int>> rows[3];   // (position, copy code) per component
         for (int c = c0; c < c1; ++c) {
             const int t = cp[c].t;
             const int comp = cp[c].q / g.np;
             if (cp[c].owned) ++out.cls_owned[cl];
             const int li = node[3 * t] - lo[0], lj = node[3 * t + 1] - lo[1], lk = node[3 * t + 2] - lo[2];
-            out.copy.push_back(cp[c].owned ? t : -1 - t);
-            out.pos.push_back(((comp * l[2] + lk) * l[1] + lj) * l[0] + li);
+            rows[comp].push_back({((comp * l[2] + lk) * l[1] + lj) * l[0] + li, cp[c].owned ? t : -1 - t});
         }
+        for (int comp = 0; comp < 3; ++comp) {
+            std::vector<std::pair<int, int>>& rc = rows[comp];
+            const int n = (int)rc.size();
+            if (n == 0) continue;
+            std::stable_sort(rc.begin(), rc.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+                return (a.first & 31) < (b.first & 31);
+            });
+            const int ng = (n + 31) / 32;
+            const size_t base = out.copy.size();
+            out.copy.resize(base + 32 * (size_t)ng, kDummyCopy);
+            out.pos.resize(base + 32 * (size_t)ng, -1);
+            for (int i = 0; i < n; ++i) {
+                const size_t slot = base + (size_t)(i % ng) * 32 + i / ng;
+                out.pos[slot] = rc[i].first;
+                out.copy[slot] = rc[i].second;
+            }
+        }
+        out.maxrows = std::max(out.maxrows, (int)out.copy.size() - out.off.back());
     }
-    out.off.push_back(nc);
+    out.off.push_back((int)out.copy.size());
     out.fixed = brick == kFixedBrick;
 }
 
@@ -394,12 +468,12 @@ void band_schwarz(const BandSchwarz<TC>& bs, const TC* invD, const Grid3& g, con
 #define DM_SCHWARZ(RV, NV)                                                                                         \
     if (bs.fixed)                                                                                                  \
         launch_b(name, bytes, k_band_schwarz<T, TC, RV, NV, true>, count, NV, smem, s, first, bs.off, bs.copy,     \
-                 bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx,   \
-                 g.sxy, bs.maxbox, bs.maxrows);                                                                  \
+                 bs.pos, bs.dims, bs.org, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g,    \
+                 bs.maxbox, bs.maxrows);                                                                         \
     else                                                                                                           \
     launch_b(name, bytes, k_band_schwarz<T, TC, RV, NV, false>, count, NV, smem, s, first, bs.off, bs.copy,      \
-             bs.pos, bs.dims, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g.np, g.sx,      \
-             g.sxy, bs.maxbox, bs.maxrows)
+             bs.pos, bs.dims, bs.org, bs.vals, bs.ncopies, band, invD, f, (const T*)x, u, omega, sweeps, g,       \
+             bs.maxbox, bs.maxrows)
         if (nt == 256) DM_SCHWARZ(1, 256);
         else if (R == 1) DM_SCHWARZ(1, 512);
         else if (R == 2) DM_SCHWARZ(2, 512);

@@ -252,6 +252,23 @@ __device__ __forceinline__ float2 ff_norm(float s, float e) {
     return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 __device__ __forceinline__ double ff_to_double(float2 v) { return (double)v.x + (double)v.y; }
+// Sum over a warp of float-float values s + e (Knuth's two-sum on the high
+// parts, the low parts and both errors added, then Fast2Sum), on the FP32
+// pipes; the result is complete in every lane.  Summing in FP64 instead costs
+// a conversion, five shuffles and five FP64 adds per lane, which on GB300's
+// FP64 rate outweighs the FP32 streaming work of a short grid-stride loop.
+__device__ __forceinline__ double ff_warp_sum(float s, float e) {
+    float2 v = ff_norm(s, e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.x, o), ol = __shfl_xor_sync(0xffffffffu, v.y, o);
+        const float t = __fadd_rn(v.x, oh);
+        const float bp = __fsub_rn(t, v.x);
+        const float err = __fadd_rn(__fsub_rn(v.x, __fsub_rn(t, bp)), __fsub_rn(oh, bp));
+        v = ff_norm(t, __fadd_rn(err, __fadd_rn(v.y, ol)));
+    }
+    return ff_to_double(v);
+}
 
 // One pass of delayed classical Gram-Schmidt (DCGS2): against the finished
 // basis Q (j vectors) and the pending vector v, with the new vector w:
@@ -294,8 +311,8 @@ __device__ __forceinline__ void dcgs_chunk(long long n2, int j, int c0, const fl
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const double t1 = warp_sum((double)ss[c] + (double)se[c]);
-            const double t2 = warp_sum((double)cs[c] + (double)ce[c]);
+            const double t1 = ff_warp_sum(ss[c], se[c]);
+            const double t2 = ff_warp_sum(cs[c], ce[c]);
             if (lane == 0) {
                 red[wid][c] = t1;
                 red[wid][8 + c] = t2;
@@ -335,8 +352,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_ff_dcgs_dots(long long n2, int 
             default: dcgs_chunk<8>(n2, j, c0, Q, ld2, v, w, first, as, ae, ds, de, partial, ldp);
         }
     }
-    const double ta = warp_sum((double)as + (double)ae);
-    const double td = warp_sum((double)ds + (double)de);
+    const double ta = ff_warp_sum(as, ae);
+    const double td = ff_warp_sum(ds, de);
     if (lane == 0) {
         red2[wid][0] = ta;
         red2[wid][1] = td;
@@ -394,7 +411,7 @@ __global__ void k_ff_dcgs_update(long long n2, int j, const float4* __restrict__
         ff_madd(o0.x, o0.y, o0.x, o0.y, ns, ne);
         ff_madd(o1.x, o1.y, o1.x, o1.y, ns, ne);
     }
-    const double t = warp_sum((double)ns + (double)ne);
+    const double t = ff_warp_sum(ns, ne);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -361,6 +361,8 @@ void vec_jacobi_zero(const VecOp<T, TC>& op, const T* f, T* y, double omega, cud
 // component (c+2)%3, each at offset -1 or 0 along axis c and 0 or +1 along the
 // column's own axis.
 constexpr int kBandSlots = 15;
+// copy code of an empty lane in the band smoother's warp groups
+constexpr int kDummyCopy = -2147483647 - 1;
 __host__ __device__ inline void band_slot(int c, int e, int& cc, int o[3]) {
     o[0] = o[1] = o[2] = 0;
     if (e < 7) {
@@ -393,6 +395,7 @@ constexpr int kSchwarzClasses = 5;
 int schwarz_class(int rows);
 struct SchwarzLayout {
     std::vector<int> off, copy, pos, dims;
+    std::vector<int> org;         // 3 per subdomain: node coordinates of its local box's first node
     int maxrows = 0, maxbox = 0;
     bool fixed = false;           // every subdomain uses the fixed box of the default brick
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
@@ -404,6 +407,7 @@ struct BandSchwarz {
     const int* copy = nullptr;
     const int* pos = nullptr;
     const int* dims = nullptr;
+    const int* org = nullptr;
     const TC* vals = nullptr;     // [15][ncopies] slot coefficients of each copy's row
     int nsub = 0, ncopies = 0, maxrows = 0, maxbox = 0;
     int cls_first[kSchwarzClasses] = {}, cls_count[kSchwarzClasses] = {};
