@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--bf16-steps", type=int, default=3, help="timed steps of the BF16 V-cycle arm (0: skip)")
     ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
     ap.add_argument("--inner-restart", type=int, default=40, help="FGMRES restart length of the shifted solves")
+    ap.add_argument("--band-sweeps", type=int, default=None,
+                    help="Jacobi sweeps of the band smoother on the fine level (library default 16)")
+    ap.add_argument("--band-sweeps-coarse", type=int, default=None,
+                    help="sweeps of the band smoother below the fine level (library default 8)")
     ap.add_argument("--no-krylov-ff", action="store_true",
                     help="FP64 operator applies inside the shifted solves' FGMRES iterations (instead of float-float)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,6 +94,8 @@ def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
          "inner_restart": args.inner_restart, "krylov_apply": "f64" if args.no_krylov_ff else "float-float",
+         "band_sweeps": [16 if args.band_sweeps is None else args.band_sweeps,
+                         8 if args.band_sweeps_coarse is None else args.band_sweeps_coarse],
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:
@@ -282,6 +288,12 @@ def run_native(args):
     nf = dm.face_count(g.nx, g.ny, g.nz)
     B_dev = torch.empty((args.nev, nf), dtype=torch.float64, device=f"cuda:{local}")
 
+    sweep_kw = {}
+    if args.band_sweeps is not None:
+        sweep_kw["band_sweeps"] = args.band_sweeps
+    if args.band_sweeps_coarse is not None:
+        sweep_kw["band_sweeps_coarse"] = args.band_sweeps_coarse
+
     def step(precision, host_io=False):
         phi = phi_host if host_io else phi_dev
         geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi, g.origin)
@@ -289,7 +301,8 @@ def run_native(args):
         k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
                                        out=None if host_io else B_dev, precision=precision,
                                        inner_tol=args.inner_tol, inner_restart=args.inner_restart,
-                                       krylov_ff=0 if (args.no_krylov_ff or precision == "f64") else 1)
+                                       krylov_ff=0 if (args.no_krylov_ff or precision == "f64") else 1,
+                                       **sweep_kw)
         geom.close()
         return k2, rep, st
 

@@ -388,6 +388,9 @@ typedef struct dm_batch_item {
  * so the kernels of small cavities overlap on the GPU.  Each item's result is
  * the same as dm_eigensolve on it.  Returns DM_OK when every item returned
  * DM_OK, else the first non-OK item status (all items are still attempted).
+ * Before the workers start, the stencil tile shapes of every distinct grid not
+ * yet in the context's autotuner cache are timed on the calling stream with
+ * the GPU otherwise idle (an operator setup per such grid).
  * Geometries must not be destroyed or shared with other calls meanwhile. */
 dm_status dm_eigensolve_batched(dm_context* ctx, int n, dm_batch_item* items, int streams);
 

@@ -2585,6 +2585,28 @@ dm_status dm_eigensolve_batched(dm_context* ctx, int n, dm_batch_item* items, in
         return (double)natural_faces(g->lv[0]->g) * std::max(1, items[i].params.nev);
     };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    // Stencil tile shapes are tuned here, before the workers start: one
+    // operator per distinct fine grid and precision on the calling context, so
+    // that the autotuner times its candidates with the GPU otherwise idle; the
+    // workers then find every shape in the cache.
+    {
+        std::vector<std::array<int, 4>> seen;
+        for (int i = 0; i < n; ++i) {
+            const dm_batch_item& it = items[order[i]];
+            if (!it.geom || it.geom->lv.empty() || !it.params.mg.autotune || it.params.mg.stencil_shape >= 0)
+                continue;
+            const Grid3& g0 = it.geom->lv[0]->g;
+            const std::array<int, 4> key{g0.nx, g0.ny, g0.nz, it.params.mg.precision};
+            if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+            seen.push_back(key);
+            bool cached = false;
+            for (const auto& kv : ctx->tuned) cached |= kv.first == key;
+            if (cached) continue;
+            dm_operator* op = nullptr;
+            if (dm_operator_create(ctx, it.geom, it.params.sigma, &it.params.mg, &op) == DM_OK) dm_operator_destroy(op);
+        }
+        ctx->err.clear();
+    }
     const int nw = std::min(streams, n);
     std::vector<dm_context*> sub(nw, nullptr);
     for (int w = 0; w < nw; ++w) {
