@@ -340,6 +340,10 @@ struct dm_operator {
 namespace {
 
 const GeoLevel& glv(const dm_operator* op, int l) { return *op->geom->lv[l]; }
+// Side streams of the band smoother's class launches; none while a trace is
+// recording, so that each traced launch is timed alone (as a profiler's
+// serialised launch list times it) rather than overlapped with its siblings.
+const Fork* fork_of(const dm_operator* op) { return (g_tracer && g_tracer->on) ? nullptr : &op->fork; }
 size_t tsize(int prec) { return prec == DM_PREC_F64 ? 8 : (prec == DM_PREC_F32 ? 4 : 2); }
 
 template <typename TC>
@@ -419,7 +423,7 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const int sweeps = band_sweeps_of(op, l);
     vec_jacobi_zero(o, f, ebuf, om, s);
     band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om, sweeps, l == 0,
-                        s, &op->fork);
+                        s, fork_of(op));
     vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
@@ -433,7 +437,7 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), ec, ebuf, g.tiles.get(), g.ntiles, s, sym);
     vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
     band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om, sweeps, l == 0,
-                        s, &op->fork);
+                        s, fork_of(op));
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------

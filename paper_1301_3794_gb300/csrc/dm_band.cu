@@ -48,9 +48,10 @@ __device__ __forceinline__ RowAddr row_addr(int p, int l3, int lx, int lxy) {
     a.b2 = c2 * l3 + n - a.sc;
     return a;
 }
+// `self` is the row's own entry d[a.b0] (kept in a register by the sweeps)
 template <typename C>
-__device__ __forceinline__ C row_dot(const C* v, const C* d, const RowAddr& a, int lx, int lxy) {
-    C acc = v[0] * d[a.b0];
+__device__ __forceinline__ C row_dot(const C* v, C self, const C* d, const RowAddr& a, int lx, int lxy) {
+    C acc = v[0] * self;
     acc += v[1] * d[a.b0 - 1] + v[2] * d[a.b0 + 1];
     acc += v[3] * d[a.b0 - lx] + v[4] * d[a.b0 + lx];
     acc += v[5] * d[a.b0 - lxy] + v[6] * d[a.b0 + lxy];
@@ -65,14 +66,14 @@ __device__ __forceinline__ C row_dot(const C* v, const C* d, const RowAddr& a, i
 constexpr int kFixedBrick = 8, kFX = 13, kFY = 12, kFZ = 12, kFXY = kFX * kFY, kF3 = kFXY * kFZ;
 
 template <typename C, int c>
-__device__ __forceinline__ C row_dot_fixed(const C* v, const C* d, int p) {
+__device__ __forceinline__ C row_dot_fixed(const C* v, C self, const C* d, int p) {
     constexpr int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
     constexpr int sc = c == 0 ? 1 : (c == 1 ? kFX : kFXY);
     constexpr int s1 = c1 == 0 ? 1 : (c1 == 1 ? kFX : kFXY);
     constexpr int s2 = c2 == 0 ? 1 : (c2 == 1 ? kFX : kFXY);
     constexpr int o1 = (c1 - c) * kF3 - sc, o2 = (c2 - c) * kF3 - sc;
     const C* q = d + p;
-    C acc = v[0] * q[0];
+    C acc = v[0] * self;
     acc += v[1] * q[-1] + v[2] * q[1];
     acc += v[3] * q[-kFX] + v[4] * q[kFX];
     acc += v[5] * q[-kFXY] + v[6] * q[kFXY];
@@ -81,8 +82,9 @@ __device__ __forceinline__ C row_dot_fixed(const C* v, const C* d, int p) {
     return acc;
 }
 template <typename C>
-__device__ __forceinline__ C row_dot_fixed(int c, const C* v, const C* d, int p) {
-    return c == 0 ? row_dot_fixed<C, 0>(v, d, p) : (c == 1 ? row_dot_fixed<C, 1>(v, d, p) : row_dot_fixed<C, 2>(v, d, p));
+__device__ __forceinline__ C row_dot_fixed(int c, const C* v, C self, const C* d, int p) {
+    return c == 0 ? row_dot_fixed<C, 0>(v, self, d, p)
+                  : (c == 1 ? row_dot_fixed<C, 1>(v, self, d, p) : row_dot_fixed<C, 2>(v, self, d, p));
 }
 
 // R > 0: each thread owns up to R rows (row r = threadIdx.x + k blockDim.x) with
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     constexpr int RR = R > 0 ? R : 1;
     C v[RR][kBandSlots];
-    C r0[RR], w[RR];
+    C r0[RR], w[RR], dself[RR];   // dself: the row's current correction (R > 0)
     RowAddr ad[RR];
     int cm[RR];
     // residual of the full row at the start values, and the first sweep from d = 0
@@ -145,7 +147,8 @@ __global__ void __launch_bounds__(NT)
         const int ps = pos[b0 + r];
 #pragma unroll
         for (int e = 0; e < kBandSlots; ++e) ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
-        const C acc = FIXED ? row_dot_fixed(ps / l3, ve, buf1, ps) : row_dot(ve, buf1, row_addr(ps, l3, lx, lxy), lx, lxy);
+        const C acc = FIXED ? row_dot_fixed(ps / l3, ve, buf1[ps], buf1, ps)
+                            : row_dot(ve, buf1[ps], buf1, row_addr(ps, l3, lx, lxy), lx, lxy);
         rr = (C)to_c(f[q]) - acc;
         ww = om * (C)invD[q];
         buf0[ps] = ww * rr;
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(NT)
             cm[k] = -1;
             if (r < nr) {
                 start_row(r, v[k], r0[k], w[k]);
+                dself[k] = w[k] * r0[k];
                 const int ps = pos[b0 + r];
                 if (ps >= 0) {
                     ad[k] = row_addr(ps, l3, lx, lxy);
@@ -179,8 +183,10 @@ __global__ void __launch_bounds__(NT)
             for (int k = 0; k < RR; ++k) {
                 const int r = threadIdx.x + k * blockDim.x;
                 if (r < nr && cm[k] >= 0) {
-                    const C acc = FIXED ? row_dot_fixed(cm[k], v[k], dc, ad[k].b0) : row_dot(v[k], dc, ad[k], lx, lxy);
-                    dn[ad[k].b0] = dc[ad[k].b0] + w[k] * (r0[k] - acc);
+                    const C acc = FIXED ? row_dot_fixed(cm[k], v[k], dself[k], dc, ad[k].b0)
+                                        : row_dot(v[k], dself[k], dc, ad[k], lx, lxy);
+                    dself[k] = dself[k] + w[k] * (r0[k] - acc);
+                    dn[ad[k].b0] = dself[k];
                 }
             }
         } else {
@@ -191,7 +197,8 @@ __global__ void __launch_bounds__(NT)
                 C ve[kBandSlots];
 #pragma unroll
                 for (int e = 0; e < kBandSlots; ++e) ve[e] = (C)vals[(size_t)e * ncopies + b0 + r];
-                dn[a.b0] = dc[a.b0] + s_w[r] * (s_r0[r] - row_dot(ve, dc, a, lx, lxy));
+                const C self = dc[a.b0];
+                dn[a.b0] = self + s_w[r] * (s_r0[r] - row_dot(ve, self, dc, a, lx, lxy));
             }
         }
         __syncthreads();
