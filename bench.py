@@ -58,9 +58,9 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
     ap.add_argument("--inner-restart", type=int, default=40, help="FGMRES restart length of the shifted solves")
     ap.add_argument("--band-sweeps", type=int, default=None,
-                    help="Jacobi sweeps of the band smoother on the fine level (library default 16)")
+                    help="Jacobi sweeps of the band smoother on the fine level (library default 24)")
     ap.add_argument("--band-sweeps-coarse", type=int, default=None,
-                    help="sweeps of the band smoother below the fine level (library default 8)")
+                    help="sweeps of the band smoother below the fine level (library default 16)")
     ap.add_argument("--no-krylov-ff", action="store_true",
                     help="FP64 operator applies inside the shifted solves' FGMRES iterations (instead of float-float)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -94,8 +94,8 @@ def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
          "inner_restart": args.inner_restart, "krylov_apply": "f64" if args.no_krylov_ff else "float-float",
-         "band_sweeps": [16 if args.band_sweeps is None else args.band_sweeps,
-                         8 if args.band_sweeps_coarse is None else args.band_sweeps_coarse],
+         "band_sweeps": [24 if args.band_sweeps is None else args.band_sweeps,
+                         16 if args.band_sweeps_coarse is None else args.band_sweeps_coarse],
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:

@@ -64,7 +64,7 @@ typedef struct dm_mg_params {
     int max_coarse;        /* halve the grid while every dim is even, >= 4, and max dim > max_coarse (4),
                               and while the level has more than dense_coarse open faces */
     int band_sweeps;       /* Jacobi sweeps of the cut-cell band smoother after each smoothing step on the
-                              fine level (16; the coarser levels take band_sweeps_coarse):
+                              fine level (24; the coarser levels take band_sweeps_coarse):
                               a restricted additive Schwarz step over bricks of band_brick^3 nodes with
                               one node of overlap; each subdomain sweeps on its own faces, couplings to
                               other faces frozen, and the brick keeps the faces it owns */
@@ -79,7 +79,7 @@ typedef struct dm_mg_params {
                               results are cached in the context by level size and precision (1) */
     int stencil_shape;     /* -1: the autotuner's choice (shape 0 when autotune = 0); 0..5: use this
                               tile shape (see dm_operator_stencil_shape) on every level (-1) */
-    int band_sweeps_coarse; /* band_sweeps of the levels below the fine one (8) */
+    int band_sweeps_coarse; /* band_sweeps of the levels below the fine one (16) */
     int symmetric_transform; /* 1: the V-cycle of Eq. fullMat2's symmetric form (Sec. 5.3): every level
                               congruence-scaled by A^-1/2, which for this cycle amounts to the transfers
                               A_c^1/2 R A^-1/2 and A^-1/2 P A_c^1/2 (smoothing and the coarsest solve

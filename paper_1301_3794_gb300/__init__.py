@@ -250,16 +250,18 @@ class Geometry:
             pass
 
 
-def mg_params(max_coarse=4, band_sweeps=16, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
+def mg_params(max_coarse=4, band_sweeps=None, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
               autotune=1, force_shape=-1, band_sweeps_coarse=None, symmetric_transform=0, dense_coarse=None,
               krylov_ff=1):
-    """band_sweeps_coarse: sweeps below the fine level (None: the library's default, 8);
+    """band_sweeps, band_sweeps_coarse: band-smoother sweeps on the fine level and below it
+    (None: the library's defaults, 24 and 16);
     symmetric_transform: 1 for the V-cycle of Eq. fullMat2's symmetric form;
     krylov_ff: 1 to form the shifted solves' FGMRES operator applies in float-float."""
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
-    p.band_sweeps = band_sweeps
+    if band_sweeps is not None:
+        p.band_sweeps = int(band_sweeps)
     p.band_brick = band_brick
     p.omega_scale = omega_scale
     p.power_iters = power_iters

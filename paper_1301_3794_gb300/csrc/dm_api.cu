@@ -1623,14 +1623,14 @@ dm_status dm_geometry_fractions(const dm_geometry* geom, int level, double* L, d
 void dm_mg_params_default(dm_mg_params* p) {
     if (!p) return;
     p->max_coarse = 4;
-    p->band_sweeps = 16;
+    p->band_sweeps = 24;
     p->band_brick = 8;
     p->omega_scale = 1.7;
     p->power_iters = 30;
     p->precision = DM_PREC_F64;
     p->autotune = 1;
     p->stencil_shape = -1;
-    p->band_sweeps_coarse = 8;
+    p->band_sweeps_coarse = 16;
     p->symmetric_transform = 0;
     p->dense_coarse = 2048;
     p->krylov_ff = 1;

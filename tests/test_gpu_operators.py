@@ -20,7 +20,7 @@ CASES = {
 }
 
 
-SWEEPS, COARSE_SWEEPS, BRICK = 16, 8, 8    # band smoother defaults of the library (fine, coarser levels, brick)
+SWEEPS, COARSE_SWEEPS, BRICK = 24, 16, 8    # band smoother defaults of the library (fine, coarser levels, brick)
 
 
 def _rel(a, b):

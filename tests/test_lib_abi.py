@@ -35,11 +35,11 @@ def test_struct_layouts_match_defaults(lib):
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
     assert p.tol == 1e-10 and p.nev == 4 and p.inner_restart == 40 and p.seed == 1301
-    assert p.mg.max_coarse == 4 and p.mg.band_sweeps == 16 and p.mg.band_brick == 8 and p.mg.omega_scale == 1.7
+    assert p.mg.max_coarse == 4 and p.mg.band_sweeps == 24 and p.mg.band_brick == 8 and p.mg.omega_scale == 1.7
     m = MGParams()
     lib.dm_mg_params_default(C.byref(m))
     assert m.power_iters == 30 and m.precision == 0
-    assert m.autotune == 1 and m.stencil_shape == -1 and m.band_sweeps_coarse == 8 and m.symmetric_transform == 0
+    assert m.autotune == 1 and m.stencil_shape == -1 and m.band_sweeps_coarse == 16 and m.symmetric_transform == 0
     assert m.dense_coarse == 2048 and m.krylov_ff == 1
     # the field after the embedded multigrid settings lands where the C struct has it
     assert p.mg.autotune == 1 and p.mg.stencil_shape == -1 and not p.learned
