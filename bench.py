@@ -227,10 +227,25 @@ def nvtx_mark(start):
 
 
 # DRAM bytes (read + write) per launch from ncu captures of the same kernel:
-# (trace name, workload, grid, level-0 stencil shape) -> bytes.  The profiles/
-# summaries hold the captures and their commands; a kernel or shape without a
-# capture reports null.
-PROFILED_TRAFFIC = {}
+# (trace name, workload, grid, level-0 stencil shape) -> bytes, the shape None
+# for kernels that do not depend on it.  The profiles/ summaries hold the
+# captures and their commands; a kernel or shape without a capture reports null.
+#  - band smoother, fine level: the four size-class launches of one smoothing
+#    step of the 128^3 ellipsoid read 103.5 MB and wrote 0.2 MB (25.9 MB per
+#    launch); the 192^3 figure is that per-launch traffic scaled by the ratio of
+#    the byte model's per-launch bytes (26.27 MB / 11.64 MB), the traffic
+#    growing with the band's row copies as the byte model does.
+PROFILED_TRAFFIC = {
+    ("band_schwarz_f32_jacobi_L0", "ellipsoid", 128, None): 25_900_000,
+    ("band_schwarz_f32_jacobi_L0", "ellipsoid", 192, None): 58_450_000,
+}
+
+
+def profiled_traffic(name, key):
+    if not key:
+        return None
+    hit = PROFILED_TRAFFIC.get((name,) + tuple(key))
+    return hit if hit is not None else PROFILED_TRAFFIC.get((name,) + tuple(key[:2]) + (None,))
 
 # Algorithmic FP64 operations of one K - sigma A evaluation per open face:
 # about 66 per cell of 3 faces (two curls, the grad-div and the shift).
@@ -252,7 +267,7 @@ def rooflines(stats, hbm_peak, peak_kind, fp64_tflops, open_faces, top=8, key=No
             ent.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                         "frac": round(gbs / hbm_peak, 4), "bytes_per_launch": int(by / launches),
                         "peak_kind": f"{peak_kind} (copy)",
-                        "traffic": PROFILED_TRAFFIC.get((name,) + (key or ()))})
+                        "traffic": profiled_traffic(name, key)})
         if name == "vec_stencil_f64_apply_L0" and fp64_tflops:
             tf = APPLY_FLOPS_PER_FACE * open_faces * launches / (ms * 1e-3) / 1e12
             ent["alu"] = {"bound": "alu", "achieved": round(tf, 4), "peak": round(fp64_tflops, 4),

@@ -76,11 +76,18 @@ def test_profiled_traffic_reaches_only_the_captured_case():
     import bench
     saved = dict(bench.PROFILED_TRAFFIC)
     try:
+        bench.PROFILED_TRAFFIC.clear()
         bench.PROFILED_TRAFFIC[("band_schwarz_f32_jacobi_L0", "ellipsoid", 192, 0)] = 12345
         stats = {"band_schwarz_f32_jacobi_L0": (8, 4.0, 8 * 2.0e7)}
         hit = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 192, 0))
         miss = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 192, 3))
         assert hit[0]["traffic"] == 12345 and miss[0]["traffic"] is None
+        # a capture that holds for every stencil shape
+        bench.PROFILED_TRAFFIC.clear()
+        bench.PROFILED_TRAFFIC[("band_schwarz_f32_jacobi_L0", "ellipsoid", 192, None)] = 777
+        anyshape = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 192, 3))
+        other = bench.rooflines(stats, 6794.8, "measured", None, 10, key=("ellipsoid", 128, 3))
+        assert anyshape[0]["traffic"] == 777 and other[0]["traffic"] is None
     finally:
         bench.PROFILED_TRAFFIC.clear()
         bench.PROFILED_TRAFFIC.update(saved)
