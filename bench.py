@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--streams", type=int, default=8, help="batch: worker streams of dm_eigensolve_batched")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison arm")
     ap.add_argument("--bf16-steps", type=int, default=3, help="timed steps of the BF16 V-cycle arm (0: skip)")
-    ap.add_argument("--inner-tol", type=float, default=1e-10, help="relative residual of each shifted solve")
+    ap.add_argument("--inner-tol", type=float, default=1e-9, help="relative residual of each shifted solve (library default 1e-9)")
     ap.add_argument("--inner-restart", type=int, default=40, help="FGMRES restart length of the shifted solves")
     ap.add_argument("--band-sweeps", type=int, default=None,
                     help="Jacobi sweeps of the band smoother on the fine level (library default 24)")
@@ -490,7 +490,8 @@ def run_batch(args):
             geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, ph if host_io else pd, g.origin)
             geoms.append(geom)
             for sg in shifts:
-                jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision})
+                jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision,
+                             "inner_tol": args.inner_tol})
         out = dm.eigensolve_batched(ctx, jobs, streams=args.streams)
         for geom in geoms:
             geom.close()
@@ -591,6 +592,7 @@ def run_ninecell(args):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, args.nev, vectors=None, precision=args.precision,
+                                       inner_tol=args.inner_tol,
                                        learned=net if learned else None)
         ev1.record(stream)
         torch.cuda.synchronize()

@@ -88,17 +88,19 @@ typedef struct dm_mg_params {
                               densely (2048; 0 = coarsen by max_coarse alone; at most 6000) */
     int krylov_ff;         /* 1: inside the shifted solves' FGMRES iterations, (K - sigma A) z is formed in
                               float-float arithmetic (two FP32 numbers per value, about 48 significant
-                              bits) on the FP32 pipes, straight into the float-float Krylov basis; the
-                              restart residuals, the final residual check and every certificate stay in
-                              FP64.  0: the FP64 apply plus a gather.  Allocates about 68 bytes per
-                              fine-level node on the geometry (1) */
+                              bits) on the FP32 pipes, straight into the float-float Krylov basis, and so
+                              is D A D^T z inside the projection's scalar iterations; the restart
+                              residuals, the final residual checks and every certificate stay in FP64.
+                              0: the FP64 applies plus a gather.  Allocates about 72 bytes per fine-level
+                              node on the geometry (1) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
     double sigma;          /* shift (Eq. shiftInv): modes with k^2 nearest sigma are found */
     int nev;               /* number of eigenpairs wanted */
     double tol;            /* Ritz residual tolerance, relative to |theta| (1e-10) */
-    double inner_tol;      /* relative residual of each shifted solve (1e-10) */
+    double inner_tol;      /* relative residual of each shifted solve (1e-9; the pairs are certified against
+                              rho_tol whatever it is, see rho_tol) */
     double proj_tol;       /* scalar-solve tolerance inside P_DM, see dm_operator_project (1e-12) */
     int basis;             /* Krylov-Schur basis size m; 0 = max(2 nev + 10, 24) capped at 64 */
     int max_restarts;      /* (100) */

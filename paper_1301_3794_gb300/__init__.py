@@ -482,7 +482,7 @@ class Learned:
             pass
 
 
-def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, max_restarts=100,
+def eig_params(sigma, nev, tol=1e-10, inner_tol=None, proj_tol=1e-12, basis=0, max_restarts=100,
                inner_restart=40, inner_maxit=400, seed=1301, learned=None, max_seconds=0.0, rho_tol=1e-8,
                **mg):
     p = EigParams()
@@ -490,7 +490,8 @@ def eig_params(sigma, nev, tol=1e-10, inner_tol=1e-10, proj_tol=1e-12, basis=0, 
     p.sigma = float(sigma)
     p.nev = int(nev)
     p.tol = tol
-    p.inner_tol = inner_tol
+    if inner_tol is not None:
+        p.inner_tol = float(inner_tol)
     p.proj_tol = proj_tol
     p.basis = basis
     p.max_restarts = max_restarts

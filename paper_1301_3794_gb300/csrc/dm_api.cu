@@ -134,7 +134,7 @@ struct GeoLevel {
     // the float-float operator apply of the shifted solves (fine level only,
     // built with the first operator that asks for them)
     DBuf<float2> ffA, ffL, ffV;
-    DBuf<int> fmap;
+    DBuf<int> fmap, fmapc;   // padded-to-compact maps of the open faces and of the active cells
     bool ff = false;
 };
 
@@ -823,6 +823,16 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
     return total;
 }
 
+// the float-float apply of the projection's scalar iterations (fine level)
+struct FFApplyScal {
+    static constexpr bool on = true;
+    dm_operator* op;
+    void operator()(const double* z, float2* wf) const {
+        const GeoLevel& l0 = glv(op, 0);
+        scal_apply_ff(l0.g, l0.tiles.get(), l0.ntiles, l0.ffA.get(), z, l0.fmapc.get(), wf, op->ctx->stream);
+    }
+};
+
 // the float-float apply of the shifted solves' iterations (fine level)
 struct FFApply {
     static constexpr bool on = true;
@@ -893,7 +903,11 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
         precond_scal(op, CompactIn{in, cl, ncl}, out, scale);
     };
     double rr = 0.0;
-    const int it = fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, kProjMaxit, &rr, tol * xscale);
+    const int it = (op->mg.krylov_ff && g0.ff)
+                       ? fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, kProjMaxit, &rr,
+                                tol * xscale, NoMonitor(), FFApplyScal{op})
+                       : fgmres(op->ctx, op->sg, nc, cl, ncl, 40, apply, prec, sv, phi, tol, kProjMaxit, &rr,
+                                tol * xscale);
     dm_sub_grad(g0.g, g0.A.get(), x, phi, y, g0.tiles.get(), g0.ntiles, s);
     return it;
 }
@@ -1159,6 +1173,8 @@ void setup_operator(dm_operator* op) {
             to_ff(n3, g0.L.get(), g0.ffL.get(), s);
             to_ff(g0.g.np, g0.invV.get(), g0.ffV.get(), s);
             compact_map(n3, g0.flist.get(), g0.nflist, g0.fmap.get(), s);
+            g0.fmapc = DBuf<int>(g0.g.np);
+            compact_map(g0.g.np, g0.clist.get(), g0.nclist, g0.fmapc.get(), s);
             Sync::stream(s);
             g0.ff = true;
         }
@@ -1888,7 +1904,7 @@ void dm_eig_params_default(dm_eig_params* p) {
     p->sigma = 0.0;
     p->nev = 4;
     p->tol = 1e-10;
-    p->inner_tol = 1e-10;
+    p->inner_tol = 1e-9;
     p->proj_tol = 1e-12;
     p->basis = 0;
     p->max_restarts = 100;

@@ -444,6 +444,10 @@ void vec_apply_dense_f64(const Grid3& g, const double* A, const double* L, const
 void vec_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A, const float2* L, const float2* invV,
                   double sigma, const double* x, const int* cmap, float2* out, cudaStream_t s);
 void to_ff(long long n, const double* a, float2* out, cudaStream_t s);
+// D A D^T x in float-float into the compact vector out (out[cmap[p]] for the
+// active cells p), over the level's active tiles; A: float-float face fractions
+void scal_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A, const double* x, const int* cmap,
+                   float2* out, cudaStream_t s);
 // cmap[q] = position of q in the ascending list (nl entries), -1 elsewhere (n3 entries)
 void compact_map(long long n3, const int* list, int nl, int* cmap, cudaStream_t s);
 void vec_diagonal(const Grid3& g, const double* A, const double* L, const double* invV, double sigma, double* d,

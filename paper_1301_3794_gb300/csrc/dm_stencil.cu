@@ -749,6 +749,30 @@ __global__ void __launch_bounds__(TX * TY * TZ) k_vec_apply_ff(Grid3 g, const fl
     }
 }
 
+// D A D^T x on the active cells in float-float (the projection's scalar
+// operator, Eq. proj), straight into the compact float-float vector of the
+// scalar FGMRES basis: out[cmap[p]] for every active cell p.  x is FP64 (split
+// on load), A the float-float face fractions, 1/h^2 float-float.
+__global__ void k_scal_apply_ff(Grid3 g, const float2* __restrict__ A, ffv rx2, ffv ry2, ffv rz2,
+                                const double* __restrict__ x, const int* __restrict__ cmap, float2* __restrict__ out,
+                                const int* __restrict__ tiles) {
+    int i, j, k;
+    block_node(g, tiles, i, j, k);
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int p = g.idx(i, j, k);
+    const int ci = cmap[p];
+    if (ci < 0) return;
+    const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
+    auto v = [&](int q) { return ff_from_double(x[q]); };
+    auto a = [&](int q) { return ff_load(A + q); };
+    const ffv v0 = v(p);
+    const ffv sx = (a(p + X) * (v0 - v(p + X)) + a(p) * (v0 - v(p - X))) * rx2;
+    const ffv sy = (a(N + p + Y) * (v0 - v(p + Y)) + a(N + p) * (v0 - v(p - Y))) * ry2;
+    const ffv sz = (a(2 * N + p + Z) * (v0 - v(p + Z)) + a(2 * N + p) * (v0 - v(p - Z))) * rz2;
+    const ffv r = sx + sy + sz;
+    out[ci] = make_float2(r.hi, r.lo);
+}
+
 // float-float copy of an FP64 array: hi = the double rounded to FP32, lo =
 // the rest rounded (setup only, FP64 arithmetic)
 __global__ void k_to_ff(long long n, const double* __restrict__ a, float2* __restrict__ out) {
@@ -792,6 +816,16 @@ void vec_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A,
     const double bytes = (double)g.nopen * (8.0 + 16.0 + 8.0 / 3.0 + 12.0);
     launch_b("vec_apply_ff_L0", bytes, k_vec_apply_ff, ntiles, dim3(TX, TY, TZ), 0, s, g, A, L, invV, host_ff(g.rhx),
              host_ff(g.rhy), host_ff(g.rhz), host_ff(sigma), x, cmap, out, tiles);
+}
+
+void scal_apply_ff(const Grid3& g, const int* tiles, int ntiles, const float2* A, const double* x, const int* cmap,
+                   float2* out, cudaStream_t s) {
+    if (ntiles <= 0) return;
+    // bytes: per active cell its x (8), three float-float face fractions (24; six faces, each shared by two
+    // cells), the output (8) and its compact index (4)
+    const double bytes = (double)g.nact * (8.0 + 24.0 + 12.0);
+    launch_b("scal_apply_ff_L0", bytes, k_scal_apply_ff, ntiles, kBlock, 0, s, g, A, host_ff(g.rhx * g.rhx),
+             host_ff(g.rhy * g.rhy), host_ff(g.rhz * g.rhz), x, cmap, out, tiles);
 }
 
 const char* stencil_name(const char* kind, int prec, int mode, bool fine) {

@@ -89,6 +89,21 @@ def test_apply_float_float(case):
     assert np.all(y[lev.mask == 0] == 0.0)
 
 
+def test_projection_with_float_float_scalar_iterations(dm, ctx, case):
+    """P_DM with the float-float scalar apply inside its FGMRES matches the
+    FP64 apply's result and the oracle's projection."""
+    w, geom, levels, op = case
+    ops = levels[0].ops
+    x = np.random.default_rng(9).standard_normal(ops.a.size) * ops.open
+    y1, it1 = op.project(x, tol=1e-12)
+    op0 = dm.Operator(ctx, geom, w.sigma, krylov_ff=0)
+    y0, it0 = op0.project(x, tol=1e-12)
+    op0.close()
+    assert abs(it1 - it0) <= 2, (it0, it1)
+    assert _rel(y1, y0) < 1e-9
+    assert _rel(y1, ops.project(x)) < 1e-9
+
+
 def test_krylov_float_float_solve_matches_f64(dm, ctx, case):
     """The shifted solve with float-float iterations reaches the same FP64
     residual, and the same solution, as with FP64 iterations."""

@@ -34,7 +34,7 @@ def test_struct_layouts_match_defaults(lib):
     from paper_1301_3794_gb300._lib import EigParams, MGParams
     p = EigParams()
     lib.dm_eig_params_default(C.byref(p))
-    assert p.tol == 1e-10 and p.nev == 4 and p.inner_restart == 40 and p.seed == 1301
+    assert p.tol == 1e-10 and p.inner_tol == 1e-9 and p.nev == 4 and p.inner_restart == 40 and p.seed == 1301
     assert p.mg.max_coarse == 4 and p.mg.band_sweeps == 24 and p.mg.band_brick == 8 and p.mg.omega_scale == 1.7
     m = MGParams()
     lib.dm_mg_params_default(C.byref(m))
