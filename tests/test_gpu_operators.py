@@ -100,8 +100,12 @@ def test_projection_with_float_float_scalar_iterations(dm, ctx, case):
     y0, it0 = op0.project(x, tol=1e-12)
     op0.close()
     assert abs(it1 - it0) <= 2, (it0, it1)
-    assert _rel(y1, y0) < 1e-9
-    assert _rel(y1, ops.project(x)) < 1e-9
+    ref = ops.project(x)
+    e1 = np.linalg.norm(y1 - ref) / np.linalg.norm(ref)
+    e0 = np.linalg.norm(y0 - ref) / np.linalg.norm(ref)
+    # the projection's own bar (test_project_matches_oracle), and no worse than the FP64 iterations
+    assert e1 < 1e-9 and e1 < max(2.0 * e0, 1e-11), (e1, e0)
+    assert np.linalg.norm(y1 - y0) / np.linalg.norm(y0) < 1e-9
 
 
 def test_krylov_float_float_solve_matches_f64(dm, ctx, case):
