@@ -302,6 +302,10 @@ def run_native(args):
     torch.cuda.synchronize()
     nf = dm.face_count(g.nx, g.ny, g.nz)
     B_dev = torch.empty((args.nev, nf), dtype=torch.float64, device=f"cuda:{local}")
+    # the end-to-end leg's host buffers: pinned, as an application that streams
+    # level sets in and eigenvectors out would hold them
+    phi_pinned = torch.from_numpy(phi_host).pin_memory()
+    B_pinned = torch.empty((args.nev, nf), dtype=torch.float64).pin_memory()
 
     sweep_kw = {}
     if args.band_sweeps is not None:
@@ -310,11 +314,11 @@ def run_native(args):
         sweep_kw["band_sweeps_coarse"] = args.band_sweeps_coarse
 
     def step(precision, host_io=False):
-        phi = phi_host if host_io else phi_dev
+        phi = phi_pinned if host_io else phi_dev
         geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi, g.origin)
         vec = "host" if host_io else "device"
         k2, B, rep, st = dm.eigensolve(ctx, geom, args.sigma, args.nev, vectors=vec,
-                                       out=None if host_io else B_dev, precision=precision,
+                                       out=B_pinned if host_io else B_dev, precision=precision,
                                        inner_tol=args.inner_tol, inner_restart=args.inner_restart,
                                        krylov_ff=0 if (args.no_krylov_ff or precision == "f64") else 1,
                                        **sweep_kw)

@@ -312,7 +312,9 @@ void dm_eig_params_default(dm_eig_params* p);
  * in the A inner product (Eq. bInner).  k2_out[nev] ascending (host).
  * b_out (nullable): nev x F, natural face layout, A-normalised (b^T A b = 1),
  * sign such that the entry of largest magnitude is positive; host or device
- * per b_on_device.  DM_ERR_NO_CONVERGENCE still fills the converged prefix
+ * per b_on_device (a host b_out in page-locked memory is written by DMA at
+ * link speed, pageable memory through the driver's staging).
+ * DM_ERR_NO_CONVERGENCE still fills the converged prefix
  * and report->n_converged.  Two failures return no pair at all (k2_out set to
  * NaN, b_out untouched, n_converged = 0, the report's iteration counts and
  * timings filled):

@@ -49,6 +49,11 @@ def _is_torch(a):
     return type(a).__module__.startswith("torch")
 
 
+def _torch():
+    import torch
+    return torch
+
+
 class _Arg:
     """Pointer to an input array plus whether it lives on the device."""
 
@@ -518,7 +523,13 @@ def eigensolve(ctx, geom, sigma, nev, vectors="host", out=None, **kw):
     dev = 0
     if vectors == "host":
         B = np.empty((nev, F)) if out is None else out
-        bptr = C.c_void_p(B.ctypes.data)
+        if _is_torch(B):
+            # a host tensor (pinned memory copies at full link speed)
+            if B.is_cuda or B.dtype != _torch().float64 or not B.is_contiguous() or B.numel() != nev * F:
+                raise ValueError(f"eigensolve: out must be a contiguous float64 host tensor of {nev} x {F} values")
+            bptr = C.c_void_p(B.data_ptr())
+        else:
+            bptr = C.c_void_p(B.ctypes.data)
     elif vectors == "device":
         import torch
         B = torch.empty((nev, F), dtype=torch.float64, device=f"cuda:{ctx.device}") if out is None else out

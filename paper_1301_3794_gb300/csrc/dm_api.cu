@@ -2229,15 +2229,18 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             delta_max = std::max(delta_max, delta[asc[c]]);
         }
         if (b_out) {
+            // host output: one staging buffer, each vector unpacked into it and
+            // copied out in stream order (a pinned destination copies at link speed)
             const size_t nf = (size_t)natural_faces(g0.g);
+            DBuf<double> t;
+            if (!b_on_device) t.alloc(nf, false);
             for (int c = 0; c < nev; ++c) {
                 const double* src = tmp.get() + (size_t)asc[c] * n;
                 if (b_on_device) {
                     unpack_faces(g0.g, src, b_out + c * nf, s);
                 } else {
-                    DBuf<double> t(nf, false);
                     unpack_faces(g0.g, src, t.get(), s);
-                    stage_out(ctx, t.get(), b_out + c * nf, 0, nf);
+                    DM_CUDA(cudaMemcpyAsync(b_out + c * nf, t.get(), sizeof(double) * nf, cudaMemcpyDeviceToHost, s));
                 }
             }
             Sync::stream(s);
