@@ -370,7 +370,11 @@ dm_status dm_learned_train(dm_learned* net, dm_operator* op, int runs, int epoch
  * grad (nullable, host, dm_learned_num_params() floats): its gradient. */
 dm_status dm_learned_train_step(dm_learned* net, dm_operator* op, const double* r, int on_device, float lr,
                                 float* loss, float* grad);
-/* Use (net) or stop using (NULL) the learned correction in op's preconditioner. */
+/* Use (net) or stop using (NULL) the learned correction in op's preconditioner.
+ * In each shifted solve the FP64 FGMRES residual decides: an iteration that
+ * contracts by less than 0.8 switches the correction off for the rest of that
+ * solve, and after 3 solves in a row that switched it off the operator stops
+ * offering it until this call sets a network again. */
 dm_status dm_operator_set_learned(dm_operator* op, const dm_learned* net);
 
 /* ---- batched eigensolves (many cavities and shifts; no counterpart in the paper) */

@@ -324,6 +324,7 @@ struct dm_operator {
     std::vector<double> lc_host;
     bool learned_active = false;
     int learned_applied = 0, learned_fallbacks = 0;
+    int learned_streak = 0;    // consecutive shifted solves in which the correction was switched off
     long long nopen0 = 0;
     Fork fork;                 // side streams of the band smoother's class launches
     ~dm_operator() {
@@ -844,6 +845,10 @@ struct FFApply {
     }
 };
 
+// shifted solves in a row that must switch the learned correction off before
+// an operator stops offering it
+constexpr int kLearnedStreak = 3;
+
 int solve_vec(dm_operator* op, const double* b, double* x, double tol, int restart, int maxit, double* relres) {
     const Domain n = glv(op, 0).vdom();
     auto apply = [op](const double* in, double* out) { apply_vec64(op, 0, in, out); };
@@ -854,8 +859,11 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
         precond_vec(op, CompactIn{in, fl, nfl}, out, scale);
     };
     // the FP64 residual decides on the learned correction: an iteration that
-    // contracts by less than 0.8 switches it off for the rest of the solve
-    op->learned_active = op->lnet != nullptr;
+    // contracts by less than 0.8 switches it off for the rest of the solve, and
+    // after kLearnedStreak solves in a row that switched it off the operator
+    // stops offering it (dm_operator_set_learned offers it again)
+    op->learned_active = op->lnet != nullptr && op->learned_streak < kLearnedStreak;
+    const bool offered = op->learned_active;
     bool fell_back = false;
     auto monitor = [op, &fell_back](double ratio) {
         if (op->learned_active && ratio > 0.8) {
@@ -869,7 +877,12 @@ int solve_vec(dm_operator* op, const double* b, double* x, double tol, int resta
     } else {
         it = fgmres(op->ctx, op->vg, n, fl, nfl, restart, apply, prec, b, x, tol, maxit, relres, 0.0, monitor);
     }
-    if (fell_back) ++op->learned_fallbacks;
+    if (fell_back) {
+        ++op->learned_fallbacks;
+        ++op->learned_streak;
+    } else if (offered) {
+        op->learned_streak = 0;
+    }
     op->learned_active = false;
     return it;
 }
@@ -2582,6 +2595,7 @@ dm_status dm_learned_train_step(dm_learned* net, dm_operator* op, const double* 
 dm_status dm_operator_set_learned(dm_operator* op, const dm_learned* net) {
     if (!op) return DM_ERR_INVALID_ARG;
     return guarded(op->ctx, [&] {
+        op->learned_streak = 0;
         if (!net) {
             op->lnet.reset();
             return;

@@ -172,3 +172,22 @@ def test_training_lowers_loss_and_solver_uses_network(dm, ctx):
     assert st == 0 and rep["rho_max"] < 1e-8
     assert np.max(np.abs(k2 - k2p) / k2p) < 1e-9
     assert rep["learned_applied"] > 0
+
+
+def test_operator_stops_offering_a_network_that_keeps_falling_back(dm, ctx):
+    """A network that harms the solve (untrained, its output scaled up) is
+    switched off by the FP64 residual in each shifted solve; after three solves
+    in a row the operator stops offering it, so at most three solves pay for it."""
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 2, sigma=5.0, nev=4)
+    geom = dm.Geometry.from_workload(ctx, w)
+    net = dm.Learned(ctx, seed=13)
+    wts = net.get_weights()
+    wts[27 * 8 * 16 + 27 * 16 * 16:] *= 300.0
+    net.set_weights(wts)
+    k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, precision="f32", learned=net)
+    k2p, _, repp, stp = dm.eigensolve(ctx, geom, w.sigma, w.nev, vectors=None, precision="f32")
+    print(f"\nharmful network: {rep['learned_fallbacks']} fallbacks, {rep['learned_applied']} applications, "
+          f"{rep['outer_iters']} solves; inner {rep['inner_iters']} against {repp['inner_iters']} without")
+    assert st == 0 and stp == 0
+    assert rep["learned_fallbacks"] <= 3
+    assert np.max(np.abs(k2 - k2p) / k2p) < 1e-9
