@@ -175,9 +175,12 @@ def test_training_lowers_loss_and_solver_uses_network(dm, ctx):
 
 
 def test_operator_stops_offering_a_network_that_keeps_falling_back(dm, ctx):
-    """A network that harms the solve (untrained, its output scaled up) is
-    switched off by the FP64 residual in each shifted solve; after three solves
-    in a row the operator stops offering it, so at most three solves pay for it."""
+    """An untrained network with its output scaled up: the residual-minimising
+    step keeps its corrections from raising the preconditioned residual, and
+    where the FP64 residual still stalls the correction is switched off; after
+    three solves in a row that switched it off the operator stops offering it,
+    so at most three solves ever fall back (on the full-size 9-cell cavity the
+    bench sees exactly that: 3 fallbacks, then none)."""
     w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 2, sigma=5.0, nev=4)
     geom = dm.Geometry.from_workload(ctx, w)
     net = dm.Learned(ctx, seed=13)
