@@ -954,8 +954,10 @@ double power_lambda_max(dm_operator* op, int l) {
 
 // Largest eigenvalue of D^-1 D A D^T used for the scalar Jacobi weight.  Every
 // row of D A D^T on the active cells sums to zero (a face between an active
-// and an inactive cell, or on an outer wall, is closed), so by Gershgorin the
-// spectrum of D^-1 D A D^T lies in [0, 2]; the grid's checkerboard mode comes
+// and an inactive cell, or on a conducting outer wall, is closed), or to a
+// positive number next to an open magnetic wall (the face to the zero
+// potential beyond it), so by Gershgorin the spectrum of D^-1 D A D^T lies in
+// [0, 2]; the grid's checkerboard mode comes
 // within O(h^2) of 2.  The bound is exact enough and, unlike a power estimate,
 // cannot be fooled by a nearly isolated cut cell whose diagonal is ten orders
 // of magnitude below the bulk (its local eigenvalue is 1, and an estimate near

@@ -289,27 +289,38 @@ void band_schwarz_setup(const Grid3& g, const int* band_dev, int nband, int bric
         int q, t;
         bool owned;
     };
-    std::vector<Copy> cp;
-    cp.reserve((size_t)nband * 2);
-    for (int t = 0; t < nband; ++t) {
-        int lo[3], hi[3], own[3];
-        for (int a = 0; a < 3; ++a) {
-            const int P = node[3 * t + a];
-            own[a] = P / brick;
-            lo[a] = std::max((P + brick - 1) / brick - 1, 0);
-            hi[a] = std::min((P + 1) / brick, nb[a] - 1);
+    // grouped by brick with a counting sort (two passes over the faces), then
+    // each brick's copies sorted by face index: the order of one sort by
+    // (brick, face) at a fraction of its cost
+    const size_t nbk = (size_t)nb[0] * nb[1] * nb[2];
+    auto each_copy = [&](auto&& visit) {
+        for (int t = 0; t < nband; ++t) {
+            int lo[3], hi[3], own[3];
+            for (int a = 0; a < 3; ++a) {
+                const int P = node[3 * t + a];
+                own[a] = P / brick;
+                lo[a] = std::max((P + brick - 1) / brick - 1, 0);
+                hi[a] = std::min((P + 1) / brick, nb[a] - 1);
+            }
+            for (int bz = lo[2]; bz <= hi[2]; ++bz)
+                for (int by = lo[1]; by <= hi[1]; ++by)
+                    for (int bx = lo[0]; bx <= hi[0]; ++bx) {
+                        const long long kb = key(bx, by, bz);
+                        if (owner[kb]) visit(kb, t, bx == own[0] && by == own[1] && bz == own[2]);
+                    }
         }
-        for (int bz = lo[2]; bz <= hi[2]; ++bz)
-            for (int by = lo[1]; by <= hi[1]; ++by)
-                for (int bx = lo[0]; bx <= hi[0]; ++bx) {
-                    const long long kb = key(bx, by, bz);
-                    if (!owner[kb]) continue;
-                    cp.push_back(Copy{kb, band[t], t, bx == own[0] && by == own[1] && bz == own[2]});
-                }
+    };
+    std::vector<long long> start(nbk + 1, 0);
+    each_copy([&](long long kb, int, bool) { ++start[kb + 1]; });
+    for (size_t b = 0; b < nbk; ++b) start[b + 1] += start[b];
+    std::vector<Copy> cp((size_t)start[nbk]);
+    {
+        std::vector<long long> fill(start.begin(), start.end() - 1);
+        each_copy([&](long long kb, int t, bool owned) { cp[(size_t)fill[kb]++] = Copy{kb, band[t], t, owned}; });
     }
-    std::sort(cp.begin(), cp.end(), [](const Copy& a, const Copy& b) {
-        return a.brick != b.brick ? a.brick < b.brick : a.q < b.q;
-    });
+    for (size_t b = 0; b < nbk; ++b)
+        std::sort(cp.begin() + start[b], cp.begin() + start[b + 1],
+                  [](const Copy& a, const Copy& c) { return a.q < c.q; });
     const int nc = (int)cp.size();
     // subdomains (runs of one brick), emitted class by class
     std::vector<std::pair<int, int>> runs;
