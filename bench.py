@@ -61,6 +61,8 @@ def parse():
                     help="Jacobi sweeps of the band smoother on the fine level (library default 24)")
     ap.add_argument("--band-sweeps-coarse", type=int, default=None,
                     help="sweeps of the band smoother below the fine level (library default 16)")
+    ap.add_argument("--jacobi-sweeps", type=int, default=None,
+                    help="damped Jacobi sweeps per smoothing step (library default 2)")
     ap.add_argument("--no-krylov-ff", action="store_true",
                     help="FP64 operator applies inside the shifted solves' FGMRES iterations (instead of float-float)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,12 +92,25 @@ def describe(args, w):
             f"{args.nev} lowest modes, residual<={RHO_TOL}")
 
 
+def mg_overrides(args):
+    """Multigrid settings given on the command line (the library's defaults otherwise)."""
+    kw = {}
+    if args.band_sweeps is not None:
+        kw["band_sweeps"] = args.band_sweeps
+    if args.band_sweeps_coarse is not None:
+        kw["band_sweeps_coarse"] = args.band_sweeps_coarse
+    if args.jacobi_sweeps is not None:
+        kw["jacobi_sweeps"] = args.jacobi_sweeps
+    return kw
+
+
 def config_of(args, w, extra=None):
     c = {"workload": describe(args, w),
          "grid": [args.grid] * 3, "nev": args.nev, "sigma": args.sigma, "inner_tol": args.inner_tol,
          "inner_restart": args.inner_restart, "krylov_apply": "f64" if args.no_krylov_ff else "float-float",
          "band_sweeps": [24 if args.band_sweeps is None else args.band_sweeps,
                          16 if args.band_sweeps_coarse is None else args.band_sweeps_coarse],
+         "jacobi_sweeps": 2 if args.jacobi_sweeps is None else args.jacobi_sweeps,
          "mg_precision": args.precision, "outer_precision": "f64",
          "l2": "inputs larger than L2 (solver working set of several GB per step)"}
     if extra:
@@ -307,11 +322,7 @@ def run_native(args):
     phi_pinned = torch.from_numpy(phi_host).pin_memory()
     B_pinned = torch.empty((args.nev, nf), dtype=torch.float64).pin_memory()
 
-    sweep_kw = {}
-    if args.band_sweeps is not None:
-        sweep_kw["band_sweeps"] = args.band_sweeps
-    if args.band_sweeps_coarse is not None:
-        sweep_kw["band_sweeps_coarse"] = args.band_sweeps_coarse
+    sweep_kw = mg_overrides(args)
 
     def step(precision, host_io=False):
         phi = phi_pinned if host_io else phi_dev
@@ -495,7 +506,7 @@ def run_batch(args):
             geoms.append(geom)
             for sg in shifts:
                 jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision,
-                             "inner_tol": args.inner_tol})
+                             "inner_tol": args.inner_tol, **mg_overrides(args)})
         out = dm.eigensolve_batched(ctx, jobs, streams=args.streams)
         for geom in geoms:
             geom.close()
@@ -583,7 +594,7 @@ def run_ninecell(args):
         phi_dev = torch.from_numpy(np.ascontiguousarray(w.phi.ravel())).to(f"cuda:{local}")
     torch.cuda.synchronize()
     geom = dm.Geometry(ctx, g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, phi_dev, g.origin)
-    op = dm.Operator(ctx, geom, w.sigma, precision=args.precision)
+    op = dm.Operator(ctx, geom, w.sigma, precision=args.precision, **mg_overrides(args))
     net = dm.Learned(ctx, seed=11)
     t0 = time.perf_counter()
     hist = net.train(op, runs=2, epochs=6, lr=2e-3, seed=7)
@@ -596,7 +607,7 @@ def run_ninecell(args):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, args.nev, vectors=None, precision=args.precision,
-                                       inner_tol=args.inner_tol,
+                                       inner_tol=args.inner_tol, **mg_overrides(args),
                                        learned=net if learned else None)
         ev1.record(stream)
         torch.cuda.synchronize()

@@ -93,6 +93,8 @@ typedef struct dm_mg_params {
                               residuals, the final residual checks and every certificate stay in FP64.
                               0: the FP64 applies plus a gather.  Allocates about 72 bytes per fine-level
                               node on the geometry (1) */
+    int jacobi_sweeps;     /* damped Jacobi sweeps of each smoothing step, before the band smoother, on
+                              every level, pre and post (2; at most 16) */
 } dm_mg_params;
 
 typedef struct dm_eig_params {
@@ -280,7 +282,7 @@ dm_status dm_operator_apply_noalloc(dm_operator* op, int level, const double* x,
 /* Diagonal of K - sigma A on `level` (natural face layout, 0 on closed faces). */
 dm_status dm_operator_diagonal(dm_operator* op, int level, double* d, int on_device);
 /* One smoothing step on `level` in the preconditioner's precision:
- * x <- x + omega D^-1 (f - (K - sigma A) x), then the band smoother (band_sweeps
+ * jacobi_sweeps times x <- x + omega D^-1 (f - (K - sigma A) x), then the band smoother (band_sweeps
  * sweeps per subdomain on the cut-cell band, see dm_mg_params).  x is updated
  * in place. */
 dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double* x, int on_device);

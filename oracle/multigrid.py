@@ -270,8 +270,12 @@ def band_schwarz(level, f, x, omega, sweeps, brick):
     return x
 
 
-def smooth(level, f, x, omega, band_sweeps, from_zero=False, brick=8):
+def smooth(level, f, x, omega, band_sweeps, from_zero=False, brick=8, jacobi_sweeps=1):
+    """``jacobi_sweeps`` damped Jacobi sweeps (the first from x = 0 when
+    ``from_zero``), then the band smoother."""
     x = omega * level.inv_d * f if from_zero else jacobi(level, f, x, omega)
+    for _ in range(jacobi_sweeps - 1):
+        x = jacobi(level, f, x, omega)
     return band_schwarz(level, f, x, omega, band_sweeps, brick)
 
 
@@ -292,20 +296,21 @@ def coarsest_solve(level, f):
     return x
 
 
-def vcycle(levels, f, omegas, band_sweeps=16, l=0, brick=8, band_sweeps_coarse=None):
-    """e ~= (K_l - sigma A_l)^-1 f: one V(1,1) cycle from a zero guess.  The
-    band smoother runs ``band_sweeps`` sweeps on the fine level and
+def vcycle(levels, f, omegas, band_sweeps=16, l=0, brick=8, band_sweeps_coarse=None, jacobi_sweeps=1):
+    """e ~= (K_l - sigma A_l)^-1 f: one V(nu,nu) cycle from a zero guess, nu =
+    ``jacobi_sweeps`` damped Jacobi sweeps per smoothing step.  The band
+    smoother runs ``band_sweeps`` sweeps on the fine level and
     ``band_sweeps_coarse`` (default: the same) on the coarser ones."""
     lev = levels[l]
     if l == len(levels) - 1:
         return coarsest_solve(lev, f)
     coarse = band_sweeps if band_sweeps_coarse is None else band_sweeps_coarse
     sweeps = band_sweeps if l == 0 else coarse
-    e = smooth(lev, f, None, omegas[l], sweeps, from_zero=True, brick=brick)
+    e = smooth(lev, f, None, omegas[l], sweeps, from_zero=True, brick=brick, jacobi_sweeps=jacobi_sweeps)
     r = f - lev.K @ e
-    ec = vcycle(levels, restrict(levels, l, r), omegas, band_sweeps, l + 1, brick, coarse)
+    ec = vcycle(levels, restrict(levels, l, r), omegas, band_sweeps, l + 1, brick, coarse, jacobi_sweeps)
     e = prolong_add(levels, l, e, ec)
-    return smooth(lev, f, e, omegas[l], sweeps, brick=brick)
+    return smooth(lev, f, e, omegas[l], sweeps, brick=brick, jacobi_sweeps=jacobi_sweeps)
 
 
 # -- scalar V-cycle -----------------------------------------------------------

@@ -257,11 +257,12 @@ class Geometry:
 
 def mg_params(max_coarse=4, band_sweeps=None, band_brick=8, omega_scale=1.7, power_iters=30, precision="f64",
               autotune=1, force_shape=-1, band_sweeps_coarse=None, symmetric_transform=0, dense_coarse=None,
-              krylov_ff=1):
+              krylov_ff=1, jacobi_sweeps=None):
     """band_sweeps, band_sweeps_coarse: band-smoother sweeps on the fine level and below it
     (None: the library's defaults, 24 and 16);
     symmetric_transform: 1 for the V-cycle of Eq. fullMat2's symmetric form;
-    krylov_ff: 1 to form the shifted solves' FGMRES operator applies in float-float."""
+    krylov_ff: 1 to form the shifted solves' FGMRES operator applies in float-float;
+    jacobi_sweeps: damped Jacobi sweeps per smoothing step (None: the library's default)."""
     p = MGParams()
     lib.dm_mg_params_default(C.byref(p))
     p.max_coarse = max_coarse
@@ -279,6 +280,8 @@ def mg_params(max_coarse=4, band_sweeps=None, band_brick=8, omega_scale=1.7, pow
     if dense_coarse is not None:
         p.dense_coarse = int(dense_coarse)
     p.krylov_ff = int(krylov_ff)
+    if jacobi_sweeps is not None:
+        p.jacobi_sweeps = int(jacobi_sweeps)
     return p
 
 

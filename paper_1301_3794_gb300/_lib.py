@@ -17,7 +17,7 @@ class MGParams(C.Structure):
     _fields_ = [("max_coarse", C.c_int), ("band_sweeps", C.c_int), ("band_brick", C.c_int), ("omega_scale", C.c_double),
                 ("power_iters", C.c_int), ("precision", C.c_int), ("autotune", C.c_int),
                 ("stencil_shape", C.c_int), ("band_sweeps_coarse", C.c_int), ("symmetric_transform", C.c_int),
-                ("dense_coarse", C.c_int), ("krylov_ff", C.c_int)]
+                ("dense_coarse", C.c_int), ("krylov_ff", C.c_int), ("jacobi_sweeps", C.c_int)]
 
 
 class EigParams(C.Structure):

@@ -422,23 +422,36 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     const double om = op->ol[l].omega;
     double* u = op->band_u.get();
     const int sweeps = band_sweeps_of(op, l);
-    vec_jacobi_zero(o, f, ebuf, om, s);
-    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, ebuf, u, om, sweeps, l == 0,
+    const int nu = op->mg.jacobi_sweeps;
+    // the iterate and the other work buffer swap roles at every Jacobi sweep
+    T* it = ebuf;
+    T* tmp = rbuf;
+    vec_jacobi_zero(o, f, it, om, s);
+    for (int k = 1; k < nu; ++k) {
+        vec_stencil(o, ST_JACOBI, it, f, tmp, om, s);
+        std::swap(it, tmp);
+    }
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, it, u, om, sweeps, l == 0,
                         s, fork_of(op));
-    vec_stencil(o, ST_RESID, ebuf, f, rbuf, 0.0, s);
+    vec_stencil(o, ST_RESID, it, f, tmp, 0.0, s);
     const GeoLevel& gc = glv(op, l + 1);
     WorkLevel& wc = op->wk[l + 1];
     T* fc = reinterpret_cast<T*>(wc.f.get());
     const bool sym = op->mg.symmetric_transform != 0;
-    if (sym) scale_sqrt_a<T, TC>(g.vdom(), Pick<T, TC>::A(g), true, rbuf, s);
-    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), rbuf, fc, gc.tiles.get(), gc.ntiles, s, sym);
+    if (sym) scale_sqrt_a<T, TC>(g.vdom(), Pick<T, TC>::A(g), true, tmp, s);
+    face_restrict<T, TC>(g.g, gc.g, Pick<T, TC>::A(gc), tmp, fc, gc.tiles.get(), gc.ntiles, s, sym);
     T* ec = reinterpret_cast<T*>(wc.r.get());
     vcycle<T, TC>(op, l + 1, fc, reinterpret_cast<T*>(wc.e.get()), ec);
     if (sym) scale_sqrt_a<T, TC>(gc.vdom(), Pick<T, TC>::A(gc), false, ec, s);
-    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), ec, ebuf, g.tiles.get(), g.ntiles, s, sym);
-    vec_stencil(o, ST_JACOBI, ebuf, f, rbuf, om, s);
-    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, rbuf, u, om, sweeps, l == 0,
+    face_prolong_add<T, TC>(g.g, gc.g, Pick<T, TC>::A(g), ec, it, g.tiles.get(), g.ntiles, s, sym);
+    for (int k = 0; k < nu; ++k) {
+        vec_stencil(o, ST_JACOBI, it, f, tmp, om, s);
+        std::swap(it, tmp);
+    }
+    band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[l]), o.invD, g.g, g.band.get(), g.nband, f, it, u, om, sweeps, l == 0,
                         s, fork_of(op));
+    // the cycle's result goes in rbuf
+    if (it != rbuf) DM_CUDA(cudaMemcpyAsync(rbuf, it, sizeof(T) * 3 * (size_t)g.g.np, cudaMemcpyDeviceToDevice, s));
 }
 
 // ---- scalar V-cycle: result in rbuf -----------------------------------------------
@@ -1665,6 +1678,7 @@ void dm_mg_params_default(dm_mg_params* p) {
     p->symmetric_transform = 0;
     p->dense_coarse = 2048;
     p->krylov_ff = 1;
+    p->jacobi_sweeps = 2;
 }
 
 dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double sigma, const dm_mg_params* mg,
@@ -1687,6 +1701,8 @@ dm_status dm_operator_create(dm_context* ctx, const dm_geometry* geom, double si
                    "band_sweeps_coarse out of range");
         DM_REQUIRE(op->mg.band_brick >= 1, DM_ERR_INVALID_ARG, "band_brick must be >= 1");
         DM_REQUIRE(op->mg.krylov_ff == 0 || op->mg.krylov_ff == 1, DM_ERR_INVALID_ARG, "krylov_ff must be 0 or 1");
+        DM_REQUIRE(op->mg.jacobi_sweeps >= 1 && op->mg.jacobi_sweeps <= 16, DM_ERR_INVALID_ARG,
+                   "jacobi_sweeps must be in [1, 16]");
         DM_REQUIRE(op->mg.precision >= 0 && op->mg.precision <= 2, DM_ERR_INVALID_ARG, "unknown precision");
         DM_REQUIRE(op->mg.power_iters >= 1, DM_ERR_INVALID_ARG, "power_iters must be >= 1");
         DM_REQUIRE(op->mg.stencil_shape >= -1 && op->mg.stencil_shape < kStencilShapes, DM_ERR_INVALID_ARG,
@@ -1783,9 +1799,15 @@ dm_status dm_operator_smooth(dm_operator* op, int level, const double* f, double
             using T = std::remove_pointer_t<std::remove_reference_t<decltype(*p)>>;
             using TC = std::conditional_t<std::is_same<T, double>::value, double, float>;
             const VecOp<T, TC> o = vop<T, TC>(op, level);
-            vec_stencil(o, ST_JACOBI, p[1], p[0], p[2], om, s);
-            band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[level]), o.invD, g.g, g.band.get(), g.nband, p[0], p[2], u, om,
+            T* it = p[1];
+            T* tmp = p[2];
+            for (int k = 0; k < op->mg.jacobi_sweeps; ++k) {
+                vec_stencil(o, ST_JACOBI, it, p[0], tmp, om, s);
+                std::swap(it, tmp);
+            }
+            band_schwarz<T, TC>(Pick<T, TC>::bs(op->ol[level]), o.invD, g.g, g.band.get(), g.nband, p[0], it, u, om,
                                 band_sweeps_of(op, level), level == 0, s);
+            if (it != p[2]) DM_CUDA(cudaMemcpyAsync(p[2], it, sizeof(T) * (size_t)n3, cudaMemcpyDeviceToDevice, s));
         };
         if (op->mg.precision == DM_PREC_F64) run(reinterpret_cast<double**>(pads));
         else if (op->mg.precision == DM_PREC_F32)

@@ -37,7 +37,8 @@ def _oracle_iterations(w, fr, tol, maxit, omegas):
     lev = levels[0]
     b = np.random.default_rng(0).standard_normal(lev.K.shape[0]) * lev.mask
     _, hist = MG.fgmres(lambda v: lev.K @ v, b,
-                        lambda v: MG.vcycle(levels, v, omegas, band_sweeps=24, band_sweeps_coarse=16), tol=tol,
+                        lambda v: MG.vcycle(levels, v, omegas, band_sweeps=24, band_sweeps_coarse=16,
+                                            jacobi_sweeps=2), tol=tol,
                         maxiter=maxit)
     return len(hist), hist[-1]
 

@@ -21,6 +21,7 @@ CASES = {
 
 
 SWEEPS, COARSE_SWEEPS, BRICK = 24, 16, 8    # band smoother defaults of the library (fine, coarser levels, brick)
+JACOBI = 2                                  # damped Jacobi sweeps per smoothing step (library default)
 
 
 def _rel(a, b):
@@ -145,7 +146,7 @@ def test_smooth_restrict_prolong(case):
         f = rng.standard_normal(lev.mask.size) * lev.mask
         x = rng.standard_normal(lev.mask.size) * lev.mask
         got = op.smooth(f, x, level=l)
-        ref = MG.smooth(lev, f, x, om, SWEEPS if l == 0 else COARSE_SWEEPS, brick=BRICK)
+        ref = MG.smooth(lev, f, x, om, SWEEPS if l == 0 else COARSE_SWEEPS, brick=BRICK, jacobi_sweeps=JACOBI)
         assert _rel(got, ref) < 1e-12, l
         r = rng.standard_normal(lev.mask.size) * lev.mask
         assert _rel(op.restrict(r, level=l), MG.restrict(levels, l, r)) < 1e-13, l
@@ -168,7 +169,7 @@ def test_band_smoother_bricks(case_name, brick, sweeps, dm, ctx):
         f = rng.standard_normal(lev.mask.size) * lev.mask
         x = rng.standard_normal(lev.mask.size) * lev.mask
         got = op.smooth(f, x, level=l)
-        ref = MG.smooth(lev, f, x, op.omega(l), sweeps, brick=brick)
+        ref = MG.smooth(lev, f, x, op.omega(l), sweeps, brick=brick, jacobi_sweeps=JACOBI)
         assert _rel(got, ref) < 1e-12, (l, _rel(got, ref))
 
 
@@ -186,8 +187,30 @@ def test_vcycle_fp64(case):
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(6).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS,
+                    jacobi_sweeps=JACOBI)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+
+
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_vcycle_and_smoother_jacobi_sweeps(nu, dm, ctx):
+    """nu damped Jacobi sweeps per smoothing step (the buffers swap roles at
+    every sweep, so odd and even counts take different paths)."""
+    w = CASES["sphere16"]()
+    geom = dm.Geometry.from_workload(ctx, w)
+    op = dm.Operator(ctx, geom, w.sigma, jacobi_sweeps=nu)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    om = [op.omega(l) for l in range(len(levels))]
+    rng = np.random.default_rng(12)
+    f = rng.standard_normal(levels[0].mask.size) * levels[0].mask
+    got = op.vcycle(f)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS,
+                    jacobi_sweeps=nu)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9
+    x = rng.standard_normal(levels[0].mask.size) * levels[0].mask
+    got = op.smooth(f, x, level=0)
+    ref = MG.smooth(levels[0], f, x, om[0], SWEEPS, brick=BRICK, jacobi_sweeps=nu)
+    assert _rel(got, ref) < 1e-12
 
 
 def test_scalar_vcycle_fp64(case, dm, ctx):
@@ -209,7 +232,8 @@ def test_vcycle_low_precision(prec, tol, dm, ctx):
     om = [op.omega(l) for l in range(len(levels))]
     f = np.random.default_rng(8).standard_normal(levels[0].mask.size) * levels[0].mask
     got = op.vcycle(f)
-    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS)
+    ref = MG.vcycle(levels, f, om, band_sweeps=SWEEPS, brick=BRICK, band_sweeps_coarse=COARSE_SWEEPS,
+                    jacobi_sweeps=JACOBI)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < tol
 
 

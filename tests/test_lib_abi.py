@@ -40,7 +40,7 @@ def test_struct_layouts_match_defaults(lib):
     lib.dm_mg_params_default(C.byref(m))
     assert m.power_iters == 30 and m.precision == 0
     assert m.autotune == 1 and m.stencil_shape == -1 and m.band_sweeps_coarse == 16 and m.symmetric_transform == 0
-    assert m.dense_coarse == 2048 and m.krylov_ff == 1
+    assert m.dense_coarse == 2048 and m.krylov_ff == 1 and m.jacobi_sweeps == 2
     # the field after the embedded multigrid settings lands where the C struct has it
     assert p.mg.autotune == 1 and p.mg.stencil_shape == -1 and not p.learned
 

@@ -268,3 +268,26 @@ def test_symmetric_transform_slows_point_smoothing_but_not_the_band_smoother():
             counts[form, sweeps] = len(hist)
     assert counts["fullMat2", 0] >= 2 * counts["fullMat", 0], counts
     assert abs(counts["fullMat2", 16] - counts["fullMat", 16]) <= 2, counts
+
+
+def test_more_jacobi_sweeps_per_smoothing_step_cut_fgmres_iterations():
+    """nu damped Jacobi sweeps before the band smoother: with nu = 1 the
+    smoothing of the bulk faces limits the V-cycle; a second sweep cuts the
+    FGMRES iterations to 1e-9 on the 16^3 cut-cell sphere by a third (12 -> 8
+    with 24/16 band sweeps), and nu = 1 reproduces the single-sweep cycle."""
+    w = W.sphere_workload(16, offset_seed=W.SEED_BASE + 1, sigma=5.0)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    om = _omegas(levels)
+    lev = levels[0]
+    b = np.random.default_rng(0).standard_normal(lev.K.shape[0]) * lev.mask
+    f = np.random.default_rng(1).standard_normal(lev.K.shape[0]) * lev.mask
+    a = MG.vcycle(levels, f, om, band_sweeps=24, band_sweeps_coarse=16)
+    c = MG.vcycle(levels, f, om, band_sweeps=24, band_sweeps_coarse=16, jacobi_sweeps=1)
+    np.testing.assert_array_equal(a, c)
+    its = []
+    for nu in (1, 2):
+        _, hist = MG.fgmres(lambda v: lev.K @ v, b,
+                            lambda v: MG.vcycle(levels, v, om, band_sweeps=24, band_sweeps_coarse=16, jacobi_sweeps=nu),
+                            tol=1e-9, maxiter=60)
+        its.append(len(hist))
+    assert its[1] <= its[0] - 3, its
