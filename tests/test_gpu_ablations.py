@@ -169,7 +169,8 @@ def test_symmetric_transform_slows_point_smoothing_but_not_the_band_smoother(dm,
     """Sec. 5.3, Eq. fullMat2: the symmetric form puts A^-1/2 inside C~, whose
     inflated entries at small cut faces ruined the paper's multigrid.  On the
     GPU (the V-cycle of the congruence-scaled hierarchy, FGMRES to 1e-6 on the
-    16^3 sphere), with point-Jacobi smoothing alone the symmetric form needs at
+    16^3 sphere, one Jacobi sweep per smoothing step as in the paper's
+    multigrid), with point-Jacobi smoothing alone the symmetric form needs at
     least twice the iterations; with the cut-cell band smoother both forms
     converge alike -- the oracle's finding on the same cavity."""
     w = W.sphere_workload(16, sigma=5.0, offset_seed=W.SEED_BASE + 2)
@@ -179,8 +180,9 @@ def test_symmetric_transform_slows_point_smoothing_but_not_the_band_smoother(dm,
     counts = {}
     for sym in (0, 1):
         for sweeps in (0, 16):
+            # one Jacobi sweep per smoothing step, the paper's single order-1 polynomial step
             op = dm.Operator(ctx, geom, w.sigma, band_sweeps=sweeps, band_sweeps_coarse=sweeps,
-                             symmetric_transform=sym)
+                             symmetric_transform=sym, jacobi_sweeps=1)
             _, it, rr = op.solve(b, tol=1e-6, maxit=200)
             assert rr <= 1e-6, (sym, sweeps, it, rr)
             counts["fullMat2" if sym else "fullMat", sweeps] = it
