@@ -61,6 +61,9 @@ def parse():
                     help="Jacobi sweeps of the band smoother on the fine level (library default 24)")
     ap.add_argument("--band-sweeps-coarse", type=int, default=None,
                     help="sweeps of the band smoother below the fine level (library default 16)")
+    ap.add_argument("--ritz-tol", type=float, default=None,
+                    help="Krylov-Schur Ritz residual tolerance relative to |theta| (library default 1e-10)")
+    ap.add_argument("--basis", type=int, default=None, help="Krylov-Schur basis size (library default)")
     ap.add_argument("--jacobi-sweeps", type=int, default=None,
                     help="damped Jacobi sweeps per smoothing step (library default 2)")
     ap.add_argument("--no-krylov-ff", action="store_true",
@@ -90,6 +93,17 @@ def describe(args, w):
     return (f"PEC sphere R=1 in [-1.1,1.1]^3, {args.grid}^3 Yee cells, seeded centre offset "
             f"{tuple(round(float(v), 5) for v in w.meta['center'])}, sigma={args.sigma}, "
             f"{args.nev} lowest modes, residual<={RHO_TOL}")
+
+
+def eig_overrides(args):
+    """Eigensolver and multigrid settings given on the command line (the
+    library's defaults otherwise)."""
+    kw = mg_overrides(args)
+    if getattr(args, "ritz_tol", None) is not None:
+        kw["tol"] = args.ritz_tol
+    if getattr(args, "basis", None) is not None:
+        kw["basis"] = args.basis
+    return kw
 
 
 def mg_overrides(args):
@@ -322,7 +336,7 @@ def run_native(args):
     phi_pinned = torch.from_numpy(phi_host).pin_memory()
     B_pinned = torch.empty((args.nev, nf), dtype=torch.float64).pin_memory()
 
-    sweep_kw = mg_overrides(args)
+    sweep_kw = eig_overrides(args)
 
     def step(precision, host_io=False):
         phi = phi_pinned if host_io else phi_dev
@@ -506,7 +520,7 @@ def run_batch(args):
             geoms.append(geom)
             for sg in shifts:
                 jobs.append({"geom": geom, "sigma": sg, "nev": nev, "precision": args.precision,
-                             "inner_tol": args.inner_tol, **mg_overrides(args)})
+                             "inner_tol": args.inner_tol, **eig_overrides(args)})
         out = dm.eigensolve_batched(ctx, jobs, streams=args.streams)
         for geom in geoms:
             geom.close()
@@ -607,7 +621,7 @@ def run_ninecell(args):
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         k2, _, rep, st = dm.eigensolve(ctx, geom, w.sigma, args.nev, vectors=None, precision=args.precision,
-                                       inner_tol=args.inner_tol, **mg_overrides(args),
+                                       inner_tol=args.inner_tol, **eig_overrides(args),
                                        learned=net if learned else None)
         ev1.record(stream)
         torch.cuda.synchronize()
