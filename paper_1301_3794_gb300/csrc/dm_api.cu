@@ -1408,7 +1408,7 @@ dm_status dm_context_create(int device, void* cuda_stream, dm_context** out) {
             DM_CUDA(cudaStreamCreate(&ctx->stream));
             ctx->own_stream = true;
         }
-        reducer_init(ctx->red, 128);
+        reducer_init(ctx->red, 160);
     });
     if (st != DM_OK) {
         delete ctx;
@@ -2074,6 +2074,51 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         const double* a = g0.A.get();
         DBuf<double> Vb((size_t)(m + 1) * n), tmp((size_t)m * n), rhs(n), x(n);
         double* V = Vb.get();
+        // With float-float Krylov work the basis also lives as float-float pairs
+        // on the open faces (compact, even stride), and its Gram-Schmidt passes
+        // run there on the FP32 pipes at HBM speed; the FP64 basis stays the
+        // one the shifted solves, the Ritz vectors and the restarts use.
+        const bool ffks = op->mg.krylov_ff && g0.ff;
+        const long long nl = g0.nflist, nlp = (nl + 1) & ~1ll;
+        DBuf<float2> Vff, tf, wf, wf2;
+        if (ffks) {
+            Vff.alloc((size_t)(m + 1) * nlp);
+            tf.alloc(nlp);
+            wf.alloc(nlp);
+            wf2.alloc(nlp);
+        }
+        Grid3 gcf = g0.g;
+        gcf.np = (int)nlp;
+        const Domain Dc{gcf, nullptr, 0, 1};
+        auto shadow = [&](int c0, int c1) {
+            if (!ffks) return;
+            for (int c = c0; c < c1; ++c)
+                ff_gather(nl, g0.flist.get(), 1.0, V + (size_t)c * n, Vff.get() + (size_t)c * nlp, s);
+        };
+        std::vector<double> ffdots(2 * (size_t)m + 4), ffcoef(2 * (size_t)m + 4);
+        // one Gram-Schmidt pass of w against V_0 .. V_j in the A inner product on
+        // the float-float basis: h = V^T A w, w <- w - V h; returns (w^T A w
+        // before, after) through wn2 (nullable) and the result
+        auto ff_pass = [&](int j, double* w, std::vector<double>& h, double* wn2) -> double {
+            const int nq = j + 1;
+            hadamard(D, a, w, rhs.get(), s);
+            ff_gather(nl, g0.flist.get(), 1.0, rhs.get(), tf.get(), s);
+            ff_gather(nl, g0.flist.get(), 1.0, w, wf.get(), s);
+            dcgs_dots(ctx->red, Dc, nq, Vff.get(), nlp, tf.get(), wf.get(), ffdots.data(), s);
+            for (int c = 0; c < nq; ++c) h[c] = ffdots[c];
+            if (wn2) *wn2 = ffdots[2 * nq + 1];
+            for (int c = 0; c < nq; ++c) {
+                ffcoef[c] = 0.0;
+                ffcoef[nq + c] = h[c];
+            }
+            ffcoef[2 * nq] = 1.0;
+            ffcoef[2 * nq + 1] = 0.0;
+            dcgs_update(ctx->red, Dc, nq, Vff.get(), nlp, ffcoef.data(), tf.get(), wf.get(), wf2.get(), s);
+            ff_scatter<double>(nl, g0.flist.get(), 1.0, wf2.get(), w, s);
+            double bn2 = 0.0;
+            mdot(ctx->red, D, 1, w, n, w, a, &bn2, s);
+            return bn2;
+        };
         // start vector: seeded random on the open faces, projected, A-normalised
         fill_random(D, p.seed, a, rhs.get(), s);
         project(op, rhs.get(), V, p.proj_tol);
@@ -2082,6 +2127,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             DM_REQUIRE(nv > 0.0, DM_ERR_GEOMETRY, "start vector vanished under the projection (no open faces?)");
             scale_copy(D, 1.0 / nv, V, V, s);
         }
+        shadow(0, 1);
         std::vector<double> H((size_t)(m + 1) * m, 0.0);
         auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
         int k = 0, restarts = 0, outer = 0, inner_total = 0, proj_total = 0, nconv = 0, proj_capped = 0;
@@ -2124,19 +2170,28 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                 // A-orthogonalise against the basis: classical Gram-Schmidt,
                 // repeated when the first pass cancelled most of w
                 std::vector<double> h(j + 1);
-                double wn2 = 0.0;
-                mdot_self(ctx->red, D, j + 1, V, n, w, a, h.data(), &wn2, s);
-                double bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
+                double wn2 = 0.0, bn2 = 0.0;
+                if (ffks) {
+                    bn2 = ff_pass(j, w, h, &wn2);
+                } else {
+                    mdot_self(ctx->red, D, j + 1, V, n, w, a, h.data(), &wn2, s);
+                    bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
+                }
                 for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
                 if (bn2 < 0.49 * wn2) {
-                    mdot(ctx->red, D, j + 1, V, n, w, a, h.data(), s);
-                    bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
+                    if (ffks) {
+                        bn2 = ff_pass(j, w, h, nullptr);
+                    } else {
+                        mdot(ctx->red, D, j + 1, V, n, w, a, h.data(), s);
+                        bn2 = maxpy_norm(ctx->red, D, j + 1, V, n, w, a, s);
+                    }
                     for (int i = 0; i <= j; ++i) Hat(i, j) += h[i];
                 }
                 const double beta = std::sqrt(std::max(bn2, 0.0));
                 Hat(j + 1, j) = beta;
                 DM_REQUIRE(beta > 0.0, DM_ERR_NO_CONVERGENCE, "Krylov space exhausted");
                 scale_copy(D, 1.0 / beta, w, w, s);
+                shadow(j + 1, j + 2);
             }
             // an interrupted expansion leaves no basis to extract pairs from
             if (stalled || timed_out) break;
@@ -2178,6 +2233,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                     const double nv = norm2(ctx, D, V, a);
                     DM_REQUIRE(nv > 0.0, DM_ERR_NO_CONVERGENCE, "restart vector vanished");
                     scale_copy(D, 1.0 / nv, V, V, s);
+                    shadow(0, 1);
                     std::fill(H.begin(), H.end(), 0.0);
                     k = 0;
                     ++restarts;
@@ -2196,6 +2252,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             vgemm(D, m, pk, V, n, Yd.get(), m, tmp.get(), n, s);
             DM_CUDA(cudaMemcpyAsync(V, tmp.get(), sizeof(double) * pk * n, cudaMemcpyDeviceToDevice, s));
             DM_CUDA(cudaMemcpyAsync(V + (size_t)pk * n, V + (size_t)m * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            shadow(0, pk + 1);
             std::fill(H.begin(), H.end(), 0.0);
             for (int c = 0; c < pk; ++c) {
                 Hat(c, c) = theta[order[c]];
