@@ -749,7 +749,9 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
     double* Z = ws.Z.get();
     double* w = ws.w.get();
     zero(x, sizeof(double) * n, s);
-    const double bnorm = norm2(ctx, D, b);
+    // b and every residual vanish outside `list` (closed faces, inactive
+    // cells), so their norms run over the list alone
+    const double bnorm = std::sqrt(std::max(dot_list(ctx->red, nl, list, b, b, s), 0.0));
     if (relres) *relres = 0.0;
     if (bnorm == 0.0) return 0;
     // converged when ||b - A x|| <= thr: relative to ||b||, or the absolute
@@ -765,7 +767,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
         if (!first) {
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
-            beta = norm2(ctx, D, w);
+            beta = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, s), 0.0));
         }
         res = beta / bnorm;
         if (beta <= thr) break;
@@ -828,7 +830,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
             // confirm with the true residual
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
-            const double tr = norm2(ctx, D, w) / bnorm;
+            const double tr = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, s), 0.0)) / bnorm;
             res = tr;
             if (tr * bnorm <= 10.0 * thr) break;
         }

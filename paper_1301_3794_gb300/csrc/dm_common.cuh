@@ -524,6 +524,8 @@ struct Reducer {
 void reducer_init(Reducer& r, int max_cols);
 void reducer_free(Reducer& r);
 // out[c] = sum_r w[r] * V[c*ld + r] * x[r] over the domain (w nullable = 1), c < m; result copied to host
+// sum of x[q] y[q] over the n listed indices (host result)
+double dot_list(Reducer& red, long long n, const int* list, const double* x, const double* y, cudaStream_t s);
 void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s);
 // as mdot, and also returns sum_r w[r] x[r]^2 in *self_out (one pass, one sync)
