@@ -426,8 +426,16 @@ void vcycle(dm_operator* op, int l, const T* f, T* ebuf, T* rbuf) {
     // the iterate and the other work buffer swap roles at every Jacobi sweep
     T* it = ebuf;
     T* tmp = rbuf;
-    vec_jacobi_zero(o, f, it, om, s);
-    for (int k = 1; k < nu; ++k) {
+    int k0 = 1;
+    if (nu >= 2) {
+        // the first sweep from zero, omega D^-1 f, is formed inside the second one
+        vec_stencil(o, ST_JACOBI2Z, f, f, tmp, om, s);
+        std::swap(it, tmp);
+        k0 = 2;
+    } else {
+        vec_jacobi_zero(o, f, it, om, s);
+    }
+    for (int k = k0; k < nu; ++k) {
         vec_stencil(o, ST_JACOBI, it, f, tmp, om, s);
         std::swap(it, tmp);
     }
@@ -665,6 +673,22 @@ void apply_scal64(dm_operator* op, int l, const double* x, double* y) {
     scal_stencil<double, double>(sop<double, double>(op, l), ST_APPLY, x, nullptr, y, 0.0, op->ctx->stream);
 }
 
+// sum of x y (times w, nullable) over the fine level's open faces, by the flat
+// list kernel once the operator has listed them (over the level's tiles before).
+// Callers pass vectors where one factor vanishes on every closed face (the
+// operator's output, an A-weighted vector, the solver's own face vectors), so
+// the result is the sum over all entries.
+double face_dot(dm_context* ctx, const GeoLevel& g0, const double* x, const double* y, const double* w = nullptr) {
+    if (g0.nflist >= 0) return dot_list(ctx->red, g0.nflist, g0.flist.get(), x, y, w, ctx->stream);
+    const Domain D = g0.vdom();
+    double r = 0.0;
+    mdot(ctx->red, D, 1, x, D.len(), y, w, &r, ctx->stream);
+    return r;
+}
+double face_norm(dm_context* ctx, const GeoLevel& g0, const double* x, const double* w = nullptr) {
+    return std::sqrt(std::max(face_dot(ctx, g0, x, x, w), 0.0));
+}
+
 double norm2(dm_context* ctx, const Domain& D, const double* x, const double* w = nullptr) {
     double r = 0.0;
     mdot(ctx->red, D, 1, x, D.len(), x, w, &r, ctx->stream);
@@ -751,7 +775,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
     zero(x, sizeof(double) * n, s);
     // b and every residual vanish outside `list` (closed faces, inactive
     // cells), so their norms run over the list alone
-    const double bnorm = std::sqrt(std::max(dot_list(ctx->red, nl, list, b, b, s), 0.0));
+    const double bnorm = std::sqrt(std::max(dot_list(ctx->red, nl, list, b, b, nullptr, s), 0.0));
     if (relres) *relres = 0.0;
     if (bnorm == 0.0) return 0;
     // converged when ||b - A x|| <= thr: relative to ||b||, or the absolute
@@ -767,7 +791,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
         if (!first) {
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
-            beta = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, s), 0.0));
+            beta = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, nullptr, s), 0.0));
         }
         res = beta / bnorm;
         if (beta <= thr) break;
@@ -830,7 +854,7 @@ int fgmres(dm_context* ctx, Fgmres& ws, const Domain& D, const int* list, long l
             // confirm with the true residual
             apply(x, w);
             axpby(D, 1.0, b, -1.0, w, s);
-            const double tr = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, s), 0.0)) / bnorm;
+            const double tr = std::sqrt(std::max(dot_list(ctx->red, nl, list, w, w, nullptr, s), 0.0)) / bnorm;
             res = tr;
             if (tr * bnorm <= 10.0 * thr) break;
         }
@@ -923,7 +947,8 @@ int project(dm_operator* op, const double* x, double* y, double tol) {
     // relative to ||D A x|| cannot be met.  The solve is accurate enough once
     // the residual is tol times the divergence scale of x itself, ||x|| / h.
     const double hmin = std::min(g0.g.hx, std::min(g0.g.hy, g0.g.hz));
-    const double xscale = norm2(op->ctx, g0.vdom(), x) / hmin;
+    // (D A x sees only the open faces, so they alone set that scale)
+    const double xscale = face_norm(op->ctx, g0, x) / hmin;
     auto apply = [op](const double* in, double* out) { apply_scal64(op, 0, in, out); };
     const int* cl = g0.clist.get();
     const long long ncl = g0.nclist;
@@ -1973,16 +1998,15 @@ void certify_padded(dm_context* ctx, const GeoLevel& g0, int n, const double* X,
         const double* b = X + (size_t)i * n3;
         vec_stencil<double, double>(o, ST_APPLY, b, nullptr, kb.get(), 0.0, s);
         hadamard(D, g0.A.get(), b, ab.get(), s);
-        double bkb = 0.0, bab = 0.0;
-        mdot(ctx->red, D, 1, b, n3, kb.get(), nullptr, &bkb, s);
-        mdot(ctx->red, D, 1, b, n3, ab.get(), nullptr, &bab, s);
+        // K b and A b vanish on closed faces, so the sums run over the open ones
+        const double bkb = face_dot(ctx, g0, b, kb.get()), bab = face_dot(ctx, g0, b, ab.get());
         const double r = bkb / bab;
         if (rq) rq[i] = r;
         const double k2 = set_k2 ? r : k2_io[i];
         if (set_k2) k2_io[i] = r;
-        const double abn = norm2(ctx, D, ab.get());
+        const double abn = face_norm(ctx, g0, ab.get());
         axpby(D, -k2, ab.get(), 1.0, kb.get(), s);
-        const double rn = norm2(ctx, D, kb.get());
+        const double rn = face_norm(ctx, g0, kb.get());
         if (rho) rho[i] = rn / (std::fabs(k2) * abn);
         dm_div_a(g0.g, g0.A.get(), b, dv.get(), g0.tiles.get(), g0.ntiles, s);
         const double dn = norm2(ctx, Dc, dv.get());
@@ -2117,15 +2141,13 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
             ffcoef[2 * nq + 1] = 0.0;
             dcgs_update(ctx->red, Dc, nq, Vff.get(), nlp, ffcoef.data(), tf.get(), wf.get(), wf2.get(), s);
             ff_scatter<double>(nl, g0.flist.get(), 1.0, wf2.get(), w, s);
-            double bn2 = 0.0;
-            mdot(ctx->red, D, 1, w, n, w, a, &bn2, s);
-            return bn2;
+            return face_dot(ctx, g0, w, w, a);
         };
         // start vector: seeded random on the open faces, projected, A-normalised
         fill_random(D, p.seed, a, rhs.get(), s);
         project(op, rhs.get(), V, p.proj_tol);
         {
-            const double nv = norm2(ctx, D, V, a);
+            const double nv = face_norm(ctx, g0, V, a);
             DM_REQUIRE(nv > 0.0, DM_ERR_GEOMETRY, "start vector vanished under the projection (no open faces?)");
             scale_copy(D, 1.0 / nv, V, V, s);
         }
@@ -2232,7 +2254,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
                     DBuf<double> od(p.nev);
                     DM_CUDA(cudaMemcpyAsync(od.get(), ones.data(), sizeof(double) * p.nev, cudaMemcpyHostToDevice, s));
                     vgemm(D, p.nev, 1, tmp.get(), n, od.get(), p.nev, V, n, s);   // tmp: the Ritz vectors
-                    const double nv = norm2(ctx, D, V, a);
+                    const double nv = face_norm(ctx, g0, V, a);
                     DM_REQUIRE(nv > 0.0, DM_ERR_NO_CONVERGENCE, "restart vector vanished");
                     scale_copy(D, 1.0 / nv, V, V, s);
                     shadow(0, 1);
@@ -2299,7 +2321,7 @@ dm_status dm_eigensolve(dm_context* ctx, const dm_geometry* geom, const dm_eig_p
         std::vector<double> k2(nev), rho(nev), delta(nev), rq(nev);
         for (int c = 0; c < nev; ++c) {
             double* b = tmp.get() + (size_t)c * n;
-            const double nb = norm2(ctx, D, b, a);
+            const double nb = face_norm(ctx, g0, b, a);
             scale_copy(D, 1.0 / nb, b, b, s);
             launch("k_max_entry_partial", k_max_entry_partial, kSignBlocks, 256, 0, s, n, (const double*)b, pv.get(),
                    pi.get());

@@ -101,16 +101,18 @@ __global__ void k_maxpy_norm(Domain d, int m, const double* __restrict__ V, long
     }
 }
 
-// partial[b] = sum over this block's share of the listed entries of x[q] y[q]:
-// a flat loop over an ascending index list, every load independent of the
-// previous one (the tile loop of k_mdot_partial waits for each tile's index)
+// partial[b] = sum over this block's share of the listed entries of x[q] y[q]
+// (times w[q] if w is given): a flat loop over an ascending index list, every
+// load independent of the previous one (the tile loop of k_mdot_partial waits
+// for each tile's index)
 __global__ void k_dot_list(long long n, const int* __restrict__ list, const double* __restrict__ x,
-                           const double* __restrict__ y, double* __restrict__ partial) {
+                           const double* __restrict__ y, const double* __restrict__ w, double* __restrict__ partial) {
     __shared__ double red[kThreads / 32];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int q = list[i];
-        acc += x[q] * y[q];
+        const double xq = w ? x[q] * w[q] : x[q];
+        acc += xq * y[q];
     }
     const double v = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
@@ -573,10 +575,12 @@ void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, c
     for (int c = 0; c < m; ++c) host_out[c] = red.host[c];
 }
 
-double dot_list(Reducer& red, long long n, const int* list, const double* x, const double* y, cudaStream_t s) {
+double dot_list(Reducer& red, long long n, const int* list, const double* x, const double* y, const double* w,
+                cudaStream_t s) {
     if (n <= 0) return 0.0;
     const int nb = (int)std::max<long long>(1, std::min<long long>((n + kThreads - 1) / kThreads, kMaxBlocks));
-    launch_b("k_dot_list", 20.0 * (double)n, k_dot_list, nb, kThreads, 0, s, n, list, x, y, red.partial);
+    launch_b("k_dot_list", (w ? 28.0 : 20.0) * (double)n, k_dot_list, nb, kThreads, 0, s, n, list, x, y, w,
+             red.partial);
     launch("k_mdot_final", k_mdot_final, 1, 256, 0, s, nb, 1, red.partial, 1, red.result);
     DM_CUDA(cudaMemcpyAsync(red.host, red.result, sizeof(double), cudaMemcpyDeviceToHost, s));
     DM_CUDA(cudaStreamSynchronize(s));

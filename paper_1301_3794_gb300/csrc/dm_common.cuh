@@ -343,14 +343,17 @@ inline void stencil_shape_dims(int shape, int& sy, int& sz) {
     sy = d[shape][0];
     sz = d[shape][1];
 }
-enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2 };
+enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_JACOBI = 2, ST_JACOBI2Z = 3 };
+constexpr int kStencilModes = 4;
 // trace name of a stencil launch: "<kind>_<precision>_<mode>_<L0|Lc>"
 template <typename T> constexpr int prec_index() {
     return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
 }
 const char* stencil_name(const char* kind, int prec, int mode, bool fine);
 // mode APPLY: y = (K - sigma A) x;  RESID: y = f - (K - sigma A) x;
-// JACOBI: y = x + omega invD (f - (K - sigma A) x)
+// JACOBI: y = x + omega invD (f - (K - sigma A) x);  JACOBI2Z: two JACOBI
+// sweeps from x = 0, the first one's iterate omega invD f (rounded to T as
+// vec_jacobi_zero stores it) formed where the second one loads x (x unused)
 template <typename T, typename TC>
 void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y, double omega, cudaStream_t s);
 template <typename T, typename TC>
@@ -523,9 +526,10 @@ struct Reducer {
 };
 void reducer_init(Reducer& r, int max_cols);
 void reducer_free(Reducer& r);
+// sum of x[q] y[q] (times w[q], w nullable = 1) over the n listed indices (host result)
+double dot_list(Reducer& red, long long n, const int* list, const double* x, const double* y, const double* w,
+                cudaStream_t s);
 // out[c] = sum_r w[r] * V[c*ld + r] * x[r] over the domain (w nullable = 1), c < m; result copied to host
-// sum of x[q] y[q] over the n listed indices (host result)
-double dot_list(Reducer& red, long long n, const int* list, const double* x, const double* y, cudaStream_t s);
 void mdot(Reducer& red, const Domain& d, int m, const double* V, long long ld, const double* x, const double* w,
           double* host_out, cudaStream_t s);
 // as mdot, and also returns sum_r w[r] x[r]^2 in *self_out (one pass, one sync)

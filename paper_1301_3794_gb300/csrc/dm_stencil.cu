@@ -39,6 +39,27 @@ struct VecAcc {
     int np;
     __device__ __forceinline__ C operator()(int c, int p) const { return (C)to_c(x[c * np + p]); }
 };
+// Accessor of the first damped Jacobi iterate from zero, omega invD f, rounded
+// to the storage type exactly as k_jacobi_zero stores it: the JACOBI2Z stencil
+// reads its x through this instead of from a vector that pass would write.
+template <typename T, typename TC, typename C>
+struct Jac0Acc {
+    const T* __restrict__ f;
+    const TC* __restrict__ invD;
+    C om;
+    int np;
+    __device__ __forceinline__ C operator()(int c, int p) const {
+        const int q = c * np + p;
+        return (C)to_c(to_store<T>(om * (C)invD[q] * (C)to_c(f[q])));
+    }
+};
+template <typename T, typename TC, typename C, int MODE>
+__device__ __forceinline__ auto x_acc(const T* x, const T* f, const TC* invD, C om, int np) {
+    if constexpr (MODE == ST_JACOBI2Z)
+        return Jac0Acc<T, TC, C>{f, invD, om, np};
+    else
+        return VecAcc<T, C>{x, np};
+}
 // Accessor of the unit vector e_q (packed index q = c*np + p); used to build
 // the coarsest matrix column by column from the same stencil.
 template <typename C>
@@ -144,7 +165,7 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
     const int p = g.idx(i, j, k);
     const int N = g.np;
     Coef<C, TC> cf{A, L, invV, N};
-    VecAcc<T, C> b{x, N};
+    const auto b = x_acc<T, TC, C, MODE>(x, f, invD, omega, N);
     C out[3];
     node_K(cf, b, p, 1, g.sx, g.sxy, inv_h<C>(g, 0), inv_h<C>(g, 1), inv_h<C>(g, 2), sigma, out);
 #pragma unroll
@@ -155,6 +176,8 @@ __global__ void k_vec_stencil(Grid3 g, const TC* __restrict__ A, const TC* __res
             v = (C)to_c(f[q]) - v;
         } else if (MODE == ST_JACOBI) {
             v = (C)to_c(x[q]) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
+        } else if (MODE == ST_JACOBI2Z) {
+            v = b(c, p) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
         }
         y[q] = to_store<T>(v);
     }
@@ -186,7 +209,7 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
     const int X = 1, Y = g.sx, Z = g.sxy, N = g.np;
     const C rdx = inv_h<C>(g, 0), rdy = inv_h<C>(g, 1), rdz = inv_h<C>(g, 2);
     Coef<C, TC> cf{A, L, invV, N};
-    VecAcc<T, C> b{x, N};
+    const auto b = x_acc<T, TC, C, MODE>(x, f, invD, omega, N);
     const int tid = threadIdx.x + TX * (threadIdx.y + SY * threadIdx.z);
     for (int e = tid; e < N_PSI; e += NT) {
         const int li = e % PSI_X, lj = (e / PSI_X) % PSI_Y, lk = e / (PSI_X * PSI_Y);
@@ -244,6 +267,8 @@ __global__ void __launch_bounds__(TX * SY * SZ) k_vec_stencil_tiled(
             v = (C)to_c(f[q]) - v;
         } else if (MODE == ST_JACOBI) {
             v = (C)to_c(x[q]) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
+        } else if (MODE == ST_JACOBI2Z) {
+            v = b(c, p) + omega * (C)invD[q] * ((C)to_c(f[q]) - v);
         }
         y[q] = to_store<T>(v);
     }
@@ -331,15 +356,16 @@ __global__ void __launch_bounds__(TX * SY, (std::is_same<T, double>::value ? 512
     const int dp0 = dval ? g.idx(di, dj, 0) : 0;
     // ring entry of array a (0..2: b, 3..5: A) at node (ii, jj) of the plane in `slot`
     auto R = [&](int slot, int a, int ii, int jj) -> C { return s_ring[slot][a * RP + (jj - j0 + 1) * RW + (ii - i0 + 1)]; };
+    const auto xa = x_acc<T, TC, C, MODE>(x, f, invD, omega, N);
     // prefetch registers: ring entries of the node and of the border entry, coefficients, f and 1/D
     C pn[6], ph[6], cv = C(0), cz = C(0), cx = C(0), cy = C(0), hc = C(0), he = C(0), pf[3], pd[3];
     auto fetch_ring = [&](int k) {
         const int pn_ = p0 + k * Z, ph_ = hp0 + k * Z;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            pn[c] = inb ? (C)to_c(x[c * N + pn_]) : C(0);
+            pn[c] = inb ? xa(c, pn_) : C(0);
             pn[3 + c] = inb ? (C)A[c * N + pn_] : C(0);
-            ph[c] = hval ? (C)to_c(x[c * N + ph_]) : C(0);
+            ph[c] = hval ? xa(c, ph_) : C(0);
             ph[3 + c] = hval ? (C)A[c * N + ph_] : C(0);
         }
     };
@@ -373,7 +399,7 @@ __global__ void __launch_bounds__(TX * SY, (std::is_same<T, double>::value ? 512
             pd[c] = C(0);
             if (MODE != ST_APPLY && own) {
                 pf[c] = (C)to_c(f[c * N + p0 + k * Z]);
-                if (MODE == ST_JACOBI) pd[c] = (C)invD[c * N + p0 + k * Z];
+                if (MODE == ST_JACOBI || MODE == ST_JACOBI2Z) pd[c] = (C)invD[c * N + p0 + k * Z];
             }
         }
     };
@@ -455,7 +481,7 @@ __global__ void __launch_bounds__(TX * SY, (std::is_same<T, double>::value ? 512
                 C v = av[c] > C(0) ? out[c] : C(0);
                 if (MODE == ST_RESID) {
                     v = pf[c] - v;
-                } else if (MODE == ST_JACOBI) {
+                } else if (MODE == ST_JACOBI || MODE == ST_JACOBI2Z) {
                     v = bv[c] + omega * pd[c] * (pf[c] - v);
                 }
                 y[c * N + p] = to_store<T>(v);
@@ -835,18 +861,19 @@ const char* stencil_name(const char* kind, int prec, int mode, bool fine) {
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     static const char* precs[3] = {"f64", "f32", "bf16"};
-    static const char* modes[3] = {"apply", "resid", "jacobi"};
+    static const char* modes[kStencilModes] = {"apply", "resid", "jacobi", "jacobi2z"};
     const std::string n = std::string(kind) + "_" + precs[prec] + "_" + modes[mode] + (fine ? "_L0" : "_Lc");
     return names->insert(n).first->c_str();
 }
 
 // Algorithmic bytes of one vector-stencil launch: per open face its x and y
-// (and f for resid / jacobi), its A (and 1/D for jacobi), about one edge
-// fraction L and a third of a cell's 1/V.
+// (and f for resid / jacobi; f instead of x for jacobi2z), its A (and 1/D for
+// jacobi, jacobi2z), about one edge fraction L and a third of a cell's 1/V.
 template <typename T, typename TC>
 double vec_stencil_bytes(const Grid3& g, int mode) {
     const double tv = sizeof(T), tc = sizeof(TC);
-    return (double)g.nopen * (tv * (2 + (mode != ST_APPLY)) + tc * (2.0 + 1.0 / 3.0 + (mode == ST_JACOBI)));
+    const bool jac = mode == ST_JACOBI || mode == ST_JACOBI2Z;
+    return (double)g.nopen * (tv * (2 + (mode == ST_RESID || mode == ST_JACOBI)) + tc * (2.0 + 1.0 / 3.0 + jac));
 }
 // per active cell: x, y (and f), three face fractions (six faces, each shared
 // by two cells), 1/D for jacobi, and the activity flag
@@ -867,24 +894,24 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         const char* nm = stencil_name("vec_stencil", prec_index<T>(), mode, op.level == 0);
         // tile shape: 0 = 32x4x2 (the level's active tiles), 1 = 32x2x4, 2 = 32x8x1; 3 = 32x8x8,
         // 4 = 32x4x8, 5 = 32x8x4 by the z-marching kernel (op.stiles is the active-tile list of that shape)
-        switch (op.shape * 3 + mode) {
+        switch (op.shape * kStencilModes + mode) {
 #define DM_TILED(SH, MD, SY, SZ)                                                                              \
-    case SH * 3 + MD:                                                                                         \
+    case SH * kStencilModes + MD:                                                                                         \
         launch_b(nm, bytes, k_vec_stencil_tiled<T, TC, MD, SY, SZ>, nt, dim3(TX, SY, SZ), 0, s, g, op.A, op.L,  \
                  op.invV, op.invD, op.sigma, x, f, y, omega, tl);                                             \
         break;
-            DM_TILED(0, ST_APPLY, 4, 2) DM_TILED(0, ST_RESID, 4, 2) DM_TILED(0, ST_JACOBI, 4, 2)
-            DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4)
-            DM_TILED(2, ST_APPLY, 8, 1) DM_TILED(2, ST_RESID, 8, 1) DM_TILED(2, ST_JACOBI, 8, 1)
+            DM_TILED(0, ST_APPLY, 4, 2) DM_TILED(0, ST_RESID, 4, 2) DM_TILED(0, ST_JACOBI, 4, 2) DM_TILED(0, ST_JACOBI2Z, 4, 2)
+            DM_TILED(1, ST_APPLY, 2, 4) DM_TILED(1, ST_RESID, 2, 4) DM_TILED(1, ST_JACOBI, 2, 4) DM_TILED(1, ST_JACOBI2Z, 2, 4)
+            DM_TILED(2, ST_APPLY, 8, 1) DM_TILED(2, ST_RESID, 8, 1) DM_TILED(2, ST_JACOBI, 8, 1) DM_TILED(2, ST_JACOBI2Z, 8, 1)
 #undef DM_TILED
 #define DM_MARCH(SH, MD, SY, KZ)                                                                                \
-    case SH * 3 + MD:                                                                                         \
+    case SH * kStencilModes + MD:                                                                                         \
         launch_b(nm, bytes, k_vec_stencil_march<T, TC, MD, SY, KZ>, nt, dim3(TX, SY, 1), 0, s, g, op.A, op.L,  \
                  op.invV, op.invD, op.sigma, x, f, y, omega, tl);                                             \
         break;
-            DM_MARCH(3, ST_APPLY, 8, 8) DM_MARCH(3, ST_RESID, 8, 8) DM_MARCH(3, ST_JACOBI, 8, 8)
-            DM_MARCH(4, ST_APPLY, 4, 8) DM_MARCH(4, ST_RESID, 4, 8) DM_MARCH(4, ST_JACOBI, 4, 8)
-            DM_MARCH(5, ST_APPLY, 8, 4) DM_MARCH(5, ST_RESID, 8, 4) DM_MARCH(5, ST_JACOBI, 8, 4)
+            DM_MARCH(3, ST_APPLY, 8, 8) DM_MARCH(3, ST_RESID, 8, 8) DM_MARCH(3, ST_JACOBI, 8, 8) DM_MARCH(3, ST_JACOBI2Z, 8, 8)
+            DM_MARCH(4, ST_APPLY, 4, 8) DM_MARCH(4, ST_RESID, 4, 8) DM_MARCH(4, ST_JACOBI, 4, 8) DM_MARCH(4, ST_JACOBI2Z, 4, 8)
+            DM_MARCH(5, ST_APPLY, 8, 4) DM_MARCH(5, ST_RESID, 8, 4) DM_MARCH(5, ST_JACOBI, 8, 4) DM_MARCH(5, ST_JACOBI2Z, 8, 4)
 #undef DM_MARCH
             default: throw Error(DM_ERR_INVALID_ARG, "unknown stencil tile shape");
         }
@@ -894,6 +921,8 @@ void vec_stencil(const VecOp<T, TC>& op, int mode, const T* x, const T* f, T* y,
         launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_APPLY, op.level == 0), bytes, k_vec_stencil<T, TC, ST_APPLY>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else if (mode == ST_RESID)
         launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_RESID, op.level == 0), bytes, k_vec_stencil<T, TC, ST_RESID>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
+    else if (mode == ST_JACOBI2Z)
+        launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI2Z, op.level == 0), bytes, k_vec_stencil<T, TC, ST_JACOBI2Z>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
     else
         launch_b(stencil_name("vec_stencil", prec_index<T>(), ST_JACOBI, op.level == 0), bytes, k_vec_stencil<T, TC, ST_JACOBI>, tile_grid(g, op.tiles, op.ntiles, 1), kBlock, 0, s, g, op.A, op.L, op.invV, op.invD, op.sigma, x, f, y, omega, op.tiles);
 }

@@ -75,3 +75,23 @@ def test_every_stencil_shape_matches_oracle(dm, ctx, shape):
     y = op.apply(x)
     yr = ops.apply_K(x, w.sigma)
     assert np.max(np.abs(y - yr)) <= 1e-12 * np.max(np.abs(yr))
+
+
+@pytest.mark.parametrize("shape", range(6))
+def test_every_stencil_shape_vcycle_two_and_three_sweeps(dm, ctx, shape):
+    """Each tile shape forced on every level, with two and three damped Jacobi
+    sweeps per smoothing step: the pre-smoothing's first two sweeps run as one
+    stencil launch that forms the first iterate omega D^-1 f where it loads x.
+    The V-cycle must equal the oracle's, which takes the sweeps one by one."""
+    from oracle import multigrid as MG
+    w = W.ellipsoid_workload(40, seed=1307, sigma=5.0)
+    g = dm.Geometry.from_workload(ctx, w)
+    levels = MG.build_vector_hierarchy(w.grid, w.phi, w.sigma)
+    f = np.random.default_rng(40 + shape).standard_normal(levels[0].mask.size) * levels[0].mask
+    for nu in (2, 3):
+        op = dm.Operator(ctx, g, w.sigma, precision="f64", autotune=0, force_shape=shape, jacobi_sweeps=nu)
+        assert op.stencil_shape(0) == shape
+        om = [op.omega(l) for l in range(len(levels))]
+        got = op.vcycle(f)
+        ref = MG.vcycle(levels, f, om, band_sweeps=24, brick=8, band_sweeps_coarse=16, jacobi_sweeps=nu)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-9, (nu, shape)
